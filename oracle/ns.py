@@ -1,0 +1,510 @@
+"""FP64 CPU oracle for one time step of the compressible Navier-Stokes equations
+with Asynchrony-Tolerant (AT) stencils at the faces of virtual PEs.
+
+TEST INFRASTRUCTURE ONLY.  Plain, slow, vectorised numpy written from the paper
+(Kumari & Donzis, arXiv 2003.10561).  It is imported only by ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``; the
+product path never imports it and shares no code with it.
+
+Paper passages followed, in the order of one step:
+
+* delay map: control parameters c_r and L (Sec. 3.1), random delays of the
+  Synchronization-Avoiding Algorithm (Algorithm 1, Sec. 3.1.1), periodic
+  delays of the Communication-Avoiding Algorithm (Algorithm 2, Sec. 3.1.2),
+  synchronous start-up over the first L + T_l steps (Algorithms 1 and 2);
+* AT derivatives at PE faces: Eq. (at) and the 4th-order rows of Table B
+  (Appendix B), standard 4th-order stencils at internal points (Sec. 2.1);
+* mixed derivatives in three steps at boundary points (Sec. 2.1);
+* right-hand side of Eqs. (cont), (mome) and the energy equation with the
+  stress / strain definitions of Sec. 2 (total energy form, see below);
+* large-scale solenoidal forcing in a shell |kappa| <= kappa_f (Sec. 4.2);
+* second-order Adams-Bashforth, Eq. (time_ab) with T = 2 (Sec. 2.2).
+
+Readings where the paper is silent (each listed in the design notes):
+
+* Non-dimensionalisation rho_0 = T_0 = c_0 = 1, so R = 1/gamma,
+  p = rho T / gamma, c^2 = T, c_p = 1/(gamma-1).
+* Energy variable: total energy E = rho e + rho |u|^2 / 2 in divergence form;
+  the viscous work and conduction terms are expanded into first, second and
+  mixed derivatives (the paper's derivative machinery).
+* Viscosity: power law mu = mu0 T^omega (Sutherland constants are not given).
+* Only stencil points outside the PE read delayed levels; the two sides of a
+  shared face have independent delays; a direction with one PE has no faces.
+* Quantity extrapolated by the AT weights: the differentiated quantity
+  (flux, velocity component, temperature) evaluated at each delayed level.
+* AB2 start: the first step after a state is set is a forward-Euler step.
+* Random delays: iid uniform on {0..L} from Philox4x32-10; periodic delays
+  k = (n - n0) mod c_r; n0 = L + T_l synchronous start-up steps.
+* Forcing: an Ornstein-Uhlenbeck process per Fourier mode (the Eswaran-Pope
+  scheme cited by the paper is not reproduced in it).
+"""
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+from .philox import philox4x32_10, split_seed
+from .stencils import (D1_CENTRAL, D2_CENTRAL, D1_FORWARD0, D1_FORWARD1,
+                       D1_BACKWARD0, D1_BACKWARD1, HALF_WIDTH, T_LEVELS,
+                       at_weights)
+
+SYNC, PERIODIC, RANDOM = 0, 1, 2
+DELAY_STREAM_TAG = 0x4154      # 4th Philox counter word of the delay stream
+FORCING_STREAM_TAG = 0x464F    # 4th Philox counter word of the forcing stream
+
+
+@dataclass
+class Config:
+    n: tuple = (32, 32, 32)          # grid points (nx, ny, nz)
+    pes: tuple = (1, 1, 1)           # virtual PEs (Px, Py, Pz)
+    gamma: float = 1.4
+    prandtl: float = 0.7
+    mu0: float = 0.02
+    visc_exp: float = 0.76
+    dt: float = 1e-3
+    max_delay: int = 2               # L
+    comm_period: int = 3             # c_r (periodic mode)
+    seed: int = 0                    # delay stream seed
+    forcing: bool = False
+    kf: float = 2.0
+    f_amp: float = 0.0
+    f_tcorr: float = 1.0
+    f_seed: int = 0
+
+    @property
+    def nloc(self):
+        return tuple(self.n[d] // self.pes[d] for d in range(3))
+
+    @property
+    def dx(self):
+        return tuple(2.0 * math.pi / self.n[d] for d in range(3))
+
+    @property
+    def n_levels(self):
+        """Time levels held: n, n-1, ..., n-(L+T_l-1)  (Sec. 3.1: L + T_l)."""
+        return self.max_delay + T_LEVELS
+
+    @property
+    def n_pes(self):
+        return self.pes[0] * self.pes[1] * self.pes[2]
+
+
+# --------------------------------------------------------------------------
+# geometry: arrays are indexed [z, y, x]; direction d = 0, 1, 2 is x, y, z
+# --------------------------------------------------------------------------
+def _axis(d):
+    return 2 - d
+
+
+def _coord(cfg, d):
+    """Index along direction d, shaped to broadcast against a [z, y, x] field."""
+    shape = [1, 1, 1]
+    shape[_axis(d)] = cfg.n[d]
+    return np.arange(cfg.n[d]).reshape(shape)
+
+
+def pe_index_field(cfg):
+    """PE number p = (pz * Py + py) * Px + px of every grid point."""
+    px = _coord(cfg, 0) // cfg.nloc[0]
+    py = _coord(cfg, 1) // cfg.nloc[1]
+    pz = _coord(cfg, 2) // cfg.nloc[2]
+    return np.broadcast_to((pz * cfg.pes[1] + py) * cfg.pes[0] + px,
+                           (cfg.n[2], cfg.n[1], cfg.n[0]))
+
+
+def boundary_fraction(cfg):
+    """N_B / N_T per PE, Eqs. (NT), (NI), (NB) with M = 2."""
+    nt = 1
+    ni = 1
+    for d in range(3):
+        nt *= cfg.nloc[d]
+        ni *= cfg.nloc[d] - 2 * HALF_WIDTH
+    return (nt - ni) / nt
+
+
+# --------------------------------------------------------------------------
+# delay map (Sec. 3.1, Algorithms 1 and 2)
+# --------------------------------------------------------------------------
+def delay_map(cfg, step, mode):
+    """Delays k[p, f] for step n; faces f = x-, x+, y-, y+, z-, z+."""
+    P = cfg.n_pes
+    k = np.zeros((P, 6), dtype=np.int64)
+    n0 = cfg.n_levels                       # synchronous start-up: L + T_l steps
+    if mode == SYNC or step < n0:
+        return k
+    if mode == PERIODIC:
+        k[:] = (step - n0) % cfg.comm_period
+        return k
+    if mode == RANDOM:
+        p = np.arange(P, dtype=np.uint64)[:, None]
+        f = np.arange(6, dtype=np.uint64)[None, :]
+        k0, k1 = split_seed(cfg.seed)
+        w0, _, _, _ = philox4x32_10(np.uint64(step), p, f, np.uint64(DELAY_STREAM_TAG), k0, k1)
+        # uniform integer on {0..L}: floor(w * (L+1) / 2^32), exact in integers
+        return ((w0.astype(np.uint64) * np.uint64(cfg.max_delay + 1)) >> np.uint64(32)).astype(np.int64)
+    raise ValueError("unknown delay mode")
+
+
+# --------------------------------------------------------------------------
+# primitive variables and differentiated quantities
+# --------------------------------------------------------------------------
+def primitives(cfg, U):
+    """rho, (u, v, w), p, T from conserved (rho, rho u, rho v, rho w, E)."""
+    rho = U[0]
+    vel = [U[1] / rho, U[2] / rho, U[3] / rho]
+    ke = 0.5 * rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)
+    p = (cfg.gamma - 1.0) * (U[4] - ke)
+    T = cfg.gamma * p / rho
+    return rho, vel, p, T
+
+
+def quantity(cfg, U, name):
+    """A differentiated quantity evaluated from one time level of U.
+
+    'F{d}{e}': component e of the inviscid flux in direction d
+               (rho u_d, rho u_i u_d + p delta_id, (E + p) u_d);
+    'u0','u1','u2': velocity components; 'T': temperature.
+    """
+    rho, vel, p, T = primitives(cfg, U)
+    if name == "T":
+        return T
+    if name[0] == "u":
+        return vel[int(name[1])]
+    d, e = int(name[1]), int(name[2])
+    if e == 0:
+        return U[1 + d]
+    if e == 4:
+        return (U[4] + p) * vel[d]
+    i = e - 1
+    return U[1 + i] * vel[d] + (p if i == d else 0.0)
+
+
+# --------------------------------------------------------------------------
+# AT derivatives (Eq. (at), Table B)
+# --------------------------------------------------------------------------
+def _face_delay_field(cfg, delays, d):
+    """Per point: delay of the face its d-stencil crosses (0 if it crosses none)."""
+    li = _coord(cfg, d) % cfg.nloc[d]
+    pe = pe_index_field(cfg)
+    k_left = delays[pe, 2 * d]
+    k_right = delays[pe, 2 * d + 1]
+    k = np.where(li < HALF_WIDTH, k_left, np.where(li >= cfg.nloc[d] - HALF_WIDTH, k_right, 0))
+    return np.broadcast_to(k, pe.shape)
+
+
+def at_derivative(cfg, qlevels, d, delays, order):
+    """First (order=1) or second (order=2) AT derivative in direction d.
+
+    qlevels[l] is the quantity at level n-l.  Literal Table B: the standard
+    stencil is evaluated once per l = 0, 1, 2 with the points outside the PE
+    taken at level n-k-l, and the three results are weighted by w_l(k).
+    Points inside the PE always use level n.  A direction with one PE is a
+    plain periodic stencil at level n.
+    """
+    stencil, denom = (D1_CENTRAL, 12.0 * cfg.dx[d]) if order == 1 else \
+                     (D2_CENTRAL, 12.0 * cfg.dx[d] ** 2)
+    ax = _axis(d)
+    if cfg.pes[d] == 1:
+        out = np.zeros_like(qlevels[0])
+        for off, c in stencil:
+            out += c * np.roll(qlevels[0], -off, axis=ax)
+        return out / denom
+    nloc = cfg.nloc[d]
+    li = _coord(cfg, d) % nloc
+    kf = _face_delay_field(cfg, delays, d)
+    Q = np.stack(qlevels)                       # [level, z, y, x]
+    out = np.zeros_like(qlevels[0])
+    for l in range(T_LEVELS):
+        w = np.vectorize(lambda kk: at_weights(kk)[l], otypes=[float])(kf)
+        S = np.zeros_like(qlevels[0])
+        for off, c in stencil:
+            inside = (li + off >= 0) & (li + off < nloc)
+            level = np.where(inside, 0, kf + l)
+            shifted = np.roll(Q, -off, axis=ax + 1)  # shifted[:, ..., i] = Q[:, ..., i+off]
+            val = np.take_along_axis(shifted, np.broadcast_to(level, kf.shape)[None], axis=0)[0]
+            S += c * val
+        out += w * S
+    return out / denom
+
+
+def _central_fits(cfg, d):
+    """True where the 5-point d-stencil stays inside the PE (or d has one PE)."""
+    li = _coord(cfg, d) % cfg.nloc[d]
+    if cfg.pes[d] == 1:
+        return np.ones_like(li, dtype=bool)
+    return (li >= HALF_WIDTH) & (li <= cfg.nloc[d] - 1 - HALF_WIDTH)
+
+
+def _apply(f, stencil, ax):
+    out = np.zeros_like(f)
+    for off, c in stencil:
+        out += c * np.roll(f, -off, axis=ax)
+    return out
+
+
+def pe_local_d1(cfg, g, d):
+    """PE-local 4th-order first derivative: central where it fits inside the
+    PE, one-sided at the two points next to each PE face (no data from other
+    PEs is read)."""
+    ax = _axis(d)
+    central = _apply(g, D1_CENTRAL, ax)
+    if cfg.pes[d] == 1:
+        return central / (12.0 * cfg.dx[d])
+    nloc = cfg.nloc[d]
+    li = _coord(cfg, d) % nloc
+    out = np.where(li == 0, _apply(g, D1_FORWARD0, ax),
+          np.where(li == 1, _apply(g, D1_FORWARD1, ax),
+          np.where(li == nloc - 2, _apply(g, D1_BACKWARD1, ax),
+          np.where(li == nloc - 1, _apply(g, D1_BACKWARD0, ax), central))))
+    return out / (12.0 * cfg.dx[d])
+
+
+def mixed_derivative(cfg, grad_b, grad_a, a, b):
+    """d/dx_a (d f/dx_b) by the three-step rule of Sec. 2.1.
+
+    grad_b = AT first derivative of f in b, grad_a = AT first derivative of f in
+    a (both already computed with AT stencils at PE faces).  At points whose
+    a- and b-stencils both fit inside the PE the standard central derivative in
+    a of grad_b is used.  At the other (boundary) points the PE-local
+    derivative in a of grad_b and the PE-local derivative in b of grad_a are
+    averaged.
+    """
+    interior = _central_fits(cfg, a) & _central_fits(cfg, b)
+    central = _apply(grad_b, D1_CENTRAL, _axis(a)) / (12.0 * cfg.dx[a])
+    boundary = 0.5 * (pe_local_d1(cfg, grad_b, a) + pe_local_d1(cfg, grad_a, b))
+    return np.where(interior, central, boundary)
+
+
+# --------------------------------------------------------------------------
+# forcing (Sec. 4.2): solenoidal, |kappa| <= kappa_f
+# --------------------------------------------------------------------------
+def forcing_modes(kf):
+    """Half set of integer wavevectors 0 < |k| <= kf: k_x > 0, or k_x = 0 and
+    k_y > 0, or k_x = k_y = 0 and k_z > 0.  Order: k_z outer, k_x inner."""
+    K = int(math.floor(kf))
+    modes = []
+    for kz in range(-K, K + 1):
+        for ky in range(-K, K + 1):
+            for kx in range(-K, K + 1):
+                k2 = kx * kx + ky * ky + kz * kz
+                if k2 == 0 or k2 > kf * kf + 1e-12:
+                    continue
+                if kx > 0 or (kx == 0 and ky > 0) or (kx == 0 and ky == 0 and kz > 0):
+                    modes.append((kx, ky, kz))
+    return modes
+
+
+def forcing_noise(cfg, step, modes):
+    """Complex standard normals xi[m, c] (Box-Muller on Philox words 0, 1)."""
+    k0, k1 = split_seed(cfg.f_seed)
+    m = np.arange(len(modes), dtype=np.uint64)[:, None]
+    c = np.arange(3, dtype=np.uint64)[None, :]
+    w0, w1, _, _ = philox4x32_10(np.uint64(step), m, c, np.uint64(FORCING_STREAM_TAG), k0, k1)
+    u1 = (w0.astype(np.float64) + 0.5) * 2.0 ** -32
+    u2 = (w1.astype(np.float64) + 0.5) * 2.0 ** -32
+    r = np.sqrt(-2.0 * np.log(u1))
+    return r * np.cos(2.0 * math.pi * u2) + 1j * r * np.sin(2.0 * math.pi * u2)
+
+
+def solenoidal_projection(modes, v):
+    """v - k (k . v) / |k|^2 for each mode."""
+    k = np.array(modes, dtype=np.float64)
+    kv = np.sum(k * v, axis=1)
+    return v - k * (kv / np.sum(k * k, axis=1))[:, None]
+
+
+def forcing_coefficients(cfg, step):
+    """OU coefficients f_hat[m, c] at step n: f^0 = s P(xi^0),
+    f^n = a f^{n-1} + s sqrt(1 - a^2) P(xi^n), a = exp(-dt / T_f)."""
+    modes = forcing_modes(cfg.kf)
+    a = math.exp(-cfg.dt / cfg.f_tcorr)
+    b = cfg.f_amp * math.sqrt(1.0 - a * a)
+    fh = cfg.f_amp * solenoidal_projection(modes, forcing_noise(cfg, 0, modes))
+    for s in range(1, step + 1):
+        fh = a * fh + b * solenoidal_projection(modes, forcing_noise(cfg, s, modes))
+    return fh
+
+
+def forcing_field(cfg, fhat):
+    """f_c(x) = sum over the half set of 2 Re(f_hat[m, c] exp(i k . x))."""
+    modes = forcing_modes(cfg.kf)
+    x = [_coord(cfg, d) * cfg.dx[d] for d in range(3)]
+    f = [np.zeros((cfg.n[2], cfg.n[1], cfg.n[0])) for _ in range(3)]
+    for m, (kx, ky, kz) in enumerate(modes):
+        phase = np.exp(1j * (kx * x[0] + ky * x[1] + kz * x[2]))
+        for c in range(3):
+            f[c] += 2.0 * np.real(fhat[m, c] * phase)
+    return f
+
+
+# --------------------------------------------------------------------------
+# right-hand side
+# --------------------------------------------------------------------------
+def rhs(cfg, levels, delays, fhat=None, return_aux=False):
+    """R(U^n) for the conserved variables.
+
+    levels[l] = U^{n-l} for l = 0 .. L+T_l-1, each shaped [5, nz, ny, nx].
+    delays[p, f] = this step's delay map.  fhat = forcing coefficients (or None).
+    """
+    nlev = len(levels)
+    g = cfg.gamma
+
+    def q_levels(name):
+        return [quantity(cfg, levels[l], name) for l in range(nlev)]
+
+    def D1(name, d):
+        return at_derivative(cfg, q_levels(name), d, delays, 1)
+
+    def D2(name, d):
+        return at_derivative(cfg, q_levels(name), d, delays, 2)
+
+    rho, vel, p, T = primitives(cfg, levels[0])
+    R = np.zeros_like(levels[0])
+
+    # inviscid part: - sum_j d/dx_j F_j
+    for d in range(3):
+        for e in range(5):
+            R[e] -= D1("F%d%d" % (d, e), d)
+
+    # first derivatives A[i][j] = d u_i / d x_j and dT/dx_j (AT at faces)
+    A = [[D1("u%d" % i, j) for j in range(3)] for i in range(3)]
+    dT = [D1("T", j) for j in range(3)]
+    # second derivatives d^2 u_i / d x_j^2 and d^2 T / d x_j^2
+    D2u = [[D2("u%d" % i, j) for j in range(3)] for i in range(3)]
+    lap_u = [D2u[i][0] + D2u[i][1] + D2u[i][2] for i in range(3)]
+    lap_T = D2("T", 0) + D2("T", 1) + D2("T", 2)
+    theta = A[0][0] + A[1][1] + A[2][2]
+
+    # d theta / d x_i = d^2 u_i / d x_i^2 + sum_{k != i} d/dx_i (d u_k / d x_k)
+    grad_theta = []
+    for i in range(3):
+        s = D2u[i][i].copy()
+        for k in range(3):
+            if k != i:
+                # mixed d/dx_i (d u_k/dx_k): grad in b=k is A[k][k], grad in a=i is A[k][i]
+                s = s + mixed_derivative(cfg, A[k][k], A[k][i], i, k)
+        grad_theta.append(s)
+
+    mu = cfg.mu0 * T ** cfg.visc_exp
+    dmu_dT = cfg.visc_exp * mu / T
+    dmu = [dmu_dT * dT[j] for j in range(3)]
+    cp = 1.0 / (g - 1.0)
+    kappa = mu * cp / cfg.prandtl
+    dkappa = [dmu[j] * cp / cfg.prandtl for j in range(3)]
+
+    delta = lambda i, j: 1.0 if i == j else 0.0
+    sigma = [[mu * (A[i][j] + A[j][i] - (2.0 / 3.0) * delta(i, j) * theta) for j in range(3)]
+             for i in range(3)]
+    S = [[0.5 * (A[i][j] + A[j][i]) for j in range(3)] for i in range(3)]
+
+    # viscous momentum term V_i = d sigma_ij / d x_j, expanded
+    V = []
+    for i in range(3):
+        v = mu * (lap_u[i] + grad_theta[i] / 3.0)
+        for j in range(3):
+            v = v + dmu[j] * (A[i][j] + A[j][i] - (2.0 / 3.0) * delta(i, j) * theta)
+        V.append(v)
+
+    if fhat is not None:
+        f = forcing_field(cfg, fhat)
+    else:
+        f = [np.zeros_like(rho)] * 3
+
+    for i in range(3):
+        R[1 + i] += V[i] + rho * f[i]
+    sigS = sum(sigma[i][j] * S[i][j] for i in range(3) for j in range(3))
+    R[4] += (sum(vel[i] * V[i] for i in range(3)) + sigS + kappa * lap_T
+             + sum(dkappa[j] * dT[j] for j in range(3))
+             + sum(rho * f[i] * vel[i] for i in range(3)))
+    if not return_aux:
+        return R
+    aux = dict(rho=rho, vel=vel, p=p, T=T, A=A, theta=theta, sigS=sigS, f=f)
+    return R, aux
+
+
+# --------------------------------------------------------------------------
+# statistics (volume averages, FP64)
+# --------------------------------------------------------------------------
+def statistics(cfg, U, aux):
+    rho, vel, p, T, A = aux["rho"], aux["vel"], aux["p"], aux["T"], aux["A"]
+    mean = lambda a: float(np.mean(a))
+    u2 = vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2
+    c = np.sqrt(T)                       # c^2 = gamma p / rho = T
+    m2 = np.mean([mean(A[i][i] ** 2) for i in range(3)])
+    m3 = np.mean([mean(A[i][i] ** 3) for i in range(3)])
+    m4 = np.mean([mean(A[i][i] ** 4) for i in range(3)])
+    om = [A[2][1] - A[1][2], A[0][2] - A[2][0], A[1][0] - A[0][1]]
+    wave = max(float(np.max(np.abs(vel[d]) + c)) for d in range(3))
+    return dict(
+        mass=mean(U[0]), mom=[mean(U[1]), mean(U[2]), mean(U[3])], energy=mean(U[4]),
+        tke=mean(0.5 * rho * u2), dissipation=mean(aux["sigS"]),
+        grad_m2=m2, grad_m3=m3, grad_m4=m4,
+        skewness=m3 / m2 ** 1.5, flatness=m4 / m2 ** 2,
+        enstrophy=mean(om[0] ** 2 + om[1] ** 2 + om[2] ** 2),
+        pressure_dilatation=mean(p * aux["theta"]),
+        forcing_power=mean(rho * (aux["f"][0] * vel[0] + aux["f"][1] * vel[1] + aux["f"][2] * vel[2])),
+        urms=math.sqrt(mean(u2) / 3.0), mach_t=math.sqrt(mean(u2)) / mean(c),
+        max_wave_speed=wave, min_rho=float(np.min(rho)), min_p=float(np.min(p)))
+
+
+def max_wave_speed(cfg, U):
+    """max over points and directions of |u_d| + c."""
+    rho, vel, p, T = primitives(cfg, U)
+    c = np.sqrt(T)
+    return max(float(np.max(np.abs(vel[d]) + c)) for d in range(3))
+
+
+def dt_from_cfl(cfg, U, cfl):
+    """Fixed time step from the convective CFL at t = 0 (Sec. 2.2): dt = r_c dx / s."""
+    rho, vel, p, T = primitives(cfg, U)
+    c = np.sqrt(T)
+    s = max(float(np.max((np.abs(vel[d]) + c) / cfg.dx[d])) for d in range(3))
+    return cfl / s
+
+
+# --------------------------------------------------------------------------
+# time stepping (Eq. (time_ab), AB2)
+# --------------------------------------------------------------------------
+def ab2_update(U, R, R_prev, dt):
+    """u^{n+1} = u^n + dt (3/2 f^n - 1/2 f^{n-1}); forward Euler when no f^{n-1}."""
+    if R_prev is None:
+        return U + dt * R
+    return U + dt * (1.5 * R - 0.5 * R_prev)
+
+
+@dataclass
+class Run:
+    """Oracle time loop: holds U^n .. U^{n-L-T_l+1} in full (levels[0] = U^n)."""
+    cfg: Config
+    mode: int
+    levels: list = field(default_factory=list)
+    step_n: int = 0
+    R_prev: object = None
+
+    @classmethod
+    def start(cls, cfg, U0, mode, step=0, history=None):
+        """All stored levels equal U0 (the synchronous start-up fill), unless an
+        explicit history [U^n, U^{n-1}, ...] is given."""
+        if history is None:
+            levels = [np.array(U0, dtype=np.float64) for _ in range(cfg.n_levels)]
+        else:
+            levels = [np.array(h, dtype=np.float64) for h in history]
+            levels += [levels[-1]] * (cfg.n_levels - len(levels))
+        return cls(cfg=cfg, mode=mode, levels=levels, step_n=step)
+
+    def delays(self):
+        return delay_map(self.cfg, self.step_n, self.mode)
+
+    def fhat(self):
+        return forcing_coefficients(self.cfg, self.step_n) if self.cfg.forcing else None
+
+    def rhs(self, return_aux=False):
+        return rhs(self.cfg, self.levels, self.delays(), self.fhat(), return_aux)
+
+    def step(self):
+        R = self.rhs()
+        U_new = ab2_update(self.levels[0], R, self.R_prev, self.cfg.dt)
+        self.levels = [U_new] + self.levels[:-1]
+        self.R_prev = R
+        self.step_n += 1
+        return U_new

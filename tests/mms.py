@@ -1,0 +1,67 @@
+"""Manufactured smooth fields and the exact right-hand side of the compressible
+Navier-Stokes equations, derived symbolically with sympy from the conservation
+laws in divergence form (Sec. 2, Eqs. (cont), (mome) and the total-energy
+equation d E/dt + d((E+p)u_j)/dx_j = d(u_i sigma_ij)/dx_j + d(k dT/dx_j)/dx_j).
+
+Nothing here is shared with the oracle's discretisation: the derivatives are
+sympy's, the viscous terms stay in divergence form, and the result is the
+exact time derivative of the conserved variables.
+"""
+import functools
+
+import numpy as np
+import sympy as sp
+
+x, y, z, t = sp.symbols("x y z t", real=True)
+
+
+def fields():
+    """Smooth periodic rho, u, v, w, T (functions of x, y, z, t)."""
+    rho = 1 + sp.Rational(1, 10) * sp.sin(x + sp.Rational(3, 10) * t) * sp.cos(y) \
+        + sp.Rational(1, 20) * sp.sin(z - sp.Rational(1, 5) * t)
+    u = sp.Rational(1, 5) * sp.sin(y) * sp.cos(z + sp.Rational(1, 10) * t) + sp.Rational(1, 10) * sp.cos(x)
+    v = sp.Rational(3, 20) * sp.sin(z) * sp.cos(x - sp.Rational(1, 5) * t) + sp.Rational(1, 20) * sp.sin(y)
+    w = sp.Rational(1, 10) * sp.sin(x) * sp.sin(y + sp.Rational(3, 10) * t) + sp.Rational(2, 25) * sp.cos(z)
+    T = 1 + sp.Rational(1, 10) * sp.cos(x - y) * sp.sin(z + sp.Rational(1, 5) * t)
+    return rho, (u, v, w), T
+
+
+@functools.lru_cache(maxsize=None)
+def exact(gamma, prandtl, mu0, omega):
+    """Return (conserved(X, Y, Z, tt), rhs(X, Y, Z, tt)) numpy callables."""
+    g = sp.nsimplify(gamma)
+    rho, vel, T = fields()
+    X = (x, y, z)
+    p = rho * T / g
+    E = p / (g - 1) + rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2) / 2
+    mu = sp.nsimplify(mu0) * T ** sp.nsimplify(omega)
+    kap = mu / (g - 1) / sp.nsimplify(prandtl)
+    dudx = [[sp.diff(vel[i], X[j]) for j in range(3)] for i in range(3)]
+    theta = dudx[0][0] + dudx[1][1] + dudx[2][2]
+    sigma = [[mu * (dudx[i][j] + dudx[j][i] - (sp.Rational(2, 3) * theta if i == j else 0))
+              for j in range(3)] for i in range(3)]
+    R = [0] * 5
+    R[0] = -sum(sp.diff(rho * vel[j], X[j]) for j in range(3))
+    for i in range(3):
+        R[1 + i] = sum(-sp.diff(rho * vel[i] * vel[j] + (p if i == j else 0), X[j])
+                       + sp.diff(sigma[i][j], X[j]) for j in range(3))
+    R[4] = sum(-sp.diff((E + p) * vel[j], X[j])
+               + sp.diff(sum(vel[i] * sigma[i][j] for i in range(3)), X[j])
+               + sp.diff(kap * sp.diff(T, X[j]), X[j]) for j in range(3))
+    cons = [rho, rho * vel[0], rho * vel[1], rho * vel[2], E]
+    fc = sp.lambdify((x, y, z, t), cons, "numpy")
+    fr = sp.lambdify((x, y, z, t), R, "numpy")
+    return fc, fr
+
+
+def grid(n):
+    """[z, y, x] coordinate arrays of the (2 pi)^3 grid."""
+    ax = [np.arange(m) * 2 * np.pi / m for m in n]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return X, Y, Z
+
+
+def evaluate(f, n, tt):
+    X, Y, Z = grid(n)
+    out = f(X, Y, Z, tt)
+    return np.stack([np.broadcast_to(np.asarray(o, dtype=np.float64), X.shape) for o in out])
