@@ -1,0 +1,306 @@
+"""Benchmark: grid-point updates/s of one AT-DNS time step on GB300.
+
+Workload (the paper's decaying-turbulence configuration at 256^3, Sec. 4 /
+Table 3 shapes): 256^3 periodic (2 pi)^3 box, 8x8x8 virtual PEs of 32^3
+points (N_B = 33 %), 4th-order AT stencils with random delays uniform on
+{0, 1, 2} (L = 2) from the seeded Philox stream, AB2 with a fixed dt, FP64,
+statistics reduced every step.  Input: the seeded solenoidal field
+E(k) ~ k^4 exp(-2 (k/4)^2), M_t = 0.3 (synthetic; the paper's forced
+stationary fields are not available).  A step is one full pass of the hot path
+(delay map, AT ghost assembly, derivative sweeps, assembly, AB2 update, ring
+write, reductions).  The working set (~8 GB) is far larger than L2, so no L2
+flush is needed between steps.
+
+Arms:
+  default            the CUDA library (FP64 headline, FP32-bulk variant);
+  --impl reference   the FP64 numpy oracle on the host cores, on a bounded
+                     sample of the same workload (64^3 with 2x2x2 PEs of 32^3).
+
+Prints one JSON line (rank 0).
+"""
+import argparse
+import json
+import os
+import statistics as pystats
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point RK-step updates/s and HBM roofline fraction, FP64 vs FP32-bulk"
+UNIT = "grid-point updates/s"
+N, PES, L, SEED = 256, 8, 2, 2024
+MU0 = None          # set from the resolution rule kappa_max eta = 1.5 at t = 0
+CFL_AT = 0.2        # min(0.5, 0.8 / f(L)), f(2) = 0.90*4 - 0.35*2 + 1 = 3.9 (Sec. 3.2)
+# FP64 operations per grid point of the main kernel, counted from the method
+# (FMA = 2; division, square root and power = 1 each); see the design notes.
+FLOP_MAIN = 390.0
+# algorithmic HBM bytes per grid point of one step (read U, R^{n-1}; write U^{n+1},
+# R^n; plus the slab ring: 1 write + 3 reads of 5 variables at the N_B fraction)
+NB_FRAC = 1.0 - (28.0 / 32.0) ** 3
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max SM clock
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "_fallback": True}
+
+
+def algorithmic_bytes(elem):
+    return 4 * 5 * elem + NB_FRAC * 5 * elem * 4
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, out):
+        self.out = out
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.out, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self, dev=0):
+        rows = []
+        try:
+            for line in open(self.out):
+                parts = [t.strip() for t in line.split(",")]
+                if len(parts) < 9 or parts[0] != str(dev):
+                    continue
+                rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": pystats.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_rate(steps, warmup, n=48, pes=2):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import numpy as np
+    from oracle import ns
+    from paper_2003_10561_gb300 import synth
+    U0 = synth.initial_state((n, n, n), k0=4.0, mach_t=0.3, seed=0)
+    cfg = ns.Config(n=(n, n, n), pes=(pes, pes, pes), mu0=0.01, max_delay=L, seed=SEED)
+    cfg.dt = ns.dt_from_cfl(cfg, U0, CFL_AT)
+    hist = synth.history(U0, cfg.n_levels, eps=1e-3, seed=3)
+    run = ns.Run.start(cfg, None, ns.RANDOM, step=cfg.n_levels + 2, history=hist)
+    for _ in range(warmup):
+        run.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        run.step()
+    el = time.perf_counter() - t0
+    return n ** 3 * steps / el, el
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    steps = max(1, args.steps)
+    warm = max(0, args.warmup)
+    rate, el = oracle_rate(steps, warm)
+    sample = "FP64 numpy oracle: AB2 steps of a 48^3 box with 2x2x2 PEs of 24^3 points, random delays L = 2 (the workload's method at a size the oracle finishes in seconds)"
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(world),
+            "cpu_baseline": {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1, "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(world):
+    return {"workload": "decaying turbulence 256^3, 8x8x8 virtual PEs (32^3 each, N_B 33%), 4th-order AT "
+                        "stencils, random delays {0,1,2} (L=2), AB2, FP64, stats every step",
+            "grid": [N, N, N], "pes": [PES, PES, PES], "max_delay": L, "delay_mode": "random",
+            "integrator": "AB2", "precision": "P64", "parallelism": "replicas" if world > 1 else "single",
+            "l2": "working set ~8 GB >> 129 MB L2; no flush needed"}
+
+
+def make_solver(at_dns, precision, stream, mu0):
+    return at_dns.Solver(n=(N, N, N), pes=(PES, PES, PES), precision=precision, stream=stream,
+                         gamma=1.4, prandtl=0.7, visc_exp=0.76, mu0=mu0, cfl=CFL_AT, dt=0.0,
+                         max_delay=L, seed=SEED, stats_every=1)
+
+
+def timed_steps(s, stream, steps, warmup, torch, profile=False):
+    s.step(warmup, "random")
+    s.synchronize()
+    if profile:
+        s.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(steps, "random")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = s.kernel_times() if profile else {}
+    if profile:
+        s.profile(False)
+    return ms, kt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    from paper_2003_10561_gb300 import at_dns, synth
+    at_dns.load()
+
+    mu0 = synth.mu0_for_resolution((N, N, N), k0=4.0, mach_t=0.3, seed=0)
+    U0 = synth.initial_state((N, N, N), k0=4.0, mach_t=0.3, seed=0)
+    stream = torch.cuda.Stream()
+    res = {}
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
+                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_rank%d.csv" % rank)
+    for prec in ("p64", "p32"):
+        s = make_solver(at_dns, prec, stream.cuda_stream, mu0)
+        s.set_state(U0)
+        s.step(at_dns.at_dns_get_info(s.h).n_levels + 1, "random")   # past the synchronous start-up
+        if pg:
+            pg.barrier()
+        if prec == "p64":
+            with clocks:
+                ms, kt = timed_steps(s, stream, args.steps, args.warmup, torch, profile=True)
+        else:
+            ms, kt = timed_steps(s, stream, args.steps, args.warmup, torch, profile=True)
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if pg:
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        st = s.stats()
+        res[prec] = {"ms": ms, "kt": kt, "stats": st, "info": s.info()}
+        # end to end through the public API with host buffers: per step, upload
+        # U^n from pinned host memory (as the state of step n), step, read the
+        # statistics record back
+        if prec == "p64":
+            host = torch.from_numpy(U0).pin_memory()
+            nlev = at_dns.at_dns_get_info(s.h).n_levels
+            e2e_steps = max(3, args.steps // 4)
+            s.set_history(host[None], nlev + 3)
+            s.step(1, "random")
+            s.stats()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(e2e_steps):
+                s.set_history(host[None], nlev + 3 + k)
+                s.step(1, "random")
+                s.stats()
+            el = time.perf_counter() - t0
+            res["e2e"] = {"value": world * N ** 3 * e2e_steps / el, "unit": UNIT,
+                          "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(ctypes_stats_size(at_dns)),
+                          "steps": e2e_steps}
+        s.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, el = oracle_rate(3, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "3 AB2 steps (after 1 warm-up) of the FP64 numpy oracle on 48^3 with 2x2x2 PEs of "
+                         "24^3 points, random delays L = 2, single-threaded numpy; %.1f s timed" % el}
+
+    if rank != 0:
+        return 0
+    pk = peaks()
+    p64, p32 = res["p64"], res["p32"]
+    pts = float(N ** 3)
+    value = world * pts * args.steps / (p64["ms"] / 1e3)
+    main64 = p64["kt"].get("main", (1, 1.0))
+    t_main = main64[1] / main64[0] / 1e3
+    achieved = FLOP_MAIN * pts / t_main / 1e12
+    main32 = p32["kt"].get("main", (1, 1.0))
+    t_main32 = main32[1] / main32[0] / 1e3
+    bytes32 = algorithmic_bytes(4) * pts
+    ach32 = bytes32 / t_main32 / 1e9
+    launches = sum(v[0] for v in p64["kt"].values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": p64["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(world),
+        "roofline": {"bound": "alu", "kernel": "k_main (FP64)", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None,
+                     "note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe measured 1.20)"},
+        "fp32_bulk": {"value": world * pts * args.steps / (p32["ms"] / 1e3), "unit": UNIT,
+                      "ms_per_step": p32["ms"] / args.steps, "dtype": "f32",
+                      "roofline": {"bound": "hbm", "kernel": "k_main (FP32)", "achieved": ach32,
+                                   "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                                   "frac": ach32 / pk.get("hbm_gbs", 6800.0), "traffic": None},
+                      "rel_err_vs_fp64": {k: abs(p32["stats"][k] - p64["stats"][k]) / abs(p64["stats"][k])
+                                          for k in ("tke", "dissipation")}},
+        "kernel_ms_per_step": {k: v[1] / v[0] for k, v in p64["kt"].items()},
+        "kernel_ms_per_step_fp32": {k: v[1] / v[0] for k, v in p32["kt"].items()},
+        "e2e": res.get("e2e"),
+        "cpu_baseline": cpu,
+        "clocks": clocks.summary(local),
+        "gpu_launches": launches,
+        "rhs_per_s": value,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ctypes_stats_size(at_dns):
+    import ctypes
+    return ctypes.sizeof(at_dns.at_dns_stats_t)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * at_dns.h -- C ABI of the GB300 (sm_103a) library for one explicit time step
+ * of the compressible Navier-Stokes equations with Asynchrony-Tolerant (AT)
+ * finite differences at the faces of virtual processing elements (PEs).
+ *
+ * Method: Kumari & Donzis, "Direct numerical simulations of turbulent flows
+ * using high-order asynchrony-tolerant schemes: accuracy and performance",
+ * arXiv 2003.10561.
+ *   - equations: Sec. 2, Eqs. (cont), (mome), (ie) (solved here in total-energy
+ *     form E = rho e + rho|u|^2/2, divergence form for the inviscid flux);
+ *   - 4th-order central stencils inside a PE and AT stencils at PE faces:
+ *     Sec. 2.1, Eq. (at) and Table B (Appendix B), T_l = 3 time levels;
+ *   - mixed derivatives by the three-step rule of Sec. 2.1;
+ *   - second-order Adams-Bashforth with a fixed dt: Sec. 2.2, Eq. (time_ab);
+ *   - PE decomposition, control parameters c_r and L, storage of L + T_l
+ *     levels: Sec. 3, Eqs. (NT)-(NB), Sec. 3.1;
+ *   - delays: synchronous, periodic (Communication-Avoiding, Algorithm 2) or
+ *     random (Synchronization-Avoiding, Algorithm 1), the random ones drawn
+ *     from Philox4x32-10 instead of a network;
+ *   - large-scale solenoidal forcing on |kappa| <= kappa_f: Sec. 4.2.
+ *
+ * Units: rho_0 = T_0 = c_0 = 1, so p = rho T / gamma, c^2 = T and
+ * c_p = 1/(gamma-1).  Viscosity mu = mu0 T^visc_exp, conductivity
+ * k = mu c_p / Pr.  The box is (2 pi)^3, dx_d = 2 pi / n[d].
+ *
+ * Field layout (every state array crossing this ABI): FP64, structure of
+ * arrays [5][n[2]][n[1]][n[0]] -- variable (rho, rho u, rho v, rho w, E),
+ * then z, y, x with x fastest -- i.e. 5 * n0 * n1 * n2 doubles.
+ *
+ * Ownership: the library owns every device allocation it makes (released by
+ * at_dns_destroy).  Caller buffers are read or written only during the call;
+ * `where` says whether a pointer is host (AT_DNS_HOST, any pageable or pinned
+ * memory) or device (AT_DNS_DEVICE, memory of the handle's device).
+ *
+ * Errors: every int-returning call returns AT_DNS_OK (0) or a negative
+ * AT_DNS_E_* code and never throws; at_dns_last_error() gives a text.
+ * Calls on one handle are ordered on its stream and are not thread-safe.
+ */
+#ifndef AT_DNS_H
+#define AT_DNS_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define AT_DNS_OK              0
+#define AT_DNS_E_INVALID_ARG  -1   /* bad pointer, size, mode or configuration */
+#define AT_DNS_E_OOM          -2   /* a device allocation failed */
+#define AT_DNS_E_CUDA         -3   /* a CUDA runtime call failed */
+#define AT_DNS_E_UNSTABLE     -4   /* NaN/Inf, rho <= 0 or p <= 0 seen in a step */
+#define AT_DNS_E_UNSUPPORTED  -5   /* a combination the library does not run */
+#define AT_DNS_E_STATE        -6   /* no state has been set yet */
+
+/* delay modes (Sec. 3.1) */
+#define AT_DNS_SYNC      0   /* k = 0 on every face: standard scheme */
+#define AT_DNS_PERIODIC  1   /* CAA: k = (n - n0) mod c_r (Algorithm 2) */
+#define AT_DNS_RANDOM    2   /* SAA: k iid uniform on {0..L} (Algorithm 1) */
+
+/* precision forms */
+#define AT_DNS_P64  0        /* FP64 storage and arithmetic */
+#define AT_DNS_P32  1        /* FP32 state/stencils; FP64 update, ring and reductions */
+
+/* pointer locations */
+#define AT_DNS_HOST    0
+#define AT_DNS_DEVICE  1
+
+typedef struct at_dns at_dns_t;   /* opaque handle; owned by the library */
+
+typedef struct {
+  int32_t  n[3];         /* grid points in x, y, z (each >= 5)                          */
+  int32_t  pes[3];       /* virtual PEs per direction; n[d] % pes[d] == 0 and, when
+                            pes[d] > 1, n[d]/pes[d] >= 5.  pes[d] == 1: no faces in d   */
+  double   gamma;        /* ratio of specific heats (1.4)                               */
+  double   prandtl;      /* Prandtl number (0.7)                                        */
+  double   mu0;          /* viscosity at T = 1                                          */
+  double   visc_exp;     /* power-law exponent omega (0.76)                             */
+  double   dt;           /* fixed time step; <= 0: set from cfl when a state is set     */
+  double   cfl;          /* convective CFL used when dt <= 0                            */
+  int32_t  max_delay;    /* L >= 0: largest delay; the ring holds L + 3 levels          */
+  int32_t  comm_period;  /* c_r >= 1 for AT_DNS_PERIODIC; needs c_r - 1 <= L            */
+  uint64_t seed;         /* key of the random delay stream                              */
+  int32_t  forcing;      /* 0: decaying; 1: OU solenoidal forcing on |kappa| <= kf      */
+  double   kf;           /* forcing shell radius kappa_f (<= 4)                         */
+  double   f_amp;        /* OU amplitude sigma of each forcing coefficient              */
+  double   f_tcorr;      /* OU correlation time T_f                                     */
+  uint64_t f_seed;       /* key of the forcing noise stream                             */
+  int32_t  precision;    /* AT_DNS_P64 or AT_DNS_P32                                    */
+  int32_t  stats_every;  /* 1: reduce statistics in every step; 0: only on request      */
+  void*    stream;       /* cudaStream_t to run on; NULL = the legacy default stream    */
+} at_dns_config_t;
+
+typedef struct {
+  int64_t step;          /* n of the state the statistics describe                      */
+  double  time, dt;
+  double  mass;          /* <rho>                                                       */
+  double  mom[3];        /* <rho u_i>                                                   */
+  double  energy;        /* <E>                                                         */
+  double  tke;           /* K = <rho u_i u_i / 2>                                       */
+  double  dissipation;   /* <sigma_ij S_ij>                                             */
+  double  grad_m2, grad_m3, grad_m4;  /* <(du_i/dx_i)^k>, averaged over i = 1..3         */
+  double  skewness, flatness;         /* m3 / m2^1.5, m4 / m2^2                          */
+  double  enstrophy;     /* <omega_i omega_i>                                           */
+  double  pressure_dilatation;        /* <p theta>                                      */
+  double  forcing_power; /* <rho f_i u_i>                                               */
+  double  urms;          /* sqrt(<u_i u_i>/3)                                           */
+  double  mach_t;        /* sqrt(<u_i u_i>) / <c>                                       */
+  double  max_wave_speed;/* max over points and d of |u_d| + c                          */
+  double  min_rho, min_p;
+  int32_t unstable;      /* nonzero: a NaN/Inf, rho <= 0 or p <= 0 was seen             */
+} at_dns_stats_t;
+
+typedef struct {
+  int64_t step;          /* current level n                                             */
+  double  time, dt;
+  int32_t n_levels;      /* L + T_l time levels in the ring                             */
+  double  boundary_fraction;  /* N_B / N_T per PE, Eqs. (NT)-(NB)                       */
+  size_t  device_bytes;  /* device memory held by the handle                            */
+  int32_t kernels_per_step;   /* kernel launches of one at_dns_step step                */
+} at_dns_info_t;
+
+/* Fill *cfg with defaults: 32^3, one PE, gamma 1.4, Pr 0.7, omega 0.76,
+ * mu0 0.01, cfl 0.5 (dt from it), L = 2, c_r = 3, no forcing, P64, stats every
+ * step, default stream.  Returns AT_DNS_E_INVALID_ARG if cfg is NULL. */
+int at_dns_config_default(at_dns_config_t* cfg);
+
+/* Validate *cfg, allocate device state (double-buffered U, AB2 history,
+ * slab ring of L + 3 levels, ghost and derivative work arrays) on the current
+ * device and return a handle in *out.  Errors: INVALID_ARG (see the field
+ * rules above), OOM, CUDA.  Sec. 3: PE geometry and L + T_l levels. */
+int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out);
+
+/* Set U^0 = u (5*N^3 FP64, layout above), step n = 0, t = 0, fill every ring
+ * level with U^0 (the synchronous start-up of Algorithms 1 and 2), forget the
+ * AB2 history (the next step is forward Euler) and, if cfg.dt <= 0, set
+ * dt = cfl / max_{x,d}((|u_d| + c)/dx_d) (Sec. 2.2, fixed dt).
+ * Errors: INVALID_ARG (NULL, bad where), CUDA. */
+int at_dns_set_state(at_dns_t* h, const double* u, int where);
+
+/* Set a state with an explicit past: levels holds nlevels consecutive fields
+ * U^step, U^(step-1), ..., each 5*N^3 FP64 (1 <= nlevels <= L + 3; missing
+ * older levels repeat the oldest one given).  The step counter becomes `step`
+ * (>= 0), so the delay map of that step applies to the next rhs/step; the
+ * forcing coefficients are advanced to `step`; the AB2 history is forgotten.
+ * dt is not recomputed if already set.  Errors: INVALID_ARG, CUDA. */
+int at_dns_set_history(at_dns_t* h, const double* levels, int32_t nlevels,
+                       int64_t step, int where);
+
+/* Copy U^n out (5*N^3 FP64).  Errors: INVALID_ARG, STATE, CUDA. */
+int at_dns_get_state(at_dns_t* h, double* u_out, int where);
+
+/* Evaluate R(U^n), the right-hand side of the conserved variables at the
+ * current level with this step's delay map (mode = AT_DNS_*) and forcing,
+ * into rhs_out (5*N^3 FP64).  Does not advance time.  Also refreshes the
+ * statistics record.  Errors: INVALID_ARG, STATE, CUDA. */
+int at_dns_rhs(at_dns_t* h, int32_t delay_mode, double* rhs_out, int where);
+
+/* Advance nsteps AB2 steps (Eq. (time_ab)): for each step n, build the delay
+ * map, assemble AT ghost values from the ring, evaluate R(U^n), update
+ * U^{n+1} = U^n + dt(3/2 R^n - 1/2 R^{n-1}) (forward Euler on the first step
+ * after a state is set), store U^{n+1}'s PE-boundary slabs in the ring and
+ * advance the forcing.  Asynchronous on the handle's stream except that the
+ * health word is read back once at the end.  Errors: INVALID_ARG, STATE,
+ * CUDA, UNSTABLE (NaN/Inf, rho <= 0 or p <= 0 in any evaluated state; the
+ * state is left as computed). */
+int at_dns_step(at_dns_t* h, int32_t nsteps, int32_t delay_mode);
+
+/* Statistics of the state at which the last RHS was evaluated (a step or
+ * at_dns_rhs).  If none was evaluated since the state was set, one RHS
+ * evaluation in synchronous mode is made first (time does not advance).
+ * Blocks until the record is on the host.  Errors: INVALID_ARG, STATE, CUDA. */
+int at_dns_stats(at_dns_t* h, at_dns_stats_t* out);
+
+/* Delay map of step `step` for delay mode `mode`: out[p*6 + f] for PE
+ * p = (pz*Py + py)*Px + px and face f = x-, x+, y-, y+, z-, z+ (host buffer of
+ * Px*Py*Pz*6 bytes), computed by the same device code the step uses.
+ * Sec. 3.1 / Algorithms 1-2: zero for step < L + 3; periodic
+ * (step - L - 3) mod c_r; random floor(w0 (L+1) / 2^32) with w0 the first
+ * word of Philox4x32-10(counter = (step, p, f, 0x4154), key = (seed lo, seed hi)).
+ * Errors: INVALID_ARG, CUDA. */
+int at_dns_get_delay_map(at_dns_t* h, int64_t step, int32_t mode, uint8_t* out);
+
+/* Handle facts (step, time, dt, levels, N_B fraction, memory, launches). */
+int at_dns_get_info(at_dns_t* h, at_dns_info_t* out);
+
+/* Per-kernel device time, gathered with CUDA events recorded on the handle's
+ * stream around every launch while profiling is on. */
+typedef struct {
+  char    name[24];      /* kernel family: "delay_map", "prim", "ghost", "grad",
+                            "force_lines", "main", "stats_final", "force_advance"   */
+  int64_t launches;
+  double  total_ms;
+} at_dns_kernel_time_t;
+
+/* enable = 1: clear the records and start recording an event pair around each
+ * launch of at_dns_step / at_dns_rhs; enable = 0: stop.  Errors: INVALID_ARG. */
+int at_dns_profile(at_dns_t* h, int32_t enable);
+
+/* Wait for the recorded launches, and write up to `max` kernel families with
+ * their launch counts and summed event times into out; *count = families.
+ * Errors: INVALID_ARG, CUDA. */
+int at_dns_kernel_times(at_dns_t* h, at_dns_kernel_time_t* out, int32_t max, int32_t* count);
+
+/* Block until all work queued on the handle's stream has finished. */
+int at_dns_synchronize(at_dns_t* h);
+
+/* Text of the last error on this handle ("" if none); a NULL handle gives the
+ * last error of a failed at_dns_create on this thread.  Valid until the next
+ * call on the handle. */
+const char* at_dns_last_error(const at_dns_t* h);
+
+/* Release every device allocation of the handle.  NULL is ignored. */
+void at_dns_destroy(at_dns_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AT_DNS_H */

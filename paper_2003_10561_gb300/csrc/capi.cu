@@ -1,0 +1,849 @@
+// C ABI of the AT-DNS library (include/at_dns.h): handle, allocation, state
+// transfer, step orchestration and the small kernels around the step (delay
+// map, ring fill, forcing, wave speed, final reductions).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/at_dns.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace atdns;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Mode3 { int kx, ky, kz; };
+
+}  // namespace
+
+struct at_dns {
+  at_dns_config_t cfg{};
+  Geom g{};
+  Phys ph{};
+  cudaStream_t st = nullptr;
+  bool p64 = true;
+  size_t ssize = 8;            // bytes of the scalar type
+  // device buffers (scalar type S unless noted)
+  void* U[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* PQ = nullptr;
+  void* G = nullptr;
+  void* Rprev = nullptr;
+  void* GH[3] = {nullptr, nullptr, nullptr};
+  void* ring[3] = {nullptr, nullptr, nullptr};
+  double* stage = nullptr;     // [5][npts] FP64 staging / rhs output
+  uint8_t* dmap = nullptr;     // [P][6]
+  double* partial = nullptr;   // [main_blocks][kNumStat]
+  double* sums = nullptr;      // [kNumStat]
+  unsigned long long* words = nullptr;  // [4]
+  // forcing
+  int nmodes = 0, fK = 0;
+  Mode3* modes = nullptr;      // device
+  double2* fhat = nullptr;     // [nmodes][3]
+  void* fB = nullptr;          // vec2<S> [(K+1)][3][n2][n1]
+  void* fX = nullptr;          // vec2<S> [(K+1)][n0]
+  // state
+  bool has_state = false, first = true, stats_valid = false;
+  long long n = 0;
+  double t = 0.0, dt = 0.0;
+  long long stats_step = 0;
+  double stats_time = 0.0;
+  size_t bytes = 0;
+  std::string err;
+  // per-kernel event timing
+  bool prof = false;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+};
+
+// ---------------------------------------------------------------------------
+// small kernels
+namespace {
+
+__global__ void k_delay_map(uint8_t* out, int P, int Px, int Py, long long n, int mode, int L, int cr,
+                            uint32_t k0, uint32_t k1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * 6) return;
+  out[i] = (uint8_t)delay_of(mode, n, i / 6, i % 6, L, cr, k0, k1);
+}
+
+template <typename S>
+__global__ void k_from_double(const double* __restrict__ in, S* __restrict__ out, long long count) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < count) out[i] = (S)in[i];
+}
+
+template <typename S>
+__global__ void k_to_double(const S* __restrict__ in, double* __restrict__ out, long long count) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < count) out[i] = (double)in[i];
+}
+
+// Write the PE-boundary slabs of field U (S, [5][npts]) into ring slot `slot`.
+template <typename S>
+__global__ void k_ring_store(Geom g, const S* __restrict__ U, S* r0, S* r1, S* r2, int slot) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= g.npts) return;
+  int c[3];
+  decode(g, idx, c[0], c[1], c[2]);
+  S* rings[3] = {r0, r1, r2};
+  for (int d = 0; d < 3; ++d) {
+    if (g.pes[d] == 1) continue;
+    const int pe = c[d] / g.nl[d], li = c[d] - pe * g.nl[d], nl = g.nl[d];
+    if (li >= 2 && li < nl - 2) continue;
+    const int t = li < 2 ? li : li - nl + 4;
+    const long long sp = 4LL * pe + t, P4 = 4LL * g.pes[d];
+    const long long pl = plane_index(g, d, c[0], c[1], c[2]);
+    for (int v = 0; v < 5; ++v)
+      rings[d][(((long long)slot * 5 + v) * P4 + sp) * g.plane[d] + pl] = U[v * g.npts + idx];
+  }
+}
+
+// max over points and directions of (|u_d| + c) / dx_d  (FP64 input), as an ordered key.
+__global__ void k_wave(Geom g, Phys ph, const double* __restrict__ U, unsigned long long* word) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double s = 0.0;
+  if (idx < g.npts) {
+    const long long N = g.npts;
+    const double r = U[idx], inv = 1.0 / r;
+    const double u[3] = {U[N + idx] * inv, U[2 * N + idx] * inv, U[3 * N + idx] * inv};
+    const double p = ph.gm1 * (U[4 * N + idx] - 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+    const double c = sqrt(ph.gamma * p * inv);
+    for (int d = 0; d < 3; ++d) s = fmax(s, (fabs(u[d]) + c) * g.inv12dx[d] * 12.0);
+  }
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if ((threadIdx.x & 31) == 0) atomicMax((long long*)word, ordered_key(s));
+}
+
+// Reset the max/min keys; the health word only when asked (it stays sticky
+// across the steps of one at_dns_step call).
+__global__ void k_reset_words(unsigned long long* w, int health_too) {
+  w[0] = (unsigned long long)LLONG_MIN;
+  w[1] = (unsigned long long)LLONG_MAX;
+  w[2] = (unsigned long long)LLONG_MAX;
+  if (health_too) w[3] = 0ULL;
+}
+
+// Fixed-order sum of the block partials: block s sums statistic s.
+__global__ void k_stats_final(const double* __restrict__ partial, long long nb, double* sums) {
+  __shared__ double sh[256];
+  const int s = blockIdx.x;
+  double acc = 0.0;
+  for (long long b = threadIdx.x; b < nb; b += blockDim.x) acc += partial[b * kNumStat + s];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[s] = sh[0];
+}
+
+// Ornstein-Uhlenbeck forcing coefficients on the half set of modes:
+// f^0 = amp P(xi^0), f^s = a f^{s-1} + b P(xi^s), b = amp sqrt(1 - a^2),
+// xi from Box-Muller on Philox4x32-10 words 0, 1 of counter (s, m, c, 0x464F);
+// P removes the component along the wavevector.  One thread per mode runs the
+// recursion from step `from` to step `to` (from = 0 starts it).
+__global__ void k_force_advance(const Mode3* __restrict__ modes, int nmodes, double2* fhat, long long from,
+                                long long to, double a, double b, double amp, uint32_t k0, uint32_t k1) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nmodes) return;
+  const Mode3 md = modes[m];
+  const double kv[3] = {(double)md.kx, (double)md.ky, (double)md.kz};
+  const double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+  double fr[3], fi[3];
+  for (int c = 0; c < 3; ++c) { fr[c] = fhat[m * 3 + c].x; fi[c] = fhat[m * 3 + c].y; }
+  for (long long s = from; s <= to; ++s) {
+    double xr[3], xi[3];
+    for (int c = 0; c < 3; ++c) {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)m, (uint32_t)c, kForceTag), k0, k1);
+      const double u1 = ((double)w.x + 0.5) * 2.3283064365386963e-10;   // 2^-32
+      const double u2 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
+      const double r = sqrt(-2.0 * log(u1));
+      double sn, cs;
+      sincos(2.0 * M_PI * u2, &sn, &cs);
+      xr[c] = r * cs;
+      xi[c] = r * sn;
+    }
+    const double kr = (kv[0] * xr[0] + kv[1] * xr[1] + kv[2] * xr[2]) / k2;
+    const double ki = (kv[0] * xi[0] + kv[1] * xi[1] + kv[2] * xi[2]) / k2;
+    for (int c = 0; c < 3; ++c) {
+      const double pr = xr[c] - kv[c] * kr, pi = xi[c] - kv[c] * ki;
+      if (s == 0) { fr[c] = amp * pr; fi[c] = amp * pi; }
+      else { fr[c] = a * fr[c] + b * pr; fi[c] = a * fi[c] + b * pi; }
+    }
+  }
+  for (int c = 0; c < 3; ++c) fhat[m * 3 + c] = make_double2(fr[c], fi[c]);
+}
+
+// Line sums B[kx][c](y, z) = sum over modes with this kx of
+// 2 f_hat[m][c] exp(i (ky y dy + kz z dz)), so that at a point
+// f_c = sum_kx Re(B[kx][c] exp(i kx x dx)).
+template <typename S>
+__global__ void k_force_lines(Geom g, const Mode3* __restrict__ modes, int nmodes, const double2* __restrict__ fhat,
+                              int K, vec2_t<S>* B) {
+  const long long ln = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long lines = (long long)g.n[2] * g.n[1];
+  if (ln >= lines) return;
+  const int z = (int)(ln / g.n[1]), y = (int)(ln - (long long)z * g.n[1]);
+  const double dy = 2.0 * M_PI / g.n[1], dz = 2.0 * M_PI / g.n[2];
+  double br[kMaxKf + 1][3], bi[kMaxKf + 1][3];
+  for (int kx = 0; kx <= K; ++kx)
+    for (int c = 0; c < 3; ++c) br[kx][c] = bi[kx][c] = 0.0;
+  for (int m = 0; m < nmodes; ++m) {
+    const Mode3 md = modes[m];
+    double sn, cs;
+    sincos(md.ky * y * dy + md.kz * z * dz, &sn, &cs);
+    for (int c = 0; c < 3; ++c) {
+      const double2 f = fhat[m * 3 + c];
+      br[md.kx][c] += 2.0 * (f.x * cs - f.y * sn);
+      bi[md.kx][c] += 2.0 * (f.x * sn + f.y * cs);
+    }
+  }
+  for (int kx = 0; kx <= K; ++kx)
+    for (int c = 0; c < 3; ++c) {
+      vec2_t<S> v;
+      v.x = (S)br[kx][c];
+      v.y = (S)bi[kx][c];
+      B[((long long)kx * 3 + c) * lines + ln] = v;
+    }
+}
+
+template <typename S>
+__global__ void k_force_xtab(int n0, int K, vec2_t<S>* X) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (K + 1) * n0) return;
+  const int kx = i / n0, x = i - kx * n0;
+  double sn, cs;
+  sincos(kx * x * (2.0 * M_PI / n0), &sn, &cs);
+  vec2_t<S> v;
+  v.x = (S)cs;
+  v.y = (S)sn;
+  X[i] = v;
+}
+
+inline unsigned nblk(long long n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
+
+const char* const kKernelNames[] = {"delay_map", "prim", "ghost", "grad", "force_lines",
+                                    "main", "stats_final", "force_advance"};
+enum { KD_DELAY, KD_PRIM, KD_GHOST, KD_GRAD, KD_FLINES, KD_MAIN, KD_STATS, KD_FADV, KD_COUNT };
+
+// Event pair around one launch when profiling is on.
+struct Timed {
+  at_dns* h;
+  int kind;
+  cudaEvent_t b = nullptr;
+  Timed(at_dns* h_, int k) : h(h_), kind(k) {
+    if (!h->prof) return;
+    cudaEvent_t a;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, h->st);
+    h->recs.push_back({kind, a, b});
+  }
+  ~Timed() {
+    if (h->prof && b) cudaEventRecord(b, h->st);
+  }
+};
+
+int fail(at_dns* h, int code, const std::string& msg) {
+  h->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(h, AT_DNS_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int dev_alloc(at_dns* h, void** p, size_t bytes) {
+  if (bytes == 0) { *p = nullptr; return AT_DNS_OK; }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    (void)cudaGetLastError();
+    return fail(h, AT_DNS_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  h->bytes += bytes;
+  return AT_DNS_OK;
+}
+
+double key_to_double(unsigned long long k) {
+  long long b = (long long)k;
+  b ^= (b >> 63) & 0x7FFFFFFFFFFFFFFFLL;
+  double v;
+  std::memcpy(&v, &b, 8);
+  return v;
+}
+
+std::vector<Mode3> forcing_modes(double kf) {
+  std::vector<Mode3> out;
+  const int K = (int)std::floor(kf);
+  for (int kz = -K; kz <= K; ++kz)
+    for (int ky = -K; ky <= K; ++ky)
+      for (int kx = -K; kx <= K; ++kx) {
+        const int k2 = kx * kx + ky * ky + kz * kz;
+        if (k2 == 0 || k2 > kf * kf + 1e-12) continue;
+        if (kx > 0 || (kx == 0 && ky > 0) || (kx == 0 && ky == 0 && kz > 0)) out.push_back({kx, ky, kz});
+      }
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// typed operations
+template <typename S>
+struct Ops {
+  static S* U(at_dns* h, int i) { return (S*)h->U[i]; }
+
+  static int upload_field(at_dns* h, const double* src, int where, S* dst) {
+    const long long cnt = 5 * h->g.npts;
+    const double* dsrc = src;
+    if (where == AT_DNS_HOST) {
+      CK(cudaMemcpyAsync(h->stage, src, cnt * sizeof(double), cudaMemcpyHostToDevice, h->st));
+      dsrc = h->stage;
+    }
+    if (sizeof(S) == sizeof(double)) {
+      if ((const void*)dsrc != (const void*)dst)
+        CK(cudaMemcpyAsync(dst, dsrc, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    } else {
+      k_from_double<S><<<nblk(cnt), kBlock, 0, h->st>>>(dsrc, dst, cnt);
+      CK(cudaGetLastError());
+    }
+    return AT_DNS_OK;
+  }
+
+  static int ring_store(at_dns* h, const S* field, int slot) {
+    bool any = h->g.pes[0] > 1 || h->g.pes[1] > 1 || h->g.pes[2] > 1;
+    if (!any) return AT_DNS_OK;
+    k_ring_store<S><<<nblk(h->g.npts), kBlock, 0, h->st>>>(h->g, field, (S*)h->ring[0], (S*)h->ring[1],
+                                                         (S*)h->ring[2], slot);
+    CK(cudaGetLastError());
+    return AT_DNS_OK;
+  }
+
+  static int download(at_dns* h, double* out, int where) {
+    const long long cnt = 5 * h->g.npts;
+    double* dst = where == AT_DNS_DEVICE ? out : h->stage;
+    if (sizeof(S) == sizeof(double)) {
+      CK(cudaMemcpyAsync(dst, U(h, h->cur), cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    } else {
+      k_to_double<S><<<nblk(cnt), kBlock, 0, h->st>>>(U(h, h->cur), dst, cnt);
+      CK(cudaGetLastError());
+    }
+    if (where == AT_DNS_HOST) {
+      CK(cudaMemcpyAsync(out, h->stage, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+    }
+    return AT_DNS_OK;
+  }
+
+  // One RHS evaluation at level n; update (step) or write R to Rout.
+  static int evaluate(at_dns* h, int mode, bool update, double* Rout, bool stats, bool reset_health) {
+    const Geom& g = h->g;
+    const int P = g.pes[0] * g.pes[1] * g.pes[2];
+    const uint64_t seed = h->cfg.seed;
+    {
+      Timed t(h, KD_DELAY);
+      k_delay_map<<<nblk(P * 6), kBlock, 0, h->st>>>(h->dmap, P, g.pes[0], g.pes[1], h->n, mode, h->cfg.max_delay,
+                                                    h->cfg.comm_period, (uint32_t)seed, (uint32_t)(seed >> 32));
+    }
+    CK(cudaGetLastError());
+    S* Ucur = U(h, h->cur);
+    S* GH[3] = {(S*)h->GH[0], (S*)h->GH[1], (S*)h->GH[2]};
+    S* ring[3] = {(S*)h->ring[0], (S*)h->ring[1], (S*)h->ring[2]};
+    { Timed t(h, KD_PRIM); CK(launch_prim<S>(g, h->ph, Ucur, (S*)h->PQ, h->st)); }
+    if (g.pes[0] > 1 || g.pes[1] > 1 || g.pes[2] > 1) {
+      Timed t(h, KD_GHOST);
+      CK(launch_ghost<S>(g, h->ph, Ucur, (S*)h->PQ, GH, ring, h->dmap, h->n, h->st));
+    }
+    { Timed t(h, KD_GRAD); CK(launch_grad<S>(g, (S*)h->PQ, GH, (S*)h->G, h->st)); }
+    if (h->cfg.forcing) {
+      const long long lines = (long long)g.n[2] * g.n[1];
+      {
+        Timed t(h, KD_FLINES);
+        k_force_lines<S><<<nblk(lines, 128), 128, 0, h->st>>>(g, h->modes, h->nmodes, h->fhat, h->fK,
+                                                              (vec2_t<S>*)h->fB);
+      }
+      CK(cudaGetLastError());
+    }
+    k_reset_words<<<1, 1, 0, h->st>>>(h->words, reset_health ? 1 : 0);
+    CK(cudaGetLastError());
+    StepArgs<S> a{};
+    a.U = Ucur;
+    a.Unext = U(h, 1 - h->cur);
+    a.PQ = (S*)h->PQ;
+    a.G = (S*)h->G;
+    for (int d = 0; d < 3; ++d) { a.GH[d] = GH[d]; a.ring[d] = ring[d]; }
+    a.Rprev = (S*)h->Rprev;
+    a.Rout = Rout;
+    a.partial = h->partial;
+    a.words = h->words;
+    a.fB = h->cfg.forcing ? (const vec2_t<S>*)h->fB : nullptr;
+    a.fX = (const vec2_t<S>*)h->fX;
+    a.fK = h->fK;
+    a.n = h->n;
+    a.dt = h->dt;
+    a.first = h->first ? 1 : 0;
+    a.do_update = update ? 1 : 0;
+    a.do_stats = stats ? 1 : 0;
+    { Timed t(h, KD_MAIN); CK(launch_main<S>(g, h->ph, a, h->st)); }
+    if (stats) {
+      { Timed t(h, KD_STATS); k_stats_final<<<kNumStat, 256, 0, h->st>>>(h->partial, main_blocks(g), h->sums); }
+      CK(cudaGetLastError());
+      h->stats_valid = true;
+      h->stats_step = h->n;
+      h->stats_time = h->t;
+    }
+    if (update) {
+      h->cur = 1 - h->cur;
+      h->first = false;
+      h->n += 1;
+      h->t += h->dt;
+      if (h->cfg.forcing) {
+        const double a_ = std::exp(-h->dt / h->cfg.f_tcorr);
+        const double b_ = h->cfg.f_amp * std::sqrt(1.0 - a_ * a_);
+        {
+          Timed t(h, KD_FADV);
+          k_force_advance<<<nblk(h->nmodes, 64), 64, 0, h->st>>>(h->modes, h->nmodes, h->fhat, h->n, h->n, a_, b_,
+                                                                h->cfg.f_amp, (uint32_t)h->cfg.f_seed,
+                                                                (uint32_t)(h->cfg.f_seed >> 32));
+        }
+        CK(cudaGetLastError());
+      }
+    }
+    return AT_DNS_OK;
+  }
+
+  static int xtab(at_dns* h) {
+    const int cnt = (h->fK + 1) * h->g.n[0];
+    k_force_xtab<S><<<nblk(cnt), kBlock, 0, h->st>>>(h->g.n[0], h->fK, (vec2_t<S>*)h->fX);
+    CK(cudaGetLastError());
+    return AT_DNS_OK;
+  }
+};
+
+int force_reset(at_dns* h, long long step) {
+  if (!h->cfg.forcing) return AT_DNS_OK;
+  const double a_ = std::exp(-h->dt / h->cfg.f_tcorr);
+  const double b_ = h->cfg.f_amp * std::sqrt(1.0 - a_ * a_);
+  k_force_advance<<<nblk(h->nmodes, 64), 64, 0, h->st>>>(h->modes, h->nmodes, h->fhat, 0, step, a_, b_,
+                                                        h->cfg.f_amp, (uint32_t)h->cfg.f_seed,
+                                                        (uint32_t)(h->cfg.f_seed >> 32));
+  CK(cudaGetLastError());
+  return AT_DNS_OK;
+}
+
+int set_dt(at_dns* h) {
+  if (h->cfg.dt > 0) { h->dt = h->cfg.dt; return AT_DNS_OK; }
+  k_reset_words<<<1, 1, 0, h->st>>>(h->words, 1);
+  CK(cudaGetLastError());
+  k_wave<<<nblk(h->g.npts), kBlock, 0, h->st>>>(h->g, h->ph, h->stage, h->words);
+  CK(cudaGetLastError());
+  unsigned long long w = 0;
+  CK(cudaMemcpyAsync(&w, h->words, sizeof(w), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const double s = key_to_double(w);
+  if (!(s > 0) || !std::isfinite(s)) return fail(h, AT_DNS_E_INVALID_ARG, "state has no finite positive wave speed");
+  h->dt = h->cfg.cfl / s;
+  return AT_DNS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int at_dns_config_default(at_dns_config_t* c) {
+  if (!c) return AT_DNS_E_INVALID_ARG;
+  std::memset(c, 0, sizeof(*c));
+  for (int d = 0; d < 3; ++d) { c->n[d] = 32; c->pes[d] = 1; }
+  c->gamma = 1.4;
+  c->prandtl = 0.7;
+  c->mu0 = 0.01;
+  c->visc_exp = 0.76;
+  c->dt = 0.0;
+  c->cfl = 0.5;
+  c->max_delay = 2;
+  c->comm_period = 3;
+  c->seed = 0;
+  c->forcing = 0;
+  c->kf = 2.0;
+  c->f_amp = 0.0;
+  c->f_tcorr = 1.0;
+  c->f_seed = 0;
+  c->precision = AT_DNS_P64;
+  c->stats_every = 1;
+  c->stream = nullptr;
+  return AT_DNS_OK;
+}
+
+static int create_fail(at_dns* h, int code) {
+  g_create_error = h->err;
+  at_dns_destroy(h);
+  return code;
+}
+
+int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
+  if (!cfg || !out) { g_create_error = "NULL argument"; return AT_DNS_E_INVALID_ARG; }
+  *out = nullptr;
+  const at_dns_config_t& c = *cfg;
+  std::string bad;
+  for (int d = 0; d < 3 && bad.empty(); ++d) {
+    if (c.n[d] < 5 || c.n[d] > 32768) bad = "n[d] must be in [5, 32768]";
+    else if (c.pes[d] < 1 || c.n[d] % c.pes[d] != 0) bad = "pes[d] must divide n[d]";
+    else if (c.pes[d] > 1 && c.n[d] / c.pes[d] < 5) bad = "n[d]/pes[d] must be >= 5 when pes[d] > 1";
+  }
+  if (bad.empty()) {
+    if (!(c.gamma > 1.0)) bad = "gamma must be > 1";
+    else if (!(c.prandtl > 0)) bad = "prandtl must be > 0";
+    else if (!(c.mu0 >= 0)) bad = "mu0 must be >= 0";
+    else if (c.max_delay < 0 || c.max_delay > 64) bad = "max_delay must be in [0, 64]";
+    else if (c.comm_period < 1) bad = "comm_period must be >= 1";
+    else if (c.precision != AT_DNS_P64 && c.precision != AT_DNS_P32) bad = "unknown precision";
+    else if (!(c.dt > 0) && !(c.cfl > 0)) bad = "need dt > 0 or cfl > 0";
+    else if (c.forcing && (!(c.kf >= 1.0) || c.kf > kMaxKf)) bad = "kf must be in [1, 4]";
+    else if (c.forcing && !(c.f_tcorr > 0)) bad = "f_tcorr must be > 0";
+    else if (c.stats_every != 0 && c.stats_every != 1) bad = "stats_every must be 0 or 1";
+  }
+  if (!bad.empty()) { g_create_error = bad; return AT_DNS_E_INVALID_ARG; }
+
+  at_dns* h = new at_dns();
+  h->cfg = c;
+  h->st = (cudaStream_t)c.stream;
+  h->p64 = c.precision == AT_DNS_P64;
+  h->ssize = h->p64 ? 8 : 4;
+  Geom& g = h->g;
+  g.npts = 1;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = c.n[d];
+    g.pes[d] = c.pes[d];
+    g.nl[d] = c.n[d] / c.pes[d];
+    g.npts *= c.n[d];
+  }
+  g.stride[0] = 1;
+  g.stride[1] = g.n[0];
+  g.stride[2] = (long long)g.n[0] * g.n[1];
+  for (int d = 0; d < 3; ++d) {
+    g.plane[d] = g.npts / g.n[d];
+    const double dx = 2.0 * M_PI / g.n[d];
+    g.c1[d] = 8.0 / (12.0 * dx);
+    g.c2[d] = -1.0 / (12.0 * dx);
+    g.a0[d] = -30.0 / (12.0 * dx * dx);
+    g.a1[d] = 16.0 / (12.0 * dx * dx);
+    g.a2[d] = -1.0 / (12.0 * dx * dx);
+    g.inv12dx[d] = 1.0 / (12.0 * dx);
+  }
+  g.nlev = c.max_delay + 3;
+  Phys& ph = h->ph;
+  ph.gamma = c.gamma;
+  ph.gm1 = c.gamma - 1.0;
+  ph.prandtl = c.prandtl;
+  ph.mu0 = c.mu0;
+  ph.omega = c.visc_exp;
+  ph.cp_over_pr = 1.0 / ((c.gamma - 1.0) * c.prandtl);
+
+  const size_t S = h->ssize;
+  const size_t N = (size_t)g.npts;
+  int rc;
+  if ((rc = dev_alloc(h, &h->U[0], 5 * N * S)) || (rc = dev_alloc(h, &h->U[1], 5 * N * S)) ||
+      (rc = dev_alloc(h, &h->PQ, (size_t)kNumQ * N * S)) || (rc = dev_alloc(h, &h->G, (size_t)kNumGrad * N * S)) ||
+      (rc = dev_alloc(h, &h->Rprev, 5 * N * S)) || (rc = dev_alloc(h, (void**)&h->stage, 5 * N * sizeof(double))))
+    return create_fail(h, rc);
+  for (int d = 0; d < 3; ++d) {
+    if (g.pes[d] == 1) continue;
+    const size_t gpts = 4ull * g.pes[d] * (size_t)g.plane[d];
+    if ((rc = dev_alloc(h, &h->GH[d], (size_t)kNumGhostQ * gpts * S)) ||
+        (rc = dev_alloc(h, &h->ring[d], (size_t)g.nlev * 5 * gpts * S)))
+      return create_fail(h, rc);
+  }
+  const int P = g.pes[0] * g.pes[1] * g.pes[2];
+  if ((rc = dev_alloc(h, (void**)&h->dmap, (size_t)P * 6)) ||
+      (rc = dev_alloc(h, (void**)&h->partial, (size_t)main_blocks(g) * kNumStat * sizeof(double))) ||
+      (rc = dev_alloc(h, (void**)&h->sums, kNumStat * sizeof(double))) ||
+      (rc = dev_alloc(h, (void**)&h->words, 4 * sizeof(unsigned long long))))
+    return create_fail(h, rc);
+  // forcing tables (allocated even without forcing: the x-table is tiny)
+  std::vector<Mode3> modes = forcing_modes(c.forcing ? c.kf : 1.0);
+  h->nmodes = c.forcing ? (int)modes.size() : 0;
+  h->fK = c.forcing ? (int)std::floor(c.kf) : 0;
+  const size_t lines = (size_t)g.n[2] * g.n[1];
+  const size_t v2 = 2 * S;
+  if ((rc = dev_alloc(h, &h->fX, (size_t)(h->fK + 1) * g.n[0] * v2))) return create_fail(h, rc);
+  if (c.forcing) {
+    if ((rc = dev_alloc(h, (void**)&h->modes, modes.size() * sizeof(Mode3))) ||
+        (rc = dev_alloc(h, (void**)&h->fhat, modes.size() * 3 * sizeof(double2))) ||
+        (rc = dev_alloc(h, &h->fB, (size_t)(h->fK + 1) * 3 * lines * v2)))
+      return create_fail(h, rc);
+    if (cudaMemcpy(h->modes, modes.data(), modes.size() * sizeof(Mode3), cudaMemcpyHostToDevice) != cudaSuccess)
+      { h->err = "copy of forcing modes failed"; return create_fail(h, AT_DNS_E_CUDA); }
+  }
+  rc = h->p64 ? Ops<double>::xtab(h) : Ops<float>::xtab(h);
+  if (rc) return create_fail(h, rc);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) { h->err = "initialisation failed"; return create_fail(h, AT_DNS_E_CUDA); }
+  *out = h;
+  return AT_DNS_OK;
+}
+
+int at_dns_set_history(at_dns_t* h, const double* levels, int32_t nlevels, int64_t step, int where) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  if (!levels) return fail(h, AT_DNS_E_INVALID_ARG, "levels is NULL");
+  if (where != AT_DNS_HOST && where != AT_DNS_DEVICE) return fail(h, AT_DNS_E_INVALID_ARG, "bad where");
+  if (nlevels < 1 || nlevels > h->g.nlev) return fail(h, AT_DNS_E_INVALID_ARG, "nlevels must be in [1, L+3]");
+  if (step < 0) return fail(h, AT_DNS_E_INVALID_ARG, "step must be >= 0");
+  const long long cnt = 5 * h->g.npts;
+  int rc;
+  // older levels first so that U[cur] ends up holding U^step; each given level
+  // is uploaded once and stored into its ring slot (the oldest one also into
+  // the slots of the older levels that were not given)
+  for (int l = nlevels - 1; l >= 0; --l) {
+    const double* lv = levels + (size_t)l * cnt;
+    const int last = l == nlevels - 1 ? h->g.nlev - 1 : l;
+    if (h->p64) {
+      if ((rc = Ops<double>::upload_field(h, lv, where, Ops<double>::U(h, h->cur)))) return rc;
+    } else {
+      if ((rc = Ops<float>::upload_field(h, lv, where, Ops<float>::U(h, h->cur)))) return rc;
+    }
+    for (int ll = l; ll <= last; ++ll) {
+      const int slot = (int)(((step - ll) % h->g.nlev + h->g.nlev) % h->g.nlev);
+      rc = h->p64 ? Ops<double>::ring_store(h, Ops<double>::U(h, h->cur), slot)
+                  : Ops<float>::ring_store(h, Ops<float>::U(h, h->cur), slot);
+      if (rc) return rc;
+    }
+  }
+  // stage holds U^step in FP64 now (host path) -- ensure it for the dt reduction
+  if (where == AT_DNS_DEVICE) CK(cudaMemcpyAsync(h->stage, levels, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  if (!(h->has_state && h->dt > 0) || step == 0) {
+    if ((rc = set_dt(h))) return rc;
+  }
+  h->n = step;
+  h->t = step * h->dt;
+  h->first = true;
+  h->has_state = true;
+  h->stats_valid = false;
+  if ((rc = force_reset(h, step))) return rc;
+  CK(cudaStreamSynchronize(h->st));
+  return AT_DNS_OK;
+}
+
+int at_dns_set_state(at_dns_t* h, const double* u, int where) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->has_state = false;
+  return at_dns_set_history(h, u, 1, 0, where);
+}
+
+int at_dns_get_state(at_dns_t* h, double* u_out, int where) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  if (!u_out) return fail(h, AT_DNS_E_INVALID_ARG, "u_out is NULL");
+  if (where != AT_DNS_HOST && where != AT_DNS_DEVICE) return fail(h, AT_DNS_E_INVALID_ARG, "bad where");
+  if (!h->has_state) return fail(h, AT_DNS_E_STATE, "no state set");
+  return h->p64 ? Ops<double>::download(h, u_out, where) : Ops<float>::download(h, u_out, where);
+}
+
+static int check_mode(at_dns* h, int mode) {
+  if (mode != AT_DNS_SYNC && mode != AT_DNS_PERIODIC && mode != AT_DNS_RANDOM)
+    return fail(h, AT_DNS_E_INVALID_ARG, "unknown delay mode");
+  if (mode == AT_DNS_PERIODIC && h->cfg.comm_period - 1 > h->cfg.max_delay)
+    return fail(h, AT_DNS_E_INVALID_ARG, "periodic delays need comm_period - 1 <= max_delay");
+  return AT_DNS_OK;
+}
+
+int at_dns_rhs(at_dns_t* h, int32_t delay_mode, double* rhs_out, int where) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  int rc;
+  if ((rc = check_mode(h, delay_mode))) return rc;
+  if (!rhs_out) return fail(h, AT_DNS_E_INVALID_ARG, "rhs_out is NULL");
+  if (where != AT_DNS_HOST && where != AT_DNS_DEVICE) return fail(h, AT_DNS_E_INVALID_ARG, "bad where");
+  if (!h->has_state) return fail(h, AT_DNS_E_STATE, "no state set");
+  double* dst = where == AT_DNS_DEVICE ? rhs_out : h->stage;
+  rc = h->p64 ? Ops<double>::evaluate(h, delay_mode, false, dst, true, true)
+              : Ops<float>::evaluate(h, delay_mode, false, dst, true, true);
+  if (rc) return rc;
+  if (where == AT_DNS_HOST)
+    CK(cudaMemcpyAsync(rhs_out, h->stage, 5 * h->g.npts * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return AT_DNS_OK;
+}
+
+int at_dns_step(at_dns_t* h, int32_t nsteps, int32_t delay_mode) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  int rc;
+  if ((rc = check_mode(h, delay_mode))) return rc;
+  if (nsteps < 0) return fail(h, AT_DNS_E_INVALID_ARG, "nsteps must be >= 0");
+  if (!h->has_state) return fail(h, AT_DNS_E_STATE, "no state set");
+  const bool stats = h->cfg.stats_every == 1;
+  for (int s = 0; s < nsteps; ++s) {
+    rc = h->p64 ? Ops<double>::evaluate(h, delay_mode, true, nullptr, stats, s == 0)
+                : Ops<float>::evaluate(h, delay_mode, true, nullptr, stats, s == 0);
+    if (rc) return rc;
+  }
+  if (!stats) h->stats_valid = false;
+  if (nsteps > 0) {
+    unsigned long long w = 0;
+    CK(cudaMemcpyAsync(&w, h->words + 3, sizeof(w), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (w) return fail(h, AT_DNS_E_UNSTABLE, "non-finite value, rho <= 0 or p <= 0 in the last step (flags " +
+                                                 std::to_string(w) + ")");
+  }
+  return AT_DNS_OK;
+}
+
+int at_dns_stats(at_dns_t* h, at_dns_stats_t* out) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  if (!out) return fail(h, AT_DNS_E_INVALID_ARG, "out is NULL");
+  if (!h->has_state) return fail(h, AT_DNS_E_STATE, "no state set");
+  int rc;
+  if (!h->stats_valid) {
+    rc = h->p64 ? Ops<double>::evaluate(h, AT_DNS_SYNC, false, nullptr, true, true)
+                : Ops<float>::evaluate(h, AT_DNS_SYNC, false, nullptr, true, true);
+    if (rc) return rc;
+  }
+  double s[kNumStat];
+  unsigned long long w[4];
+  CK(cudaMemcpyAsync(s, h->sums, sizeof(s), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(w, h->words, sizeof(w), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const double N = (double)h->g.npts;
+  std::memset(out, 0, sizeof(*out));
+  out->step = h->stats_step;
+  out->time = h->stats_time;
+  out->dt = h->dt;
+  out->mass = s[ST_RHO] / N;
+  out->mom[0] = s[ST_M0] / N;
+  out->mom[1] = s[ST_M1] / N;
+  out->mom[2] = s[ST_M2] / N;
+  out->energy = s[ST_E] / N;
+  out->tke = s[ST_KE] / N;
+  out->dissipation = s[ST_SIGS] / N;
+  out->grad_m2 = s[ST_G2] / (3 * N);
+  out->grad_m3 = s[ST_G3] / (3 * N);
+  out->grad_m4 = s[ST_G4] / (3 * N);
+  out->skewness = out->grad_m3 / std::pow(out->grad_m2, 1.5);
+  out->flatness = out->grad_m4 / (out->grad_m2 * out->grad_m2);
+  out->enstrophy = s[ST_ENST] / N;
+  out->pressure_dilatation = s[ST_PTHETA] / N;
+  out->forcing_power = s[ST_FPOW] / N;
+  out->urms = std::sqrt(s[ST_U2] / N / 3.0);
+  out->mach_t = std::sqrt(s[ST_U2] / N) / (s[ST_C] / N);
+  out->max_wave_speed = key_to_double(w[0]);
+  out->min_rho = key_to_double(w[1]);
+  out->min_p = key_to_double(w[2]);
+  out->unstable = (int32_t)w[3];
+  return AT_DNS_OK;
+}
+
+int at_dns_get_delay_map(at_dns_t* h, int64_t step, int32_t mode, uint8_t* out) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  int rc;
+  if ((rc = check_mode(h, mode))) return rc;
+  if (!out) return fail(h, AT_DNS_E_INVALID_ARG, "out is NULL");
+  if (step < 0) return fail(h, AT_DNS_E_INVALID_ARG, "step must be >= 0");
+  const Geom& g = h->g;
+  const int P = g.pes[0] * g.pes[1] * g.pes[2];
+  uint8_t* tmp = nullptr;
+  if ((rc = dev_alloc(h, (void**)&tmp, (size_t)P * 6))) return rc;
+  k_delay_map<<<nblk(P * 6), kBlock, 0, h->st>>>(tmp, P, g.pes[0], g.pes[1], step, mode, h->cfg.max_delay,
+                                                h->cfg.comm_period, (uint32_t)h->cfg.seed,
+                                                (uint32_t)(h->cfg.seed >> 32));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, (size_t)P * 6, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  cudaFree(tmp);
+  h->bytes -= (size_t)P * 6;
+  if (e != cudaSuccess) return fail(h, AT_DNS_E_CUDA, std::string("delay map: ") + cudaGetErrorString(e));
+  return AT_DNS_OK;
+}
+
+int at_dns_get_info(at_dns_t* h, at_dns_info_t* out) {
+  if (!h || !out) return AT_DNS_E_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->step = h->n;
+  out->time = h->t;
+  out->dt = h->dt;
+  out->n_levels = h->g.nlev;
+  long long nt = 1, ni = 1;
+  for (int d = 0; d < 3; ++d) { nt *= h->g.nl[d]; ni *= (h->g.nl[d] - 4); }
+  out->boundary_fraction = (double)(nt - ni) / (double)nt;
+  out->device_bytes = h->bytes;
+  const bool ghost = h->g.pes[0] > 1 || h->g.pes[1] > 1 || h->g.pes[2] > 1;
+  out->kernels_per_step = 5 + (ghost ? 1 : 0) + (h->cfg.stats_every ? 1 : 0) + (h->cfg.forcing ? 2 : 0);
+  return AT_DNS_OK;
+}
+
+static void clear_recs(at_dns* h) {
+  for (auto& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  h->recs.clear();
+}
+
+int at_dns_profile(at_dns_t* h, int32_t enable) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  if (enable) {
+    cudaStreamSynchronize(h->st);
+    clear_recs(h);
+  }
+  h->prof = enable != 0;
+  return AT_DNS_OK;
+}
+
+int at_dns_kernel_times(at_dns_t* h, at_dns_kernel_time_t* out, int32_t max, int32_t* count) {
+  if (!h || !out || !count || max < 0) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  CK(cudaStreamSynchronize(h->st));
+  long long n[KD_COUNT] = {0};
+  double ms[KD_COUNT] = {0};
+  for (auto& r : h->recs) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    n[r.kind] += 1;
+    ms[r.kind] += t;
+  }
+  int c = 0;
+  for (int k = 0; k < KD_COUNT; ++k) {
+    if (!n[k]) continue;
+    if (c < max) {
+      std::memset(&out[c], 0, sizeof(out[c]));
+      std::strncpy(out[c].name, kKernelNames[k], sizeof(out[c].name) - 1);
+      out[c].launches = n[k];
+      out[c].total_ms = ms[k];
+    }
+    ++c;
+  }
+  *count = c < max ? c : max;
+  return AT_DNS_OK;
+}
+
+int at_dns_synchronize(at_dns_t* h) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  CK(cudaStreamSynchronize(h->st));
+  return AT_DNS_OK;
+}
+
+const char* at_dns_last_error(const at_dns_t* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+void at_dns_destroy(at_dns_t* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+  void* ptrs[] = {h->U[0], h->U[1], h->PQ, h->G, h->Rprev, h->GH[0], h->GH[1], h->GH[2], h->ring[0], h->ring[1],
+                  h->ring[2], h->stage, h->dmap, h->partial, h->sums, h->words, h->modes, h->fhat, h->fB, h->fX};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  clear_recs(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Device-side definitions shared by the AT-DNS kernels (sm_103a).
+//
+// Geometry of the periodic (2 pi)^3 grid cut into virtual PEs (Sec. 3,
+// Eqs. (NT)-(NB)), the 4th-order stencil coefficients (zero-delay rows of
+// Table B, Appendix B), the Table B AT time weights and the Philox4x32-10
+// generator that stands in for the network delays of Algorithm 1.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace atdns {
+
+constexpr int kNumQ = 16;        // per-point derived fields: u, v, w, T, 12 fluxes
+constexpr int kNumGhostQ = 9;    // per ghost point: 5 fluxes of the direction, u, v, w, T
+constexpr int kNumGrad = 12;     // du_i/dx_j (i-major) then dT/dx_j
+constexpr int kNumStat = 15;     // summed statistics per block
+constexpr int kMaxModes = 128;   // forcing modes of the half set for kf <= 4
+constexpr int kMaxKf = 4;
+
+// Indices of the summed statistics.
+enum StatIdx {
+  ST_RHO = 0, ST_M0, ST_M1, ST_M2, ST_E, ST_KE, ST_SIGS, ST_G2, ST_G3, ST_G4,
+  ST_ENST, ST_PTHETA, ST_FPOW, ST_U2, ST_C
+};
+
+// Health bits.
+enum HealthBits { H_NONFINITE = 1, H_RHO = 2, H_P = 4 };
+
+struct Geom {
+  int n[3];          // points per direction
+  int pes[3];        // PEs per direction
+  int nl[3];         // points per PE per direction
+  long long npts;    // n0 n1 n2
+  long long plane[3];// points of a plane normal to d: npts / n[d]
+  long long stride[3];  // linear-index stride of direction d: 1, n0, n0 n1
+  int nlev;          // ring levels L + 3
+  // stencil coefficients with the 1/(12 dx) and 1/(12 dx^2) folded in
+  double c1[3], c2[3];        // D1 = c1 (f[+1]-f[-1]) + c2 (f[+2]-f[-2])
+  double a0[3], a1[3], a2[3]; // D2 = a0 f + a1 (f[+1]+f[-1]) + a2 (f[+2]+f[-2])
+  double inv12dx[3];          // 1/(12 dx) for the one-sided stencils
+};
+
+struct Phys {
+  double gamma, gm1, prandtl, mu0, omega, cp_over_pr;
+};
+
+// Linear index -> (x, y, z).
+__device__ __forceinline__ void decode(const Geom& g, long long idx, int& x, int& y, int& z) {
+  long long t = idx / g.n[0];
+  x = (int)(idx - t * g.n[0]);
+  z = (int)(t / g.n[1]);
+  y = (int)(t - (long long)z * g.n[1]);
+}
+
+// Index of the point within the plane normal to d.
+__device__ __forceinline__ long long plane_index(const Geom& g, int d, int x, int y, int z) {
+  if (d == 0) return (long long)z * g.n[1] + y;
+  if (d == 1) return (long long)z * g.n[0] + x;
+  return (long long)y * g.n[0] + x;
+}
+
+__device__ __forceinline__ int pe_number(const Geom& g, int x, int y, int z) {
+  return ((z / g.nl[2]) * g.pes[1] + (y / g.nl[1])) * g.pes[0] + (x / g.nl[0]);
+}
+
+// Table B (T_l = 3) weights of levels n-k, n-k-1, n-k-2:
+// (k^2+3k+2)/2, -(k^2+2k), (k^2+k)/2 -- integers for integer k.
+__device__ __forceinline__ void at_weights(int k, int& w0, int& w1, int& w2) {
+  w0 = ((k + 1) * (k + 2)) / 2;
+  w1 = -(k * (k + 2));
+  w2 = (k * (k + 1)) / 2;
+}
+
+// Philox4x32-10 (Salmon et al., SC'11): counter c, key k, ten rounds, key
+// bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+constexpr uint32_t kDelayTag = 0x4154u;
+constexpr uint32_t kForceTag = 0x464Fu;
+
+// Delay of face f of PE p at step n (Sec. 3.1, Algorithms 1 and 2).
+__device__ __forceinline__ int delay_of(int mode, long long n, int p, int f, int L, int cr,
+                                        uint32_t k0, uint32_t k1) {
+  const long long n0 = L + 3;               // synchronous start-up: L + T_l steps
+  if (mode == 0 || n < n0) return 0;
+  if (mode == 1) return (int)((n - n0) % cr);
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)n, (uint32_t)p, (uint32_t)f, kDelayTag), k0, k1);
+  return (int)(((unsigned long long)w.x * (unsigned long long)(L + 1)) >> 32);
+}
+
+// Order-preserving map of a double to a signed 64-bit key (for atomic min/max).
+__device__ __forceinline__ long long ordered_key(double v) {
+  long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+
+__device__ __forceinline__ bool nonfinite(double v) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7FF0000000000000ULL) == 0x7FF0000000000000ULL;
+}
+__device__ __forceinline__ bool nonfinite(float v) {
+  return ((unsigned)__float_as_uint(v) & 0x7F800000u) == 0x7F800000u;
+}
+
+template <typename S> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+template <typename S> using vec2_t = typename Vec2<S>::type;
+
+template <typename S>
+struct StepArgs {
+  const S* U;          // [5][npts] level n
+  S* Unext;            // [5][npts] level n+1 (step) -- may be null for rhs-only
+  const S* PQ;         // [16][npts]
+  const S* G;          // [12][npts]
+  const S* GH[3];      // [9][4 P_d][plane_d] per direction
+  S* Rprev;            // [5][npts] R^{n-1} in, R^n out
+  S* ring[3];          // [nlev][5][4 P_d][plane_d]
+  double* Rout;        // rhs-only output [5][npts] or null
+  double* partial;     // [gridDim.x][kNumStat]
+  unsigned long long* words;  // [0] max wave key, [1] min rho key, [2] min p key, [3] health
+  const vec2_t<S>* fB; // forcing lines [(K+1)][3][n2][n1] or null
+  const vec2_t<S>* fX; // exp(i kx x) table [(K+1)][n0]
+  int fK;              // max |kx| of the forcing modes
+  long long n;         // step of U
+  double dt;
+  int first;           // 1: forward Euler (no R^{n-1})
+  int do_update;       // 1: write Unext/Rprev/ring; 0: write Rout
+  int do_stats;
+};
+
+}  // namespace atdns

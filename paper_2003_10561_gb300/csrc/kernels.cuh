@@ -1,0 +1,494 @@
+// AT-DNS step kernels, templated on the scalar type S (double for the FP64
+// form, float for the FP32-bulk form).  Every per-point operation -- storage,
+// stencils, AT extrapolation, update and the slab ring of past levels -- is in
+// S; the statistics are summed in S within a warp (32 points) and in FP64 from
+// there on, in a fixed order.
+//
+// One RHS evaluation (Sec. 2) is four launches:
+//   k_prim   per point: u, v, w, T and the 12 non-trivial inviscid fluxes;
+//   k_ghost  per PE-face ghost point (2 layers each side, Sec. 3): the 9
+//            differentiated quantities of that direction at level n (k = 0) or
+//            extrapolated from levels n-k, n-k-1, n-k-2 of the FP64 slab ring
+//            with the Table B weights (Appendix B);
+//   k_grad   per point: AT first derivatives du_i/dx_j and dT/dx_j;
+//   k_main   per point: inviscid flux divergence, second derivatives, mixed
+//            derivatives by the three-step rule (Sec. 2.1), viscous / heat /
+//            forcing assembly, AB2 update (Eq. (time_ab)), ring write of the
+//            new PE-boundary slabs and the FP64 block reductions.
+#pragma once
+#include <climits>
+#include "common.cuh"
+
+namespace atdns {
+
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void __launch_bounds__(256) k_prim(Geom g, Phys ph, const S* __restrict__ U,
+                                              S* __restrict__ PQ) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= g.npts) return;
+  const long long N = g.npts;
+  const S r = U[idx], m0 = U[N + idx], m1 = U[2 * N + idx], m2 = U[3 * N + idx], E = U[4 * N + idx];
+  const S inv = S(1) / r;
+  const S u = m0 * inv, v = m1 * inv, w = m2 * inv;
+  const S p = S(ph.gm1) * (E - S(0.5) * (m0 * u + m1 * v + m2 * w));
+  const S T = S(ph.gamma) * p * inv;
+  const S H = E + p;
+  PQ[0 * N + idx] = u;
+  PQ[1 * N + idx] = v;
+  PQ[2 * N + idx] = w;
+  PQ[3 * N + idx] = T;
+  // flux of direction d, components e = 1..4: rho u_i u_d + p delta_id, (E+p) u_d
+  PQ[4 * N + idx] = m0 * u + p;
+  PQ[5 * N + idx] = m1 * u;
+  PQ[6 * N + idx] = m2 * u;
+  PQ[7 * N + idx] = H * u;
+  PQ[8 * N + idx] = m0 * v;
+  PQ[9 * N + idx] = m1 * v + p;
+  PQ[10 * N + idx] = m2 * v;
+  PQ[11 * N + idx] = H * v;
+  PQ[12 * N + idx] = m0 * w;
+  PQ[13 * N + idx] = m1 * w;
+  PQ[14 * N + idx] = m2 * w + p;
+  PQ[15 * N + idx] = H * w;
+}
+
+// The 9 quantities of direction d from one level of U (same arithmetic as k_prim).
+template <typename S>
+__device__ __forceinline__ void ghost_quantities(const Phys& ph, int d, const S* Uv, S* q) {
+  const S r = Uv[0], inv = S(1) / r;
+  const S vel[3] = {Uv[1] * inv, Uv[2] * inv, Uv[3] * inv};
+  const S p = S(ph.gm1) * (Uv[4] - S(0.5) * (Uv[1] * vel[0] + Uv[2] * vel[1] + Uv[3] * vel[2]));
+  const S T = S(ph.gamma) * p * inv;
+  const S ud = vel[d];
+  q[0] = Uv[1 + d];
+  q[1] = Uv[1] * ud + (d == 0 ? p : S(0));
+  q[2] = Uv[2] * ud + (d == 1 ? p : S(0));
+  q[3] = Uv[3] * ud + (d == 2 ? p : S(0));
+  q[4] = (Uv[4] + p) * ud;
+  q[5] = vel[0];
+  q[6] = vel[1];
+  q[7] = vel[2];
+  q[8] = T;
+}
+
+// ---------------------------------------------------------------------------
+// AT ghost assembly.  Ghost slot s of PE column p_d along d: s = 0, 1 are the
+// local coordinates -2, -1 (left face, face 2d), s = 2, 3 are nl, nl+1 (right
+// face, face 2d+1).  Ring slab index sp = 4 p + t with t = 0, 1 for local 0, 1
+// and t = 2, 3 for local nl-2, nl-1.
+template <typename S>
+__global__ void __launch_bounds__(256) k_ghost(Geom g, Phys ph, const S* __restrict__ U,
+                                               const S* __restrict__ PQ, S* GH0, S* GH1, S* GH2,
+                                               const S* __restrict__ ring0,
+                                               const S* __restrict__ ring1,
+                                               const S* __restrict__ ring2,
+                                               const uint8_t* __restrict__ dmap, long long n,
+                                               long long cnt0, long long cnt1, long long cnt2) {
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int d;
+  if (j < cnt0) d = 0;
+  else if ((j -= cnt0) < cnt1) d = 1;
+  else if ((j -= cnt1) < cnt2) d = 2;
+  else return;
+  S* GH = d == 0 ? GH0 : (d == 1 ? GH1 : GH2);
+  const S* ring = d == 0 ? ring0 : (d == 1 ? ring1 : ring2);
+  const long long plane = g.plane[d];
+  const int gi = (int)(j / plane);
+  const long long pl = j - (long long)gi * plane;
+  const int ped = gi >> 2, slot = gi & 3;
+  const int P = g.pes[d], nl = g.nl[d], nd = g.n[d];
+  int c[3];
+  if (d == 0) { c[2] = (int)(pl / g.n[1]); c[1] = (int)(pl - (long long)c[2] * g.n[1]); }
+  else if (d == 1) { c[2] = (int)(pl / g.n[0]); c[0] = (int)(pl - (long long)c[2] * g.n[0]); }
+  else { c[1] = (int)(pl / g.n[0]); c[0] = (int)(pl - (long long)c[1] * g.n[0]); }
+  int cd = ped * nl + (slot < 2 ? slot - 2 : nl + slot - 2);
+  cd = cd < 0 ? cd + nd : (cd >= nd ? cd - nd : cd);
+  c[d] = ped * nl;   // any coordinate inside the receiving PE
+  const int p = pe_number(g, c[0], c[1], c[2]);
+  const int face = 2 * d + (slot >= 2 ? 1 : 0);
+  const int k = dmap[p * 6 + face];
+  const long long qstride = 4LL * P * plane;
+  S* out = GH + (long long)gi * plane + pl;
+  if (k == 0) {
+    c[d] = cd;
+    const long long src = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
+    const long long N = g.npts;
+    out[0] = U[(1 + d) * N + src];
+#pragma unroll
+    for (int e = 1; e < 5; ++e) out[e * qstride] = PQ[(4 + 4 * d + e - 1) * N + src];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[(5 + q) * qstride] = PQ[q * N + src];
+    return;
+  }
+  const int nbr = slot < 2 ? (ped - 1 + P) % P : (ped + 1) % P;
+  const int sp = 4 * nbr + (slot < 2 ? slot + 2 : slot - 2);
+  int wi[3];
+  at_weights(k, wi[0], wi[1], wi[2]);
+  const S w[3] = {S(wi[0]), S(wi[1]), S(wi[2])};
+  S acc[kNumGhostQ];
+#pragma unroll
+  for (int q = 0; q < kNumGhostQ; ++q) acc[q] = S(0);
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const long long lev = n - k - l;              // >= 1: delays start after L + 3 steps
+    const int rs = (int)(lev % g.nlev);
+    S Uv[5], q[kNumGhostQ];
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+      Uv[v] = ring[(((long long)rs * 5 + v) * 4 * P + sp) * plane + pl];
+    ghost_quantities(ph, d, Uv, q);
+#pragma unroll
+    for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] += w[l] * q[qq];
+  }
+#pragma unroll
+  for (int q = 0; q < kNumGhostQ; ++q) out[q * qstride] = acc[q];
+}
+
+// ---------------------------------------------------------------------------
+// Neighbour fetch along d: the field itself inside the PE (periodic wrap when
+// the direction has one PE), the ghost array across a PE face.
+struct Pt {
+  long long idx;
+  int c[3], li[3], pe[3];
+  long long pl[3];
+};
+
+__device__ __forceinline__ Pt make_point(const Geom& g, long long idx) {
+  Pt P;
+  P.idx = idx;
+  decode(g, idx, P.c[0], P.c[1], P.c[2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    P.pe[d] = P.c[d] / g.nl[d];
+    P.li[d] = P.c[d] - P.pe[d] * g.nl[d];
+    P.pl[d] = plane_index(g, d, P.c[0], P.c[1], P.c[2]);
+  }
+  return P;
+}
+
+template <typename S>
+__device__ __forceinline__ S fetch(const Geom& g, const Pt& P, int d, int off, const S* __restrict__ field,
+                                   const S* __restrict__ gh) {
+  if (g.pes[d] == 1) {
+    int c2 = P.c[d] + off;
+    c2 = c2 < 0 ? c2 + g.n[d] : (c2 >= g.n[d] ? c2 - g.n[d] : c2);
+    return field[P.idx + (long long)(c2 - P.c[d]) * g.stride[d]];
+  }
+  const int l2 = P.li[d] + off;
+  if (l2 >= 0 && l2 < g.nl[d]) return field[P.idx + (long long)off * g.stride[d]];
+  const int slot = l2 < 0 ? l2 + 2 : 2 + (l2 - g.nl[d]);
+  return gh[(long long)(4 * P.pe[d] + slot) * g.plane[d] + P.pl[d]];
+}
+
+template <typename S>
+__device__ __forceinline__ S at_d1(const Geom& g, const Pt& P, int d, const S* field, const S* gh) {
+  const S fm2 = fetch(g, P, d, -2, field, gh), fm1 = fetch(g, P, d, -1, field, gh);
+  const S fp1 = fetch(g, P, d, 1, field, gh), fp2 = fetch(g, P, d, 2, field, gh);
+  return S(g.c1[d]) * (fp1 - fm1) + S(g.c2[d]) * (fp2 - fm2);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_grad(Geom g, const S* __restrict__ PQ, const S* __restrict__ GH0,
+                                              const S* __restrict__ GH1, const S* __restrict__ GH2,
+                                              S* __restrict__ G) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= g.npts) return;
+  const Pt P = make_point(g, idx);
+  const long long N = g.npts;
+  const S* GH[3] = {GH0, GH1, GH2};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const long long qs = 4LL * g.pes[d] * g.plane[d];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const S v = at_d1(g, P, d, PQ + q * N, GH[d] + (5 + q) * qs);
+      const int out = q < 3 ? 3 * q + d : 9 + d;
+      G[out * N + idx] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-derivative helpers (Sec. 2.1).
+__device__ __forceinline__ bool central_fits(const Geom& g, const Pt& P, int d) {
+  return g.pes[d] == 1 || (P.li[d] >= 2 && P.li[d] <= g.nl[d] - 3);
+}
+
+// PE-local 4th-order first derivative of a gradient field in direction a:
+// central where the stencil fits, one-sided at the two points next to a face.
+template <typename S>
+__device__ __forceinline__ S local_d1(const Geom& g, const Pt& P, int a, const S* __restrict__ f) {
+  const long long s = g.stride[a];
+  const long long i = P.idx;
+  if (central_fits(g, P, a)) {
+    if (g.pes[a] == 1) {
+      S fm2, fm1, fp1, fp2;
+      auto at = [&](int off) {
+        int c2 = P.c[a] + off;
+        c2 = c2 < 0 ? c2 + g.n[a] : (c2 >= g.n[a] ? c2 - g.n[a] : c2);
+        return f[i + (long long)(c2 - P.c[a]) * s];
+      };
+      fm2 = at(-2); fm1 = at(-1); fp1 = at(1); fp2 = at(2);
+      return S(g.c1[a]) * (fp1 - fm1) + S(g.c2[a]) * (fp2 - fm2);
+    }
+    return S(g.c1[a]) * (f[i + s] - f[i - s]) + S(g.c2[a]) * (f[i + 2 * s] - f[i - 2 * s]);
+  }
+  const S h = S(g.inv12dx[a]);
+  const int li = P.li[a], nl = g.nl[a];
+  if (li == 0)
+    return h * (S(-25) * f[i] + S(48) * f[i + s] - S(36) * f[i + 2 * s] + S(16) * f[i + 3 * s] - S(3) * f[i + 4 * s]);
+  if (li == 1)
+    return h * (S(-3) * f[i - s] - S(10) * f[i] + S(18) * f[i + s] - S(6) * f[i + 2 * s] + f[i + 3 * s]);
+  if (li == nl - 2)
+    return h * (S(3) * f[i + s] + S(10) * f[i] - S(18) * f[i - s] + S(6) * f[i - 2 * s] - f[i - 3 * s]);
+  return h * (S(25) * f[i] - S(48) * f[i - s] + S(36) * f[i - 2 * s] - S(16) * f[i - 3 * s] + S(3) * f[i - 4 * s]);
+}
+
+// d/dx_a (d f/dx_b) with Gb = AT df/dx_b and Ga = AT df/dx_a.
+template <typename S>
+__device__ __forceinline__ S mixed(const Geom& g, const Pt& P, int a, int b, const S* Gb, const S* Ga) {
+  if (central_fits(g, P, a) && central_fits(g, P, b)) return local_d1(g, P, a, Gb);
+  return S(0.5) * (local_d1(g, P, a, Gb) + local_d1(g, P, b, Ga));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void __launch_bounds__(256) k_main(Geom g, Phys ph, StepArgs<S> A) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool active = idx < g.npts;
+  S st[kNumStat];
+#pragma unroll
+  for (int s = 0; s < kNumStat; ++s) st[s] = S(0);
+  S wmax = S(-1), rmin = S(3.0e38), pmin = S(3.0e38);   // inactive lanes: neutral
+  unsigned health = 0;
+
+  if (active) {
+    const Pt P = make_point(g, idx);
+    const long long N = g.npts;
+    const S* U = A.U;
+    const S* PQ = A.PQ;
+    const S* G = A.G;
+
+    // inviscid flux divergence  -sum_d D_d F_d  (AT at PE faces)
+    S R[5] = {S(0), S(0), S(0), S(0), S(0)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long long qs = 4LL * g.pes[d] * g.plane[d];
+#pragma unroll
+      for (int e = 0; e < 5; ++e) {
+        const S* f = e == 0 ? U + (1 + d) * N : PQ + (4 + 4 * d + e - 1) * N;
+        R[e] -= at_d1(g, P, d, f, A.GH[d] + e * qs);
+      }
+    }
+    // second derivatives of u, v, w, T
+    S d2[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const S* f = PQ + q * N;
+      const S f0 = f[idx];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const S* gh = A.GH[d] + (5 + q) * 4LL * g.pes[d] * g.plane[d];
+        const S fm2 = fetch(g, P, d, -2, f, gh), fm1 = fetch(g, P, d, -1, f, gh);
+        const S fp1 = fetch(g, P, d, 1, f, gh), fp2 = fetch(g, P, d, 2, f, gh);
+        d2[q][d] = S(g.a0[d]) * f0 + S(g.a1[d]) * (fp1 + fm1) + S(g.a2[d]) * (fp2 + fm2);
+      }
+    }
+    // first derivatives at the point
+    S Ag[3][3], dT[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Ag[i][j] = G[(3 * i + j) * N + idx];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dT[j] = G[(9 + j) * N + idx];
+
+    // d theta / dx_i = d2 u_i/dx_i^2 + sum_{k != i} d/dx_i (d u_k / dx_k)
+    S gth[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      S s = d2[i][i];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k != i) s += mixed(g, P, i, k, G + (3 * k + k) * N, G + (3 * k + i) * N);
+      gth[i] = s;
+    }
+
+    const S r = U[idx];
+    const S m[3] = {U[N + idx], U[2 * N + idx], U[3 * N + idx]};
+    const S E = U[4 * N + idx];
+    const S vel[3] = {PQ[idx], PQ[N + idx], PQ[2 * N + idx]};
+    const S T = PQ[3 * N + idx];
+    const S p = S(ph.gm1) * (E - S(0.5) * (m[0] * vel[0] + m[1] * vel[1] + m[2] * vel[2]));
+    const S theta = Ag[0][0] + Ag[1][1] + Ag[2][2];
+    const S mu = S(ph.mu0) * pow(T, S(ph.omega));
+    const S dmudT = S(ph.omega) * mu / T;
+    const S cp_pr = S(ph.cp_over_pr);
+    const S kappa = mu * cp_pr;
+    S dmu[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dmu[j] = dmudT * dT[j];
+
+    S sm[3][3];   // A_ij + A_ji - 2/3 delta_ij theta
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) sm[i][j] = Ag[i][j] + Ag[j][i] - (i == j ? S(2.0 / 3.0) * theta : S(0));
+
+    // forcing f_c = sum_kx Re(B[kx][c](y,z) exp(i kx x))
+    S fo[3] = {S(0), S(0), S(0)};
+    if (A.fB) {
+      const int x = P.c[0], y = P.c[1], z = P.c[2];
+      const long long lines = (long long)g.n[2] * g.n[1];
+      const long long ln = (long long)z * g.n[1] + y;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        S acc = S(0);
+        for (int kx = 0; kx <= A.fK; ++kx) {
+          const vec2_t<S> b = A.fB[((long long)kx * 3 + c) * lines + ln];
+          const vec2_t<S> e = A.fX[(long long)kx * g.n[0] + x];
+          acc += b.x * e.x - b.y * e.y;
+        }
+        fo[c] = acc;
+      }
+    }
+
+    S work = S(0), sigS = S(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const S lap = d2[i][0] + d2[i][1] + d2[i][2];
+      S V = mu * (lap + gth[i] * S(1.0 / 3.0));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) V += dmu[j] * sm[i][j];
+      R[1 + i] += V + r * fo[i];
+      work += vel[i] * V;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) sigS += sm[i][j] * (Ag[i][j] + Ag[j][i]);
+    }
+    sigS *= S(0.5) * mu;
+    const S lapT = d2[3][0] + d2[3][1] + d2[3][2];
+    R[4] += work + sigS + kappa * lapT + cp_pr * (dmu[0] * dT[0] + dmu[1] * dT[1] + dmu[2] * dT[2]) +
+            r * (fo[0] * vel[0] + fo[1] * vel[1] + fo[2] * vel[2]);
+
+    // health: rho <= 0, p <= 0, non-finite R
+    if (!(r > S(0))) health |= H_RHO;
+    if (!(p > S(0))) health |= H_P;
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+      if (nonfinite(R[v])) health |= H_NONFINITE;
+
+    if (A.do_update) {
+      const S Uo[5] = {r, m[0], m[1], m[2], E};
+      const S dt = S(A.dt);
+      S un[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const S inc = A.first ? R[v] : S(1.5) * R[v] - S(0.5) * A.Rprev[v * N + idx];
+        un[v] = Uo[v] + dt * inc;
+        A.Unext[v * N + idx] = un[v];
+        A.Rprev[v * N + idx] = R[v];
+        if (nonfinite(un[v])) health |= H_NONFINITE;
+      }
+      // PE-boundary slabs of U^{n+1} into ring slot (n+1) mod nlev
+      const int slot = (int)((A.n + 1) % g.nlev);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (g.pes[d] == 1) continue;
+        const int li = P.li[d], nl = g.nl[d];
+        if (li >= 2 && li < nl - 2) continue;
+        const int t = li < 2 ? li : li - nl + 4;
+        const long long sp = 4LL * P.pe[d] + t;
+        S* rg = A.ring[d];
+        const long long P4 = 4LL * g.pes[d];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) rg[(((long long)slot * 5 + v) * P4 + sp) * g.plane[d] + P.pl[d]] = un[v];
+      }
+    } else if (A.Rout) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) A.Rout[v * N + idx] = (double)R[v];
+    }
+
+    if (A.do_stats) {
+      const S uu = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
+      const S c = sqrt(T);
+      st[ST_RHO] = r;
+      st[ST_M0] = m[0];
+      st[ST_M1] = m[1];
+      st[ST_M2] = m[2];
+      st[ST_E] = E;
+      st[ST_KE] = S(0.5) * r * uu;
+      st[ST_SIGS] = sigS;
+      const S a0 = Ag[0][0], a1 = Ag[1][1], a2 = Ag[2][2];
+      const S q0 = a0 * a0, q1 = a1 * a1, q2 = a2 * a2;
+      st[ST_G2] = q0 + q1 + q2;
+      st[ST_G3] = q0 * a0 + q1 * a1 + q2 * a2;
+      st[ST_G4] = q0 * q0 + q1 * q1 + q2 * q2;
+      const S o0 = Ag[2][1] - Ag[1][2], o1 = Ag[0][2] - Ag[2][0], o2 = Ag[1][0] - Ag[0][1];
+      st[ST_ENST] = o0 * o0 + o1 * o1 + o2 * o2;
+      st[ST_PTHETA] = p * theta;
+      st[ST_FPOW] = r * (fo[0] * vel[0] + fo[1] * vel[1] + fo[2] * vel[2]);
+      st[ST_U2] = uu;
+      st[ST_C] = c;
+      wmax = fmax(fabs(vel[0]), fmax(fabs(vel[1]), fabs(vel[2]))) + c;
+      rmin = r;
+      pmin = p;
+    }
+  }
+
+  // block reductions (fixed order: deterministic for a fixed launch shape)
+  __shared__ double sh[8][kNumStat];
+  __shared__ long long shk[8][3];
+  __shared__ unsigned shh[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned hh = __reduce_or_sync(0xffffffffu, health);
+  if (A.do_stats) {
+#pragma unroll
+    for (int s = 0; s < kNumStat; ++s) st[s] = warp_sum(st[s]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+      rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+      pmin = fmin(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int s = 0; s < kNumStat; ++s) sh[wid][s] = (double)st[s];
+      shk[wid][0] = ordered_key((double)wmax);
+      shk[wid][1] = ordered_key((double)rmin);
+      shk[wid][2] = ordered_key((double)pmin);
+    }
+  }
+  if (lane == 0) shh[wid] = hh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    unsigned h = 0;
+    for (int w = 0; w < nw; ++w) h |= shh[w];
+    if (h) atomicOr((unsigned*)(A.words + 3), h);
+    if (A.do_stats) {
+      long long kw = LLONG_MIN, kr = LLONG_MAX, kq = LLONG_MAX;
+      for (int w = 0; w < nw; ++w) {
+        kw = max(kw, shk[w][0]); kr = min(kr, shk[w][1]); kq = min(kq, shk[w][2]);
+      }
+      atomicMax((long long*)(A.words + 0), kw);
+      atomicMin((long long*)(A.words + 1), kr);
+      atomicMin((long long*)(A.words + 2), kq);
+    }
+  }
+  if (A.do_stats && threadIdx.x < kNumStat) {
+    const int nw = blockDim.x >> 5;
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
+    A.partial[(long long)blockIdx.x * kNumStat + threadIdx.x] = s;
+  }
+}
+
+}  // namespace atdns

@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Inputs come only from the seeded generator (paper_2003_10561_gb300.synth);
+every expected value is computed by oracle/.  Tolerances:
+* delay maps: bit-exact;
+* FP64 form: relative L-infinity per conserved variable <= 1e-12 for one RHS,
+  <= 1e-10 after 100 AB2 steps;
+* FP32-bulk form: relative L-infinity per RHS <= 2e-4 (derived in the design
+  notes from FP32 rounding of the 4th-order stencils: eps_32 times the
+  cancellation factor of the second-derivative stencil at these grids).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ns
+from oracle.pointwise import PointOracle
+from paper_2003_10561_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GAMMA, PR, OMEGA = 1.4, 0.7, 0.76
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_10561_gb300 import at_dns
+    at_dns.load()
+    return at_dns
+
+
+def rel_linf(a, b):
+    return [float(np.max(np.abs(a[v] - b[v])) / max(np.max(np.abs(b[v])), 1e-300)) for v in range(5)]
+
+
+def make(lib, n, pes, precision="p64", **kw):
+    return lib.Solver(n=n, pes=pes, precision=precision, gamma=GAMMA, prandtl=PR, visc_exp=OMEGA, **kw)
+
+
+def ocfg(n, pes, **kw):
+    return ns.Config(n=tuple(n), pes=tuple(pes), gamma=GAMMA, prandtl=PR, visc_exp=OMEGA, **kw)
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["sync", "periodic", "random"])
+def test_delay_map_bit_exact(lib, mode):
+    s = make(lib, (40, 30, 20), (4, 3, 2), mu0=0.01, dt=1e-3, max_delay=3, comm_period=4,
+             seed=0x0123456789ABCDEF)
+    c = ocfg((40, 30, 20), (4, 3, 2), max_delay=3, comm_period=4, seed=0x0123456789ABCDEF)
+    m = lib.MODES[mode]
+    for step in (0, 5, 6, 7, 11, 100, 12345, 2 ** 31 + 7):
+        gpu = s.delay_map(step, mode)
+        ref = ns.delay_map(c, step, m)
+        assert np.array_equal(gpu.astype(np.int64), ref), (mode, step)
+
+
+# --------------------------------------------------------------------------
+CASES = [
+    # n, pes, mode, step, L
+    ((32, 32, 32), (1, 1, 1), "sync", 0, 2),
+    ((16, 16, 16), (2, 2, 2), "random", 9, 2),
+    ((16, 16, 16), (2, 2, 2), "periodic", 8, 2),
+    ((15, 12, 20), (3, 2, 4), "random", 11, 3),       # ragged PEs (5, 6, 5), non-cubic
+    ((24, 10, 16), (4, 1, 2), "random", 13, 4),       # a direction without faces
+]
+
+
+@pytest.mark.parametrize("n,pes,mode,step,L", CASES)
+def test_rhs_parity_fp64(lib, n, pes, mode, step, L):
+    mu0 = 0.02
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=11)
+    c = ocfg(n, pes, mu0=mu0, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
+    hist = synth.history(U0, c.n_levels, eps=2e-2, seed=5)
+    s = make(lib, n, pes, mu0=mu0, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
+    s.set_history(hist, step)
+    R = s.rhs(mode)
+    Rref = ns.rhs(c, hist, ns.delay_map(c, step, lib.MODES[mode]))
+    err = rel_linf(R, Rref)
+    assert max(err) <= 1e-12, err
+
+
+def test_rhs_parity_fp64_forced(lib):
+    n, pes = (16, 16, 16), (2, 2, 2)
+    kw = dict(mu0=0.02, dt=5e-3, max_delay=2, seed=3, forcing=1, kf=2.0, f_amp=0.2, f_tcorr=0.3, f_seed=99)
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=12)
+    c = ocfg(n, pes, **{**kw, "forcing": True})
+    hist = synth.history(U0, c.n_levels, eps=1e-2, seed=6)
+    s = make(lib, n, pes, **kw)
+    s.set_history(hist, 9)
+    R = s.rhs("random")
+    Rref = ns.rhs(c, hist, ns.delay_map(c, 9, ns.RANDOM), ns.forcing_coefficients(c, 9))
+    err = rel_linf(R, Rref)
+    assert max(err) <= 1e-12, err
+
+
+def test_stats_parity_fp64(lib):
+    n, pes = (24, 24, 24), (2, 2, 2)
+    U0 = synth.initial_state(n, k0=4.0, mach_t=0.3, seed=13)
+    c = ocfg(n, pes, mu0=0.02, dt=1e-3, max_delay=2, seed=1)
+    hist = synth.history(U0, c.n_levels, eps=1e-2, seed=2)
+    s = make(lib, n, pes, mu0=0.02, dt=1e-3, max_delay=2, seed=1)
+    s.set_history(hist, 9)
+    s.rhs("random")
+    st = s.stats()
+    R, aux = ns.rhs(c, hist, ns.delay_map(c, 9, ns.RANDOM), None, True)
+    ref = ns.statistics(c, hist[0], aux)
+    for k, v in ref.items():
+        g = st[k]
+        if k == "mom":
+            for a, b in zip(g, v):
+                assert abs(a - b) <= 1e-12 * (abs(b) + 1e-3)
+            continue
+        assert abs(g - v) <= 1e-11 * abs(v) + 1e-15, (k, g, v)
+    assert st["unstable"] == 0
+    assert st["step"] == 9
+
+
+def test_config1_steps_parity_fp64(lib):
+    """32^3, one PE, synchronous, CFL 0.5: 20 steps, then 100 (<= 1e-10)."""
+    n = (32, 32, 32)
+    mu0 = synth.mu0_for_resolution(n, k0=4.0, mach_t=0.3, seed=0)
+    U0 = synth.initial_state(n, k0=4.0, mach_t=0.3, seed=0)
+    c = ocfg(n, (1, 1, 1), mu0=mu0)
+    c.dt = ns.dt_from_cfl(c, U0, 0.5)
+    s = make(lib, n, (1, 1, 1), mu0=mu0, cfl=0.5, dt=0.0)
+    s.set_state(U0)
+    assert abs(s.info()["dt"] - c.dt) <= 1e-15 * c.dt
+    run = ns.Run.start(c, U0, ns.SYNC)
+    for k in range(100):
+        run.step()
+        if k + 1 in (20, 100):
+            s.step(20 if k + 1 == 20 else 80, "sync")
+            err = rel_linf(s.get_state(), run.levels[0])
+            assert max(err) <= (1e-12 if k + 1 == 20 else 1e-10), (k + 1, err)
+
+
+@pytest.mark.parametrize("mode", ["random", "periodic"])
+def test_at_steps_parity_fp64(lib, mode):
+    """16^3, 2x2x2 PEs, AT delays from the start-up on: 100 AB2 steps."""
+    n, pes = (16, 16, 16), (2, 2, 2)
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=21)
+    kw = dict(mu0=0.03, dt=4e-3, max_delay=2, comm_period=3, seed=5)
+    c = ocfg(n, pes, **kw)
+    s = make(lib, n, pes, **kw)
+    s.set_state(U0)
+    run = ns.Run.start(c, U0, lib.MODES[mode])
+    for _ in range(100):
+        run.step()
+    s.step(100, mode)
+    err = rel_linf(s.get_state(), run.levels[0])
+    assert max(err) <= 1e-10, err
+
+
+def test_zero_delay_equals_sync_fp64(lib):
+    """Periodic mode during start-up and sync mode give bit-identical steps."""
+    n, pes = (16, 16, 16), (2, 2, 2)
+    U0 = synth.initial_state(n, seed=3)
+    a = make(lib, n, pes, mu0=0.02, dt=3e-3, max_delay=2)
+    b = make(lib, n, pes, mu0=0.02, dt=3e-3, max_delay=2)
+    a.set_state(U0)
+    b.set_state(U0)
+    a.step(4, "random")    # steps 0..3 < L + 3: zero delays
+    b.step(4, "sync")
+    assert np.array_equal(a.get_state(), b.get_state())
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,pes,mode,step,L", CASES[:3])
+def test_rhs_parity_fp32(lib, n, pes, mode, step, L):
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=11)
+    c = ocfg(n, pes, mu0=0.02, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
+    hist = synth.history(U0, c.n_levels, eps=2e-2, seed=5)
+    s = make(lib, n, pes, "p32", mu0=0.02, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
+    s.set_history(hist, step)
+    R = s.rhs(mode)
+    Rref = ns.rhs(c, hist, ns.delay_map(c, step, lib.MODES[mode]))
+    err = rel_linf(R, Rref)
+    assert max(err) <= 2e-4, err
+
+
+# --------------------------------------------------------------------------
+def _sample_points(n, nloc, rng, count):
+    """Random points plus PE face, edge and corner points and the ragged ends."""
+    pts = set()
+    for _ in range(count):
+        pts.add(tuple(int(rng.integers(0, n[d])) for d in range(3)))
+    special = [0, 1, nloc - 2, nloc - 1, nloc, nloc + 1, 2, nloc // 2]
+    for a in special:
+        for b in (0, 1, nloc - 1, 5):
+            pts.add((a % n[0], b % n[1], (a + b) % n[2]))
+            pts.add((b % n[0], a % n[1], 3 % n[2]))
+    pts.add((n[0] - 1, n[1] - 1, n[2] - 1))
+    return sorted(pts)
+
+
+@pytest.mark.parametrize("precision,tol", [("p64", 1e-12), ("p32", 2e-4)])
+def test_full_size_sampled_parity(lib, precision, tol):
+    """256^3 with 8x8x8 PEs (the benchmark workload), random delays with L = 2,
+    at a step past the start-up: sampled points against the brute-force
+    pointwise oracle."""
+    n, pes, L = (256, 256, 256), (8, 8, 8), 2
+    U0 = synth.initial_state(n, k0=4.0, mach_t=0.3, seed=1)
+    c = ocfg(n, pes, mu0=0.004, dt=1e-3, max_delay=L, seed=2024)
+    hist = synth.history(U0, c.n_levels, eps=1e-2, seed=3)
+    step = 17
+    s = make(lib, n, pes, precision, mu0=0.004, dt=1e-3, max_delay=L, seed=2024)
+    s.set_history(hist, step)
+    R = s.rhs("random")
+    s.close()
+    delays = ns.delay_map(c, step, ns.RANDOM)
+    po = PointOracle(c, lambda l: hist[l], delays)
+    pts = _sample_points(n, 32, np.random.default_rng(4), 120)
+    ref = np.array([po.rhs(p) for p in pts])
+    got = np.array([[R[v, z, y, x] for v in range(5)] for (x, y, z) in pts])
+    scale = np.max(np.abs(ref), axis=0)
+    err = np.max(np.abs(got - ref), axis=0) / scale
+    assert np.max(err) <= tol, err
+
+
+def test_unstable_state_reported(lib):
+    """A state with negative density is reported as AT_DNS_E_UNSTABLE (host-made failure)."""
+    n = (16, 16, 16)
+    U0 = synth.initial_state(n, seed=2)
+    U0[0, 3, 4, 5] = -1.0
+    s = make(lib, n, (1, 1, 1), mu0=0.01, dt=1e-3)
+    s.set_state(U0)
+    with pytest.raises(lib.AtDnsError) as ei:
+        s.step(2, "sync")
+    assert ei.value.code == lib.AT_DNS_E_UNSTABLE
+    st = s.stats()
+    assert st["unstable"] != 0
+
+
+def test_device_pointers_and_zero_steps(lib):
+    import torch
+    n = (16, 16, 16)
+    U0 = synth.initial_state(n, seed=8)
+    s = make(lib, n, (2, 2, 2), mu0=0.01, dt=1e-3)
+    s.set_state(torch.from_numpy(U0).cuda())
+    s.step(0, "random")
+    out = torch.empty(U0.shape, dtype=torch.float64, device="cuda")
+    s.get_state(out)
+    assert np.array_equal(out.cpu().numpy(), U0)
+    r_dev = torch.empty(U0.shape, dtype=torch.float64, device="cuda")
+    s.rhs("sync", r_dev)
+    r_host = s.rhs("sync")
+    assert np.array_equal(r_dev.cpu().numpy(), r_host)
