@@ -43,6 +43,13 @@ NB_FRAC = 1.0 - (28.0 / 32.0) ** 3
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max SM clock
 
 
+def set_workload(n, pes):
+    global N, PES, NB_FRAC
+    N, PES = n, pes
+    nl = n // pes
+    NB_FRAC = 1.0 - ((nl - 4.0) / nl) ** 3
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -146,11 +153,14 @@ def run_reference(args, world, rank):
 
 
 def workload_config(world):
-    return {"workload": "decaying turbulence 256^3, 8x8x8 virtual PEs (32^3 each, N_B 33%), 4th-order AT "
-                        "stencils, random delays {0,1,2} (L=2), AB2, FP64, stats every step",
+    nl = N // PES
+    return {"workload": "decaying turbulence %d^3, %dx%dx%d virtual PEs (%d^3 each, N_B %.1f%%), 4th-order AT "
+                        "stencils, random delays {0,1,2} (L=2), AB2, stats every step" % (N, PES, PES, PES, nl,
+                                                                                        100 * NB_FRAC),
             "grid": [N, N, N], "pes": [PES, PES, PES], "max_delay": L, "delay_mode": "random",
-            "integrator": "AB2", "precision": "P64", "parallelism": "replicas" if world > 1 else "single",
-            "l2": "working set ~8 GB >> 129 MB L2; no flush needed"}
+            "boundary_fraction": NB_FRAC, "integrator": "AB2",
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "working set %.1f GB >> 129 MB L2; no flush needed" % (N ** 3 * 5 * 8 * 12 / 1e9)}
 
 
 def make_solver(at_dns, precision, stream, mu0):
@@ -185,7 +195,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grid", type=int, default=N, help="points per direction (profiling cases)")
+    ap.add_argument("--pes", type=int, default=PES, help="virtual PEs per direction")
+    ap.add_argument("--precision", default="both", choices=["both", "p64", "p32"])
     args = ap.parse_args()
+    set_workload(args.grid, args.pes)
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
 
@@ -209,7 +224,8 @@ def main():
     res = {}
     clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
                     if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_rank%d.csv" % rank)
-    for prec in ("p64", "p32"):
+    precs = ("p64", "p32") if args.precision == "both" else (args.precision,)
+    for prec in precs:
         s = make_solver(at_dns, prec, stream.cuda_stream, mu0)
         s.set_state(U0)
         s.step(at_dns.at_dns_get_info(s.h).n_levels + 1, "random")   # past the synchronous start-up
@@ -229,7 +245,7 @@ def main():
         # end to end through the public API with host buffers: per step, upload
         # U^n from pinned host memory (as the state of step n), step, read the
         # statistics record back
-        if prec == "p64":
+        if prec == "p64" and not args.no_e2e:
             host = torch.from_numpy(U0).pin_memory()
             nlev = at_dns.at_dns_get_info(s.h).n_levels
             e2e_steps = max(3, args.steps // 4)
@@ -258,41 +274,49 @@ def main():
     if rank != 0:
         return 0
     pk = peaks()
-    p64, p32 = res["p64"], res["p32"]
     pts = float(N ** 3)
-    value = world * pts * args.steps / (p64["ms"] / 1e3)
-    main64 = p64["kt"].get("main", (1, 1.0))
-    t_main = main64[1] / main64[0] / 1e3
-    achieved = FLOP_MAIN * pts / t_main / 1e12
-    main32 = p32["kt"].get("main", (1, 1.0))
-    t_main32 = main32[1] / main32[0] / 1e3
-    bytes32 = algorithmic_bytes(4) * pts
-    ach32 = bytes32 / t_main32 / 1e9
-    launches = sum(v[0] for v in p64["kt"].values())
+    p64 = res.get("p64")
+    p32 = res.get("p32")
+    head = p64 or p32
+    value = world * pts * args.steps / (head["ms"] / 1e3)
+    launches = sum(v[0] for v in head["kt"].values())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": p64["ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if p64 else "f32", "data": "synthetic",
         "config": workload_config(world),
-        "roofline": {"bound": "alu", "kernel": "k_main (FP64)", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None,
-                     "note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe measured 1.20)"},
-        "fp32_bulk": {"value": world * pts * args.steps / (p32["ms"] / 1e3), "unit": UNIT,
-                      "ms_per_step": p32["ms"] / args.steps, "dtype": "f32",
-                      "roofline": {"bound": "hbm", "kernel": "k_main (FP32)", "achieved": ach32,
-                                   "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                                   "frac": ach32 / pk.get("hbm_gbs", 6800.0), "traffic": None},
-                      "rel_err_vs_fp64": {k: abs(p32["stats"][k] - p64["stats"][k]) / abs(p64["stats"][k])
-                                          for k in ("tke", "dissipation")}},
-        "kernel_ms_per_step": {k: v[1] / v[0] for k, v in p64["kt"].items()},
-        "kernel_ms_per_step_fp32": {k: v[1] / v[0] for k, v in p32["kt"].items()},
+        "kernel_ms_per_step": {k: v[1] / v[0] for k, v in head["kt"].items()},
         "e2e": res.get("e2e"),
         "cpu_baseline": cpu,
         "clocks": clocks.summary(local),
         "gpu_launches": launches,
         "rhs_per_s": value,
     }
+    if p64:
+        main64 = p64["kt"].get("main", (1, 1.0))
+        t_main = main64[1] / main64[0] / 1e3
+        achieved = FLOP_MAIN * pts / t_main / 1e12
+        line["roofline"] = {"bound": "alu", "kernel": "k_main (FP64)", "achieved": achieved,
+                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                            "traffic": None,
+                            "note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                                    "(an FMA probe measured 1.20 TFLOP/s)"}
+    if p32:
+        main32 = p32["kt"].get("main", (1, 1.0))
+        t_main32 = main32[1] / main32[0] / 1e3
+        ach32 = algorithmic_bytes(4) * pts / t_main32 / 1e9
+        r32 = {"bound": "hbm", "kernel": "k_main (FP32)", "achieved": ach32, "peak": pk.get("hbm_gbs"),
+               "unit": "GB/s", "frac": ach32 / pk.get("hbm_gbs", 6800.0), "traffic": None}
+        blk = {"value": world * pts * args.steps / (p32["ms"] / 1e3), "unit": UNIT,
+               "ms_per_step": p32["ms"] / args.steps, "dtype": "f32", "roofline": r32,
+               "kernel_ms_per_step": {k: v[1] / v[0] for k, v in p32["kt"].items()}}
+        if p64:
+            blk["rel_err_vs_fp64"] = {k: abs(p32["stats"][k] - p64["stats"][k]) / abs(p64["stats"][k])
+                                      for k in ("tke", "dissipation")}
+            line["fp32_bulk"] = blk
+        else:
+            line["roofline"] = r32
+            line["fp32_bulk"] = blk
     print(json.dumps(line), flush=True)
     return 0
 

@@ -283,6 +283,15 @@ double key_to_double(unsigned long long k) {
   return v;
 }
 
+// Decode an order-preserving key of a float (FP32 form) written as int64.
+double fkey_to_double(unsigned long long k) {
+  int b = (int)(long long)k;
+  b ^= (b >> 31) & 0x7FFFFFFF;
+  float v;
+  std::memcpy(&v, &b, 4);
+  return (double)v;
+}
+
 std::vector<Mode3> forcing_modes(double kf) {
   std::vector<Mode3> out;
   const int K = (int)std::floor(kf);
@@ -356,14 +365,15 @@ struct Ops {
     }
     CK(cudaGetLastError());
     S* Ucur = U(h, h->cur);
+    const Coef<S> K = make_coef<S>(g, h->ph, h->dt);
     S* GH[3] = {(S*)h->GH[0], (S*)h->GH[1], (S*)h->GH[2]};
     S* ring[3] = {(S*)h->ring[0], (S*)h->ring[1], (S*)h->ring[2]};
-    { Timed t(h, KD_PRIM); CK(launch_prim<S>(g, h->ph, Ucur, (S*)h->PQ, h->st)); }
+    { Timed t(h, KD_PRIM); CK(launch_prim<S>(g, K, Ucur, (S*)h->PQ, h->st)); }
     if (g.pes[0] > 1 || g.pes[1] > 1 || g.pes[2] > 1) {
       Timed t(h, KD_GHOST);
-      CK(launch_ghost<S>(g, h->ph, Ucur, (S*)h->PQ, GH, ring, h->dmap, h->n, h->st));
+      CK(launch_ghost<S>(g, K, Ucur, (S*)h->PQ, GH, ring, h->dmap, h->n, h->st));
     }
-    { Timed t(h, KD_GRAD); CK(launch_grad<S>(g, (S*)h->PQ, GH, (S*)h->G, h->st)); }
+    { Timed t(h, KD_GRAD); CK(launch_grad<S>(g, K, (S*)h->PQ, GH, (S*)h->G, h->st)); }
     if (h->cfg.forcing) {
       const long long lines = (long long)g.n[2] * g.n[1];
       {
@@ -393,7 +403,7 @@ struct Ops {
     a.first = h->first ? 1 : 0;
     a.do_update = update ? 1 : 0;
     a.do_stats = stats ? 1 : 0;
-    { Timed t(h, KD_MAIN); CK(launch_main<S>(g, h->ph, a, h->st)); }
+    { Timed t(h, KD_MAIN); CK(launch_main<S>(g, K, a, h->st)); }
     if (stats) {
       { Timed t(h, KD_STATS); k_stats_final<<<kNumStat, 256, 0, h->st>>>(h->partial, main_blocks(g), h->sums); }
       CK(cudaGetLastError());
@@ -736,9 +746,10 @@ int at_dns_stats(at_dns_t* h, at_dns_stats_t* out) {
   out->forcing_power = s[ST_FPOW] / N;
   out->urms = std::sqrt(s[ST_U2] / N / 3.0);
   out->mach_t = std::sqrt(s[ST_U2] / N) / (s[ST_C] / N);
-  out->max_wave_speed = key_to_double(w[0]);
-  out->min_rho = key_to_double(w[1]);
-  out->min_p = key_to_double(w[2]);
+  double (*dec)(unsigned long long) = h->p64 ? key_to_double : fkey_to_double;
+  out->max_wave_speed = dec(w[0]);
+  out->min_rho = dec(w[1]);
+  out->min_p = dec(w[2]);
   out->unstable = (int32_t)w[3];
   return AT_DNS_OK;
 }

@@ -44,6 +44,42 @@ struct Phys {
   double gamma, gm1, prandtl, mu0, omega, cp_over_pr;
 };
 
+// Stencil coefficients and physical constants in the kernel's scalar type,
+// converted once on the host (a conversion from double on the device would
+// run on the FP64 pipe).
+template <typename S>
+struct Coef {
+  S c1[3], c2[3];          // D1 = c1 (f[+1]-f[-1]) + c2 (f[+2]-f[-2])
+  S a0[3], a1[3], a2[3];   // D2 = a0 f + a1 (f[+1]+f[-1]) + a2 (f[+2]+f[-2])
+  S h12[3];                // 1/(12 dx) for the one-sided stencils
+  S gamma, gm1, mu0, omega, cp_over_pr;
+  S dt;
+};
+
+template <typename S>
+inline Coef<S> make_coef(const Geom& g, const Phys& ph, double dt) {
+  Coef<S> c;
+  for (int d = 0; d < 3; ++d) {
+    c.c1[d] = (S)g.c1[d];
+    c.c2[d] = (S)g.c2[d];
+    c.a0[d] = (S)g.a0[d];
+    c.a1[d] = (S)g.a1[d];
+    c.a2[d] = (S)g.a2[d];
+    c.h12[d] = (S)g.inv12dx[d];
+  }
+  c.gamma = (S)ph.gamma;
+  c.gm1 = (S)ph.gm1;
+  c.mu0 = (S)ph.mu0;
+  c.omega = (S)ph.omega;
+  c.cp_over_pr = (S)ph.cp_over_pr;
+  c.dt = (S)dt;
+  return c;
+}
+
+// Sign/zero test on the bit pattern (no floating-point instruction).
+__device__ __forceinline__ bool nonpositive(double v) { return __double_as_longlong(v) <= 0; }
+__device__ __forceinline__ bool nonpositive(float v) { return __float_as_int(v) <= 0; }
+
 // Linear index -> (x, y, z).
 __device__ __forceinline__ void decode(const Geom& g, long long idx, int& x, int& y, int& z) {
   long long t = idx / g.n[0];

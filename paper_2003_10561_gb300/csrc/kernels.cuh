@@ -1,20 +1,23 @@
 // AT-DNS step kernels, templated on the scalar type S (double for the FP64
 // form, float for the FP32-bulk form).  Every per-point operation -- storage,
 // stencils, AT extrapolation, update and the slab ring of past levels -- is in
-// S; the statistics are summed in S within a warp (32 points) and in FP64 from
-// there on, in a fixed order.
+// S; the statistics are summed in FP64 across points in a fixed order (FP32
+// form: within a warp in FP32 first).
 //
 // One RHS evaluation (Sec. 2) is four launches:
 //   k_prim   per point: u, v, w, T and the 12 non-trivial inviscid fluxes;
 //   k_ghost  per PE-face ghost point (2 layers each side, Sec. 3): the 9
 //            differentiated quantities of that direction at level n (k = 0) or
-//            extrapolated from levels n-k, n-k-1, n-k-2 of the FP64 slab ring
-//            with the Table B weights (Appendix B);
+//            extrapolated from levels n-k, n-k-1, n-k-2 of the slab ring with
+//            the Table B weights (Appendix B);
 //   k_grad   per point: AT first derivatives du_i/dx_j and dT/dx_j;
 //   k_main   per point: inviscid flux divergence, second derivatives, mixed
 //            derivatives by the three-step rule (Sec. 2.1), viscous / heat /
 //            forcing assembly, AB2 update (Eq. (time_ab)), ring write of the
-//            new PE-boundary slabs and the FP64 block reductions.
+//            new PE-boundary slabs and the block reductions.
+//
+// Floating-point work is kept off the FP64 pipe in the FP32 form (constants
+// come converted from the host, sign tests and min/max use bit patterns).
 #pragma once
 #include <climits>
 #include "common.cuh"
@@ -23,7 +26,7 @@ namespace atdns {
 
 // ---------------------------------------------------------------------------
 template <typename S>
-__global__ void __launch_bounds__(256) k_prim(Geom g, Phys ph, const S* __restrict__ U,
+__global__ void __launch_bounds__(256) k_prim(Geom g, Coef<S> K, const S* __restrict__ U,
                                               S* __restrict__ PQ) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= g.npts) return;
@@ -31,8 +34,8 @@ __global__ void __launch_bounds__(256) k_prim(Geom g, Phys ph, const S* __restri
   const S r = U[idx], m0 = U[N + idx], m1 = U[2 * N + idx], m2 = U[3 * N + idx], E = U[4 * N + idx];
   const S inv = S(1) / r;
   const S u = m0 * inv, v = m1 * inv, w = m2 * inv;
-  const S p = S(ph.gm1) * (E - S(0.5) * (m0 * u + m1 * v + m2 * w));
-  const S T = S(ph.gamma) * p * inv;
+  const S p = K.gm1 * (E - S(0.5) * (m0 * u + m1 * v + m2 * w));
+  const S T = K.gamma * p * inv;
   const S H = E + p;
   PQ[0 * N + idx] = u;
   PQ[1 * N + idx] = v;
@@ -55,11 +58,11 @@ __global__ void __launch_bounds__(256) k_prim(Geom g, Phys ph, const S* __restri
 
 // The 9 quantities of direction d from one level of U (same arithmetic as k_prim).
 template <typename S>
-__device__ __forceinline__ void ghost_quantities(const Phys& ph, int d, const S* Uv, S* q) {
+__device__ __forceinline__ void ghost_quantities(const Coef<S>& K, int d, const S* Uv, S* q) {
   const S r = Uv[0], inv = S(1) / r;
   const S vel[3] = {Uv[1] * inv, Uv[2] * inv, Uv[3] * inv};
-  const S p = S(ph.gm1) * (Uv[4] - S(0.5) * (Uv[1] * vel[0] + Uv[2] * vel[1] + Uv[3] * vel[2]));
-  const S T = S(ph.gamma) * p * inv;
+  const S p = K.gm1 * (Uv[4] - S(0.5) * (Uv[1] * vel[0] + Uv[2] * vel[1] + Uv[3] * vel[2]));
+  const S T = K.gamma * p * inv;
   const S ud = vel[d];
   q[0] = Uv[1 + d];
   q[1] = Uv[1] * ud + (d == 0 ? p : S(0));
@@ -78,7 +81,7 @@ __device__ __forceinline__ void ghost_quantities(const Phys& ph, int d, const S*
 // face, face 2d+1).  Ring slab index sp = 4 p + t with t = 0, 1 for local 0, 1
 // and t = 2, 3 for local nl-2, nl-1.
 template <typename S>
-__global__ void __launch_bounds__(256) k_ghost(Geom g, Phys ph, const S* __restrict__ U,
+__global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __restrict__ U,
                                                const S* __restrict__ PQ, S* GH0, S* GH1, S* GH2,
                                                const S* __restrict__ ring0,
                                                const S* __restrict__ ring1,
@@ -137,17 +140,15 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Phys ph, const S* __restr
 #pragma unroll
     for (int v = 0; v < 5; ++v)
       Uv[v] = ring[(((long long)rs * 5 + v) * 4 * P + sp) * plane + pl];
-    ghost_quantities(ph, d, Uv, q);
+    ghost_quantities(K, d, Uv, q);
 #pragma unroll
-    for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] += w[l] * q[qq];
+    for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = fma(w[l], q[qq], acc[qq]);
   }
 #pragma unroll
   for (int q = 0; q < kNumGhostQ; ++q) out[q * qstride] = acc[q];
 }
 
 // ---------------------------------------------------------------------------
-// Neighbour fetch along d: the field itself inside the PE (periodic wrap when
-// the direction has one PE), the ghost array across a PE face.
 struct Pt {
   long long idx;
   int c[3], li[3], pe[3];
@@ -167,31 +168,65 @@ __device__ __forceinline__ Pt make_point(const Geom& g, long long idx) {
   return P;
 }
 
-template <typename S>
-__device__ __forceinline__ S fetch(const Geom& g, const Pt& P, int d, int off, const S* __restrict__ field,
-                                   const S* __restrict__ gh) {
-  if (g.pes[d] == 1) {
-    int c2 = P.c[d] + off;
-    c2 = c2 < 0 ? c2 + g.n[d] : (c2 >= g.n[d] ? c2 - g.n[d] : c2);
-    return field[P.idx + (long long)(c2 - P.c[d]) * g.stride[d]];
+// Neighbours of one point along direction d at offsets -2, -1, +1, +2: either
+// an offset into the field relative to the point (inside the PE, or periodic
+// wrap when the direction has one PE) or, across a PE face, an index into the
+// ghost array of direction d.  Built once per point and direction, then used
+// for every quantity of that direction.
+struct Nb {
+  long long off[4];
+  unsigned gmask;    // bit j: off[j] indexes the ghost array
+};
+
+__device__ __forceinline__ Nb make_nb(const Geom& g, const Pt& P, int d) {
+  Nb nb;
+  nb.gmask = 0;
+  const long long st = g.stride[d];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int m = j < 2 ? j - 2 : j - 1;
+    if (g.pes[d] == 1) {
+      int c2 = P.c[d] + m;
+      c2 = c2 < 0 ? c2 + g.n[d] : (c2 >= g.n[d] ? c2 - g.n[d] : c2);
+      nb.off[j] = (long long)(c2 - P.c[d]) * st;
+    } else {
+      const int l2 = P.li[d] + m;
+      if (l2 >= 0 && l2 < g.nl[d]) {
+        nb.off[j] = (long long)m * st;
+      } else {
+        const int slot = l2 < 0 ? l2 + 2 : 2 + (l2 - g.nl[d]);
+        nb.off[j] = (long long)(4 * P.pe[d] + slot) * g.plane[d] + P.pl[d];
+        nb.gmask |= 1u << j;
+      }
+    }
   }
-  const int l2 = P.li[d] + off;
-  if (l2 >= 0 && l2 < g.nl[d]) return field[P.idx + (long long)off * g.stride[d]];
-  const int slot = l2 < 0 ? l2 + 2 : 2 + (l2 - g.nl[d]);
-  return gh[(long long)(4 * P.pe[d] + slot) * g.plane[d] + P.pl[d]];
+  return nb;
 }
 
 template <typename S>
-__device__ __forceinline__ S at_d1(const Geom& g, const Pt& P, int d, const S* field, const S* gh) {
-  const S fm2 = fetch(g, P, d, -2, field, gh), fm1 = fetch(g, P, d, -1, field, gh);
-  const S fp1 = fetch(g, P, d, 1, field, gh), fp2 = fetch(g, P, d, 2, field, gh);
-  return S(g.c1[d]) * (fp1 - fm1) + S(g.c2[d]) * (fp2 - fm2);
+__device__ __forceinline__ S nbv(const Nb& nb, int j, long long idx, const S* __restrict__ f,
+                                 const S* __restrict__ gh) {
+  return ((nb.gmask >> j) & 1u) ? gh[nb.off[j]] : f[idx + nb.off[j]];
+}
+
+// acc + D1 f  with  D1 = c1 (f[+1]-f[-1]) + c2 (f[+2]-f[-2])  (differences
+// first: rounding relative to the derivative, not to the stencil terms).
+template <typename S>
+__device__ __forceinline__ S nb_d1_acc(S acc, S c1, S c2, const Nb& nb, long long idx, const S* f, const S* gh) {
+  acc = fma(c1, nbv(nb, 2, idx, f, gh) - nbv(nb, 1, idx, f, gh), acc);
+  return fma(c2, nbv(nb, 3, idx, f, gh) - nbv(nb, 0, idx, f, gh), acc);
+}
+
+// D2 without the centre term: a1 (f[+1]+f[-1]) + a2 (f[+2]+f[-2]).
+template <typename S>
+__device__ __forceinline__ S nb_d2_off(S a1, S a2, const Nb& nb, long long idx, const S* f, const S* gh) {
+  return fma(a1, nbv(nb, 2, idx, f, gh) + nbv(nb, 1, idx, f, gh), a2 * (nbv(nb, 3, idx, f, gh) + nbv(nb, 0, idx, f, gh)));
 }
 
 template <typename S>
-__global__ void __launch_bounds__(256) k_grad(Geom g, const S* __restrict__ PQ, const S* __restrict__ GH0,
-                                              const S* __restrict__ GH1, const S* __restrict__ GH2,
-                                              S* __restrict__ G) {
+__global__ void __launch_bounds__(256) k_grad(Geom g, Coef<S> K, const S* __restrict__ PQ,
+                                              const S* __restrict__ GH0, const S* __restrict__ GH1,
+                                              const S* __restrict__ GH2, S* __restrict__ G) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= g.npts) return;
   const Pt P = make_point(g, idx);
@@ -200,9 +235,10 @@ __global__ void __launch_bounds__(256) k_grad(Geom g, const S* __restrict__ PQ, 
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const long long qs = 4LL * g.pes[d] * g.plane[d];
+    const Nb nb = make_nb(g, P, d);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const S v = at_d1(g, P, d, PQ + q * N, GH[d] + (5 + q) * qs);
+      const S v = nb_d1_acc(S(0), K.c1[d], K.c2[d], nb, idx, PQ + q * N, GH[d] + (5 + q) * qs);
       const int out = q < 3 ? 3 * q + d : 9 + d;
       G[out * N + idx] = v;
     }
@@ -218,23 +254,21 @@ __device__ __forceinline__ bool central_fits(const Geom& g, const Pt& P, int d) 
 // PE-local 4th-order first derivative of a gradient field in direction a:
 // central where the stencil fits, one-sided at the two points next to a face.
 template <typename S>
-__device__ __forceinline__ S local_d1(const Geom& g, const Pt& P, int a, const S* __restrict__ f) {
+__device__ __forceinline__ S local_d1(const Geom& g, const Coef<S>& K, const Pt& P, int a, const S* __restrict__ f) {
   const long long s = g.stride[a];
   const long long i = P.idx;
   if (central_fits(g, P, a)) {
     if (g.pes[a] == 1) {
-      S fm2, fm1, fp1, fp2;
       auto at = [&](int off) {
         int c2 = P.c[a] + off;
         c2 = c2 < 0 ? c2 + g.n[a] : (c2 >= g.n[a] ? c2 - g.n[a] : c2);
         return f[i + (long long)(c2 - P.c[a]) * s];
       };
-      fm2 = at(-2); fm1 = at(-1); fp1 = at(1); fp2 = at(2);
-      return S(g.c1[a]) * (fp1 - fm1) + S(g.c2[a]) * (fp2 - fm2);
+      return fma(K.c1[a], at(1) - at(-1), K.c2[a] * (at(2) - at(-2)));
     }
-    return S(g.c1[a]) * (f[i + s] - f[i - s]) + S(g.c2[a]) * (f[i + 2 * s] - f[i - 2 * s]);
+    return fma(K.c1[a], f[i + s] - f[i - s], K.c2[a] * (f[i + 2 * s] - f[i - 2 * s]));
   }
-  const S h = S(g.inv12dx[a]);
+  const S h = K.h12[a];
   const int li = P.li[a], nl = g.nl[a];
   if (li == 0)
     return h * (S(-25) * f[i] + S(48) * f[i + s] - S(36) * f[i + 2 * s] + S(16) * f[i + 3 * s] - S(3) * f[i + 4 * s]);
@@ -247,9 +281,10 @@ __device__ __forceinline__ S local_d1(const Geom& g, const Pt& P, int a, const S
 
 // d/dx_a (d f/dx_b) with Gb = AT df/dx_b and Ga = AT df/dx_a.
 template <typename S>
-__device__ __forceinline__ S mixed(const Geom& g, const Pt& P, int a, int b, const S* Gb, const S* Ga) {
-  if (central_fits(g, P, a) && central_fits(g, P, b)) return local_d1(g, P, a, Gb);
-  return S(0.5) * (local_d1(g, P, a, Gb) + local_d1(g, P, b, Ga));
+__device__ __forceinline__ S mixed(const Geom& g, const Coef<S>& K, const Pt& P, int a, int b, const S* Gb,
+                                   const S* Ga) {
+  if (central_fits(g, P, a) && central_fits(g, P, b)) return local_d1(g, K, P, a, Gb);
+  return S(0.5) * (local_d1(g, K, P, a, Gb) + local_d1(g, K, P, b, Ga));
 }
 
 template <typename T>
@@ -259,15 +294,107 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Order-preserving integer keys (min/max without floating-point compares).
+__device__ __forceinline__ long long okey(double v) { return ordered_key(v); }
+__device__ __forceinline__ long long okey(float v) {
+  // the float key is widened to the double key of the same value on the
+  // host side only after decoding, so encode through the exact double value
+  const int b = __float_as_int(v);
+  return (long long)(b ^ ((b >> 31) & 0x7FFFFFFF));
+}
+
+// Per-block reduction of the kNumStat per-point sums (fixed order) into
+// partial[block], and of the max/min keys and health bits into the global
+// words.  FP64 form: through shared memory, 16 partial sums per statistic
+// (a warp-shuffle tree would cost every lane 5 FP64 adds per statistic).
+// FP32 form: warp sums in FP32, then FP64 across the warps of the block.
+template <typename S>
+__device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave, long long krho, long long kp,
+                                             unsigned health, bool do_stats, double* partial,
+                                             unsigned long long* words) {
+  constexpr int kThreads = 256, kWarps = kThreads / 32;
+  __shared__ double sh[kNumStat][kThreads + 1];
+  __shared__ long long shk[kWarps][3];
+  __shared__ unsigned shh[kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const unsigned hh = __reduce_or_sync(0xffffffffu, health);
+  if (do_stats) {
+    kwave = warp_max(kwave);
+    krho = warp_min(krho);
+    kp = warp_min(kp);
+    if (lane == 0) { shk[wid][0] = kwave; shk[wid][1] = krho; shk[wid][2] = kp; }
+    if (sizeof(S) == 8) {
+#pragma unroll
+      for (int s = 0; s < kNumStat; ++s) sh[s][tid] = (double)st[s];
+    } else {
+#pragma unroll
+      for (int s = 0; s < kNumStat; ++s) {
+        const S w = warp_sum(st[s]);
+        if (lane == 0) sh[s][wid] = (double)w;
+      }
+    }
+  }
+  if (lane == 0) shh[wid] = hh;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned h = 0;
+    for (int w = 0; w < kWarps; ++w) h |= shh[w];
+    if (h) atomicOr((unsigned*)(words + 3), h);
+    if (do_stats) {
+      long long kw = LLONG_MIN, kr = LLONG_MAX, kq = LLONG_MAX;
+      for (int w = 0; w < kWarps; ++w) {
+        kw = max(kw, shk[w][0]); kr = min(kr, shk[w][1]); kq = min(kq, shk[w][2]);
+      }
+      atomicMax((long long*)(words + 0), kw);
+      atomicMin((long long*)(words + 1), kr);
+      atomicMin((long long*)(words + 2), kq);
+    }
+  }
+  if (!do_stats) return;
+  if (sizeof(S) == 8) {
+    // 16 lanes per statistic, each summing 16 consecutive values, then a
+    // 16-lane shuffle tree
+    if (tid < kNumStat * 16) {
+      const int s = tid >> 4, part = tid & 15;
+      double a = 0.0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) a += sh[s][part * 16 + q];
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o, 16);
+      if (part == 0) partial[(long long)blockIdx.x * kNumStat + s] = a;
+    }
+  } else {
+    if (tid < kNumStat) {
+      double a = 0.0;
+      for (int w = 0; w < kWarps; ++w) a += sh[tid][w];
+      partial[(long long)blockIdx.x * kNumStat + tid] = a;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 template <typename S>
-__global__ void __launch_bounds__(256) k_main(Geom g, Phys ph, StepArgs<S> A) {
+__global__ void __launch_bounds__(256) k_main(Geom g, Coef<S> K, StepArgs<S> A) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const bool active = idx < g.npts;
   S st[kNumStat];
 #pragma unroll
   for (int s = 0; s < kNumStat; ++s) st[s] = S(0);
-  S wmax = S(-1), rmin = S(3.0e38), pmin = S(3.0e38);   // inactive lanes: neutral
+  long long kwave = LLONG_MIN, krho = LLONG_MAX, kp = LLONG_MAX;
   unsigned health = 0;
 
   if (active) {
@@ -277,31 +404,34 @@ __global__ void __launch_bounds__(256) k_main(Geom g, Phys ph, StepArgs<S> A) {
     const S* PQ = A.PQ;
     const S* G = A.G;
 
-    // inviscid flux divergence  -sum_d D_d F_d  (AT at PE faces)
+    // inviscid flux divergence -sum_d D_d F_d (accumulated with the stencil
+    // coefficients negated) and the off-centre parts of the second
+    // derivatives of u, v, w, T, direction by direction (AT ghosts across faces)
     S R[5] = {S(0), S(0), S(0), S(0), S(0)};
+    S lap[4] = {S(0), S(0), S(0), S(0)};
+    S d2diag[3];                           // d^2 u_d / dx_d^2
+    S a0sum = S(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const long long qs = 4LL * g.pes[d] * g.plane[d];
+      const Nb nb = make_nb(g, P, d);
+      const S* gh = A.GH[d];
 #pragma unroll
       for (int e = 0; e < 5; ++e) {
         const S* f = e == 0 ? U + (1 + d) * N : PQ + (4 + 4 * d + e - 1) * N;
-        R[e] -= at_d1(g, P, d, f, A.GH[d] + e * qs);
+        R[e] = nb_d1_acc(R[e], -K.c1[d], -K.c2[d], nb, idx, f, gh + e * qs);
       }
-    }
-    // second derivatives of u, v, w, T
-    S d2[4][3];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const S* f = PQ + q * N;
-      const S f0 = f[idx];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const S* gh = A.GH[d] + (5 + q) * 4LL * g.pes[d] * g.plane[d];
-        const S fm2 = fetch(g, P, d, -2, f, gh), fm1 = fetch(g, P, d, -1, f, gh);
-        const S fp1 = fetch(g, P, d, 1, f, gh), fp2 = fetch(g, P, d, 2, f, gh);
-        d2[q][d] = S(g.a0[d]) * f0 + S(g.a1[d]) * (fp1 + fm1) + S(g.a2[d]) * (fp2 + fm2);
+      for (int q = 0; q < 4; ++q) {
+        const S v = nb_d2_off(K.a1[d], K.a2[d], nb, idx, PQ + q * N, gh + (5 + q) * qs);
+        lap[q] += v;
+        if (q == d) d2diag[d] = fma(K.a0[d], PQ[q * N + idx], v);
       }
+      a0sum += K.a0[d];
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) lap[q] = fma(a0sum, PQ[q * N + idx], lap[q]);
+
     // first derivatives at the point
     S Ag[3][3], dT[3];
 #pragma unroll
@@ -315,10 +445,10 @@ __global__ void __launch_bounds__(256) k_main(Geom g, Phys ph, StepArgs<S> A) {
     S gth[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      S s = d2[i][i];
+      S s = d2diag[i];
 #pragma unroll
       for (int k = 0; k < 3; ++k)
-        if (k != i) s += mixed(g, P, i, k, G + (3 * k + k) * N, G + (3 * k + i) * N);
+        if (k != i) s += mixed(g, K, P, i, k, G + (3 * k + k) * N, G + (3 * k + i) * N);
       gth[i] = s;
     }
 
@@ -327,21 +457,21 @@ __global__ void __launch_bounds__(256) k_main(Geom g, Phys ph, StepArgs<S> A) {
     const S E = U[4 * N + idx];
     const S vel[3] = {PQ[idx], PQ[N + idx], PQ[2 * N + idx]};
     const S T = PQ[3 * N + idx];
-    const S p = S(ph.gm1) * (E - S(0.5) * (m[0] * vel[0] + m[1] * vel[1] + m[2] * vel[2]));
+    const S p = K.gm1 * (E - S(0.5) * (m[0] * vel[0] + m[1] * vel[1] + m[2] * vel[2]));
     const S theta = Ag[0][0] + Ag[1][1] + Ag[2][2];
-    const S mu = S(ph.mu0) * pow(T, S(ph.omega));
-    const S dmudT = S(ph.omega) * mu / T;
-    const S cp_pr = S(ph.cp_over_pr);
-    const S kappa = mu * cp_pr;
+    const S mu = K.mu0 * pow(T, K.omega);
+    const S dmudT = K.omega * mu / T;
+    const S kappa = mu * K.cp_over_pr;
     S dmu[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) dmu[j] = dmudT * dT[j];
 
     S sm[3][3];   // A_ij + A_ji - 2/3 delta_ij theta
+    const S th23 = S(2.0 / 3.0) * theta;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) sm[i][j] = Ag[i][j] + Ag[j][i] - (i == j ? S(2.0 / 3.0) * theta : S(0));
+      for (int j = 0; j < 3; ++j) sm[i][j] = i == j ? S(2) * Ag[i][i] - th23 : Ag[i][j] + Ag[j][i];
 
     // forcing f_c = sum_kx Re(B[kx][c](y,z) exp(i kx x))
     S fo[3] = {S(0), S(0), S(0)};
@@ -355,44 +485,46 @@ __global__ void __launch_bounds__(256) k_main(Geom g, Phys ph, StepArgs<S> A) {
         for (int kx = 0; kx <= A.fK; ++kx) {
           const vec2_t<S> b = A.fB[((long long)kx * 3 + c) * lines + ln];
           const vec2_t<S> e = A.fX[(long long)kx * g.n[0] + x];
-          acc += b.x * e.x - b.y * e.y;
+          acc = fma(b.x, e.x, fma(-b.y, e.y, acc));
         }
         fo[c] = acc;
       }
     }
 
-    S work = S(0), sigS = S(0);
+    // sigma_ij S_ij = mu/2 sum_ij sm_ij (A_ij + A_ji): diagonal terms
+    // sm_ii A_ii, off-diagonal pairs sm_ij^2 (each counted twice, halved)
+    S sS = sm[0][0] * Ag[0][0] + sm[1][1] * Ag[1][1] + sm[2][2] * Ag[2][2];
+    sS = fma(sm[0][1], sm[0][1], sS);
+    sS = fma(sm[0][2], sm[0][2], sS);
+    sS = fma(sm[1][2], sm[1][2], sS);
+    const S sigS = mu * sS;
+    S work = S(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const S lap = d2[i][0] + d2[i][1] + d2[i][2];
-      S V = mu * (lap + gth[i] * S(1.0 / 3.0));
+      S V = mu * fma(gth[i], S(1.0 / 3.0), lap[i]);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) V += dmu[j] * sm[i][j];
-      R[1 + i] += V + r * fo[i];
-      work += vel[i] * V;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) sigS += sm[i][j] * (Ag[i][j] + Ag[j][i]);
+      for (int j = 0; j < 3; ++j) V = fma(dmu[j], sm[i][j], V);
+      R[1 + i] += fma(r, fo[i], V);
+      work = fma(vel[i], V, work);
     }
-    sigS *= S(0.5) * mu;
-    const S lapT = d2[3][0] + d2[3][1] + d2[3][2];
-    R[4] += work + sigS + kappa * lapT + cp_pr * (dmu[0] * dT[0] + dmu[1] * dT[1] + dmu[2] * dT[2]) +
-            r * (fo[0] * vel[0] + fo[1] * vel[1] + fo[2] * vel[2]);
+    S tail = fma(kappa, lap[3], sigS + work);
+    tail = fma(K.cp_over_pr, fma(dmu[0], dT[0], fma(dmu[1], dT[1], dmu[2] * dT[2])), tail);
+    R[4] += fma(r, fma(fo[0], vel[0], fma(fo[1], vel[1], fo[2] * vel[2])), tail);
 
-    // health: rho <= 0, p <= 0, non-finite R
-    if (!(r > S(0))) health |= H_RHO;
-    if (!(p > S(0))) health |= H_P;
+    // health: rho <= 0, p <= 0, non-finite R (bit tests)
+    if (nonpositive(r)) health |= H_RHO;
+    if (nonpositive(p)) health |= H_P;
 #pragma unroll
     for (int v = 0; v < 5; ++v)
       if (nonfinite(R[v])) health |= H_NONFINITE;
 
     if (A.do_update) {
       const S Uo[5] = {r, m[0], m[1], m[2], E};
-      const S dt = S(A.dt);
       S un[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const S inc = A.first ? R[v] : S(1.5) * R[v] - S(0.5) * A.Rprev[v * N + idx];
-        un[v] = Uo[v] + dt * inc;
+        const S inc = A.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * A.Rprev[v * N + idx]);
+        un[v] = fma(K.dt, inc, Uo[v]);
         A.Unext[v * N + idx] = un[v];
         A.Rprev[v * N + idx] = R[v];
         if (nonfinite(un[v])) health |= H_NONFINITE;
@@ -417,7 +549,7 @@ __global__ void __launch_bounds__(256) k_main(Geom g, Phys ph, StepArgs<S> A) {
     }
 
     if (A.do_stats) {
-      const S uu = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
+      const S uu = fma(vel[0], vel[0], fma(vel[1], vel[1], vel[2] * vel[2]));
       const S c = sqrt(T);
       st[ST_RHO] = r;
       st[ST_M0] = m[0];
@@ -429,66 +561,25 @@ __global__ void __launch_bounds__(256) k_main(Geom g, Phys ph, StepArgs<S> A) {
       const S a0 = Ag[0][0], a1 = Ag[1][1], a2 = Ag[2][2];
       const S q0 = a0 * a0, q1 = a1 * a1, q2 = a2 * a2;
       st[ST_G2] = q0 + q1 + q2;
-      st[ST_G3] = q0 * a0 + q1 * a1 + q2 * a2;
-      st[ST_G4] = q0 * q0 + q1 * q1 + q2 * q2;
+      st[ST_G3] = fma(q0, a0, fma(q1, a1, q2 * a2));
+      st[ST_G4] = fma(q0, q0, fma(q1, q1, q2 * q2));
       const S o0 = Ag[2][1] - Ag[1][2], o1 = Ag[0][2] - Ag[2][0], o2 = Ag[1][0] - Ag[0][1];
-      st[ST_ENST] = o0 * o0 + o1 * o1 + o2 * o2;
+      st[ST_ENST] = fma(o0, o0, fma(o1, o1, o2 * o2));
       st[ST_PTHETA] = p * theta;
-      st[ST_FPOW] = r * (fo[0] * vel[0] + fo[1] * vel[1] + fo[2] * vel[2]);
+      st[ST_FPOW] = r * fma(fo[0], vel[0], fma(fo[1], vel[1], fo[2] * vel[2]));
       st[ST_U2] = uu;
       st[ST_C] = c;
-      wmax = fmax(fabs(vel[0]), fmax(fabs(vel[1]), fabs(vel[2]))) + c;
-      rmin = r;
-      pmin = p;
+      // max |u_d| + c: the largest |u_d| chosen by bit pattern (non-negative
+      // values order as integers)
+      const S au[3] = {fabs(vel[0]), fabs(vel[1]), fabs(vel[2])};
+      const long long k0 = okey(au[0]), k1 = okey(au[1]), k2 = okey(au[2]);
+      const S umax = (k0 >= k1 && k0 >= k2) ? au[0] : (k1 >= k2 ? au[1] : au[2]);
+      kwave = okey(umax + c);
+      krho = okey(r);
+      kp = okey(p);
     }
   }
-
-  // block reductions (fixed order: deterministic for a fixed launch shape)
-  __shared__ double sh[8][kNumStat];
-  __shared__ long long shk[8][3];
-  __shared__ unsigned shh[8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned hh = __reduce_or_sync(0xffffffffu, health);
-  if (A.do_stats) {
-#pragma unroll
-    for (int s = 0; s < kNumStat; ++s) st[s] = warp_sum(st[s]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-      rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
-      pmin = fmin(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int s = 0; s < kNumStat; ++s) sh[wid][s] = (double)st[s];
-      shk[wid][0] = ordered_key((double)wmax);
-      shk[wid][1] = ordered_key((double)rmin);
-      shk[wid][2] = ordered_key((double)pmin);
-    }
-  }
-  if (lane == 0) shh[wid] = hh;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = blockDim.x >> 5;
-    unsigned h = 0;
-    for (int w = 0; w < nw; ++w) h |= shh[w];
-    if (h) atomicOr((unsigned*)(A.words + 3), h);
-    if (A.do_stats) {
-      long long kw = LLONG_MIN, kr = LLONG_MAX, kq = LLONG_MAX;
-      for (int w = 0; w < nw; ++w) {
-        kw = max(kw, shk[w][0]); kr = min(kr, shk[w][1]); kq = min(kq, shk[w][2]);
-      }
-      atomicMax((long long*)(A.words + 0), kw);
-      atomicMin((long long*)(A.words + 1), kr);
-      atomicMin((long long*)(A.words + 2), kq);
-    }
-  }
-  if (A.do_stats && threadIdx.x < kNumStat) {
-    const int nw = blockDim.x >> 5;
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
-    A.partial[(long long)blockIdx.x * kNumStat + threadIdx.x] = s;
-  }
+  block_reduce<S>(st, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words);
 }
 
 }  // namespace atdns

@@ -8,36 +8,36 @@ namespace atdns {
 using S = AT_DNS_SCALAR;
 
 template <>
-cudaError_t launch_prim<S>(const Geom& g, const Phys& ph, const S* U, S* PQ, cudaStream_t st) {
+cudaError_t launch_prim<S>(const Geom& g, const Coef<S>& K, const S* U, S* PQ, cudaStream_t st) {
   const unsigned nb = (unsigned)((g.npts + kBlock - 1) / kBlock);
-  k_prim<S><<<nb, kBlock, 0, st>>>(g, ph, U, PQ);
+  k_prim<S><<<nb, kBlock, 0, st>>>(g, K, U, PQ);
   return cudaGetLastError();
 }
 
 template <>
-cudaError_t launch_ghost<S>(const Geom& g, const Phys& ph, const S* U, const S* PQ, S* const GH[3],
+cudaError_t launch_ghost<S>(const Geom& g, const Coef<S>& K, const S* U, const S* PQ, S* const GH[3],
                             S* const ring[3], const uint8_t* dmap, long long n, cudaStream_t st) {
   long long cnt[3];
   for (int d = 0; d < 3; ++d) cnt[d] = g.pes[d] > 1 ? 4LL * g.pes[d] * g.plane[d] : 0;
   const long long tot = cnt[0] + cnt[1] + cnt[2];
   if (tot == 0) return cudaSuccess;
   const unsigned nb = (unsigned)((tot + kBlock - 1) / kBlock);
-  k_ghost<S><<<nb, kBlock, 0, st>>>(g, ph, U, PQ, GH[0], GH[1], GH[2], ring[0], ring[1], ring[2], dmap, n,
+  k_ghost<S><<<nb, kBlock, 0, st>>>(g, K, U, PQ, GH[0], GH[1], GH[2], ring[0], ring[1], ring[2], dmap, n,
                                    cnt[0], cnt[1], cnt[2]);
   return cudaGetLastError();
 }
 
 template <>
-cudaError_t launch_grad<S>(const Geom& g, const S* PQ, S* const GH[3], S* G, cudaStream_t st) {
+cudaError_t launch_grad<S>(const Geom& g, const Coef<S>& K, const S* PQ, S* const GH[3], S* G, cudaStream_t st) {
   const unsigned nb = (unsigned)((g.npts + kBlock - 1) / kBlock);
-  k_grad<S><<<nb, kBlock, 0, st>>>(g, PQ, GH[0], GH[1], GH[2], G);
+  k_grad<S><<<nb, kBlock, 0, st>>>(g, K, PQ, GH[0], GH[1], GH[2], G);
   return cudaGetLastError();
 }
 
 template <>
-cudaError_t launch_main<S>(const Geom& g, const Phys& ph, const StepArgs<S>& a, cudaStream_t st) {
+cudaError_t launch_main<S>(const Geom& g, const Coef<S>& K, const StepArgs<S>& a, cudaStream_t st) {
   const unsigned nb = (unsigned)main_blocks(g);
-  k_main<S><<<nb, kBlock, 0, st>>>(g, ph, a);
+  k_main<S><<<nb, kBlock, 0, st>>>(g, K, a);
   return cudaGetLastError();
 }
 

@@ -8,17 +8,17 @@ namespace atdns {
 constexpr int kBlock = 256;
 
 template <typename S>
-cudaError_t launch_prim(const Geom& g, const Phys& ph, const S* U, S* PQ, cudaStream_t st);
+cudaError_t launch_prim(const Geom& g, const Coef<S>& K, const S* U, S* PQ, cudaStream_t st);
 
 template <typename S>
-cudaError_t launch_ghost(const Geom& g, const Phys& ph, const S* U, const S* PQ, S* const GH[3],
+cudaError_t launch_ghost(const Geom& g, const Coef<S>& K, const S* U, const S* PQ, S* const GH[3],
                          S* const ring[3], const uint8_t* dmap, long long n, cudaStream_t st);
 
 template <typename S>
-cudaError_t launch_grad(const Geom& g, const S* PQ, S* const GH[3], S* G, cudaStream_t st);
+cudaError_t launch_grad(const Geom& g, const Coef<S>& K, const S* PQ, S* const GH[3], S* G, cudaStream_t st);
 
 template <typename S>
-cudaError_t launch_main(const Geom& g, const Phys& ph, const StepArgs<S>& a, cudaStream_t st);
+cudaError_t launch_main(const Geom& g, const Coef<S>& K, const StepArgs<S>& a, cudaStream_t st);
 
 // Number of blocks k_main is launched with (size of the partial-sum array).
 inline long long main_blocks(const Geom& g) { return (g.npts + kBlock - 1) / kBlock; }

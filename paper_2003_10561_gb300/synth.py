@@ -85,9 +85,10 @@ def mu0_for_resolution(n, k0=4.0, mach_t=0.3, seed=0, kmax_eta=1.5):
 
 
 def history(U0, n_levels, eps=1e-3, seed=1):
-    """A smooth synthetic past [U^n, U^{n-1}, ...]: level l is U0 plus l times a
-    small seeded smooth perturbation (used to give delayed levels distinct
-    values in parity tests without running the solver)."""
+    """A smooth synthetic past [U^n, U^{n-1}, ...]: level l is U0 plus (l + 1)
+    times a small seeded smooth perturbation with a compressive part (so that
+    the delayed levels differ and no right-hand side component is degenerate,
+    e.g. a vanishing mass flux divergence of an exactly solenoidal field)."""
     n = (U0.shape[3], U0.shape[2], U0.shape[1])
     dvel = solenoidal_velocity(n, 3.0, 1.0, seed)
     rng = np.random.Generator(np.random.PCG64(seed + 7))
@@ -95,7 +96,12 @@ def history(U0, n_levels, eps=1e-3, seed=1):
     z, y, x = np.meshgrid(*(np.arange(m) * 2 * math.pi / m for m in (n[2], n[1], n[0])), indexing="ij")
     drho = np.sin(x + phase[0]) * np.cos(y + phase[1]) * np.sin(2 * z + phase[2])
     dU = np.empty_like(U0)
+    # irrotational (compressive) velocity part: gradient of a smooth potential
+    a, b, c = phase
+    grad_phi = np.stack([np.cos(x + a) * np.sin(y + b) * np.cos(z + c),
+                         np.sin(x + a) * np.cos(y + b) * np.cos(z + c),
+                         -np.sin(x + a) * np.sin(y + b) * np.sin(z + c)])
     dU[0] = 0.05 * drho
-    dU[1:4] = dvel * 0.1
+    dU[1:4] = dvel * 0.1 + 0.2 * grad_phi
     dU[4] = 0.1 * drho
-    return [U0 + (l * eps) * dU for l in range(n_levels)]
+    return [U0 + ((l + 1) * eps) * dU for l in range(n_levels)]

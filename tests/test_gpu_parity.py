@@ -197,7 +197,13 @@ def _sample_points(n, nloc, rng, count):
     return sorted(pts)
 
 
-@pytest.mark.parametrize("precision,tol", [("p64", 1e-12), ("p32", 2e-4)])
+# Tolerance at 256^3: the per-RHS bounds above hold at the 32^3 parity grid.
+# Rounding in a first-derivative stencil is relative to its terms, which grow
+# as 1/dx relative to the derivative (8x from 32^3 to 256^3), and second
+# derivatives as 1/dx^2 but carry the small coefficients mu and k; the bounds
+# are scaled by the 8x of the first derivatives plus margin: 1e-11 (FP64) and
+# 2e-3 (FP32).
+@pytest.mark.parametrize("precision,tol", [("p64", 1e-11), ("p32", 2e-3)])
 def test_full_size_sampled_parity(lib, precision, tol):
     """256^3 with 8x8x8 PEs (the benchmark workload), random delays with L = 2,
     at a step past the start-up: sampled points against the brute-force
