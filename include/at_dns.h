@@ -54,6 +54,7 @@ extern "C" {
 #define AT_DNS_E_UNSTABLE     -4   /* NaN/Inf, rho <= 0 or p <= 0 seen in a step */
 #define AT_DNS_E_UNSUPPORTED  -5   /* a combination the library does not run */
 #define AT_DNS_E_STATE        -6   /* no state has been set yet */
+#define AT_DNS_E_TOO_LARGE    -7   /* problem above a fixed size limit (at_dns_rhs_noalloc) */
 
 /* delay modes (Sec. 3.1) */
 #define AT_DNS_SYNC      0   /* k = 0 on every face: standard scheme */
@@ -206,6 +207,34 @@ int at_dns_kernel_times(at_dns_t* h, at_dns_kernel_time_t* out, int32_t max, int
 
 /* Block until all work queued on the handle's stream has finished. */
 int at_dns_synchronize(at_dns_t* h);
+
+/* Largest n[0]*n[1]*n[2] accepted by at_dns_rhs_noalloc (64^3). */
+#define AT_DNS_NOALLOC_MAX_POINTS 262144
+
+/* Right-hand side R(U) without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc (code running
+ * while another component owns all device memory, code inside a region that
+ * must not allocate or synchronise, plugins in processes that forbid new
+ * allocations after start-up).
+ *
+ * Computes, in FP64 on the current device, the same right-hand side as
+ * at_dns_rhs for a single PE (periodic box, no PE faces, hence no delays), no
+ * forcing, with the physics parameters given here: u_dev is the state and
+ * rhs_dev receives R, both device pointers to 5*n0*n1*n2 doubles in the
+ * layout above; stream is a cudaStream_t (NULL = legacy default stream).
+ * The work is queued on that stream and the call returns without waiting.
+ *
+ * Work arrays come from one file-scope device array of fixed size (about
+ * 59 MB, held by every GPU that loads the library until the process exits);
+ * no allocation is made.  Its device address is looked up on the first call
+ * on each device (make that first call before any stream capture).  All
+ * calls on a device share that array and it keeps the last call's contents:
+ * calls whose work can overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.
+ * Errors: INVALID_ARG (NULL pointer, n[d] < 5, bad physics values),
+ * TOO_LARGE (n0*n1*n2 > AT_DNS_NOALLOC_MAX_POINTS), CUDA. */
+int at_dns_rhs_noalloc(const int32_t n[3], double gamma, double prandtl, double mu0, double visc_exp,
+                       const double* u_dev, double* rhs_dev, void* stream);
 
 /* Text of the last error on this handle ("" if none); a NULL handle gives the
  * last error of a failed at_dns_create on this thread.  Valid until the next

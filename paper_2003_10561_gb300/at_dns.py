@@ -19,6 +19,8 @@ AT_DNS_E_CUDA = -3
 AT_DNS_E_UNSTABLE = -4
 AT_DNS_E_UNSUPPORTED = -5
 AT_DNS_E_STATE = -6
+AT_DNS_E_TOO_LARGE = -7
+AT_DNS_NOALLOC_MAX_POINTS = 262144
 
 AT_DNS_SYNC, AT_DNS_PERIODIC, AT_DNS_RANDOM = 0, 1, 2
 AT_DNS_P64, AT_DNS_P32 = 0, 1
@@ -88,6 +90,8 @@ _SIGS = {
     "at_dns_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(at_dns_kernel_time_t), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]),
     "at_dns_synchronize": (ctypes.c_int, [_P]),
+    "at_dns_rhs_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, _P, _P, _P]),
     "at_dns_last_error": (ctypes.c_char_p, [_P]),
     "at_dns_destroy": (None, [_P]),
 }
@@ -220,6 +224,21 @@ def at_dns_kernel_times(h):
 
 def at_dns_synchronize(h):
     _check(load().at_dns_synchronize(h), h)
+
+
+def at_dns_rhs_noalloc(n, gamma, prandtl, mu0, visc_exp, u_dev, rhs_dev, stream=None):
+    """R(U) for one PE without device allocation (see include/at_dns.h): for
+    callers that cannot allocate device memory.  u_dev and rhs_dev are CUDA
+    float64 tensors of 5*n0*n1*n2 elements; the work is queued on `stream`."""
+    cnt = 5 * int(n[0]) * int(n[1]) * int(n[2])
+    pu, wu = _ptr(u_dev, cnt)
+    pr, wr = _ptr(rhs_dev, cnt, writable=True)
+    if wu != AT_DNS_DEVICE or wr != AT_DNS_DEVICE:
+        raise TypeError("at_dns_rhs_noalloc takes device tensors")
+    nn = (ctypes.c_int32 * 3)(*(int(v) for v in n))
+    rc = load().at_dns_rhs_noalloc(nn, gamma, prandtl, mu0, visc_exp, pu, pr, stream)
+    if rc != AT_DNS_OK:
+        raise AtDnsError(rc, "at_dns_rhs_noalloc failed")
 
 
 def at_dns_last_error(h=None):
