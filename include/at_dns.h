@@ -63,7 +63,7 @@ extern "C" {
 
 /* precision forms */
 #define AT_DNS_P64  0        /* FP64 storage and arithmetic */
-#define AT_DNS_P32  1        /* FP32 state/stencils; FP64 update, ring and reductions */
+#define AT_DNS_P32  1        /* FP32 state, stencils, update and ring; FP64 reductions */
 
 /* pointer locations */
 #define AT_DNS_HOST    0
