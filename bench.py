@@ -163,8 +163,8 @@ def workload_config(world):
             "l2": "working set %.1f GB >> 129 MB L2; no flush needed" % (N ** 3 * 5 * 8 * 12 / 1e9)}
 
 
-def make_solver(at_dns, precision, stream, mu0):
-    return at_dns.Solver(n=(N, N, N), pes=(PES, PES, PES), precision=precision, stream=stream,
+def make_solver(at_dns, precision, stream, mu0, path="auto"):
+    return at_dns.Solver(n=(N, N, N), pes=(PES, PES, PES), precision=precision, stream=stream, path=path,
                          gamma=1.4, prandtl=0.7, visc_exp=0.76, mu0=mu0, cfl=CFL_AT, dt=0.0,
                          max_delay=L, seed=SEED, stats_every=1)
 
@@ -199,6 +199,7 @@ def main():
     ap.add_argument("--grid", type=int, default=N, help="points per direction (profiling cases)")
     ap.add_argument("--pes", type=int, default=PES, help="virtual PEs per direction")
     ap.add_argument("--precision", default="both", choices=["both", "p64", "p32"])
+    ap.add_argument("--path", default="auto", choices=["auto", "multipass", "fused"])
     args = ap.parse_args()
     set_workload(args.grid, args.pes)
     args.warmup = max(args.warmup, 3)
@@ -226,7 +227,7 @@ def main():
                     if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_rank%d.csv" % rank)
     precs = ("p64", "p32") if args.precision == "both" else (args.precision,)
     for prec in precs:
-        s = make_solver(at_dns, prec, stream.cuda_stream, mu0)
+        s = make_solver(at_dns, prec, stream.cuda_stream, mu0, args.path)
         s.set_state(U0)
         s.step(at_dns.at_dns_get_info(s.h).n_levels + 1, "random")   # past the synchronous start-up
         if pg:
@@ -242,6 +243,7 @@ def main():
         ms = float(t.item())
         st = s.stats()
         res[prec] = {"ms": ms, "kt": kt, "stats": st, "info": s.info()}
+        res[prec]["path"] = "fused" if res[prec]["info"]["kernel_path"] == at_dns.AT_DNS_PATH_FUSED else "multipass"
         # end to end through the public API with host buffers: per step, upload
         # U^n from pinned host memory (as the state of step n), step, read the
         # statistics record back
@@ -291,6 +293,7 @@ def main():
         "clocks": clocks.summary(local),
         "gpu_launches": launches,
         "rhs_per_s": value,
+        "kernel_path": head["path"],
     }
     if p64:
         main64 = p64["kt"].get("main", (1, 1.0))
@@ -307,7 +310,7 @@ def main():
         ach32 = algorithmic_bytes(4) * pts / t_main32 / 1e9
         r32 = {"bound": "hbm", "kernel": "k_main (FP32)", "achieved": ach32, "peak": pk.get("hbm_gbs"),
                "unit": "GB/s", "frac": ach32 / pk.get("hbm_gbs", 6800.0), "traffic": None}
-        blk = {"value": world * pts * args.steps / (p32["ms"] / 1e3), "unit": UNIT,
+        blk = {"value": world * pts * args.steps / (p32["ms"] / 1e3), "unit": UNIT, "kernel_path": p32["path"],
                "ms_per_step": p32["ms"] / args.steps, "dtype": "f32", "roofline": r32,
                "kernel_ms_per_step": {k: v[1] / v[0] for k, v in p32["kt"].items()}}
         if p64:

@@ -92,7 +92,18 @@ typedef struct {
   int32_t  precision;    /* AT_DNS_P64 or AT_DNS_P32                                    */
   int32_t  stats_every;  /* 1: reduce statistics in every step; 0: only on request      */
   void*    stream;       /* cudaStream_t to run on; NULL = the legacy default stream    */
+  int32_t  kernel_path;  /* AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS or AT_DNS_PATH_FUSED */
 } at_dns_config_t;
+
+/* kernel paths (same results up to rounding): the multi-pass path stores
+ * derived fields and gradients between kernels; the fused path does one pass
+ * over U per step on PE-aligned tiles (needs the per-direction PE extent, or
+ * the grid extent where a direction has one PE, to be a multiple of 8 and the
+ * tile to hold a multiple of 32 points).  AUTO takes the multi-pass path,
+ * which is the faster one on GB300 at the benchmark workload. */
+#define AT_DNS_PATH_AUTO       0
+#define AT_DNS_PATH_MULTIPASS  1
+#define AT_DNS_PATH_FUSED      2
 
 typedef struct {
   int64_t step;          /* n of the state the statistics describe                      */
@@ -121,6 +132,8 @@ typedef struct {
   double  boundary_fraction;  /* N_B / N_T per PE, Eqs. (NT)-(NB)                       */
   size_t  device_bytes;  /* device memory held by the handle                            */
   int32_t kernels_per_step;   /* kernel launches of one at_dns_step step                */
+  int32_t kernel_path;   /* path in use: AT_DNS_PATH_MULTIPASS or AT_DNS_PATH_FUSED     */
+  int32_t tile[3];       /* fused path: TX, TY, planes per CTA (0 on the multi-pass path)*/
 } at_dns_info_t;
 
 /* Fill *cfg with defaults: 32^3, one PE, gamma 1.4, Pr 0.7, omega 0.76,

@@ -25,6 +25,8 @@ AT_DNS_NOALLOC_MAX_POINTS = 262144
 AT_DNS_SYNC, AT_DNS_PERIODIC, AT_DNS_RANDOM = 0, 1, 2
 AT_DNS_P64, AT_DNS_P32 = 0, 1
 AT_DNS_HOST, AT_DNS_DEVICE = 0, 1
+AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS, AT_DNS_PATH_FUSED = 0, 1, 2
+PATHS = {"auto": AT_DNS_PATH_AUTO, "multipass": AT_DNS_PATH_MULTIPASS, "fused": AT_DNS_PATH_FUSED}
 
 MODES = {"sync": AT_DNS_SYNC, "periodic": AT_DNS_PERIODIC, "random": AT_DNS_RANDOM}
 PRECISIONS = {"p64": AT_DNS_P64, "p32": AT_DNS_P32}
@@ -39,6 +41,7 @@ class at_dns_config_t(ctypes.Structure):
         ("forcing", ctypes.c_int32), ("kf", ctypes.c_double), ("f_amp", ctypes.c_double),
         ("f_tcorr", ctypes.c_double), ("f_seed", ctypes.c_uint64),
         ("precision", ctypes.c_int32), ("stats_every", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("kernel_path", ctypes.c_int32),
     ]
 
 
@@ -67,6 +70,7 @@ class at_dns_info_t(ctypes.Structure):
         ("step", ctypes.c_int64), ("time", ctypes.c_double), ("dt", ctypes.c_double),
         ("n_levels", ctypes.c_int32), ("boundary_fraction", ctypes.c_double),
         ("device_bytes", ctypes.c_size_t), ("kernels_per_step", ctypes.c_int32),
+        ("kernel_path", ctypes.c_int32), ("tile", ctypes.c_int32 * 3),
     ]
 
 
@@ -253,8 +257,9 @@ def at_dns_destroy(h):
 class Solver:
     """Owns one handle; methods map one-to-one onto the C ABI."""
 
-    def __init__(self, n=(32, 32, 32), pes=(1, 1, 1), precision="p64", stream=None, **kw):
+    def __init__(self, n=(32, 32, 32), pes=(1, 1, 1), precision="p64", stream=None, path="auto", **kw):
         cfg = at_dns_config_default()
+        cfg.kernel_path = PATHS[path] if isinstance(path, str) else int(path)
         for d in range(3):
             cfg.n[d] = int(n[d])
             cfg.pes[d] = int(pes[d])
@@ -310,7 +315,9 @@ class Solver:
 
     def info(self):
         i = at_dns_get_info(self.h)
-        return {name: getattr(i, name) for name, _ in i._fields_}
+        out = {name: getattr(i, name) for name, _ in i._fields_}
+        out["tile"] = list(i.tile)
+        return out
 
     def synchronize(self):
         at_dns_synchronize(self.h)

@@ -55,6 +55,10 @@ struct at_dns {
   double stats_time = 0.0;
   size_t bytes = 0;
   std::string err;
+  // kernel path: fused single pass on TX x TY tiles marching ZC planes, or multi-pass
+  bool fused = false;
+  int TX = 0, TY = 0, ZC = 0;
+  long long nblk_step = 0;     // blocks of the kernel that writes the statistics partials
   // per-kernel event timing
   bool prof = false;
   struct Rec { int kind; cudaEvent_t a, b; };
@@ -368,12 +372,12 @@ struct Ops {
     const Coef<S> K = make_coef<S>(g, h->ph, h->dt);
     S* GH[3] = {(S*)h->GH[0], (S*)h->GH[1], (S*)h->GH[2]};
     S* ring[3] = {(S*)h->ring[0], (S*)h->ring[1], (S*)h->ring[2]};
-    { Timed t(h, KD_PRIM); CK(launch_prim<S>(g, K, Ucur, (S*)h->PQ, h->st)); }
+    if (!h->fused) { Timed t(h, KD_PRIM); CK(launch_prim<S>(g, K, Ucur, (S*)h->PQ, h->st)); }
     if (g.pes[0] > 1 || g.pes[1] > 1 || g.pes[2] > 1) {
       Timed t(h, KD_GHOST);
-      CK(launch_ghost<S>(g, K, Ucur, (S*)h->PQ, GH, ring, h->dmap, h->n, h->st));
+      CK(launch_ghost<S>(g, K, Ucur, h->fused ? nullptr : (S*)h->PQ, GH, ring, h->dmap, h->n, h->st));
     }
-    { Timed t(h, KD_GRAD); CK(launch_grad<S>(g, K, (S*)h->PQ, GH, (S*)h->G, h->st)); }
+    if (!h->fused) { Timed t(h, KD_GRAD); CK(launch_grad<S>(g, K, (S*)h->PQ, GH, (S*)h->G, h->st)); }
     if (h->cfg.forcing) {
       const long long lines = (long long)g.n[2] * g.n[1];
       {
@@ -403,9 +407,15 @@ struct Ops {
     a.first = h->first ? 1 : 0;
     a.do_update = update ? 1 : 0;
     a.do_stats = stats ? 1 : 0;
-    { Timed t(h, KD_MAIN); CK(launch_main<S>(g, K, a, h->st)); }
+    if (h->fused) {
+      Timed t(h, KD_MAIN);
+      CK(launch_fused<S>(g, K, a, h->TX, h->TY, h->ZC, h->st));
+    } else {
+      Timed t(h, KD_MAIN);
+      CK(launch_main<S>(g, K, a, h->st));
+    }
     if (stats) {
-      { Timed t(h, KD_STATS); k_stats_final<<<kNumStat, 256, 0, h->st>>>(h->partial, main_blocks(g), h->sums); }
+      { Timed t(h, KD_STATS); k_stats_final<<<kNumStat, 256, 0, h->st>>>(h->partial, h->nblk_step, h->sums); }
       CK(cudaGetLastError());
       h->stats_valid = true;
       h->stats_step = h->n;
@@ -438,6 +448,27 @@ struct Ops {
     return AT_DNS_OK;
   }
 };
+
+// Tile shape of the fused path, or false if it does not apply: tiles must not
+// straddle PE faces, hold a multiple of 32 points (at most 256) and be at least
+// 8 wide in x and y (the one-sided mixed stencils reach 4 points into a PE).
+bool pick_fused_shape(const Geom& g, int& TX, int& TY, int& ZC) {
+  int ext[3];
+  for (int d = 0; d < 3; ++d) ext[d] = g.pes[d] > 1 ? g.nl[d] : g.n[d];
+  TX = TY = ZC = 0;
+  for (int t : {32, 16, 8})
+    if (ext[0] % t == 0) { TX = t; break; }
+  if (!TX) return false;
+  // compiled tile shapes: 32x8, 16x16, 16x8, 8x32, 8x16, 8x8
+  for (int t : {32, 16, 8})
+    if (TX * t <= 256 && (TX * t) % 32 == 0 && ext[1] % t == 0 && !(TX == 32 && t != 8)) { TY = t; break; }
+  if (!TY) return false;
+  if (ext[2] <= 64) ZC = ext[2];
+  else
+    for (int t = 64; t >= 8; --t)
+      if (ext[2] % t == 0) { ZC = t; break; }
+  return ZC > 0;
+}
 
 int force_reset(at_dns* h, long long step) {
   if (!h->cfg.forcing) return AT_DNS_OK;
@@ -521,6 +552,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     else if (c.forcing && (!(c.kf >= 1.0) || c.kf > kMaxKf)) bad = "kf must be in [1, 4]";
     else if (c.forcing && !(c.f_tcorr > 0)) bad = "f_tcorr must be > 0";
     else if (c.stats_every != 0 && c.stats_every != 1) bad = "stats_every must be 0 or 1";
+    else if (c.kernel_path < 0 || c.kernel_path > 2) bad = "unknown kernel_path";
   }
   if (!bad.empty()) { g_create_error = bad; return AT_DNS_E_INVALID_ARG; }
 
@@ -562,10 +594,24 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   const size_t S = h->ssize;
   const size_t N = (size_t)g.npts;
   int rc;
+  const bool can_fuse = pick_fused_shape(g, h->TX, h->TY, h->ZC);
+  if (c.kernel_path == AT_DNS_PATH_FUSED && !can_fuse) {
+    h->err = "the fused path needs PE (or grid) extents that are multiples of 8 in x and y";
+    return create_fail(h, AT_DNS_E_UNSUPPORTED);
+  }
+  // AUTO takes the multi-pass path: it is the faster one on GB300 in both
+  // precisions at the benchmark workload (FP64 is bound by the FP64 pipe, where
+  // the fused path's halo recompute costs more than the work arrays' traffic)
+  h->fused = can_fuse && c.kernel_path == AT_DNS_PATH_FUSED;
+  if (!h->fused) h->TX = h->TY = h->ZC = 0;
+  h->nblk_step = h->fused ? (long long)(g.n[0] / h->TX) * (g.n[1] / h->TY) * (g.n[2] / h->ZC) : main_blocks(g);
   if ((rc = dev_alloc(h, &h->U[0], 5 * N * S)) || (rc = dev_alloc(h, &h->U[1], 5 * N * S)) ||
-      (rc = dev_alloc(h, &h->PQ, (size_t)kNumQ * N * S)) || (rc = dev_alloc(h, &h->G, (size_t)kNumGrad * N * S)) ||
       (rc = dev_alloc(h, &h->Rprev, 5 * N * S)) || (rc = dev_alloc(h, (void**)&h->stage, 5 * N * sizeof(double))))
     return create_fail(h, rc);
+  if (!h->fused) {
+    if ((rc = dev_alloc(h, &h->PQ, (size_t)kNumQ * N * S)) || (rc = dev_alloc(h, &h->G, (size_t)kNumGrad * N * S)))
+      return create_fail(h, rc);
+  }
   for (int d = 0; d < 3; ++d) {
     if (g.pes[d] == 1) continue;
     const size_t gpts = 4ull * g.pes[d] * (size_t)g.plane[d];
@@ -575,7 +621,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   }
   const int P = g.pes[0] * g.pes[1] * g.pes[2];
   if ((rc = dev_alloc(h, (void**)&h->dmap, (size_t)P * 6)) ||
-      (rc = dev_alloc(h, (void**)&h->partial, (size_t)main_blocks(g) * kNumStat * sizeof(double))) ||
+      (rc = dev_alloc(h, (void**)&h->partial, (size_t)h->nblk_step * kNumStat * sizeof(double))) ||
       (rc = dev_alloc(h, (void**)&h->sums, kNumStat * sizeof(double))) ||
       (rc = dev_alloc(h, (void**)&h->words, 4 * sizeof(unsigned long long))))
     return create_fail(h, rc);
@@ -789,7 +835,12 @@ int at_dns_get_info(at_dns_t* h, at_dns_info_t* out) {
   out->boundary_fraction = (double)(nt - ni) / (double)nt;
   out->device_bytes = h->bytes;
   const bool ghost = h->g.pes[0] > 1 || h->g.pes[1] > 1 || h->g.pes[2] > 1;
-  out->kernels_per_step = 5 + (ghost ? 1 : 0) + (h->cfg.stats_every ? 1 : 0) + (h->cfg.forcing ? 2 : 0);
+  out->kernels_per_step = (h->fused ? 3 : 5) + (ghost ? 1 : 0) + (h->cfg.stats_every ? 1 : 0) +
+                          (h->cfg.forcing ? 2 : 0);
+  out->kernel_path = h->fused ? AT_DNS_PATH_FUSED : AT_DNS_PATH_MULTIPASS;
+  out->tile[0] = h->TX;
+  out->tile[1] = h->TY;
+  out->tile[2] = h->ZC;
   return AT_DNS_OK;
 }
 

@@ -53,6 +53,7 @@ struct Coef {
   S a0[3], a1[3], a2[3];   // D2 = a0 f + a1 (f[+1]+f[-1]) + a2 (f[+2]+f[-2])
   S h12[3];                // 1/(12 dx) for the one-sided stencils
   S gamma, gm1, mu0, omega, cp_over_pr;
+  S inv_gamma;
   S dt;
 };
 
@@ -72,6 +73,7 @@ inline Coef<S> make_coef(const Geom& g, const Phys& ph, double dt) {
   c.mu0 = (S)ph.mu0;
   c.omega = (S)ph.omega;
   c.cp_over_pr = (S)ph.cp_over_pr;
+  c.inv_gamma = (S)(1.0 / ph.gamma);
   c.dt = (S)dt;
   return c;
 }

@@ -117,11 +117,21 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
     c[d] = cd;
     const long long src = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
     const long long N = g.npts;
-    out[0] = U[(1 + d) * N + src];
+    if (PQ) {
+      // the derived fields of level n already exist (multi-pass path)
+      out[0] = U[(1 + d) * N + src];
 #pragma unroll
-    for (int e = 1; e < 5; ++e) out[e * qstride] = PQ[(4 + 4 * d + e - 1) * N + src];
+      for (int e = 1; e < 5; ++e) out[e * qstride] = PQ[(4 + 4 * d + e - 1) * N + src];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) out[(5 + q) * qstride] = PQ[q * N + src];
+      for (int q = 0; q < 4; ++q) out[(5 + q) * qstride] = PQ[q * N + src];
+    } else {
+      S Uv[5], q[kNumGhostQ];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Uv[v] = U[v * N + src];
+      ghost_quantities(K, d, Uv, q);
+#pragma unroll
+      for (int qq = 0; qq < kNumGhostQ; ++qq) out[qq * qstride] = q[qq];
+    }
     return;
   }
   const int nbr = slot < 2 ? (ped - 1 + P) % P : (ped + 1) % P;
@@ -317,29 +327,42 @@ __device__ __forceinline__ long long okey(float v) {
   return (long long)(b ^ ((b >> 31) & 0x7FFFFFFF));
 }
 
-// Per-block reduction of the kNumStat per-point sums (fixed order) into
+// Per-block reduction of the kNumStat per-thread sums (fixed order) into
 // partial[block], and of the max/min keys and health bits into the global
-// words.  FP64 form: through shared memory, 16 partial sums per statistic
-// (a warp-shuffle tree would cost every lane 5 FP64 adds per statistic).
-// FP32 form: warp sums in FP32, then FP64 across the warps of the block.
+// words.  Blocks have a multiple of 32 threads, at most 256.  FP64 values go
+// through shared memory: each statistic in 16 partial sums of 16 threads, then
+// one sum of the 16 (a warp-shuffle tree would cost every lane 5 FP64 adds per
+// statistic).  FP32 values are summed within a warp in FP32 first.
+constexpr int kReduceScratchDoubles = kNumStat * 257;
+
+// scratch: at least kReduceScratchDoubles doubles of shared memory that no
+// other thread of the block still reads (k_fused passes its dead window).
 template <typename S>
 __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave, long long krho, long long kp,
                                              unsigned health, bool do_stats, double* partial,
-                                             unsigned long long* words) {
-  constexpr int kThreads = 256, kWarps = kThreads / 32;
-  __shared__ double sh[kNumStat][kThreads + 1];
-  __shared__ long long shk[kWarps][3];
-  __shared__ unsigned shh[kWarps];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+                                             unsigned long long* words, double* scratch) {
+  constexpr int kMaxThreads = 256, kMaxWarps = kMaxThreads / 32;
+  double (*sh)[kMaxThreads + 1] = reinterpret_cast<double (*)[kMaxThreads + 1]>(scratch);
+  __shared__ long long shk[kMaxWarps][3];
+  __shared__ unsigned shh[kMaxWarps];
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int nwarps = nthreads >> 5;
+  const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   const unsigned hh = __reduce_or_sync(0xffffffffu, health);
+  const bool by_warp = sizeof(S) == 4;
   if (do_stats) {
     kwave = warp_max(kwave);
     krho = warp_min(krho);
     kp = warp_min(kp);
     if (lane == 0) { shk[wid][0] = kwave; shk[wid][1] = krho; shk[wid][2] = kp; }
-    if (sizeof(S) == 8) {
+    if (!by_warp) {
 #pragma unroll
       for (int s = 0; s < kNumStat; ++s) sh[s][tid] = (double)st[s];
+      for (int j = nthreads + tid; j < kMaxThreads; j += nthreads)
+#pragma unroll
+        for (int s = 0; s < kNumStat; ++s) sh[s][j] = 0.0;
     } else {
 #pragma unroll
       for (int s = 0; s < kNumStat; ++s) {
@@ -352,11 +375,11 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
   __syncthreads();
   if (tid == 0) {
     unsigned h = 0;
-    for (int w = 0; w < kWarps; ++w) h |= shh[w];
+    for (int w = 0; w < nwarps; ++w) h |= shh[w];
     if (h) atomicOr((unsigned*)(words + 3), h);
     if (do_stats) {
       long long kw = LLONG_MIN, kr = LLONG_MAX, kq = LLONG_MAX;
-      for (int w = 0; w < kWarps; ++w) {
+      for (int w = 0; w < nwarps; ++w) {
         kw = max(kw, shk[w][0]); kr = min(kr, shk[w][1]); kq = min(kq, shk[w][2]);
       }
       atomicMax((long long*)(words + 0), kw);
@@ -365,23 +388,27 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
     }
   }
   if (!do_stats) return;
-  if (sizeof(S) == 8) {
-    // 16 lanes per statistic, each summing 16 consecutive values, then a
-    // 16-lane shuffle tree
-    if (tid < kNumStat * 16) {
-      const int s = tid >> 4, part = tid & 15;
+  if (!by_warp) {
+    // 16 consecutive entries per (statistic, part), written back in place
+    for (int j = tid; j < kNumStat * 16; j += nthreads) {
+      const int s = j >> 4, part = j & 15;
       double a = 0.0;
 #pragma unroll
       for (int q = 0; q < 16; ++q) a += sh[s][part * 16 + q];
+      sh[s][part * 16] = a;
+    }
+    __syncthreads();
+    for (int s = tid; s < kNumStat; s += nthreads) {
+      double a = 0.0;
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o, 16);
-      if (part == 0) partial[(long long)blockIdx.x * kNumStat + s] = a;
+      for (int part = 0; part < 16; ++part) a += sh[s][part * 16];
+      partial[blk * kNumStat + s] = a;
     }
   } else {
-    if (tid < kNumStat) {
+    for (int s = tid; s < kNumStat; s += nthreads) {
       double a = 0.0;
-      for (int w = 0; w < kWarps; ++w) a += sh[tid][w];
-      partial[(long long)blockIdx.x * kNumStat + tid] = a;
+      for (int w = 0; w < nwarps; ++w) a += sh[s][w];
+      partial[blk * kNumStat + s] = a;
     }
   }
 }
@@ -579,7 +606,8 @@ __global__ void __launch_bounds__(256) k_main(Geom g, Coef<S> K, StepArgs<S> A) 
       kp = okey(p);
     }
   }
-  block_reduce<S>(st, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words);
+  __shared__ double red_scratch[kReduceScratchDoubles];
+  block_reduce<S>(st, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words, red_scratch);
 }
 
 }  // namespace atdns

@@ -1,0 +1,457 @@
+// Fused AT-DNS step kernel: one pass over U per step.
+//
+// A CTA owns a TX x TY tile of one PE in x and y and marches in z through a
+// chunk of ZC planes of one PE.  A shared-memory window holds nine planes
+// (z-4 .. z+4) of six per-point fields -- u, v, w, T, rho, H = E + p -- on the
+// tile plus a two-cell halo in x and y.  Halo cells beyond a PE face hold the
+// AT ghost values of that direction (Table B extrapolation done by k_ghost),
+// planes beyond a PE z-face hold the z ghosts, so every stencil of Sec. 2.1 is
+// a plain read of the window:
+//   * first / second derivatives of u, v, w, T in x, y, z;
+//   * inviscid fluxes recomputed from (rho, u, v, w, T, H) at window cells, or
+//     read from the ghost arrays across a PE face;
+//   * mixed derivatives: the central cross stencil D_a(D_b f) inside, and at
+//     PE-boundary points the average of the PE-local derivative in a of the AT
+//     derivative in b and vice versa -- the inner AT derivatives are formed from
+//     the window on the fly (the one-sided reach of 4 planes in z is why the
+//     window is nine planes deep).
+// Then the assembly, forcing, AB2 update, ring write and statistics of k_main.
+// No per-point work arrays (derived fields, gradients) exist on this path.
+//
+// The tile shape is a template parameter so that every window access is one
+// shared-memory load at a constant offset from one of nine per-plane bases.
+#pragma once
+#include "kernels.cuh"
+
+namespace atdns {
+
+constexpr int kWinPlanes = 9;
+constexpr int kWinFields = 6;
+enum WinField { WF_U = 0, WF_V, WF_W, WF_T, WF_R, WF_H };
+
+template <int TX, int TY>
+struct TileShape {
+  static constexpr int CX = TX + 4, CY = TY + 4, CELLS = CX * CY;
+  static constexpr int PLANE = kWinFields * CELLS;     // elements per window plane
+  static constexpr int THREADS = TX * TY;
+};
+
+template <typename S>
+inline size_t fused_smem_bytes(int TX, int TY) {
+  const size_t win = (size_t)kWinPlanes * kWinFields * (TX + 4) * (TY + 4) * sizeof(S);
+  const size_t red = (size_t)kReduceScratchDoubles * sizeof(double);
+  return win > red ? win : red;
+}
+
+__device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
+// Geometry of one CTA: tile origin, PE of the tile (z: of the chunk), PE origin.
+struct FusedGeo {
+  int x0, y0, pe[3], base[3];
+  __device__ __forceinline__ bool beyond(const Geom& g, int d, int c) const {
+    if (g.pes[d] == 1) return false;
+    const int l = c - base[d];
+    return l < 0 || l >= g.nl[d];
+  }
+  __device__ __forceinline__ int ghost_slot(const Geom& g, int d, int c) const {
+    const int l = c - base[d];
+    return l < 0 ? l + 2 : 2 + (l - g.nl[d]);
+  }
+};
+
+// Fill window plane zp (stored at element offset `pbase`).
+template <typename S, int TX, int TY>
+__device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K, const StepArgs<S>& A,
+                                                 const FusedGeo& F, S* win, int pbase, int zp) {
+  using T_ = TileShape<TX, TY>;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const long long N = g.npts;
+  const bool bz = F.beyond(g, 2, zp);
+  const int lz = zp - F.base[2];
+  const bool zfar = bz && (lz < -2 || lz >= g.nl[2] + 2);
+#pragma unroll
+  for (int c0 = 0; c0 < T_::CELLS; c0 += T_::THREADS) {
+    const int c = c0 + tid;
+    if (c >= T_::CELLS) break;
+    const int cy = c / T_::CX, cx = c - cy * T_::CX;
+    const int xg = F.x0 - 2 + cx, yg = F.y0 - 2 + cy;
+    const bool bx = F.beyond(g, 0, xg), by = F.beyond(g, 1, yg);
+    S u = S(0), v = S(0), w = S(0), T = S(0), r = S(0), H = S(0);
+    const S* gh = nullptr;
+    long long gi = 0, qs = 0;
+    if (bz) {
+      if (!zfar && !bx && !by) {
+        const int xw = wrapc(xg, g.n[0]), yw = wrapc(yg, g.n[1]);
+        gh = A.GH[2];
+        qs = 4LL * g.pes[2] * g.plane[2];
+        gi = (long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] + (long long)yw * g.n[0] + xw;
+      }
+    } else if (bx) {
+      if (!by) {
+        const int yw = wrapc(yg, g.n[1]), zw = wrapc(zp, g.n[2]);
+        gh = A.GH[0];
+        qs = 4LL * g.pes[0] * g.plane[0];
+        gi = (long long)(4 * F.pe[0] + F.ghost_slot(g, 0, xg)) * g.plane[0] + (long long)zw * g.n[1] + yw;
+      }
+    } else if (by) {
+      const int xw = wrapc(xg, g.n[0]), zw = wrapc(zp, g.n[2]);
+      gh = A.GH[1];
+      qs = 4LL * g.pes[1] * g.plane[1];
+      gi = (long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] + (long long)zw * g.n[0] + xw;
+    } else {
+      const int xw = wrapc(xg, g.n[0]), yw = wrapc(yg, g.n[1]), zw = wrapc(zp, g.n[2]);
+      const long long idx = ((long long)zw * g.n[1] + yw) * g.n[0] + xw;
+      const S* U = A.U;
+      r = U[idx];
+      const S m0 = U[N + idx], m1 = U[2 * N + idx], m2 = U[3 * N + idx], E = U[4 * N + idx];
+      const S inv = S(1) / r;
+      u = m0 * inv;
+      v = m1 * inv;
+      w = m2 * inv;
+      const S p = K.gm1 * (E - S(0.5) * (m0 * u + m1 * v + m2 * w));
+      T = K.gamma * p * inv;
+      H = E + p;
+    }
+    if (gh) {
+      u = gh[5 * qs + gi];
+      v = gh[6 * qs + gi];
+      w = gh[7 * qs + gi];
+      T = gh[8 * qs + gi];
+    }
+    S* cell = win + pbase + c;
+    cell[WF_U * T_::CELLS] = u;
+    cell[WF_V * T_::CELLS] = v;
+    cell[WF_W * T_::CELLS] = w;
+    cell[WF_T * T_::CELLS] = T;
+    cell[WF_R * T_::CELLS] = r;
+    cell[WF_H * T_::CELLS] = H;
+  }
+}
+
+// PE-local first-derivative stencil kind of the Sec. 2.1 mixed rule at local
+// index li of a direction with nl points: 0 central, 1 first point, 2 second,
+// 3 second to last, 4 last point of the PE.
+__device__ __forceinline__ int local_kind(int pes, int li, int nl) {
+  if (pes == 1 || (li >= 2 && li <= nl - 3)) return 0;
+  if (li == 0) return 1;
+  if (li == 1) return 2;
+  if (li == nl - 2) return 3;
+  return 4;
+}
+
+// 12 dx times the PE-local first derivative of kind `kind`, val(o) giving the
+// value at offset o: central (1, -8, 0, 8, -1), one-sided (-25, 48, -36, 16, -3)
+// on 0..4, (-3, -10, 18, -6, 1) on -1..3 and their mirror images.
+template <typename S, typename F>
+__device__ __forceinline__ S apply_local(int kind, F&& val) {
+  switch (kind) {
+    case 1: return S(-25) * val(0) + S(48) * val(1) - S(36) * val(2) + S(16) * val(3) - S(3) * val(4);
+    case 2: return S(-3) * val(-1) - S(10) * val(0) + S(18) * val(1) - S(6) * val(2) + val(3);
+    case 3: return S(3) * val(1) + S(10) * val(0) - S(18) * val(-1) + S(6) * val(-2) - val(-3);
+    case 4: return S(25) * val(0) - S(48) * val(-1) + S(36) * val(-2) - S(16) * val(-3) + S(3) * val(-4);
+    default: return fma(S(8), val(1) - val(-1), val(-2) - val(2));
+  }
+}
+
+// The window seen from one point: plane bases for offsets -4..4 (already
+// including the point's cell), so a value at (dx, dy, dz) of field f is one
+// load at a constant offset.
+template <typename S, int TX, int TY>
+struct PointWin {
+  using T_ = TileShape<TX, TY>;
+  const S* win;                 // the shared-memory window
+  int pb[kWinPlanes];           // element offsets of the point's cell in planes z-4 .. z+4
+  __device__ __forceinline__ S at(int f, int dx, int dy, int dz) const {
+    return win[pb[4 + dz] + f * T_::CELLS + dy * T_::CX + dx];
+  }
+  // value shifted by m along direction d
+  __device__ __forceinline__ S sh(int f, int d, int m, int dx = 0, int dy = 0, int dz = 0) const {
+    return at(f, dx + (d == 0 ? m : 0), dy + (d == 1 ? m : 0), dz + (d == 2 ? m : 0));
+  }
+  // AT first derivative in direction b at the cell (dx, dy, dz) from the point
+  __device__ __forceinline__ S d1(const Coef<S>& K, int f, int b, int dx, int dy, int dz) const {
+    return fma(K.c1[b], sh(f, b, 1, dx, dy, dz) - sh(f, b, -1, dx, dy, dz),
+               K.c2[b] * (sh(f, b, 2, dx, dy, dz) - sh(f, b, -2, dx, dy, dz)));
+  }
+  // flux component e of direction d at the cell (dx, dy, dz): rho u_d,
+  // rho u_i u_d + p delta_id, H u_d with p = rho T / gamma
+  __device__ __forceinline__ S flux(const Coef<S>& K, int d, int e, int dx, int dy, int dz) const {
+    const S r = at(WF_R, dx, dy, dz);
+    const S ud = at(WF_U + d, dx, dy, dz);
+    if (e == 0) return r * ud;
+    if (e == 4) return at(WF_H, dx, dy, dz) * ud;
+    const int i = e - 1;
+    const S rud = r * ud;
+    const S ui = at(WF_U + i, dx, dy, dz);
+    if (i != d) return rud * ui;
+    return fma(rud, ui, r * at(WF_T, dx, dy, dz) * K.inv_gamma);
+  }
+  // d/dx_a (d f/dx_b) by the three-step rule of Sec. 2.1
+  __device__ __forceinline__ S mixed(const Coef<S>& K, int f, int a, int b, const int (&kind)[3]) const {
+    auto inner = [&](int outer, int in, int off) {
+      return d1(K, f, in, outer == 0 ? off : 0, outer == 1 ? off : 0, outer == 2 ? off : 0);
+    };
+    if (kind[a] == 0 && kind[b] == 0)
+      return K.h12[a] * apply_local<S>(0, [&](int o) { return inner(a, b, o); });
+    const S pa = K.h12[a] * apply_local<S>(kind[a], [&](int o) { return inner(a, b, o); });
+    const S pb_ = K.h12[b] * apply_local<S>(kind[b], [&](int o) { return inner(b, a, o); });
+    return S(0.5) * (pa + pb_);
+  }
+};
+
+// Per-thread statistics accumulators: FP64 form sums in FP64, FP32 form in
+// compensated (Kahan) FP32; both reach FP64 before crossing threads.
+template <typename S> struct StatAcc;
+template <> struct StatAcc<double> {
+  double s[kNumStat];
+  __device__ void init() { for (int i = 0; i < kNumStat; ++i) s[i] = 0.0; }
+  __device__ void add(int i, double v) { s[i] += v; }
+  __device__ double get(int i) const { return s[i]; }
+};
+template <> struct StatAcc<float> {
+  float s[kNumStat], c[kNumStat];
+  __device__ void init() { for (int i = 0; i < kNumStat; ++i) { s[i] = 0.f; c[i] = 0.f; } }
+  __device__ void add(int i, float v) {
+    const float y = v - c[i];
+    const float t = s[i] + y;
+    c[i] = (t - s[i]) - y;
+    s[i] = t;
+  }
+  __device__ double get(int i) const { return (double)s[i] - (double)c[i]; }
+};
+
+template <typename S, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S> A, int ZC) {
+  using T_ = TileShape<TX, TY>;
+  extern __shared__ __align__(16) unsigned char fused_smem[];
+  S* win = reinterpret_cast<S*>(fused_smem);
+  FusedGeo F;
+  F.x0 = blockIdx.x * TX;
+  F.y0 = blockIdx.y * TY;
+  const int zs = blockIdx.z * ZC;
+  F.pe[0] = F.x0 / g.nl[0];
+  F.pe[1] = F.y0 / g.nl[1];
+  F.pe[2] = zs / g.nl[2];
+  for (int d = 0; d < 3; ++d) F.base[d] = F.pe[d] * g.nl[d];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = F.x0 + tx, y = F.y0 + ty;
+  const int cell = (ty + 2) * T_::CX + (tx + 2);
+  const long long N = g.npts;
+
+  StatAcc<S> st;
+  st.init();
+  long long kwave = LLONG_MIN, krho = LLONG_MAX, kp = LLONG_MAX;
+  unsigned health = 0;
+
+  // window slot of plane zs - 4 is 0; plane zs - 4 + k lives in slot k mod 9
+  for (int k = 0; k < 8; ++k) fused_load_plane<S, TX, TY>(g, K, A, F, win, k * T_::PLANE, zs - 4 + k);
+
+  const int li_x = x - F.base[0], li_y = y - F.base[1];
+  const int kind_x = local_kind(g.pes[0], li_x, g.nl[0]), kind_y = local_kind(g.pes[1], li_y, g.nl[1]);
+  const S a0sum = K.a0[0] + K.a0[1] + K.a0[2];
+  int s0 = 0;                                  // slot of plane z - 4
+  for (int z = zs; z < zs + ZC; ++z) {
+    const int snew = s0 + 8 >= kWinPlanes ? s0 + 8 - kWinPlanes : s0 + 8;   // slot of plane z + 4
+    fused_load_plane<S, TX, TY>(g, K, A, F, win, snew * T_::PLANE, z + 4);
+    __syncthreads();
+    PointWin<S, TX, TY> W;
+    W.win = win;
+#pragma unroll
+    for (int k = 0; k < kWinPlanes; ++k) {
+      const int sl = s0 + k >= kWinPlanes ? s0 + k - kWinPlanes : s0 + k;
+      W.pb[k] = sl * T_::PLANE + cell;
+    }
+    const int li_z = z - F.base[2];
+    const int kind[3] = {kind_x, kind_y, local_kind(g.pes[2], li_z, g.nl[2])};
+    const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
+
+    // ---- inviscid flux divergence: -sum_d D_d F_d (ghost fluxes across PE faces)
+    S R[5] = {S(0), S(0), S(0), S(0), S(0)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int gc = d == 0 ? x : (d == 1 ? y : z);
+      const long long qs = 4LL * g.pes[d] * g.plane[d];
+      const long long pl = d == 0 ? (long long)z * g.n[1] + y : (d == 1 ? (long long)z * g.n[0] + x
+                                                                          : (long long)y * g.n[0] + x);
+      bool gb[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) gb[j] = F.beyond(g, d, gc + (j < 2 ? j - 2 : j - 1));
+#pragma unroll
+      for (int e = 0; e < 5; ++e) {
+        S fv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int m = j < 2 ? j - 2 : j - 1;
+          if (gb[j])
+            fv[j] = A.GH[d][e * qs + (long long)(4 * F.pe[d] + F.ghost_slot(g, d, gc + m)) * g.plane[d] + pl];
+          else
+            fv[j] = W.flux(K, d, e, d == 0 ? m : 0, d == 1 ? m : 0, d == 2 ? m : 0);
+        }
+        R[e] = fma(-K.c1[d], fv[2] - fv[1], R[e]);
+        R[e] = fma(-K.c2[d], fv[3] - fv[0], R[e]);
+      }
+    }
+
+    // ---- second derivatives of u, v, w, T; first derivatives at the point
+    S lap[4], d2diag[3], Ag[3][3], dT[3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const S f0 = W.at(WF_U + q, 0, 0, 0);
+      S accq = a0sum * f0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const S fm2 = W.sh(WF_U + q, d, -2), fm1 = W.sh(WF_U + q, d, -1);
+        const S fp1 = W.sh(WF_U + q, d, 1), fp2 = W.sh(WF_U + q, d, 2);
+        const S off = fma(K.a1[d], fp1 + fm1, K.a2[d] * (fp2 + fm2));
+        accq += off;
+        if (q == d) d2diag[d] = fma(K.a0[d], f0, off);
+        const S d1 = fma(K.c1[d], fp1 - fm1, K.c2[d] * (fp2 - fm2));
+        if (q < 3) Ag[q][d] = d1; else dT[d] = d1;
+      }
+      lap[q] = accq;
+    }
+
+    // ---- d theta/dx_i = d2 u_i/dx_i^2 + sum_{k != i} d/dx_i (d u_k/dx_k)
+    S gth[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      S s = d2diag[i];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k != i) s += W.mixed(K, WF_U + k, i, k, kind);
+      gth[i] = s;
+    }
+
+    // ---- point values
+    const S r = W.at(WF_R, 0, 0, 0);
+    const S vel[3] = {W.at(WF_U, 0, 0, 0), W.at(WF_V, 0, 0, 0), W.at(WF_W, 0, 0, 0)};
+    const S T = W.at(WF_T, 0, 0, 0);
+    const S m[3] = {A.U[N + idx], A.U[2 * N + idx], A.U[3 * N + idx]};
+    const S Ecur = A.U[4 * N + idx];
+    const S p = K.gm1 * (Ecur - S(0.5) * (m[0] * vel[0] + m[1] * vel[1] + m[2] * vel[2]));
+    const S theta = Ag[0][0] + Ag[1][1] + Ag[2][2];
+    const S mu = K.mu0 * pow(T, K.omega);
+    const S dmudT = K.omega * mu / T;
+    const S kappa = mu * K.cp_over_pr;
+    S dmu[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dmu[j] = dmudT * dT[j];
+    S sm[3][3];
+    const S th23 = S(2.0 / 3.0) * theta;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) sm[i][j] = i == j ? S(2) * Ag[i][i] - th23 : Ag[i][j] + Ag[j][i];
+
+    S fo[3] = {S(0), S(0), S(0)};
+    if (A.fB) {
+      const long long lines = (long long)g.n[2] * g.n[1];
+      const long long ln = (long long)z * g.n[1] + y;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        S acc = S(0);
+        for (int kx = 0; kx <= A.fK; ++kx) {
+          const vec2_t<S> b = A.fB[((long long)kx * 3 + c) * lines + ln];
+          const vec2_t<S> e = A.fX[(long long)kx * g.n[0] + x];
+          acc = fma(b.x, e.x, fma(-b.y, e.y, acc));
+        }
+        fo[c] = acc;
+      }
+    }
+
+    S sS = sm[0][0] * Ag[0][0] + sm[1][1] * Ag[1][1] + sm[2][2] * Ag[2][2];
+    sS = fma(sm[0][1], sm[0][1], sS);
+    sS = fma(sm[0][2], sm[0][2], sS);
+    sS = fma(sm[1][2], sm[1][2], sS);
+    const S sigS = mu * sS;
+    S work = S(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      S V = mu * fma(gth[i], S(1.0 / 3.0), lap[i]);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) V = fma(dmu[j], sm[i][j], V);
+      R[1 + i] += fma(r, fo[i], V);
+      work = fma(vel[i], V, work);
+    }
+    S tail = fma(kappa, lap[3], sigS + work);
+    tail = fma(K.cp_over_pr, fma(dmu[0], dT[0], fma(dmu[1], dT[1], dmu[2] * dT[2])), tail);
+    R[4] += fma(r, fma(fo[0], vel[0], fma(fo[1], vel[1], fo[2] * vel[2])), tail);
+
+    if (nonpositive(r)) health |= H_RHO;
+    if (nonpositive(p)) health |= H_P;
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+      if (nonfinite(R[v])) health |= H_NONFINITE;
+
+    if (A.do_update) {
+      const S Uo[5] = {r, m[0], m[1], m[2], Ecur};
+      S un[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const S inc = A.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * A.Rprev[v * N + idx]);
+        un[v] = fma(K.dt, inc, Uo[v]);
+        A.Unext[v * N + idx] = un[v];
+        A.Rprev[v * N + idx] = R[v];
+        if (nonfinite(un[v])) health |= H_NONFINITE;
+      }
+      const int slot = (int)((A.n + 1) % g.nlev);
+      const int li[3] = {li_x, li_y, li_z};
+      const int c3[3] = {x, y, z};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (g.pes[d] == 1) continue;
+        const int nl = g.nl[d];
+        if (li[d] >= 2 && li[d] < nl - 2) continue;
+        const int t = li[d] < 2 ? li[d] : li[d] - nl + 4;
+        const long long sp = 4LL * F.pe[d] + t;
+        const long long pl = plane_index(g, d, c3[0], c3[1], c3[2]);
+        S* rg = A.ring[d];
+        const long long P4 = 4LL * g.pes[d];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) rg[(((long long)slot * 5 + v) * P4 + sp) * g.plane[d] + pl] = un[v];
+      }
+    } else if (A.Rout) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) A.Rout[v * N + idx] = (double)R[v];
+    }
+
+    if (A.do_stats) {
+      const S uu = fma(vel[0], vel[0], fma(vel[1], vel[1], vel[2] * vel[2]));
+      const S c = sqrt(T);
+      st.add(ST_RHO, r);
+      st.add(ST_M0, m[0]);
+      st.add(ST_M1, m[1]);
+      st.add(ST_M2, m[2]);
+      st.add(ST_E, Ecur);
+      st.add(ST_KE, S(0.5) * r * uu);
+      st.add(ST_SIGS, sigS);
+      const S a0 = Ag[0][0], a1 = Ag[1][1], a2 = Ag[2][2];
+      const S q0 = a0 * a0, q1 = a1 * a1, q2 = a2 * a2;
+      st.add(ST_G2, q0 + q1 + q2);
+      st.add(ST_G3, fma(q0, a0, fma(q1, a1, q2 * a2)));
+      st.add(ST_G4, fma(q0, q0, fma(q1, q1, q2 * q2)));
+      const S o0 = Ag[2][1] - Ag[1][2], o1 = Ag[0][2] - Ag[2][0], o2 = Ag[1][0] - Ag[0][1];
+      st.add(ST_ENST, fma(o0, o0, fma(o1, o1, o2 * o2)));
+      st.add(ST_PTHETA, p * theta);
+      st.add(ST_FPOW, r * fma(fo[0], vel[0], fma(fo[1], vel[1], fo[2] * vel[2])));
+      st.add(ST_U2, uu);
+      st.add(ST_C, c);
+      const S au[3] = {fabs(vel[0]), fabs(vel[1]), fabs(vel[2])};
+      const long long k0 = okey(au[0]), k1 = okey(au[1]), k2 = okey(au[2]);
+      const S umax = (k0 >= k1 && k0 >= k2) ? au[0] : (k1 >= k2 ? au[1] : au[2]);
+      kwave = max(kwave, okey(umax + c));
+      krho = min(krho, okey(r));
+      kp = min(kp, okey(p));
+    }
+    s0 = s0 + 1 >= kWinPlanes ? 0 : s0 + 1;
+    __syncthreads();
+  }
+  double tot[kNumStat];
+#pragma unroll
+  for (int s = 0; s < kNumStat; ++s) tot[s] = st.get(s);
+  // the window is dead after the last barrier: reuse it as reduction scratch
+  block_reduce<double>(tot, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words,
+                       reinterpret_cast<double*>(fused_smem));
+}
+
+}  // namespace atdns

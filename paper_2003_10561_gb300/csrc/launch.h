@@ -20,6 +20,11 @@ cudaError_t launch_grad(const Geom& g, const Coef<S>& K, const S* PQ, S* const G
 template <typename S>
 cudaError_t launch_main(const Geom& g, const Coef<S>& K, const StepArgs<S>& a, cudaStream_t st);
 
+// Fused single-pass step kernel on TX x TY tiles marching ZC planes in z.
+template <typename S>
+cudaError_t launch_fused(const Geom& g, const Coef<S>& K, const StepArgs<S>& a, int TX, int TY, int ZC,
+                         cudaStream_t st);
+
 // Number of blocks k_main is launched with (size of the partial-sum array).
 inline long long main_blocks(const Geom& g) { return (g.npts + kBlock - 1) / kBlock; }
 

@@ -37,8 +37,19 @@ def rel_linf(a, b):
     return [float(np.max(np.abs(a[v] - b[v])) / max(np.max(np.abs(b[v])), 1e-300)) for v in range(5)]
 
 
-def make(lib, n, pes, precision="p64", **kw):
-    return lib.Solver(n=n, pes=pes, precision=precision, gamma=GAMMA, prandtl=PR, visc_exp=OMEGA, **kw)
+PATHS = ["multipass", "fused"]
+
+
+def make(lib, n, pes, precision="p64", path="auto", **kw):
+    """A solver on the requested kernel path; skips when the fused path does not
+    apply to this grid / PE shape."""
+    try:
+        return lib.Solver(n=n, pes=pes, precision=precision, path=path, gamma=GAMMA, prandtl=PR,
+                          visc_exp=OMEGA, **kw)
+    except lib.AtDnsError as e:
+        if path == "fused" and e.code == lib.AT_DNS_E_UNSUPPORTED:
+            pytest.skip("fused path does not apply to n=%s pes=%s" % (n, pes))
+        raise
 
 
 def ocfg(n, pes, **kw):
@@ -66,16 +77,20 @@ CASES = [
     ((16, 16, 16), (2, 2, 2), "periodic", 8, 2),
     ((15, 12, 20), (3, 2, 4), "random", 11, 3),       # ragged PEs (5, 6, 5), non-cubic
     ((24, 10, 16), (4, 1, 2), "random", 13, 4),       # a direction without faces
+    ((40, 24, 16), (5, 3, 2), "random", 10, 2),       # 8^3 PEs (fused tiles 8 x 8)
+    ((48, 32, 24), (3, 2, 3), "periodic", 9, 2),      # 16 x 16 x 8 PEs
+    ((32, 16, 24), (1, 2, 3), "random", 12, 3),       # x without faces, periodic wrap in a tile
 ]
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("n,pes,mode,step,L", CASES)
-def test_rhs_parity_fp64(lib, n, pes, mode, step, L):
+def test_rhs_parity_fp64(lib, n, pes, mode, step, L, path):
     mu0 = 0.02
     U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=11)
     c = ocfg(n, pes, mu0=mu0, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
     hist = synth.history(U0, c.n_levels, eps=2e-2, seed=5)
-    s = make(lib, n, pes, mu0=mu0, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
+    s = make(lib, n, pes, path=path, mu0=mu0, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
     s.set_history(hist, step)
     R = s.rhs(mode)
     Rref = ns.rhs(c, hist, ns.delay_map(c, step, lib.MODES[mode]))
@@ -83,13 +98,14 @@ def test_rhs_parity_fp64(lib, n, pes, mode, step, L):
     assert max(err) <= 1e-12, err
 
 
-def test_rhs_parity_fp64_forced(lib):
+@pytest.mark.parametrize("path", PATHS)
+def test_rhs_parity_fp64_forced(lib, path):
     n, pes = (16, 16, 16), (2, 2, 2)
     kw = dict(mu0=0.02, dt=5e-3, max_delay=2, seed=3, forcing=1, kf=2.0, f_amp=0.2, f_tcorr=0.3, f_seed=99)
     U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=12)
     c = ocfg(n, pes, **{**kw, "forcing": True})
     hist = synth.history(U0, c.n_levels, eps=1e-2, seed=6)
-    s = make(lib, n, pes, **kw)
+    s = make(lib, n, pes, path=path, **kw)
     s.set_history(hist, 9)
     R = s.rhs("random")
     Rref = ns.rhs(c, hist, ns.delay_map(c, 9, ns.RANDOM), ns.forcing_coefficients(c, 9))
@@ -97,12 +113,13 @@ def test_rhs_parity_fp64_forced(lib):
     assert max(err) <= 1e-12, err
 
 
-def test_stats_parity_fp64(lib):
-    n, pes = (24, 24, 24), (2, 2, 2)
+@pytest.mark.parametrize("path", PATHS)
+def test_stats_parity_fp64(lib, path):
+    n, pes = (32, 32, 32), (2, 2, 2)
     U0 = synth.initial_state(n, k0=4.0, mach_t=0.3, seed=13)
     c = ocfg(n, pes, mu0=0.02, dt=1e-3, max_delay=2, seed=1)
     hist = synth.history(U0, c.n_levels, eps=1e-2, seed=2)
-    s = make(lib, n, pes, mu0=0.02, dt=1e-3, max_delay=2, seed=1)
+    s = make(lib, n, pes, path=path, mu0=0.02, dt=1e-3, max_delay=2, seed=1)
     s.set_history(hist, 9)
     s.rhs("random")
     st = s.stats()
@@ -119,14 +136,15 @@ def test_stats_parity_fp64(lib):
     assert st["step"] == 9
 
 
-def test_config1_steps_parity_fp64(lib):
+@pytest.mark.parametrize("path", PATHS)
+def test_config1_steps_parity_fp64(lib, path):
     """32^3, one PE, synchronous, CFL 0.5: 20 steps, then 100 (<= 1e-10)."""
     n = (32, 32, 32)
     mu0 = synth.mu0_for_resolution(n, k0=4.0, mach_t=0.3, seed=0)
     U0 = synth.initial_state(n, k0=4.0, mach_t=0.3, seed=0)
     c = ocfg(n, (1, 1, 1), mu0=mu0)
     c.dt = ns.dt_from_cfl(c, U0, 0.5)
-    s = make(lib, n, (1, 1, 1), mu0=mu0, cfl=0.5, dt=0.0)
+    s = make(lib, n, (1, 1, 1), path=path, mu0=mu0, cfl=0.5, dt=0.0)
     s.set_state(U0)
     assert abs(s.info()["dt"] - c.dt) <= 1e-15 * c.dt
     run = ns.Run.start(c, U0, ns.SYNC)
@@ -138,14 +156,15 @@ def test_config1_steps_parity_fp64(lib):
             assert max(err) <= (1e-12 if k + 1 == 20 else 1e-10), (k + 1, err)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("mode", ["random", "periodic"])
-def test_at_steps_parity_fp64(lib, mode):
+def test_at_steps_parity_fp64(lib, mode, path):
     """16^3, 2x2x2 PEs, AT delays from the start-up on: 100 AB2 steps."""
     n, pes = (16, 16, 16), (2, 2, 2)
     U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=21)
     kw = dict(mu0=0.03, dt=4e-3, max_delay=2, comm_period=3, seed=5)
     c = ocfg(n, pes, **kw)
-    s = make(lib, n, pes, **kw)
+    s = make(lib, n, pes, path=path, **kw)
     s.set_state(U0)
     run = ns.Run.start(c, U0, lib.MODES[mode])
     for _ in range(100):
@@ -169,12 +188,13 @@ def test_zero_delay_equals_sync_fp64(lib):
 
 
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("n,pes,mode,step,L", CASES[:3])
-def test_rhs_parity_fp32(lib, n, pes, mode, step, L):
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("n,pes,mode,step,L", CASES[:3] + CASES[5:7])
+def test_rhs_parity_fp32(lib, n, pes, mode, step, L, path):
     U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=11)
     c = ocfg(n, pes, mu0=0.02, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
     hist = synth.history(U0, c.n_levels, eps=2e-2, seed=5)
-    s = make(lib, n, pes, "p32", mu0=0.02, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
+    s = make(lib, n, pes, "p32", path=path, mu0=0.02, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
     s.set_history(hist, step)
     R = s.rhs(mode)
     Rref = ns.rhs(c, hist, ns.delay_map(c, step, lib.MODES[mode]))
@@ -203,8 +223,9 @@ def _sample_points(n, nloc, rng, count):
 # derivatives as 1/dx^2 but carry the small coefficients mu and k; the bounds
 # are scaled by the 8x of the first derivatives plus margin: 1e-11 (FP64) and
 # 2e-3 (FP32).
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("precision,tol", [("p64", 1e-11), ("p32", 2e-3)])
-def test_full_size_sampled_parity(lib, precision, tol):
+def test_full_size_sampled_parity(lib, precision, tol, path):
     """256^3 with 8x8x8 PEs (the benchmark workload), random delays with L = 2,
     at a step past the start-up: sampled points against the brute-force
     pointwise oracle."""
@@ -213,7 +234,7 @@ def test_full_size_sampled_parity(lib, precision, tol):
     c = ocfg(n, pes, mu0=0.004, dt=1e-3, max_delay=L, seed=2024)
     hist = synth.history(U0, c.n_levels, eps=1e-2, seed=3)
     step = 17
-    s = make(lib, n, pes, precision, mu0=0.004, dt=1e-3, max_delay=L, seed=2024)
+    s = make(lib, n, pes, precision, path=path, mu0=0.004, dt=1e-3, max_delay=L, seed=2024)
     s.set_history(hist, step)
     R = s.rhs("random")
     s.close()
@@ -255,3 +276,20 @@ def test_device_pointers_and_zero_steps(lib):
     s.rhs("sync", r_dev)
     r_host = s.rhs("sync")
     assert np.array_equal(r_dev.cpu().numpy(), r_host)
+
+
+def test_paths_agree_and_report(lib):
+    """Both kernel paths give the same steps up to rounding, and report themselves."""
+    n, pes = (32, 32, 32), (4, 4, 4)
+    U0 = synth.initial_state(n, seed=31)
+    kw = dict(mu0=0.02, dt=3e-3, max_delay=2, seed=9)
+    a = make(lib, n, pes, path="multipass", **kw)
+    b = make(lib, n, pes, path="fused", **kw)
+    assert make(lib, n, pes, **kw).info()["kernel_path"] == lib.AT_DNS_PATH_MULTIPASS
+    assert a.info()["kernel_path"] == lib.AT_DNS_PATH_MULTIPASS
+    assert b.info()["kernel_path"] == lib.AT_DNS_PATH_FUSED and b.info()["tile"] == [8, 8, 8]
+    for s in (a, b):
+        s.set_state(U0)
+        s.step(12, "random")
+    err = rel_linf(b.get_state(), a.get_state())
+    assert max(err) <= 1e-12, err
