@@ -41,6 +41,10 @@ FLOP_MAIN = 390.0
 # R^n; plus the slab ring: 1 write + 3 reads of 5 variables at the N_B fraction)
 NB_FRAC = 1.0 - (28.0 / 32.0) ** 3
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max SM clock
+# DRAM bytes (read + write) of one k_main launch, FP64 multi-pass path: ncu at
+# 128^3 (877.2 MB, profiles/k_main_fp64_128cube_4x4x4pes.md) scaled by the
+# point count to the 256^3 workload (traffic grows with the points)
+K_MAIN_FP64_TRAFFIC_256 = 8 * 877.2e6
 
 
 def set_workload(n, pes):
@@ -114,6 +118,21 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """Slowest rank's time (the job's time); identity on one process."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, points, steps, ms):
+    """Whole-job updates/s: every rank advances its own replica of `points`."""
+    return world * points * steps / (ms / 1e3)
 
 
 def oracle_rate(steps, warmup, n=48, pes=2):
@@ -237,10 +256,7 @@ def main():
                 ms, kt = timed_steps(s, stream, args.steps, args.warmup, torch, profile=True)
         else:
             ms, kt = timed_steps(s, stream, args.steps, args.warmup, torch, profile=True)
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        if pg:
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, pg, "cuda")
         st = s.stats()
         res[prec] = {"ms": ms, "kt": kt, "stats": st, "info": s.info()}
         res[prec]["path"] = "fused" if res[prec]["info"]["kernel_path"] == at_dns.AT_DNS_PATH_FUSED else "multipass"
@@ -280,7 +296,7 @@ def main():
     p64 = res.get("p64")
     p32 = res.get("p32")
     head = p64 or p32
-    value = world * pts * args.steps / (head["ms"] / 1e3)
+    value = job_rate(world, pts, args.steps, head["ms"])
     launches = sum(v[0] for v in head["kt"].values())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -301,7 +317,8 @@ def main():
         achieved = FLOP_MAIN * pts / t_main / 1e12
         line["roofline"] = {"bound": "alu", "kernel": "k_main (FP64)", "achieved": achieved,
                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                            "traffic": None,
+                            "traffic": (K_MAIN_FP64_TRAFFIC_256 if (N == 256 and PES == 8 and p64["path"] == "multipass")
+                                        else None),
                             "note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
                                     "(an FMA probe measured 1.20 TFLOP/s)"}
     if p32:
@@ -310,7 +327,7 @@ def main():
         ach32 = algorithmic_bytes(4) * pts / t_main32 / 1e9
         r32 = {"bound": "hbm", "kernel": "k_main (FP32)", "achieved": ach32, "peak": pk.get("hbm_gbs"),
                "unit": "GB/s", "frac": ach32 / pk.get("hbm_gbs", 6800.0), "traffic": None}
-        blk = {"value": world * pts * args.steps / (p32["ms"] / 1e3), "unit": UNIT, "kernel_path": p32["path"],
+        blk = {"value": job_rate(world, pts, args.steps, p32["ms"]), "unit": UNIT, "kernel_path": p32["path"],
                "ms_per_step": p32["ms"] / args.steps, "dtype": "f32", "roofline": r32,
                "kernel_ms_per_step": {k: v[1] / v[0] for k, v in p32["kt"].items()}}
         if p64:

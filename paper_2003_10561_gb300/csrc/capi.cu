@@ -554,6 +554,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     else if (c.stats_every != 0 && c.stats_every != 1) bad = "stats_every must be 0 or 1";
     else if (c.kernel_path < 0 || c.kernel_path > 2) bad = "unknown kernel_path";
   }
+  if (bad.empty() && (long long)c.n[0] * c.n[1] * c.n[2] >= (1LL << 31)) bad = "grids must hold fewer than 2^31 points";
   if (!bad.empty()) { g_create_error = bad; return AT_DNS_E_INVALID_ARG; }
 
   at_dns* h = new at_dns();

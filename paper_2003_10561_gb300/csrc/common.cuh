@@ -82,12 +82,15 @@ inline Coef<S> make_coef(const Geom& g, const Phys& ph, double dt) {
 __device__ __forceinline__ bool nonpositive(double v) { return __double_as_longlong(v) <= 0; }
 __device__ __forceinline__ bool nonpositive(float v) { return __float_as_int(v) <= 0; }
 
-// Linear index -> (x, y, z).
+// Linear index -> (x, y, z).  Grids hold fewer than 2^31 points (the create
+// call checks), so 32-bit unsigned division suffices (a 64-bit integer
+// division is a long software sequence).
 __device__ __forceinline__ void decode(const Geom& g, long long idx, int& x, int& y, int& z) {
-  long long t = idx / g.n[0];
-  x = (int)(idx - t * g.n[0]);
-  z = (int)(t / g.n[1]);
-  y = (int)(t - (long long)z * g.n[1]);
+  const unsigned i = (unsigned)idx;
+  const unsigned t = i / (unsigned)g.n[0];
+  x = (int)(i - t * (unsigned)g.n[0]);
+  z = (int)(t / (unsigned)g.n[1]);
+  y = (int)(t - (unsigned)z * (unsigned)g.n[1]);
 }
 
 // Index of the point within the plane normal to d.

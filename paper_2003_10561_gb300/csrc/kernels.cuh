@@ -345,6 +345,7 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
   double (*sh)[kMaxThreads + 1] = reinterpret_cast<double (*)[kMaxThreads + 1]>(scratch);
   __shared__ long long shk[kMaxWarps][3];
   __shared__ unsigned shh[kMaxWarps];
+  __shared__ float shf[kNumStat][kMaxWarps];   // FP32 warp sums (FP32 form)
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
   const int nwarps = nthreads >> 5;
   const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
@@ -364,10 +365,12 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
 #pragma unroll
         for (int s = 0; s < kNumStat; ++s) sh[s][j] = 0.0;
     } else {
+      // stays FP32 here: a conversion to FP64 is an FP64-pipe warp
+      // instruction even with one active lane
 #pragma unroll
       for (int s = 0; s < kNumStat; ++s) {
         const S w = warp_sum(st[s]);
-        if (lane == 0) sh[s][wid] = (double)w;
+        if (lane == 0) shf[s][wid] = (float)w;
       }
     }
   }
@@ -405,9 +408,10 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
       partial[blk * kNumStat + s] = a;
     }
   } else {
+    // one warp converts and sums the warp sums in FP64
     for (int s = tid; s < kNumStat; s += nthreads) {
       double a = 0.0;
-      for (int w = 0; w < nwarps; ++w) a += sh[s][w];
+      for (int w = 0; w < nwarps; ++w) a += (double)shf[s][w];
       partial[blk * kNumStat + s] = a;
     }
   }
