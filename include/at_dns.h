@@ -64,6 +64,8 @@ extern "C" {
 /* precision forms */
 #define AT_DNS_P64  0        /* FP64 storage and arithmetic */
 #define AT_DNS_P32  1        /* FP32 state, stencils, update and ring; FP64 reductions */
+#define AT_DNS_P32C 2        /* as P32, but the state is carried as FP32 hi + lo words and
+                                updated by TwoSum (compensated, ~48-bit accumulation) */
 
 /* pointer locations */
 #define AT_DNS_HOST    0
@@ -89,7 +91,7 @@ typedef struct {
   double   f_amp;        /* OU amplitude sigma of each forcing coefficient              */
   double   f_tcorr;      /* OU correlation time T_f                                     */
   uint64_t f_seed;       /* key of the forcing noise stream                             */
-  int32_t  precision;    /* AT_DNS_P64 or AT_DNS_P32                                    */
+  int32_t  precision;    /* AT_DNS_P64, AT_DNS_P32 or AT_DNS_P32C                       */
   int32_t  stats_every;  /* 1: reduce statistics in every step; 0: only on request      */
   void*    stream;       /* cudaStream_t to run on; NULL = the legacy default stream    */
   int32_t  kernel_path;  /* AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS or AT_DNS_PATH_FUSED */

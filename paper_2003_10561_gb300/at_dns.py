@@ -23,13 +23,13 @@ AT_DNS_E_TOO_LARGE = -7
 AT_DNS_NOALLOC_MAX_POINTS = 262144
 
 AT_DNS_SYNC, AT_DNS_PERIODIC, AT_DNS_RANDOM = 0, 1, 2
-AT_DNS_P64, AT_DNS_P32 = 0, 1
+AT_DNS_P64, AT_DNS_P32, AT_DNS_P32C = 0, 1, 2
 AT_DNS_HOST, AT_DNS_DEVICE = 0, 1
 AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS, AT_DNS_PATH_FUSED = 0, 1, 2
 PATHS = {"auto": AT_DNS_PATH_AUTO, "multipass": AT_DNS_PATH_MULTIPASS, "fused": AT_DNS_PATH_FUSED}
 
 MODES = {"sync": AT_DNS_SYNC, "periodic": AT_DNS_PERIODIC, "random": AT_DNS_RANDOM}
-PRECISIONS = {"p64": AT_DNS_P64, "p32": AT_DNS_P32}
+PRECISIONS = {"p64": AT_DNS_P64, "p32": AT_DNS_P32, "p32c": AT_DNS_P32C}
 
 
 class at_dns_config_t(ctypes.Structure):

@@ -30,6 +30,8 @@ struct at_dns {
   size_t ssize = 8;            // bytes of the scalar type
   // device buffers (scalar type S unless noted)
   void* U[2] = {nullptr, nullptr};
+  void* Ulo[2] = {nullptr, nullptr};   // compensated form: low words of U
+  bool comp = false;
   int cur = 0;
   void* PQ = nullptr;
   void* G = nullptr;
@@ -86,6 +88,23 @@ template <typename S>
 __global__ void k_to_double(const S* __restrict__ in, double* __restrict__ out, long long count) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < count) out[i] = (double)in[i];
+}
+
+// Compensated form: FP64 value -> FP32 high word + FP32 low word (the rest).
+__global__ void k_split_double(const double* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo,
+                               long long count) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double v = in[i];
+  const float h = (float)v;
+  hi[i] = h;
+  lo[i] = (float)(v - (double)h);
+}
+
+__global__ void k_join_double(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ out,
+                              long long count) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < count) out[i] = (double)hi[i] + (double)lo[i];
 }
 
 // Write the PE-boundary slabs of field U (S, [5][npts]) into ring slot `slot`.
@@ -325,6 +344,9 @@ struct Ops {
     if (sizeof(S) == sizeof(double)) {
       if ((const void*)dsrc != (const void*)dst)
         CK(cudaMemcpyAsync(dst, dsrc, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    } else if (h->comp) {
+      k_split_double<<<nblk(cnt), kBlock, 0, h->st>>>(dsrc, (float*)dst, (float*)h->Ulo[h->cur], cnt);
+      CK(cudaGetLastError());
     } else {
       k_from_double<S><<<nblk(cnt), kBlock, 0, h->st>>>(dsrc, dst, cnt);
       CK(cudaGetLastError());
@@ -346,6 +368,10 @@ struct Ops {
     double* dst = where == AT_DNS_DEVICE ? out : h->stage;
     if (sizeof(S) == sizeof(double)) {
       CK(cudaMemcpyAsync(dst, U(h, h->cur), cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    } else if (h->comp) {
+      k_join_double<<<nblk(cnt), kBlock, 0, h->st>>>((const float*)U(h, h->cur), (const float*)h->Ulo[h->cur], dst,
+                                                    cnt);
+      CK(cudaGetLastError());
     } else {
       k_to_double<S><<<nblk(cnt), kBlock, 0, h->st>>>(U(h, h->cur), dst, cnt);
       CK(cudaGetLastError());
@@ -396,6 +422,8 @@ struct Ops {
     a.G = (S*)h->G;
     for (int d = 0; d < 3; ++d) { a.GH[d] = GH[d]; a.ring[d] = ring[d]; }
     a.Rprev = (S*)h->Rprev;
+    a.Ulo = h->comp ? (const S*)h->Ulo[h->cur] : nullptr;
+    a.Ulo_next = h->comp ? (S*)h->Ulo[1 - h->cur] : nullptr;
     a.Rout = Rout;
     a.partial = h->partial;
     a.words = h->words;
@@ -547,7 +575,8 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     else if (!(c.mu0 >= 0)) bad = "mu0 must be >= 0";
     else if (c.max_delay < 0 || c.max_delay > 64) bad = "max_delay must be in [0, 64]";
     else if (c.comm_period < 1) bad = "comm_period must be >= 1";
-    else if (c.precision != AT_DNS_P64 && c.precision != AT_DNS_P32) bad = "unknown precision";
+    else if (c.precision != AT_DNS_P64 && c.precision != AT_DNS_P32 && c.precision != AT_DNS_P32C)
+      bad = "unknown precision";
     else if (!(c.dt > 0) && !(c.cfl > 0)) bad = "need dt > 0 or cfl > 0";
     else if (c.forcing && (!(c.kf >= 1.0) || c.kf > kMaxKf)) bad = "kf must be in [1, 4]";
     else if (c.forcing && !(c.f_tcorr > 0)) bad = "f_tcorr must be > 0";
@@ -561,6 +590,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   h->cfg = c;
   h->st = (cudaStream_t)c.stream;
   h->p64 = c.precision == AT_DNS_P64;
+  h->comp = c.precision == AT_DNS_P32C;
   h->ssize = h->p64 ? 8 : 4;
   Geom& g = h->g;
   g.npts = 1;
@@ -611,6 +641,10 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     return create_fail(h, rc);
   if (!h->fused) {
     if ((rc = dev_alloc(h, &h->PQ, (size_t)kNumQ * N * S)) || (rc = dev_alloc(h, &h->G, (size_t)kNumGrad * N * S)))
+      return create_fail(h, rc);
+  }
+  if (h->comp) {
+    if ((rc = dev_alloc(h, &h->Ulo[0], 5 * N * S)) || (rc = dev_alloc(h, &h->Ulo[1], 5 * N * S)))
       return create_fail(h, rc);
   }
   for (int d = 0; d < 3; ++d) {
@@ -901,7 +935,7 @@ const char* at_dns_last_error(const at_dns_t* h) {
 void at_dns_destroy(at_dns_t* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
-  void* ptrs[] = {h->U[0], h->U[1], h->PQ, h->G, h->Rprev, h->GH[0], h->GH[1], h->GH[2], h->ring[0], h->ring[1],
+  void* ptrs[] = {h->U[0], h->U[1], h->Ulo[0], h->Ulo[1], h->PQ, h->G, h->Rprev, h->GH[0], h->GH[1], h->GH[2], h->ring[0], h->ring[1],
                   h->ring[2], h->stage, h->dmap, h->partial, h->sums, h->words, h->modes, h->fhat, h->fB, h->fX};
   for (void* p : ptrs)
     if (p) cudaFree(p);

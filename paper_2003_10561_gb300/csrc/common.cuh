@@ -164,6 +164,8 @@ struct StepArgs {
   const S* G;          // [12][npts]
   const S* GH[3];      // [9][4 P_d][plane_d] per direction
   S* Rprev;            // [5][npts] R^{n-1} in, R^n out
+  const S* Ulo;        // compensated form: low words of U (else null)
+  S* Ulo_next;         // compensated form: low words of U^{n+1}
   S* ring[3];          // [nlev][5][4 P_d][plane_d]
   double* Rout;        // rhs-only output [5][npts] or null
   double* partial;     // [gridDim.x][kNumStat]
@@ -177,5 +179,43 @@ struct StepArgs {
   int do_update;       // 1: write Unext/Rprev/ring; 0: write Rout
   int do_stats;
 };
+
+// Separately rounded products / sums (never contracted into an FMA), for the
+// error-free transformations of the compensated update.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+// AB2 update of the five variables of one point (Eq. (time_ab)):
+// U^{n+1} = U^n + dt (3/2 R^n - 1/2 R^{n-1}), forward Euler on the first step.
+// With low words (compensated FP32 form) the state is carried as hi + lo and
+// the increment is added by TwoSum (Knuth), so no increment is lost below the
+// resolution of the high word; the stencils read the high word only.
+template <typename S>
+__device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& A, long long idx, long long N,
+                                           const S (&Uo)[5], const S (&R)[5], S (&un)[5], unsigned& health) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const S inc = A.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * A.Rprev[v * N + idx]);
+    if (A.Ulo) {
+      const S dlt = mul_rn(K.dt, inc);
+      const S s = add_rn(Uo[v], dlt);                           // TwoSum(U_hi, dlt)
+      const S bp = sub_rn(s, Uo[v]);
+      const S e = add_rn(sub_rn(Uo[v], sub_rn(s, bp)), sub_rn(dlt, bp));
+      const S lo = add_rn(A.Ulo[v * N + idx], e);
+      const S hi = add_rn(s, lo);                               // renormalise
+      A.Ulo_next[v * N + idx] = sub_rn(lo, sub_rn(hi, s));
+      un[v] = hi;
+    } else {
+      un[v] = fma(K.dt, inc, Uo[v]);
+    }
+    A.Unext[v * N + idx] = un[v];
+    A.Rprev[v * N + idx] = R[v];
+    if (nonfinite(un[v])) health |= H_NONFINITE;
+  }
+}
 
 }  // namespace atdns

@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
     const S Ecur = A.U[4 * N + idx];
     const S p = K.gm1 * (Ecur - S(0.5) * (m[0] * vel[0] + m[1] * vel[1] + m[2] * vel[2]));
     const S theta = Ag[0][0] + Ag[1][1] + Ag[2][2];
-    const S mu = K.mu0 * pow(T, K.omega);
+    const S mu = K.mu0 * exp(K.omega * log(T));   // mu0 T^omega
     const S dmudT = K.omega * mu / T;
     const S kappa = mu * K.cp_over_pr;
     S dmu[3];
@@ -386,14 +386,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
     if (A.do_update) {
       const S Uo[5] = {r, m[0], m[1], m[2], Ecur};
       S un[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const S inc = A.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * A.Rprev[v * N + idx]);
-        un[v] = fma(K.dt, inc, Uo[v]);
-        A.Unext[v * N + idx] = un[v];
-        A.Rprev[v * N + idx] = R[v];
-        if (nonfinite(un[v])) health |= H_NONFINITE;
-      }
+      ab2_update(K, A, idx, N, Uo, R, un, health);
       const int slot = (int)((A.n + 1) % g.nlev);
       const int li[3] = {li_x, li_y, li_z};
       const int c3[3] = {x, y, z};
