@@ -138,6 +138,20 @@ __device__ __forceinline__ int delay_of(int mode, long long n, int p, int f, int
   return (int)(((unsigned long long)w.x * (unsigned long long)(L + 1)) >> 32);
 }
 
+// PE-local 4th-order first-derivative stencils of the mixed-derivative rule
+// (Sec. 2.1), as (offset, coefficient x 12) rows indexed by kind: 0 central
+// (1, -8, 0, 8, -1), 1 first point (-25, 48, -36, 16, -3) on 0..4, 2 second
+// point (-3, -10, 18, -6, 1) on -1..3, 3 and 4 their mirror images at the last
+// two points of a PE.  Central rows pad with a zero coefficient.
+__constant__ int kLocalOff[5][5] = {
+    {-2, -1, 1, 2, 0}, {0, 1, 2, 3, 4}, {-1, 0, 1, 2, 3}, {1, 0, -1, -2, -3}, {0, -1, -2, -3, -4}};
+__constant__ float kLocalCoefF[5][5] = {
+    {1, -8, 8, -1, 0}, {-25, 48, -36, 16, -3}, {-3, -10, 18, -6, 1}, {3, 10, -18, 6, -1}, {25, -48, 36, -16, 3}};
+__constant__ double kLocalCoefD[5][5] = {
+    {1, -8, 8, -1, 0}, {-25, 48, -36, 16, -3}, {-3, -10, 18, -6, 1}, {3, 10, -18, 6, -1}, {25, -48, 36, -16, 3}};
+__device__ __forceinline__ float local_coef(float, int kind, int i) { return kLocalCoefF[kind][i]; }
+__device__ __forceinline__ double local_coef(double, int kind, int i) { return kLocalCoefD[kind][i]; }
+
 // Order-preserving map of a double to a signed 64-bit key (for atomic min/max).
 __device__ __forceinline__ long long ordered_key(double v) {
   long long b = __double_as_longlong(v);

@@ -261,13 +261,42 @@ __device__ __forceinline__ bool central_fits(const Geom& g, const Pt& P, int d) 
   return g.pes[d] == 1 || (P.li[d] >= 2 && P.li[d] <= g.nl[d] - 3);
 }
 
-// PE-local 4th-order first derivative of a gradient field in direction a:
-// central where the stencil fits, one-sided at the two points next to a face.
+// PE-local 4th-order first derivative of a gradient field in direction a at a
+// point where the stencil is one-sided or central (kind as in kLocalOff): a
+// table-driven loop, so only the one stencil that applies is evaluated.
+__device__ __forceinline__ int local_kind_of(const Geom& g, const Pt& P, int d) {
+  if (g.pes[d] == 1) return 0;
+  const int li = P.li[d], nl = g.nl[d];
+  if (li >= 2 && li <= nl - 3) return 0;
+  return li == 0 ? 1 : (li == 1 ? 2 : (li == nl - 2 ? 3 : 4));
+}
+
+template <typename S>
+__device__ __noinline__ S local_d1_table(const Geom& g, const Coef<S>& K, const Pt& P, int a, const S* __restrict__ f,
+                                         int kind) {
+  const long long s = g.stride[a];
+  S acc = S(0);
+  for (int i = 0; i < 5; ++i) {
+    const S c = local_coef(S(0), kind, i);
+    int off = kLocalOff[kind][i];
+    if (g.pes[a] == 1) {   // central with periodic wrap
+      int c2 = P.c[a] + off;
+      c2 = c2 < 0 ? c2 + g.n[a] : (c2 >= g.n[a] ? c2 - g.n[a] : c2);
+      off = c2 - P.c[a];
+    }
+    if (c != S(0)) acc = fma(c, f[P.idx + (long long)off * s], acc);
+  }
+  return acc * K.h12[a];
+}
+
+// PE-local 4th-order first derivative with the stencil written out per kind
+// (the FP32 form: cheaper than the table when the FP64 pipe is not the limit).
 template <typename S>
 __device__ __forceinline__ S local_d1(const Geom& g, const Coef<S>& K, const Pt& P, int a, const S* __restrict__ f) {
   const long long s = g.stride[a];
   const long long i = P.idx;
-  if (central_fits(g, P, a)) {
+  const int kind = local_kind_of(g, P, a);
+  if (kind == 0) {
     if (g.pes[a] == 1) {
       auto at = [&](int off) {
         int c2 = P.c[a] + off;
@@ -279,22 +308,34 @@ __device__ __forceinline__ S local_d1(const Geom& g, const Coef<S>& K, const Pt&
     return fma(K.c1[a], f[i + s] - f[i - s], K.c2[a] * (f[i + 2 * s] - f[i - 2 * s]));
   }
   const S h = K.h12[a];
-  const int li = P.li[a], nl = g.nl[a];
-  if (li == 0)
+  if (kind == 1)
     return h * (S(-25) * f[i] + S(48) * f[i + s] - S(36) * f[i + 2 * s] + S(16) * f[i + 3 * s] - S(3) * f[i + 4 * s]);
-  if (li == 1)
+  if (kind == 2)
     return h * (S(-3) * f[i - s] - S(10) * f[i] + S(18) * f[i + s] - S(6) * f[i + 2 * s] + f[i + 3 * s]);
-  if (li == nl - 2)
+  if (kind == 3)
     return h * (S(3) * f[i + s] + S(10) * f[i] - S(18) * f[i - s] + S(6) * f[i - 2 * s] - f[i - 3 * s]);
   return h * (S(25) * f[i] - S(48) * f[i - s] + S(36) * f[i - 2 * s] - S(16) * f[i - 3 * s] + S(3) * f[i - 4 * s]);
 }
 
-// d/dx_a (d f/dx_b) with Gb = AT df/dx_b and Ga = AT df/dx_a.
+// d/dx_a (d f/dx_b) with Gb = AT df/dx_b and Ga = AT df/dx_a (Sec. 2.1): the
+// central derivative in a of Gb inside (fast path), the average of the two
+// PE-local derivatives at PE-boundary points.  The FP64 form evaluates the
+// one-sided stencils from a table out of line (fewer FP64-pipe instructions);
+// the FP32 form keeps them inline.
 template <typename S>
 __device__ __forceinline__ S mixed(const Geom& g, const Coef<S>& K, const Pt& P, int a, int b, const S* Gb,
                                    const S* Ga) {
-  if (central_fits(g, P, a) && central_fits(g, P, b)) return local_d1(g, K, P, a, Gb);
-  return S(0.5) * (local_d1(g, K, P, a, Gb) + local_d1(g, K, P, b, Ga));
+  if (sizeof(S) == 4) {
+    if (local_kind_of(g, P, a) == 0 && local_kind_of(g, P, b) == 0) return local_d1(g, K, P, a, Gb);
+    return S(0.5) * (local_d1(g, K, P, a, Gb) + local_d1(g, K, P, b, Ga));
+  }
+  const int ka = local_kind_of(g, P, a), kb = local_kind_of(g, P, b);
+  if (ka == 0 && kb == 0 && g.pes[a] > 1) {
+    const long long s = g.stride[a], i = P.idx;
+    return fma(K.c1[a], Gb[i + s] - Gb[i - s], K.c2[a] * (Gb[i + 2 * s] - Gb[i - 2 * s]));
+  }
+  if (ka == 0 && kb == 0) return local_d1_table(g, K, P, a, Gb, 0);
+  return S(0.5) * (local_d1_table(g, K, P, a, Gb, ka) + local_d1_table(g, K, P, b, Ga, kb));
 }
 
 template <typename T>
@@ -419,7 +460,7 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
 
 // ---------------------------------------------------------------------------
 template <typename S>
-__global__ void __launch_bounds__(256) k_main(Geom g, Coef<S> K, StepArgs<S> A) {
+__global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> A) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const bool active = idx < g.npts;
   S st[kNumStat];

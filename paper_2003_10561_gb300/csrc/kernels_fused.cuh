@@ -8,8 +8,9 @@
 // planes beyond a PE z-face hold the z ghosts, so every stencil of Sec. 2.1 is
 // a plain read of the window:
 //   * first / second derivatives of u, v, w, T in x, y, z;
-//   * inviscid fluxes recomputed from (rho, u, v, w, T, H) at window cells, or
-//     read from the ghost arrays across a PE face;
+//   * inviscid fluxes: each plane's x and y fluxes are formed once into shared
+//     arrays (from the window, or from the ghost arrays across a PE face) and
+//     the column's z fluxes are carried in a five-plane register queue;
 //   * mixed derivatives: the central cross stencil D_a(D_b f) inside, and at
 //     PE-boundary points the average of the PE-local derivative in a of the AT
 //     derivative in b and vice versa -- the inner AT derivatives are formed from
@@ -38,7 +39,10 @@ struct TileShape {
 
 template <typename S>
 inline size_t fused_smem_bytes(int TX, int TY) {
-  const size_t win = (size_t)kWinPlanes * kWinFields * (TX + 4) * (TY + 4) * sizeof(S);
+  // nine window planes, then the x fluxes of the current plane on TY rows of
+  // TX+4 cells and the y fluxes on TY+4 rows of TX cells
+  const size_t win = ((size_t)kWinPlanes * kWinFields * (TX + 4) * (TY + 4) +
+                      5 * (size_t)TY * (TX + 4) + 5 * (size_t)(TY + 4) * TX) * sizeof(S);
   const size_t red = (size_t)kReduceScratchDoubles * sizeof(double);
   return win > red ? win : red;
 }
@@ -128,6 +132,23 @@ __device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K
   }
 }
 
+// Inviscid flux component e of direction d of the window cell at element
+// offset `at` (plane base + cell): rho u_d, rho u_i u_d + p delta_id, H u_d,
+// with p = rho T / gamma.
+template <typename S, int TX, int TY>
+__device__ __forceinline__ S cell_flux(const Coef<S>& K, const S* win, int at, int d, int e) {
+  using T_ = TileShape<TX, TY>;
+  const S r = win[at + WF_R * T_::CELLS];
+  const S ud = win[at + (WF_U + d) * T_::CELLS];
+  if (e == 0) return r * ud;
+  if (e == 4) return win[at + WF_H * T_::CELLS] * ud;
+  const int i = e - 1;
+  const S rud = r * ud;
+  const S ui = win[at + (WF_U + i) * T_::CELLS];
+  if (i != d) return rud * ui;
+  return fma(rud, ui, r * win[at + WF_T * T_::CELLS] * K.inv_gamma);
+}
+
 // PE-local first-derivative stencil kind of the Sec. 2.1 mixed rule at local
 // index li of a direction with nl points: 0 central, 1 first point, 2 second,
 // 3 second to last, 4 last point of the PE.
@@ -173,29 +194,46 @@ struct PointWin {
     return fma(K.c1[b], sh(f, b, 1, dx, dy, dz) - sh(f, b, -1, dx, dy, dz),
                K.c2[b] * (sh(f, b, 2, dx, dy, dz) - sh(f, b, -2, dx, dy, dz)));
   }
-  // flux component e of direction d at the cell (dx, dy, dz): rho u_d,
-  // rho u_i u_d + p delta_id, H u_d with p = rho T / gamma
-  __device__ __forceinline__ S flux(const Coef<S>& K, int d, int e, int dx, int dy, int dz) const {
-    const S r = at(WF_R, dx, dy, dz);
-    const S ud = at(WF_U + d, dx, dy, dz);
-    if (e == 0) return r * ud;
-    if (e == 4) return at(WF_H, dx, dy, dz) * ud;
-    const int i = e - 1;
-    const S rud = r * ud;
-    const S ui = at(WF_U + i, dx, dy, dz);
-    if (i != d) return rud * ui;
-    return fma(rud, ui, r * at(WF_T, dx, dy, dz) * K.inv_gamma);
-  }
-  // d/dx_a (d f/dx_b) by the three-step rule of Sec. 2.1
-  __device__ __forceinline__ S mixed(const Coef<S>& K, int f, int a, int b, const int (&kind)[3]) const {
+  // d/dx_a (d f/dx_b) by the three-step rule of Sec. 2.1: central fast path
+  // inside; at PE-boundary points the FP64 form runs the one PE-local stencil
+  // that applies from a table out of line (fewer FP64-pipe instructions), the
+  // FP32 form keeps the stencils inline
+  __device__ __forceinline__ S mixed(const Coef<S>& K, int f, int a, int b, const int (&kind)[3], int s0) const {
     auto inner = [&](int outer, int in, int off) {
       return d1(K, f, in, outer == 0 ? off : 0, outer == 1 ? off : 0, outer == 2 ? off : 0);
     };
     if (kind[a] == 0 && kind[b] == 0)
       return K.h12[a] * apply_local<S>(0, [&](int o) { return inner(a, b, o); });
-    const S pa = K.h12[a] * apply_local<S>(kind[a], [&](int o) { return inner(a, b, o); });
-    const S pb_ = K.h12[b] * apply_local<S>(kind[b], [&](int o) { return inner(b, a, o); });
-    return S(0.5) * (pa + pb_);
+    if (sizeof(S) == 4) {   // FP32 form: the stencils inline
+      const S pa = K.h12[a] * apply_local<S>(kind[a], [&](int o) { return inner(a, b, o); });
+      const S pb_ = K.h12[b] * apply_local<S>(kind[b], [&](int o) { return inner(b, a, o); });
+      return S(0.5) * (pa + pb_);
+    }
+    return S(0.5) * (boundary_part(K, f, a, b, kind[a], s0) + boundary_part(K, f, b, a, kind[b], s0));
+  }
+  // PE-local derivative along `outer` (stencil `kind`) of the AT derivative
+  // along `in`, offsets taken from the table at run time
+  __device__ __noinline__ S boundary_part(const Coef<S>& K, int f, int outer, int in, int kind, int s0) const {
+    S acc = S(0);
+    for (int i = 0; i < 5; ++i) {
+      const S c = local_coef(S(0), kind, i);
+      if (c == S(0)) continue;
+      const int o = kLocalOff[kind][i];
+      int dz = 0, dx = 0, dy = 0;
+      if (outer == 0) dx = o; else if (outer == 1) dy = o; else dz = o;
+      // plane z + dz + k for the inner offsets k (only when the inner direction is z)
+      auto val = [&](int k) {
+        int zz = dz + (in == 2 ? k : 0);
+        int sl = s0 + 4 + zz;
+        sl = sl >= kWinPlanes ? sl - kWinPlanes : sl;
+        const int cellp = pb[4] - (((s0 + 4) % kWinPlanes) * T_::PLANE);   // the point's cell
+        const int xx = dx + (in == 0 ? k : 0), yy = dy + (in == 1 ? k : 0);
+        return win[sl * T_::PLANE + cellp + f * T_::CELLS + yy * T_::CX + xx];
+      };
+      const S d = fma(K.c1[in], val(1) - val(-1), K.c2[in] * (val(2) - val(-2)));
+      acc = fma(c, d, acc);
+    }
+    return acc * K.h12[outer];
   }
 };
 
@@ -249,10 +287,78 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
   const int li_x = x - F.base[0], li_y = y - F.base[1];
   const int kind_x = local_kind(g.pes[0], li_x, g.nl[0]), kind_y = local_kind(g.pes[1], li_y, g.nl[1]);
   const S a0sum = K.a0[0] + K.a0[1] + K.a0[2];
+  const int tid = ty * TX + tx;
+  S* FX = win + kWinPlanes * T_::PLANE;        // [5][TY][TX+4]
+  S* FY = FX + 5 * TY * T_::CX;                // [5][TY+4][TX]
+  const long long qsx = 4LL * g.pes[0] * g.plane[0], qsy = 4LL * g.pes[1] * g.plane[1];
+  const long long qsz = 4LL * g.pes[2] * g.plane[2];
+
+  // z fluxes of this column at one plane (z ghosts beyond a PE z-face)
+  auto zflux = [&](int zp, int slot, S (&out)[5]) {
+    if (F.beyond(g, 2, zp)) {
+      const long long gi = (long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] + (long long)y * g.n[0] + x;
+#pragma unroll
+      for (int e = 0; e < 5; ++e) out[e] = A.GH[2][e * qsz + gi];
+    } else {
+#pragma unroll
+      for (int e = 0; e < 5; ++e) out[e] = cell_flux<S, TX, TY>(K, win, slot * T_::PLANE + cell, 2, e);
+    }
+  };
+  // queue of the z fluxes at planes z-2, z-1, z, z+1, z+2
+  S qz[5][5];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) zflux(zs - 2 + k, 2 + k, qz[k]);
+
   int s0 = 0;                                  // slot of plane z - 4
   for (int z = zs; z < zs + ZC; ++z) {
     const int snew = s0 + 8 >= kWinPlanes ? s0 + 8 - kWinPlanes : s0 + 8;   // slot of plane z + 4
     fused_load_plane<S, TX, TY>(g, K, A, F, win, snew * T_::PLANE, z + 4);
+    __syncthreads();
+    // fluxes of the current plane: x on x-extended rows, y on y-extended columns
+    {
+      const int sz = s0 + 4 >= kWinPlanes ? s0 + 4 - kWinPlanes : s0 + 4;   // slot of plane z
+      const int pbz = sz * T_::PLANE;
+#pragma unroll
+      for (int c0 = 0; c0 < TY * T_::CX; c0 += T_::THREADS) {
+        const int c = c0 + tid;
+        if (c < TY * T_::CX) {
+          const int r = c / T_::CX, cxw = c - r * T_::CX;
+          const int xg = F.x0 - 2 + cxw, yg = F.y0 + r;
+          if (F.beyond(g, 0, xg)) {
+            const long long gi = (long long)(4 * F.pe[0] + F.ghost_slot(g, 0, xg)) * g.plane[0] +
+                                 (long long)z * g.n[1] + yg;
+#pragma unroll
+            for (int e = 0; e < 5; ++e) FX[e * TY * T_::CX + c] = A.GH[0][e * qsx + gi];
+          } else {
+            const int at = pbz + (r + 2) * T_::CX + cxw;
+#pragma unroll
+            for (int e = 0; e < 5; ++e) FX[e * TY * T_::CX + c] = cell_flux<S, TX, TY>(K, win, at, 0, e);
+          }
+        }
+      }
+#pragma unroll
+      for (int c0 = 0; c0 < (TY + 4) * TX; c0 += T_::THREADS) {
+        const int c = c0 + tid;
+        if (c < (TY + 4) * TX) {
+          const int r = c / TX, cxl = c - r * TX;
+          const int xg = F.x0 + cxl, yg = F.y0 - 2 + r;
+          if (F.beyond(g, 1, yg)) {
+            const long long gi = (long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] +
+                                 (long long)z * g.n[0] + xg;
+#pragma unroll
+            for (int e = 0; e < 5; ++e) FY[e * (TY + 4) * TX + c] = A.GH[1][e * qsy + gi];
+          } else {
+            const int at = pbz + r * T_::CX + cxl + 2;
+#pragma unroll
+            for (int e = 0; e < 5; ++e) FY[e * (TY + 4) * TX + c] = cell_flux<S, TX, TY>(K, win, at, 1, e);
+          }
+        }
+      }
+      // z fluxes of this column at plane z+2 enter the queue
+      const int s2 = s0 + 6 >= kWinPlanes ? s0 + 6 - kWinPlanes : s0 + 6;
+      zflux(z + 2, s2, qz[4]);
+    }
     __syncthreads();
     PointWin<S, TX, TY> W;
     W.win = win;
@@ -265,31 +371,21 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
     const int kind[3] = {kind_x, kind_y, local_kind(g.pes[2], li_z, g.nl[2])};
     const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
 
-    // ---- inviscid flux divergence: -sum_d D_d F_d (ghost fluxes across PE faces)
-    S R[5] = {S(0), S(0), S(0), S(0), S(0)};
+    // ---- inviscid flux divergence: -sum_d D_d F_d (ghost fluxes already in
+    // the flux arrays / queue across PE faces)
+    S R[5];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int gc = d == 0 ? x : (d == 1 ? y : z);
-      const long long qs = 4LL * g.pes[d] * g.plane[d];
-      const long long pl = d == 0 ? (long long)z * g.n[1] + y : (d == 1 ? (long long)z * g.n[0] + x
-                                                                          : (long long)y * g.n[0] + x);
-      bool gb[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) gb[j] = F.beyond(g, d, gc + (j < 2 ? j - 2 : j - 1));
-#pragma unroll
-      for (int e = 0; e < 5; ++e) {
-        S fv[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int m = j < 2 ? j - 2 : j - 1;
-          if (gb[j])
-            fv[j] = A.GH[d][e * qs + (long long)(4 * F.pe[d] + F.ghost_slot(g, d, gc + m)) * g.plane[d] + pl];
-          else
-            fv[j] = W.flux(K, d, e, d == 0 ? m : 0, d == 1 ? m : 0, d == 2 ? m : 0);
-        }
-        R[e] = fma(-K.c1[d], fv[2] - fv[1], R[e]);
-        R[e] = fma(-K.c2[d], fv[3] - fv[0], R[e]);
-      }
+    for (int e = 0; e < 5; ++e) {
+      const S* fx = FX + e * TY * T_::CX + ty * T_::CX + tx + 2;
+      const S* fy = FY + e * (TY + 4) * TX + (ty + 2) * TX + tx;
+      S acc = S(0);
+      acc = fma(-K.c1[0], fx[1] - fx[-1], acc);
+      acc = fma(-K.c2[0], fx[2] - fx[-2], acc);
+      acc = fma(-K.c1[1], fy[TX] - fy[-TX], acc);
+      acc = fma(-K.c2[1], fy[2 * TX] - fy[-2 * TX], acc);
+      acc = fma(-K.c1[2], qz[3][e] - qz[1][e], acc);
+      acc = fma(-K.c2[2], qz[4][e] - qz[0][e], acc);
+      R[e] = acc;
     }
 
     // ---- second derivatives of u, v, w, T; first derivatives at the point
@@ -318,7 +414,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
       S s = d2diag[i];
 #pragma unroll
       for (int k = 0; k < 3; ++k)
-        if (k != i) s += W.mixed(K, WF_U + k, i, k, kind);
+        if (k != i) s += W.mixed(K, WF_U + k, i, k, kind, s0);
       gth[i] = s;
     }
 
@@ -437,6 +533,10 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
       kp = min(kp, okey(p));
     }
     s0 = s0 + 1 >= kWinPlanes ? 0 : s0 + 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int e = 0; e < 5; ++e) qz[k][e] = qz[k + 1][e];
     __syncthreads();
   }
   double tot[kNumStat];
