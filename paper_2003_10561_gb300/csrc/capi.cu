@@ -57,6 +57,11 @@ struct at_dns {
   double stats_time = 0.0;
   size_t bytes = 0;
   std::string err;
+  DevState* ds = nullptr;       // device copy of (n, first, cur)
+  // captured one-step graphs per delay mode (replayed by at_dns_step)
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+  double gdt[3] = {0, 0, 0};    // dt the graphs were captured with
+  bool use_graphs = true;
   // kernel path: fused single pass on TX x TY tiles marching ZC planes, or multi-pass
   bool fused = false;
   int TX = 0, TY = 0, ZC = 0;
@@ -71,11 +76,25 @@ struct at_dns {
 // small kernels
 namespace {
 
-__global__ void k_delay_map(uint8_t* out, int P, int Px, int Py, long long n, int mode, int L, int cr,
+__global__ void k_delay_map(uint8_t* out, int P, long long n, const DevState* ds, int mode, int L, int cr,
                             uint32_t k0, uint32_t k1) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P * 6) return;
+  if (ds) n = ds->n;
   out[i] = (uint8_t)delay_of(mode, n, i / 6, i % 6, L, cr, k0, k1);
+}
+
+__global__ void k_set_state(DevState* ds, long long n, int first, int cur) {
+  ds->n = n;
+  ds->first = first;
+  ds->cur = cur;
+}
+
+// End of a step: level n+1 is in the other buffer and the next step is AB2.
+__global__ void k_advance_state(DevState* ds) {
+  ds->n += 1;
+  ds->first = 0;
+  ds->cur = 1 - ds->cur;
 }
 
 template <typename S>
@@ -173,9 +192,11 @@ __global__ void k_stats_final(const double* __restrict__ partial, long long nb, 
 // P removes the component along the wavevector.  One thread per mode runs the
 // recursion from step `from` to step `to` (from = 0 starts it).
 __global__ void k_force_advance(const Mode3* __restrict__ modes, int nmodes, double2* fhat, long long from,
-                                long long to, double a, double b, double amp, uint32_t k0, uint32_t k1) {
+                                long long to, const DevState* ds, double a, double b, double amp, uint32_t k0,
+                                uint32_t k1) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= nmodes) return;
+  if (ds) from = to = ds->n;   // advance to the current step only
   const Mode3 md = modes[m];
   const double kv[3] = {(double)md.kx, (double)md.ky, (double)md.kz};
   const double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
@@ -383,68 +404,92 @@ struct Ops {
     return AT_DNS_OK;
   }
 
-  // One RHS evaluation at level n; update (step) or write R to Rout.
-  static int evaluate(at_dns* h, int mode, bool update, double* Rout, bool stats, bool reset_health) {
+  // Queue one RHS evaluation at the device level n on stream `st`: update
+  // (a step, advancing the device step state) or write R to Rout.  Touches no
+  // host-side state, so it can be captured into a graph.
+  static int launch_step(at_dns* h, int mode, bool update, double* Rout, bool stats, bool reset_health,
+                         cudaStream_t st) {
     const Geom& g = h->g;
     const int P = g.pes[0] * g.pes[1] * g.pes[2];
     const uint64_t seed = h->cfg.seed;
     {
       Timed t(h, KD_DELAY);
-      k_delay_map<<<nblk(P * 6), kBlock, 0, h->st>>>(h->dmap, P, g.pes[0], g.pes[1], h->n, mode, h->cfg.max_delay,
-                                                    h->cfg.comm_period, (uint32_t)seed, (uint32_t)(seed >> 32));
+      k_delay_map<<<nblk(P * 6), kBlock, 0, st>>>(h->dmap, P, 0, h->ds, mode, h->cfg.max_delay,
+                                                 h->cfg.comm_period, (uint32_t)seed, (uint32_t)(seed >> 32));
     }
     CK(cudaGetLastError());
-    S* Ucur = U(h, h->cur);
+    const S* U0 = U(h, 0);
+    const S* U1 = U(h, 1);
     const Coef<S> K = make_coef<S>(g, h->ph, h->dt);
     S* GH[3] = {(S*)h->GH[0], (S*)h->GH[1], (S*)h->GH[2]};
     S* ring[3] = {(S*)h->ring[0], (S*)h->ring[1], (S*)h->ring[2]};
-    if (!h->fused) { Timed t(h, KD_PRIM); CK(launch_prim<S>(g, K, Ucur, (S*)h->PQ, h->st)); }
+    if (!h->fused) { Timed t(h, KD_PRIM); CK(launch_prim<S>(g, K, U0, U1, h->ds, (S*)h->PQ, st)); }
     if (g.pes[0] > 1 || g.pes[1] > 1 || g.pes[2] > 1) {
       Timed t(h, KD_GHOST);
-      CK(launch_ghost<S>(g, K, Ucur, h->fused ? nullptr : (S*)h->PQ, GH, ring, h->dmap, h->n, h->st));
+      CK(launch_ghost<S>(g, K, U0, U1, h->ds, h->fused ? nullptr : (S*)h->PQ, GH, ring, h->dmap, 0, st));
     }
-    if (!h->fused) { Timed t(h, KD_GRAD); CK(launch_grad<S>(g, K, (S*)h->PQ, GH, (S*)h->G, h->st)); }
+    if (!h->fused) { Timed t(h, KD_GRAD); CK(launch_grad<S>(g, K, (S*)h->PQ, GH, (S*)h->G, st)); }
     if (h->cfg.forcing) {
       const long long lines = (long long)g.n[2] * g.n[1];
       {
         Timed t(h, KD_FLINES);
-        k_force_lines<S><<<nblk(lines, 128), 128, 0, h->st>>>(g, h->modes, h->nmodes, h->fhat, h->fK,
-                                                              (vec2_t<S>*)h->fB);
+        k_force_lines<S><<<nblk(lines, 128), 128, 0, st>>>(g, h->modes, h->nmodes, h->fhat, h->fK, (vec2_t<S>*)h->fB);
       }
       CK(cudaGetLastError());
     }
-    k_reset_words<<<1, 1, 0, h->st>>>(h->words, reset_health ? 1 : 0);
+    k_reset_words<<<1, 1, 0, st>>>(h->words, reset_health ? 1 : 0);
     CK(cudaGetLastError());
     StepArgs<S> a{};
-    a.U = Ucur;
-    a.Unext = U(h, 1 - h->cur);
+    a.Ub[0] = U0;
+    a.Ub[1] = U1;
+    a.Ulob[0] = h->comp ? (S*)h->Ulo[0] : nullptr;
+    a.Ulob[1] = h->comp ? (S*)h->Ulo[1] : nullptr;
+    a.ds = h->ds;
     a.PQ = (S*)h->PQ;
     a.G = (S*)h->G;
     for (int d = 0; d < 3; ++d) { a.GH[d] = GH[d]; a.ring[d] = ring[d]; }
     a.Rprev = (S*)h->Rprev;
-    a.Ulo = h->comp ? (const S*)h->Ulo[h->cur] : nullptr;
-    a.Ulo_next = h->comp ? (S*)h->Ulo[1 - h->cur] : nullptr;
     a.Rout = Rout;
     a.partial = h->partial;
     a.words = h->words;
     a.fB = h->cfg.forcing ? (const vec2_t<S>*)h->fB : nullptr;
     a.fX = (const vec2_t<S>*)h->fX;
     a.fK = h->fK;
-    a.n = h->n;
     a.dt = h->dt;
-    a.first = h->first ? 1 : 0;
     a.do_update = update ? 1 : 0;
     a.do_stats = stats ? 1 : 0;
     if (h->fused) {
       Timed t(h, KD_MAIN);
-      CK(launch_fused<S>(g, K, a, h->TX, h->TY, h->ZC, h->st));
+      CK(launch_fused<S>(g, K, a, h->TX, h->TY, h->ZC, st));
     } else {
       Timed t(h, KD_MAIN);
-      CK(launch_main<S>(g, K, a, h->st));
+      CK(launch_main<S>(g, K, a, st));
     }
     if (stats) {
-      { Timed t(h, KD_STATS); k_stats_final<<<kNumStat, 256, 0, h->st>>>(h->partial, h->nblk_step, h->sums); }
+      { Timed t(h, KD_STATS); k_stats_final<<<kNumStat, 256, 0, st>>>(h->partial, h->nblk_step, h->sums); }
       CK(cudaGetLastError());
+    }
+    if (update) {
+      k_advance_state<<<1, 1, 0, st>>>(h->ds);
+      CK(cudaGetLastError());
+      if (h->cfg.forcing) {
+        const double a_ = std::exp(-h->dt / h->cfg.f_tcorr);
+        const double b_ = h->cfg.f_amp * std::sqrt(1.0 - a_ * a_);
+        {
+          Timed t(h, KD_FADV);
+          k_force_advance<<<nblk(h->nmodes, 64), 64, 0, st>>>(h->modes, h->nmodes, h->fhat, 0, 0, h->ds, a_, b_,
+                                                             h->cfg.f_amp, (uint32_t)h->cfg.f_seed,
+                                                             (uint32_t)(h->cfg.f_seed >> 32));
+        }
+        CK(cudaGetLastError());
+      }
+    }
+    return AT_DNS_OK;
+  }
+
+  // Host-side bookkeeping of one queued evaluation (mirrors the device state).
+  static void account(at_dns* h, bool update, bool stats) {
+    if (stats) {
       h->stats_valid = true;
       h->stats_step = h->n;
       h->stats_time = h->t;
@@ -454,18 +499,13 @@ struct Ops {
       h->first = false;
       h->n += 1;
       h->t += h->dt;
-      if (h->cfg.forcing) {
-        const double a_ = std::exp(-h->dt / h->cfg.f_tcorr);
-        const double b_ = h->cfg.f_amp * std::sqrt(1.0 - a_ * a_);
-        {
-          Timed t(h, KD_FADV);
-          k_force_advance<<<nblk(h->nmodes, 64), 64, 0, h->st>>>(h->modes, h->nmodes, h->fhat, h->n, h->n, a_, b_,
-                                                                h->cfg.f_amp, (uint32_t)h->cfg.f_seed,
-                                                                (uint32_t)(h->cfg.f_seed >> 32));
-        }
-        CK(cudaGetLastError());
-      }
     }
+  }
+
+  static int evaluate(at_dns* h, int mode, bool update, double* Rout, bool stats, bool reset_health) {
+    int rc = launch_step(h, mode, update, Rout, stats, reset_health, h->st);
+    if (rc) return rc;
+    account(h, update, stats);
     return AT_DNS_OK;
   }
 
@@ -498,11 +538,40 @@ bool pick_fused_shape(const Geom& g, int& TX, int& TY, int& ZC) {
   return ZC > 0;
 }
 
+void drop_graphs(at_dns* h) {
+  for (int m = 0; m < 3; ++m)
+    if (h->gexec[m]) {
+      cudaGraphExecDestroy(h->gexec[m]);
+      h->gexec[m] = nullptr;
+    }
+}
+
+// Capture (once per delay mode and dt) the kernels of one step into a graph.
+int step_graph(at_dns* h, int mode, bool stats) {
+  if (h->gexec[mode] && h->gdt[mode] == h->dt) return AT_DNS_OK;
+  if (h->gexec[mode]) { cudaGraphExecDestroy(h->gexec[mode]); h->gexec[mode] = nullptr; }
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
+  const int rc = h->p64 ? Ops<double>::launch_step(h, mode, true, nullptr, stats, false, h->st)
+                        : Ops<float>::launch_step(h, mode, true, nullptr, stats, false, h->st);
+  const cudaError_t e = cudaStreamEndCapture(h->st, &graph);
+  if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+  if (e != cudaSuccess) return fail(h, AT_DNS_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  const cudaError_t e2 = cudaGraphInstantiate(&h->gexec[mode], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) {
+    h->gexec[mode] = nullptr;
+    return fail(h, AT_DNS_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+  }
+  h->gdt[mode] = h->dt;
+  return AT_DNS_OK;
+}
+
 int force_reset(at_dns* h, long long step) {
   if (!h->cfg.forcing) return AT_DNS_OK;
   const double a_ = std::exp(-h->dt / h->cfg.f_tcorr);
   const double b_ = h->cfg.f_amp * std::sqrt(1.0 - a_ * a_);
-  k_force_advance<<<nblk(h->nmodes, 64), 64, 0, h->st>>>(h->modes, h->nmodes, h->fhat, 0, step, a_, b_,
+  k_force_advance<<<nblk(h->nmodes, 64), 64, 0, h->st>>>(h->modes, h->nmodes, h->fhat, 0, step, nullptr, a_, b_,
                                                         h->cfg.f_amp, (uint32_t)h->cfg.f_seed,
                                                         (uint32_t)(h->cfg.f_seed >> 32));
   CK(cudaGetLastError());
@@ -655,7 +724,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
       return create_fail(h, rc);
   }
   const int P = g.pes[0] * g.pes[1] * g.pes[2];
-  if ((rc = dev_alloc(h, (void**)&h->dmap, (size_t)P * 6)) ||
+  if ((rc = dev_alloc(h, (void**)&h->ds, sizeof(DevState))) || (rc = dev_alloc(h, (void**)&h->dmap, (size_t)P * 6)) ||
       (rc = dev_alloc(h, (void**)&h->partial, (size_t)h->nblk_step * kNumStat * sizeof(double))) ||
       (rc = dev_alloc(h, (void**)&h->sums, kNumStat * sizeof(double))) ||
       (rc = dev_alloc(h, (void**)&h->words, 4 * sizeof(unsigned long long))))
@@ -718,6 +787,8 @@ int at_dns_set_history(at_dns_t* h, const double* levels, int32_t nlevels, int64
   h->t = step * h->dt;
   h->first = true;
   h->has_state = true;
+  k_set_state<<<1, 1, 0, h->st>>>(h->ds, step, 1, h->cur);
+  CK(cudaGetLastError());
   h->stats_valid = false;
   if ((rc = force_reset(h, step))) return rc;
   CK(cudaStreamSynchronize(h->st));
@@ -773,10 +844,24 @@ int at_dns_step(at_dns_t* h, int32_t nsteps, int32_t delay_mode) {
   if (nsteps < 0) return fail(h, AT_DNS_E_INVALID_ARG, "nsteps must be >= 0");
   if (!h->has_state) return fail(h, AT_DNS_E_STATE, "no state set");
   const bool stats = h->cfg.stats_every == 1;
-  for (int s = 0; s < nsteps; ++s) {
-    rc = h->p64 ? Ops<double>::evaluate(h, delay_mode, true, nullptr, stats, s == 0)
-                : Ops<float>::evaluate(h, delay_mode, true, nullptr, stats, s == 0);
-    if (rc) return rc;
+  // replay a captured one-step graph when the handle runs on its own stream
+  // (the legacy default stream cannot be captured) and no per-launch event
+  // timing is requested; otherwise launch kernel by kernel
+  const bool graph = h->use_graphs && h->st != nullptr && !h->prof && nsteps > 1;
+  if (graph) {
+    if ((rc = step_graph(h, delay_mode, stats))) return rc;
+    k_reset_words<<<1, 1, 0, h->st>>>(h->words, 1);
+    CK(cudaGetLastError());
+    for (int s = 0; s < nsteps; ++s) {
+      CK(cudaGraphLaunch(h->gexec[delay_mode], h->st));
+      if (h->p64) Ops<double>::account(h, true, stats); else Ops<float>::account(h, true, stats);
+    }
+  } else {
+    for (int s = 0; s < nsteps; ++s) {
+      rc = h->p64 ? Ops<double>::evaluate(h, delay_mode, true, nullptr, stats, s == 0)
+                  : Ops<float>::evaluate(h, delay_mode, true, nullptr, stats, s == 0);
+      if (rc) return rc;
+    }
   }
   if (!stats) h->stats_valid = false;
   if (nsteps > 0) {
@@ -846,7 +931,7 @@ int at_dns_get_delay_map(at_dns_t* h, int64_t step, int32_t mode, uint8_t* out) 
   const int P = g.pes[0] * g.pes[1] * g.pes[2];
   uint8_t* tmp = nullptr;
   if ((rc = dev_alloc(h, (void**)&tmp, (size_t)P * 6))) return rc;
-  k_delay_map<<<nblk(P * 6), kBlock, 0, h->st>>>(tmp, P, g.pes[0], g.pes[1], step, mode, h->cfg.max_delay,
+  k_delay_map<<<nblk(P * 6), kBlock, 0, h->st>>>(tmp, P, step, nullptr, mode, h->cfg.max_delay,
                                                 h->cfg.comm_period, (uint32_t)h->cfg.seed,
                                                 (uint32_t)(h->cfg.seed >> 32));
   cudaError_t e = cudaGetLastError();
@@ -870,7 +955,9 @@ int at_dns_get_info(at_dns_t* h, at_dns_info_t* out) {
   out->boundary_fraction = (double)(nt - ni) / (double)nt;
   out->device_bytes = h->bytes;
   const bool ghost = h->g.pes[0] > 1 || h->g.pes[1] > 1 || h->g.pes[2] > 1;
-  out->kernels_per_step = (h->fused ? 3 : 5) + (ghost ? 1 : 0) + (h->cfg.stats_every ? 1 : 0) +
+  // delay map, word reset, main kernel, step-state advance (+ derived fields
+  // and gradients on the multi-pass path)
+  out->kernels_per_step = (h->fused ? 4 : 6) + (ghost ? 1 : 0) + (h->cfg.stats_every ? 1 : 0) +
                           (h->cfg.forcing ? 2 : 0);
   out->kernel_path = h->fused ? AT_DNS_PATH_FUSED : AT_DNS_PATH_MULTIPASS;
   out->tile[0] = h->TX;
@@ -935,7 +1022,8 @@ const char* at_dns_last_error(const at_dns_t* h) {
 void at_dns_destroy(at_dns_t* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
-  void* ptrs[] = {h->U[0], h->U[1], h->Ulo[0], h->Ulo[1], h->PQ, h->G, h->Rprev, h->GH[0], h->GH[1], h->GH[2], h->ring[0], h->ring[1],
+  drop_graphs(h);
+  void* ptrs[] = {h->ds, h->U[0], h->U[1], h->Ulo[0], h->Ulo[1], h->PQ, h->G, h->Rprev, h->GH[0], h->GH[1], h->GH[2], h->ring[0], h->ring[1],
                   h->ring[2], h->stage, h->dmap, h->partial, h->sums, h->words, h->modes, h->fhat, h->fB, h->fX};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -170,8 +170,20 @@ template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
 template <typename S> using vec2_t = typename Vec2<S>::type;
 
+// Step state kept on the device, so that one captured step can be replayed:
+// level n of the state, the forward-Euler flag of the first AB2 step and which
+// of the two state buffers holds U^n.
+struct DevState {
+  long long n;
+  int first;
+  int cur;
+};
+
 template <typename S>
 struct StepArgs {
+  const S* Ub[2];      // both state buffers; U^n is Ub[cur]
+  S* Ulob[2];          // both low-word buffers (compensated form) or null
+  const DevState* ds;  // device step state (null: U, Unext, ... below are used as given)
   const S* U;          // [5][npts] level n
   S* Unext;            // [5][npts] level n+1 (step) -- may be null for rhs-only
   const S* PQ;         // [16][npts]
@@ -193,6 +205,19 @@ struct StepArgs {
   int do_update;       // 1: write Unext/Rprev/ring; 0: write Rout
   int do_stats;
 };
+
+// Fill the per-step fields of the arguments from the device step state.
+template <typename S>
+__device__ __forceinline__ void resolve_step(StepArgs<S>& A) {
+  if (!A.ds) return;
+  const int cur = A.ds->cur;
+  A.U = A.Ub[cur];
+  A.Unext = const_cast<S*>(A.Ub[1 - cur]);
+  A.Ulo = A.Ulob[cur];
+  A.Ulo_next = A.Ulob[1 - cur];
+  A.n = A.ds->n;
+  A.first = A.ds->first;
+}
 
 // Separately rounded products / sums (never contracted into an FMA), for the
 // error-free transformations of the compensated update.

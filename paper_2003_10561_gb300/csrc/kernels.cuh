@@ -26,10 +26,11 @@ namespace atdns {
 
 // ---------------------------------------------------------------------------
 template <typename S>
-__global__ void __launch_bounds__(256) k_prim(Geom g, Coef<S> K, const S* __restrict__ U,
-                                              S* __restrict__ PQ) {
+__global__ void __launch_bounds__(256) k_prim(Geom g, Coef<S> K, const S* __restrict__ U0, const S* __restrict__ U1,
+                                              const DevState* __restrict__ ds, S* __restrict__ PQ) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= g.npts) return;
+  const S* __restrict__ U = (ds && ds->cur) ? U1 : U0;
   const long long N = g.npts;
   const S r = U[idx], m0 = U[N + idx], m1 = U[2 * N + idx], m2 = U[3 * N + idx], E = U[4 * N + idx];
   const S inv = S(1) / r;
@@ -81,7 +82,8 @@ __device__ __forceinline__ void ghost_quantities(const Coef<S>& K, int d, const 
 // face, face 2d+1).  Ring slab index sp = 4 p + t with t = 0, 1 for local 0, 1
 // and t = 2, 3 for local nl-2, nl-1.
 template <typename S>
-__global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __restrict__ U,
+__global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __restrict__ U0,
+                                               const S* __restrict__ U1, const DevState* __restrict__ ds,
                                                const S* __restrict__ PQ, S* GH0, S* GH1, S* GH2,
                                                const S* __restrict__ ring0,
                                                const S* __restrict__ ring1,
@@ -89,6 +91,8 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
                                                const uint8_t* __restrict__ dmap, long long n,
                                                long long cnt0, long long cnt1, long long cnt2) {
   long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const S* __restrict__ U = (ds && ds->cur) ? U1 : U0;
+  if (ds) n = ds->n;
   int d;
   if (j < cnt0) d = 0;
   else if ((j -= cnt0) < cnt1) d = 1;
@@ -460,7 +464,9 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
 
 // ---------------------------------------------------------------------------
 template <typename S>
-__global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> A) {
+__global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> A0) {
+  StepArgs<S> A = A0;
+  resolve_step(A);
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const bool active = idx < g.npts;
   S st[kNumStat];

@@ -259,7 +259,9 @@ template <> struct StatAcc<float> {
 };
 
 template <typename S, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S> A, int ZC) {
+__global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S> A0, int ZC) {
+  StepArgs<S> A = A0;
+  resolve_step(A);
   using T_ = TileShape<TX, TY>;
   extern __shared__ __align__(16) unsigned char fused_smem[];
   S* win = reinterpret_cast<S*>(fused_smem);

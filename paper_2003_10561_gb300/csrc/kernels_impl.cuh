@@ -8,21 +8,23 @@ namespace atdns {
 using S = AT_DNS_SCALAR;
 
 template <>
-cudaError_t launch_prim<S>(const Geom& g, const Coef<S>& K, const S* U, S* PQ, cudaStream_t st) {
+cudaError_t launch_prim<S>(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds, S* PQ,
+                           cudaStream_t st) {
   const unsigned nb = (unsigned)((g.npts + kBlock - 1) / kBlock);
-  k_prim<S><<<nb, kBlock, 0, st>>>(g, K, U, PQ);
+  k_prim<S><<<nb, kBlock, 0, st>>>(g, K, U0, U1, ds, PQ);
   return cudaGetLastError();
 }
 
 template <>
-cudaError_t launch_ghost<S>(const Geom& g, const Coef<S>& K, const S* U, const S* PQ, S* const GH[3],
+cudaError_t launch_ghost<S>(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds,
+                            const S* PQ, S* const GH[3],
                             S* const ring[3], const uint8_t* dmap, long long n, cudaStream_t st) {
   long long cnt[3];
   for (int d = 0; d < 3; ++d) cnt[d] = g.pes[d] > 1 ? 4LL * g.pes[d] * g.plane[d] : 0;
   const long long tot = cnt[0] + cnt[1] + cnt[2];
   if (tot == 0) return cudaSuccess;
   const unsigned nb = (unsigned)((tot + kBlock - 1) / kBlock);
-  k_ghost<S><<<nb, kBlock, 0, st>>>(g, K, U, PQ, GH[0], GH[1], GH[2], ring[0], ring[1], ring[2], dmap, n,
+  k_ghost<S><<<nb, kBlock, 0, st>>>(g, K, U0, U1, ds, PQ, GH[0], GH[1], GH[2], ring[0], ring[1], ring[2], dmap, n,
                                    cnt[0], cnt[1], cnt[2]);
   return cudaGetLastError();
 }

@@ -8,10 +8,12 @@ namespace atdns {
 constexpr int kBlock = 256;
 
 template <typename S>
-cudaError_t launch_prim(const Geom& g, const Coef<S>& K, const S* U, S* PQ, cudaStream_t st);
+cudaError_t launch_prim(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds, S* PQ,
+                        cudaStream_t st);
 
 template <typename S>
-cudaError_t launch_ghost(const Geom& g, const Coef<S>& K, const S* U, const S* PQ, S* const GH[3],
+cudaError_t launch_ghost(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds,
+                         const S* PQ, S* const GH[3],
                          S* const ring[3], const uint8_t* dmap, long long n, cudaStream_t st);
 
 template <typename S>

@@ -113,7 +113,7 @@ extern "C" int at_dns_rhs_noalloc(const int32_t n[3], double gamma, double prand
 
   k_noalloc_reset<<<1, 1, 0, st>>>(words);   // the words must start cleared
   if (cudaGetLastError() != cudaSuccess) return AT_DNS_E_CUDA;
-  if (launch_prim<double>(g, K, u_dev, PQ, st) != cudaSuccess) return AT_DNS_E_CUDA;
+  if (launch_prim<double>(g, K, u_dev, u_dev, nullptr, PQ, st) != cudaSuccess) return AT_DNS_E_CUDA;
   if (launch_grad<double>(g, K, PQ, GH, G, st) != cudaSuccess) return AT_DNS_E_CUDA;
   StepArgs<double> a{};
   a.U = u_dev;

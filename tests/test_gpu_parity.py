@@ -336,3 +336,26 @@ def test_compensated_accumulation_keeps_small_increments(lib, path):
     # compensated: tracks FP64 up to the FP32 rounding of the stencil terms
     # (p and rho u u of a nearly uniform flow); plain FP32: increments lost
     assert err_c < 0.05 and err_p > 0.5 and err_c < err_p / 10, (err_c, err_p)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_graph_replay_matches_direct_launches(lib, path):
+    """Steps replayed from a captured one-step graph (handle on its own stream)
+    equal steps launched kernel by kernel (legacy stream), bit for bit, with
+    random delays and forcing active."""
+    import torch
+    n, pes = (16, 16, 16), (2, 2, 2)
+    U0 = synth.initial_state(n, k0=3.0, seed=40)
+    kw = dict(mu0=0.02, dt=3e-3, max_delay=2, seed=11, forcing=1, kf=2.0, f_amp=0.05, f_tcorr=0.4, f_seed=5)
+    stream = torch.cuda.Stream()
+    a = make(lib, n, pes, path=path, stream=stream.cuda_stream, **kw)
+    b = make(lib, n, pes, path=path, **kw)
+    for s in (a, b):
+        s.set_state(U0)
+        s.step(9, "random")
+        s.step(3, "periodic")
+    a.synchronize()
+    assert np.array_equal(a.get_state(), b.get_state())
+    sa, sb = a.stats(), b.stats()
+    assert sa["step"] == sb["step"] == 11
+    assert sa["tke"] == sb["tke"] and sa["dissipation"] == sb["dissipation"]
