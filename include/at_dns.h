@@ -220,8 +220,48 @@ int at_dns_profile(at_dns_t* h, int32_t enable);
  * Errors: INVALID_ARG, CUDA. */
 int at_dns_kernel_times(at_dns_t* h, at_dns_kernel_time_t* out, int32_t max, int32_t* count);
 
+/* Autotuner: for the current state, time `trials` right-hand-side
+ * evaluations (no state change) of every kernel path that applies -- the
+ * multi-pass path and each compiled fused tile shape (32x8, 16x16, 16x8, 8x32,
+ * 8x16, 8x8) with whole-PE, half and quarter z chunks -- and keep the fastest
+ * (at_dns_get_info reports it).  *best_ms (may be NULL) receives its time per
+ * evaluation.  Candidates that cannot get their work arrays are skipped.
+ * Errors: INVALID_ARG, STATE, CUDA. */
+int at_dns_tune(at_dns_t* h, int32_t delay_mode, int32_t trials, double* best_ms);
+
 /* Block until all work queued on the handle's stream has finished. */
 int at_dns_synchronize(at_dns_t* h);
+
+/* ---- batched ensembles --------------------------------------------------
+ * Independent members (own grid, PEs, physics, precision, delays) advance
+ * together: each at_dns_batch_step step is one launch of a captured graph
+ * holding one step of every member on its own branch, so members of uneven
+ * size run concurrently.  Members are ordinary handles (set their state, read
+ * them back through at_dns_batch_member); each runs on a stream the batch
+ * owns, and a batch step is ordered after earlier work on those streams. */
+typedef struct at_dns_batch at_dns_batch_t;
+
+/* Create `count` members from cfgs[0..count-1] (their `stream` fields are
+ * ignored); `stream` is the cudaStream_t the batch steps run on (NULL: a
+ * stream owned by the batch).  Errors: INVALID_ARG, OOM, CUDA. */
+int at_dns_batch_create(const at_dns_config_t* cfgs, int32_t count, void* stream, at_dns_batch_t** out);
+
+/* Handle of member i (owned by the batch; do not destroy it). */
+int at_dns_batch_member(at_dns_batch_t* b, int32_t i, at_dns_t** out);
+
+/* Advance every member nsteps AB2 steps with delay mode `delay_mode`; blocks
+ * until done.  Errors: INVALID_ARG, STATE (a member without state), CUDA,
+ * UNSTABLE (a member saw NaN/Inf, rho <= 0 or p <= 0). */
+int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode);
+
+/* at_dns_tune on every member. */
+int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials);
+
+/* Text of the last batch error (NULL batch: last failed batch create). */
+const char* at_dns_batch_last_error(const at_dns_batch_t* b);
+
+/* Destroy the members, their streams and the batch. */
+void at_dns_batch_destroy(at_dns_batch_t* b);
 
 /* Largest n[0]*n[1]*n[2] accepted by at_dns_rhs_noalloc (64^3). */
 #define AT_DNS_NOALLOC_MAX_POINTS 262144

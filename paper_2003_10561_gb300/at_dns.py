@@ -94,6 +94,13 @@ _SIGS = {
     "at_dns_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(at_dns_kernel_time_t), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]),
     "at_dns_synchronize": (ctypes.c_int, [_P]),
+    "at_dns_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "at_dns_batch_create": (ctypes.c_int, [ctypes.POINTER(at_dns_config_t), ctypes.c_int32, _P, ctypes.POINTER(_P)]),
+    "at_dns_batch_member": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "at_dns_batch_step": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "at_dns_batch_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "at_dns_batch_last_error": (ctypes.c_char_p, [_P]),
+    "at_dns_batch_destroy": (None, [_P]),
     "at_dns_rhs_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, _P, _P, _P]),
     "at_dns_last_error": (ctypes.c_char_p, [_P]),
@@ -245,6 +252,43 @@ def at_dns_rhs_noalloc(n, gamma, prandtl, mu0, visc_exp, u_dev, rhs_dev, stream=
         raise AtDnsError(rc, "at_dns_rhs_noalloc failed")
 
 
+def at_dns_tune(h, delay_mode, trials=3):
+    best = ctypes.c_double(0.0)
+    _check(load().at_dns_tune(h, delay_mode, trials, ctypes.byref(best)), h)
+    return best.value
+
+
+def _bcheck(rc, b=None):
+    if rc != AT_DNS_OK:
+        msg = load().at_dns_batch_last_error(b)
+        raise AtDnsError(rc, msg.decode() if msg else "")
+
+
+def at_dns_batch_create(cfgs, stream=None):
+    arr = (at_dns_config_t * len(cfgs))(*cfgs)
+    b = _P()
+    _bcheck(load().at_dns_batch_create(arr, len(cfgs), stream, ctypes.byref(b)))
+    return b
+
+
+def at_dns_batch_member(b, i):
+    h = _P()
+    _bcheck(load().at_dns_batch_member(b, i, ctypes.byref(h)), b)
+    return h
+
+
+def at_dns_batch_step(b, nsteps, delay_mode):
+    _bcheck(load().at_dns_batch_step(b, nsteps, delay_mode), b)
+
+
+def at_dns_batch_tune(b, delay_mode, trials=3):
+    _bcheck(load().at_dns_batch_tune(b, delay_mode, trials), b)
+
+
+def at_dns_batch_destroy(b):
+    load().at_dns_batch_destroy(b)
+
+
 def at_dns_last_error(h=None):
     m = load().at_dns_last_error(h)
     return m.decode() if m else ""
@@ -254,27 +298,73 @@ def at_dns_destroy(h):
     load().at_dns_destroy(h)
 
 
+def make_config(n=(32, 32, 32), pes=(1, 1, 1), precision="p64", stream=None, path="auto", **kw):
+    cfg = at_dns_config_default()
+    cfg.kernel_path = PATHS[path] if isinstance(path, str) else int(path)
+    for d in range(3):
+        cfg.n[d] = int(n[d])
+        cfg.pes[d] = int(pes[d])
+    cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if stream is not None:
+        cfg.stream = stream
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise TypeError("unknown configuration field %r" % k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Batch:
+    """Independent members advancing together (one graph launch per step).
+    `members` is a list of dicts of Solver arguments (n, pes, precision, ...)."""
+
+    def __init__(self, members, stream=None):
+        self.specs = [dict(m) for m in members]
+        cfgs = [make_config(**m) for m in self.specs]
+        self.b = at_dns_batch_create(cfgs, stream)
+        self.members = []
+        for i, m in enumerate(self.specs):
+            h = at_dns_batch_member(self.b, i)
+            self.members.append(Solver(n=m.get("n", (32, 32, 32)), pes=m.get("pes", (1, 1, 1)), handle=h))
+
+    def __len__(self):
+        return len(self.members)
+
+    def __getitem__(self, i):
+        return self.members[i]
+
+    def step(self, nsteps=1, mode="sync"):
+        at_dns_batch_step(self.b, nsteps, MODES.get(mode, mode))
+
+    def tune(self, mode="random", trials=3):
+        at_dns_batch_tune(self.b, MODES.get(mode, mode), trials)
+
+    def close(self):
+        if self.b:
+            for m in self.members:
+                m.h = None
+            at_dns_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Solver:
     """Owns one handle; methods map one-to-one onto the C ABI."""
 
-    def __init__(self, n=(32, 32, 32), pes=(1, 1, 1), precision="p64", stream=None, path="auto", **kw):
-        cfg = at_dns_config_default()
-        cfg.kernel_path = PATHS[path] if isinstance(path, str) else int(path)
-        for d in range(3):
-            cfg.n[d] = int(n[d])
-            cfg.pes[d] = int(pes[d])
-        cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        if stream is not None:
-            cfg.stream = stream
-        for k, v in kw.items():
-            if not hasattr(cfg, k):
-                raise TypeError("unknown configuration field %r" % k)
-            setattr(cfg, k, v)
+    def __init__(self, n=(32, 32, 32), pes=(1, 1, 1), precision="p64", stream=None, path="auto", handle=None,
+                 **kw):
+        cfg = make_config(n, pes, precision, stream, path, **kw)
         self.cfg = cfg
         self.n = tuple(int(v) for v in n)
         self.pes = tuple(int(v) for v in pes)
         self.npts = self.n[0] * self.n[1] * self.n[2]
-        self.h = at_dns_create(cfg)
+        self._owned = handle is None
+        self.h = at_dns_create(cfg) if handle is None else handle
 
     @property
     def n_pes(self):
@@ -328,10 +418,13 @@ class Solver:
     def kernel_times(self):
         return at_dns_kernel_times(self.h)
 
+    def tune(self, mode="random", trials=3):
+        return at_dns_tune(self.h, MODES.get(mode, mode), trials)
+
     def close(self):
-        if self.h:
+        if self.h and self._owned:
             at_dns_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

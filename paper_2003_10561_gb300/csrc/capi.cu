@@ -567,6 +567,55 @@ int step_graph(at_dns* h, int mode, bool stats) {
   return AT_DNS_OK;
 }
 
+// Switch the kernel path of a handle (allocating the multi-pass work arrays
+// on first use); captured graphs are dropped.
+int set_path(at_dns* h, bool fused, int TX, int TY, int ZC) {
+  const Geom& g = h->g;
+  if (!fused && !h->PQ) {
+    const size_t N = (size_t)g.npts;
+    int rc;
+    if ((rc = dev_alloc(h, &h->PQ, (size_t)kNumQ * N * h->ssize)) ||
+        (rc = dev_alloc(h, &h->G, (size_t)kNumGrad * N * h->ssize))) {
+      if (h->PQ) { cudaFree(h->PQ); h->PQ = nullptr; }
+      return rc;
+    }
+  }
+  h->fused = fused;
+  h->TX = fused ? TX : 0;
+  h->TY = fused ? TY : 0;
+  h->ZC = fused ? ZC : 0;
+  h->nblk_step = fused ? (long long)(g.n[0] / TX) * (g.n[1] / TY) * (g.n[2] / ZC) : main_blocks(g);
+  drop_graphs(h);
+  return AT_DNS_OK;
+}
+
+struct Candidate { bool fused; int TX, TY, ZC; };
+
+// Kernel-path candidates of the autotuner: the multi-pass path and every
+// compiled fused tile shape that fits the PE extents, with whole-PE, half and
+// quarter z chunks (at least 8 planes).
+std::vector<Candidate> tune_candidates(const Geom& g) {
+  std::vector<Candidate> out;
+  out.push_back({false, 0, 0, 0});
+  int ext[3];
+  for (int d = 0; d < 3; ++d) ext[d] = g.pes[d] > 1 ? g.nl[d] : g.n[d];
+  const int shapes[6][2] = {{32, 8}, {16, 16}, {16, 8}, {8, 32}, {8, 16}, {8, 8}};
+  int zmax = 0;
+  if (ext[2] <= 64) zmax = ext[2];
+  else
+    for (int t = 64; t >= 8; --t)
+      if (ext[2] % t == 0) { zmax = t; break; }
+  for (auto& sh : shapes) {
+    if (ext[0] % sh[0] || ext[1] % sh[1]) continue;
+    for (int div : {1, 2, 4}) {
+      const int zc = zmax / div;
+      if (zc < 8 || zmax % div || ext[2] % zc) continue;
+      out.push_back({true, sh[0], sh[1], zc});
+    }
+  }
+  return out;
+}
+
 int force_reset(at_dns* h, long long step) {
   if (!h->cfg.forcing) return AT_DNS_OK;
   const double a_ = std::exp(-h->dt / h->cfg.f_tcorr);
@@ -699,7 +748,8 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     h->err = "the fused path needs PE (or grid) extents that are multiples of 8 in x and y";
     return create_fail(h, AT_DNS_E_UNSUPPORTED);
   }
-  // AUTO takes the multi-pass path: it is the faster one on GB300 in both
+  // AUTO takes the multi-pass path (at_dns_tune can switch): it is the faster
+  // one on GB300 in both
   // precisions at the benchmark workload (FP64 is bound by the FP64 pipe, where
   // the fused path's halo recompute costs more than the work arrays' traffic)
   h->fused = can_fuse && c.kernel_path == AT_DNS_PATH_FUSED;
@@ -725,7 +775,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   }
   const int P = g.pes[0] * g.pes[1] * g.pes[2];
   if ((rc = dev_alloc(h, (void**)&h->ds, sizeof(DevState))) || (rc = dev_alloc(h, (void**)&h->dmap, (size_t)P * 6)) ||
-      (rc = dev_alloc(h, (void**)&h->partial, (size_t)h->nblk_step * kNumStat * sizeof(double))) ||
+      (rc = dev_alloc(h, (void**)&h->partial, (size_t)main_blocks(g) * kNumStat * sizeof(double))) ||
       (rc = dev_alloc(h, (void**)&h->sums, kNumStat * sizeof(double))) ||
       (rc = dev_alloc(h, (void**)&h->words, 4 * sizeof(unsigned long long))))
     return create_fail(h, rc);
@@ -1008,6 +1058,46 @@ int at_dns_kernel_times(at_dns_t* h, at_dns_kernel_time_t* out, int32_t max, int
   return AT_DNS_OK;
 }
 
+int at_dns_tune(at_dns_t* h, int32_t delay_mode, int32_t trials, double* best_ms) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  int rc;
+  if ((rc = check_mode(h, delay_mode))) return rc;
+  if (trials < 1) return fail(h, AT_DNS_E_INVALID_ARG, "trials must be >= 1");
+  if (!h->has_state) return fail(h, AT_DNS_E_STATE, "no state set");
+  const bool was_prof = h->prof;
+  h->prof = false;
+  const bool stats = h->cfg.stats_every == 1;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  Candidate pick{h->fused, h->TX, h->TY, h->ZC};
+  for (const Candidate& c : tune_candidates(h->g)) {
+    if (set_path(h, c.fused, c.TX, c.TY, c.ZC) != AT_DNS_OK) continue;   // e.g. no memory for work arrays
+    // one untimed evaluation, then `trials` timed right-hand sides (no state change)
+    for (int t = 0; t <= trials; ++t) {
+      if (t == 1) CK(cudaEventRecord(e0, h->st));
+      rc = h->p64 ? Ops<double>::launch_step(h, delay_mode, false, nullptr, stats, true, h->st)
+                  : Ops<float>::launch_step(h, delay_mode, false, nullptr, stats, true, h->st);
+      if (rc) break;
+    }
+    if (rc) { h->err.clear(); rc = AT_DNS_OK; continue; }
+    CK(cudaEventRecord(e1, h->st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms / trials < best) { best = ms / trials; pick = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if ((rc = set_path(h, pick.fused, pick.TX, pick.TY, pick.ZC))) return rc;
+  h->stats_valid = false;
+  h->prof = was_prof;
+  if (best_ms) *best_ms = best;
+  return AT_DNS_OK;
+}
+
 int at_dns_synchronize(at_dns_t* h) {
   if (!h) return AT_DNS_E_INVALID_ARG;
   CK(cudaStreamSynchronize(h->st));
@@ -1029,6 +1119,192 @@ void at_dns_destroy(at_dns_t* h) {
     if (p) cudaFree(p);
   clear_recs(h);
   delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched ensembles: independent members, one graph launch per step
+struct at_dns_batch {
+  std::vector<at_dns*> m;
+  std::vector<cudaStream_t> ms;       // one stream per member (owned)
+  std::vector<cudaEvent_t> ev;        // per-member ordering / join events
+  cudaEvent_t fork = nullptr, done = nullptr;
+  cudaStream_t st = nullptr;          // batch stream
+  bool own_st = false;
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+  std::vector<std::string> gkey[3];   // member path + dt each graph was captured with
+  std::string err;
+};
+
+namespace {
+
+std::string member_key(const at_dns* h) {
+  char buf[128];
+  std::snprintf(buf, sizeof(buf), "%d:%d:%d:%d:%.17g", (int)h->fused, h->TX, h->TY, h->ZC, h->dt);
+  return buf;
+}
+
+int batch_fail(at_dns_batch* b, int code, const std::string& msg) {
+  b->err = msg;
+  return code;
+}
+
+void batch_drop(at_dns_batch* b) {
+  for (int k = 0; k < 3; ++k)
+    if (b->gexec[k]) { cudaGraphExecDestroy(b->gexec[k]); b->gexec[k] = nullptr; }
+}
+
+}  // namespace
+
+extern "C" {
+
+void at_dns_batch_destroy(at_dns_batch_t* b);
+
+int at_dns_batch_create(const at_dns_config_t* cfgs, int32_t count, void* stream, at_dns_batch_t** out) {
+  if (!cfgs || !out || count < 1) { g_create_error = "bad batch arguments"; return AT_DNS_E_INVALID_ARG; }
+  *out = nullptr;
+  at_dns_batch* b = new at_dns_batch();
+  if (stream) b->st = (cudaStream_t)stream;
+  else {
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+      g_create_error = "cannot create the batch stream";
+      delete b;
+      return AT_DNS_E_CUDA;
+    }
+    b->own_st = true;
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+    g_create_error = "cannot create events";
+    at_dns_batch_destroy(b);
+    return AT_DNS_E_CUDA;
+  }
+  for (int i = 0; i < count; ++i) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      g_create_error = "cannot create member streams";
+      at_dns_batch_destroy(b);
+      return AT_DNS_E_CUDA;
+    }
+    b->ms.push_back(s);
+    b->ev.push_back(e);
+    at_dns_config_t c = cfgs[i];
+    c.stream = s;
+    at_dns* h = nullptr;
+    const int rc = at_dns_create(&c, &h);
+    if (rc) {
+      g_create_error = "member " + std::to_string(i) + ": " + g_create_error;
+      at_dns_batch_destroy(b);
+      return rc;
+    }
+    b->m.push_back(h);
+  }
+  *out = b;
+  return AT_DNS_OK;
+}
+
+int at_dns_batch_member(at_dns_batch_t* b, int32_t i, at_dns_t** out) {
+  if (!b || !out || i < 0 || i >= (int)b->m.size()) return AT_DNS_E_INVALID_ARG;
+  *out = b->m[i];
+  return AT_DNS_OK;
+}
+
+int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode) {
+  if (!b) return AT_DNS_E_INVALID_ARG;
+  b->err.clear();
+  if (nsteps < 0 || delay_mode < 0 || delay_mode > 2) return batch_fail(b, AT_DNS_E_INVALID_ARG, "bad arguments");
+  const int M = (int)b->m.size();
+  std::vector<std::string> key(M);
+  for (int i = 0; i < M; ++i) {
+    at_dns* h = b->m[i];
+    if (!h->has_state) return batch_fail(b, AT_DNS_E_STATE, "member " + std::to_string(i) + " has no state");
+    if (check_mode(h, delay_mode)) return batch_fail(b, AT_DNS_E_INVALID_ARG, "member " + std::to_string(i) + ": " + h->err);
+    key[i] = member_key(h);
+  }
+  if (nsteps == 0) return AT_DNS_OK;
+  cudaGraphExec_t& ge = b->gexec[delay_mode];
+  if (!ge || b->gkey[delay_mode] != key) {
+    if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
+    // one step of every member, each on its own branch of the graph
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return batch_fail(b, AT_DNS_E_CUDA, "graph capture failed to start");
+    int rc = AT_DNS_OK;
+    cudaEventRecord(b->fork, b->st);
+    for (int i = 0; i < M && !rc; ++i) {
+      at_dns* h = b->m[i];
+      cudaStreamWaitEvent(b->ms[i], b->fork, 0);
+      const bool stats = h->cfg.stats_every == 1;
+      rc = h->p64 ? Ops<double>::launch_step(h, delay_mode, true, nullptr, stats, false, b->ms[i])
+                  : Ops<float>::launch_step(h, delay_mode, true, nullptr, stats, false, b->ms[i]);
+      cudaEventRecord(b->ev[i], b->ms[i]);
+      cudaStreamWaitEvent(b->st, b->ev[i], 0);
+    }
+    const cudaError_t e = cudaStreamEndCapture(b->st, &graph);
+    if (rc) { if (graph) cudaGraphDestroy(graph); return batch_fail(b, rc, "capture: " + b->m[0]->err); }
+    if (e != cudaSuccess) return batch_fail(b, AT_DNS_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&ge, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) { ge = nullptr; return batch_fail(b, AT_DNS_E_CUDA, "graph instantiate failed"); }
+    b->gkey[delay_mode] = key;
+  }
+  // order after each member's own stream, reset the health words, replay
+  for (int i = 0; i < M; ++i) {
+    k_reset_words<<<1, 1, 0, b->ms[i]>>>(b->m[i]->words, 1);
+    cudaEventRecord(b->ev[i], b->ms[i]);
+    cudaStreamWaitEvent(b->st, b->ev[i], 0);
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    const cudaError_t e = cudaGraphLaunch(ge, b->st);
+    if (e != cudaSuccess) return batch_fail(b, AT_DNS_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    for (int i = 0; i < M; ++i) {
+      at_dns* h = b->m[i];
+      const bool stats = h->cfg.stats_every == 1;
+      if (h->p64) Ops<double>::account(h, true, stats); else Ops<float>::account(h, true, stats);
+    }
+  }
+  cudaEventRecord(b->done, b->st);
+  std::vector<unsigned long long> w(M, 0);
+  for (int i = 0; i < M; ++i) {
+    cudaStreamWaitEvent(b->ms[i], b->done, 0);
+    cudaMemcpyAsync(&w[i], b->m[i]->words + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->ms[i]);
+  }
+  for (int i = 0; i < M; ++i) {
+    const cudaError_t e = cudaStreamSynchronize(b->ms[i]);
+    if (e != cudaSuccess) return batch_fail(b, AT_DNS_E_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
+  }
+  for (int i = 0; i < M; ++i)
+    if (w[i]) return batch_fail(b, AT_DNS_E_UNSTABLE, "member " + std::to_string(i) + " became unstable");
+  return AT_DNS_OK;
+}
+
+int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials) {
+  if (!b) return AT_DNS_E_INVALID_ARG;
+  b->err.clear();
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    const int rc = at_dns_tune(b->m[i], delay_mode, trials, nullptr);
+    if (rc) return batch_fail(b, rc, "member " + std::to_string(i) + ": " + b->m[i]->err);
+  }
+  batch_drop(b);
+  return AT_DNS_OK;
+}
+
+const char* at_dns_batch_last_error(const at_dns_batch_t* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+void at_dns_batch_destroy(at_dns_batch_t* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  batch_drop(b);
+  for (at_dns* h : b->m) at_dns_destroy(h);
+  for (cudaStream_t s : b->ms) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->own_st) cudaStreamDestroy(b->st);
+  delete b;
 }
 
 }  // extern "C"

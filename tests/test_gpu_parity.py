@@ -359,3 +359,48 @@ def test_graph_replay_matches_direct_launches(lib, path):
     sa, sb = a.stats(), b.stats()
     assert sa["step"] == sb["step"] == 11
     assert sa["tke"] == sb["tke"] and sa["dissipation"] == sb["dissipation"]
+
+
+def test_batch_of_uneven_members_matches_members_alone(lib):
+    """One graph launch per step advances members of different grids, PE
+    layouts and precisions; each ends bit-identical to the same member stepped
+    alone (config 4's batched ensemble, with seeds and Mach numbers varied)."""
+    specs = [
+        dict(n=(16, 16, 16), pes=(2, 2, 2), precision="p64", mu0=0.02, dt=3e-3, max_delay=2, seed=1),
+        dict(n=(24, 24, 24), pes=(1, 1, 1), precision="p64", mu0=0.01, dt=2e-3, max_delay=2, seed=2),
+        dict(n=(32, 32, 32), pes=(4, 4, 4), precision="p32", mu0=0.02, dt=2e-3, max_delay=2, seed=3),
+        dict(n=(16, 24, 32), pes=(2, 3, 4), precision="p64", mu0=0.02, dt=2e-3, max_delay=2, seed=4,
+             path="fused"),
+    ]
+    for sp in specs:
+        sp.update(gamma=GAMMA, prandtl=PR, visc_exp=OMEGA)
+    states = [synth.initial_state(sp["n"], k0=3.0, mach_t=0.1 + 0.1 * i, seed=50 + i) for i, sp in enumerate(specs)]
+    batch = lib.Batch(specs)
+    for m, U0 in zip(batch.members, states):
+        m.set_state(U0)
+    batch.step(8, "random")
+    batch.step(4, "random")
+    for sp, m, U0 in zip(specs, batch.members, states):
+        alone = lib.Solver(**sp)
+        alone.set_state(U0)
+        alone.step(12, "random")
+        assert np.array_equal(m.get_state(), alone.get_state())
+        assert m.info()["step"] == 12
+    batch.close()
+
+
+def test_tuner_keeps_parity(lib):
+    """The autotuner times every applicable kernel path / tile / z chunk and
+    keeps the fastest; the result still matches the oracle."""
+    n, pes, step = (32, 32, 32), (4, 4, 4), 9
+    U0 = synth.initial_state(n, k0=3.0, seed=61)
+    c = ocfg(n, pes, mu0=0.02, dt=2e-3, max_delay=2, seed=8)
+    hist = synth.history(U0, c.n_levels, eps=2e-2, seed=62)
+    s = make(lib, n, pes, mu0=0.02, dt=2e-3, max_delay=2, seed=8)
+    s.set_history(hist, step)
+    best = s.tune("random", trials=2)
+    info = s.info()
+    assert best > 0 and info["kernel_path"] in (lib.AT_DNS_PATH_MULTIPASS, lib.AT_DNS_PATH_FUSED)
+    R = s.rhs("random")
+    Rref = ns.rhs(c, hist, ns.delay_map(c, step, ns.RANDOM))
+    assert max(rel_linf(R, Rref)) <= 1e-12
