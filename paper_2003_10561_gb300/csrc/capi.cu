@@ -319,6 +319,13 @@ int dev_alloc(at_dns* h, void** p, size_t bytes) {
   return AT_DNS_OK;
 }
 
+// FP64 staging buffer for host transfers, allocated on first use (a caller
+// that only passes device pointers never pays its 40 bytes per point).
+int get_stage(at_dns* h) {
+  if (h->stage) return AT_DNS_OK;
+  return dev_alloc(h, (void**)&h->stage, 5 * (size_t)h->g.npts * sizeof(double));
+}
+
 double key_to_double(unsigned long long k) {
   long long b = (long long)k;
   b ^= (b >> 63) & 0x7FFFFFFFFFFFFFFFLL;
@@ -359,6 +366,8 @@ struct Ops {
     const long long cnt = 5 * h->g.npts;
     const double* dsrc = src;
     if (where == AT_DNS_HOST) {
+      int rc;
+      if ((rc = get_stage(h))) return rc;
       CK(cudaMemcpyAsync(h->stage, src, cnt * sizeof(double), cudaMemcpyHostToDevice, h->st));
       dsrc = h->stage;
     }
@@ -386,6 +395,10 @@ struct Ops {
 
   static int download(at_dns* h, double* out, int where) {
     const long long cnt = 5 * h->g.npts;
+    if (where == AT_DNS_HOST) {
+      int rc;
+      if ((rc = get_stage(h))) return rc;
+    }
     double* dst = where == AT_DNS_DEVICE ? out : h->stage;
     if (sizeof(S) == sizeof(double)) {
       CK(cudaMemcpyAsync(dst, U(h, h->cur), cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
@@ -627,11 +640,12 @@ int force_reset(at_dns* h, long long step) {
   return AT_DNS_OK;
 }
 
-int set_dt(at_dns* h) {
+// dt from the CFL number and the state U^step (FP64, device memory).
+int set_dt(at_dns* h, const double* U) {
   if (h->cfg.dt > 0) { h->dt = h->cfg.dt; return AT_DNS_OK; }
   k_reset_words<<<1, 1, 0, h->st>>>(h->words, 1);
   CK(cudaGetLastError());
-  k_wave<<<nblk(h->g.npts), kBlock, 0, h->st>>>(h->g, h->ph, h->stage, h->words);
+  k_wave<<<nblk(h->g.npts), kBlock, 0, h->st>>>(h->g, h->ph, U, h->words);
   CK(cudaGetLastError());
   unsigned long long w = 0;
   CK(cudaMemcpyAsync(&w, h->words, sizeof(w), cudaMemcpyDeviceToHost, h->st));
@@ -756,7 +770,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   if (!h->fused) h->TX = h->TY = h->ZC = 0;
   h->nblk_step = h->fused ? (long long)(g.n[0] / h->TX) * (g.n[1] / h->TY) * (g.n[2] / h->ZC) : main_blocks(g);
   if ((rc = dev_alloc(h, &h->U[0], 5 * N * S)) || (rc = dev_alloc(h, &h->U[1], 5 * N * S)) ||
-      (rc = dev_alloc(h, &h->Rprev, 5 * N * S)) || (rc = dev_alloc(h, (void**)&h->stage, 5 * N * sizeof(double))))
+      (rc = dev_alloc(h, &h->Rprev, 5 * N * S)))
     return create_fail(h, rc);
   if (!h->fused) {
     if ((rc = dev_alloc(h, &h->PQ, (size_t)kNumQ * N * S)) || (rc = dev_alloc(h, &h->G, (size_t)kNumGrad * N * S)))
@@ -829,9 +843,11 @@ int at_dns_set_history(at_dns_t* h, const double* levels, int32_t nlevels, int64
     }
   }
   // stage holds U^step in FP64 now (host path) -- ensure it for the dt reduction
-  if (where == AT_DNS_DEVICE) CK(cudaMemcpyAsync(h->stage, levels, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  // U^step in FP64 on the device for the CFL reduction: the caller's level 0,
+  // or the staging buffer the host path just filled with it
+  const double* u0 = where == AT_DNS_DEVICE ? levels : h->stage;
   if (!(h->has_state && h->dt > 0) || step == 0) {
-    if ((rc = set_dt(h))) return rc;
+    if ((rc = set_dt(h, u0))) return rc;
   }
   h->n = step;
   h->t = step * h->dt;
@@ -876,6 +892,7 @@ int at_dns_rhs(at_dns_t* h, int32_t delay_mode, double* rhs_out, int where) {
   if (!rhs_out) return fail(h, AT_DNS_E_INVALID_ARG, "rhs_out is NULL");
   if (where != AT_DNS_HOST && where != AT_DNS_DEVICE) return fail(h, AT_DNS_E_INVALID_ARG, "bad where");
   if (!h->has_state) return fail(h, AT_DNS_E_STATE, "no state set");
+  if (where == AT_DNS_HOST && (rc = get_stage(h))) return rc;
   double* dst = where == AT_DNS_DEVICE ? rhs_out : h->stage;
   rc = h->p64 ? Ops<double>::evaluate(h, delay_mode, false, dst, true, true)
               : Ops<float>::evaluate(h, delay_mode, false, dst, true, true);
