@@ -14,6 +14,8 @@ Paper passages followed, in the order of one step:
   synchronous start-up over the first L + T_l steps (Algorithms 1 and 2);
 * AT derivatives at PE faces: Eq. (at) and the 4th-order rows of Table B
   (Appendix B), standard 4th-order stencils at internal points (Sec. 2.1);
+  optionally the 6th-order rows of Table B (T_l = 4) with standard 6th-order
+  stencils inside (the sixth-order comparison of Sec. 4.1.2);
 * mixed derivatives in three steps at boundary points (Sec. 2.1);
 * right-hand side of Eqs. (cont), (mome) and the energy equation with the
   stress / strain definitions of Sec. 2 (total energy form, see below);
@@ -44,9 +46,7 @@ import math
 import numpy as np
 
 from .philox import philox4x32_10, split_seed
-from .stencils import (D1_CENTRAL, D2_CENTRAL, D1_FORWARD0, D1_FORWARD1,
-                       D1_BACKWARD0, D1_BACKWARD1, HALF_WIDTH, T_LEVELS,
-                       at_weights)
+from .stencils import Scheme
 
 SYNC, PERIODIC, RANDOM = 0, 1, 2
 DELAY_STREAM_TAG = 0x4154      # 4th Philox counter word of the delay stream
@@ -70,6 +70,11 @@ class Config:
     f_amp: float = 0.0
     f_tcorr: float = 1.0
     f_seed: int = 0
+    order: int = 4                   # spatial order: 4 (T_l = 3) or 6 (T_l = 4)
+
+    @property
+    def scheme(self):
+        return Scheme(self.order)
 
     @property
     def nloc(self):
@@ -82,7 +87,7 @@ class Config:
     @property
     def n_levels(self):
         """Time levels held: n, n-1, ..., n-(L+T_l-1)  (Sec. 3.1: L + T_l)."""
-        return self.max_delay + T_LEVELS
+        return self.max_delay + self.scheme.T
 
     @property
     def n_pes(self):
@@ -113,12 +118,13 @@ def pe_index_field(cfg):
 
 
 def boundary_fraction(cfg):
-    """N_B / N_T per PE, Eqs. (NT), (NI), (NB) with M = 2."""
+    """N_B / N_T per PE, Eqs. (NT), (NI), (NB) (M = order / 2)."""
+    M = cfg.scheme.M
     nt = 1
     ni = 1
     for d in range(3):
         nt *= cfg.nloc[d]
-        ni *= cfg.nloc[d] - 2 * HALF_WIDTH
+        ni *= cfg.nloc[d] - 2 * M
     return (nt - ni) / nt
 
 
@@ -188,7 +194,8 @@ def _face_delay_field(cfg, delays, d):
     pe = pe_index_field(cfg)
     k_left = delays[pe, 2 * d]
     k_right = delays[pe, 2 * d + 1]
-    k = np.where(li < HALF_WIDTH, k_left, np.where(li >= cfg.nloc[d] - HALF_WIDTH, k_right, 0))
+    M = cfg.scheme.M
+    k = np.where(li < M, k_left, np.where(li >= cfg.nloc[d] - M, k_right, 0))
     return np.broadcast_to(k, pe.shape)
 
 
@@ -196,13 +203,14 @@ def at_derivative(cfg, qlevels, d, delays, order):
     """First (order=1) or second (order=2) AT derivative in direction d.
 
     qlevels[l] is the quantity at level n-l.  Literal Table B: the standard
-    stencil is evaluated once per l = 0, 1, 2 with the points outside the PE
-    taken at level n-k-l, and the three results are weighted by w_l(k).
+    stencil is evaluated once per l = 0 .. T_l-1 with the points outside the
+    PE taken at level n-k-l, and the T_l results are weighted by w_l(k).
     Points inside the PE always use level n.  A direction with one PE is a
     plain periodic stencil at level n.
     """
-    stencil, denom = (D1_CENTRAL, 12.0 * cfg.dx[d]) if order == 1 else \
-                     (D2_CENTRAL, 12.0 * cfg.dx[d] ** 2)
+    sc = cfg.scheme
+    stencil, denom = (sc.d1, sc.d1_den * cfg.dx[d]) if order == 1 else \
+                     (sc.d2, sc.d2_den * cfg.dx[d] ** 2)
     ax = _axis(d)
     if cfg.pes[d] == 1:
         out = np.zeros_like(qlevels[0])
@@ -214,8 +222,8 @@ def at_derivative(cfg, qlevels, d, delays, order):
     kf = _face_delay_field(cfg, delays, d)
     Q = np.stack(qlevels)                       # [level, z, y, x]
     out = np.zeros_like(qlevels[0])
-    for l in range(T_LEVELS):
-        w = np.vectorize(lambda kk: at_weights(kk)[l], otypes=[float])(kf)
+    for l in range(sc.T):
+        w = np.vectorize(lambda kk: sc.weights(kk)[l], otypes=[float])(kf)
         S = np.zeros_like(qlevels[0])
         for off, c in stencil:
             inside = (li + off >= 0) & (li + off < nloc)
@@ -228,11 +236,12 @@ def at_derivative(cfg, qlevels, d, delays, order):
 
 
 def _central_fits(cfg, d):
-    """True where the 5-point d-stencil stays inside the PE (or d has one PE)."""
+    """True where the central d-stencil stays inside the PE (or d has one PE)."""
     li = _coord(cfg, d) % cfg.nloc[d]
     if cfg.pes[d] == 1:
         return np.ones_like(li, dtype=bool)
-    return (li >= HALF_WIDTH) & (li <= cfg.nloc[d] - 1 - HALF_WIDTH)
+    M = cfg.scheme.M
+    return (li >= M) & (li <= cfg.nloc[d] - 1 - M)
 
 
 def _apply(f, stencil, ax):
@@ -243,20 +252,20 @@ def _apply(f, stencil, ax):
 
 
 def pe_local_d1(cfg, g, d):
-    """PE-local 4th-order first derivative: central where it fits inside the
-    PE, one-sided at the two points next to each PE face (no data from other
-    PEs is read)."""
+    """PE-local first derivative of the scheme's order: central where it fits
+    inside the PE, one-sided at the M points next to each PE face (no data
+    from other PEs is read)."""
+    sc = cfg.scheme
     ax = _axis(d)
-    central = _apply(g, D1_CENTRAL, ax)
+    den = sc.d1_den * cfg.dx[d]
+    out = _apply(g, sc.d1, ax)
     if cfg.pes[d] == 1:
-        return central / (12.0 * cfg.dx[d])
+        return out / den
     nloc = cfg.nloc[d]
     li = _coord(cfg, d) % nloc
-    out = np.where(li == 0, _apply(g, D1_FORWARD0, ax),
-          np.where(li == 1, _apply(g, D1_FORWARD1, ax),
-          np.where(li == nloc - 2, _apply(g, D1_BACKWARD1, ax),
-          np.where(li == nloc - 1, _apply(g, D1_BACKWARD0, ax), central))))
-    return out / (12.0 * cfg.dx[d])
+    for j in list(range(sc.M)) + list(range(nloc - sc.M, nloc)):
+        out = np.where(li == j, _apply(g, sc.one_sided(j, nloc), ax), out)
+    return out / den
 
 
 def mixed_derivative(cfg, grad_b, grad_a, a, b):
@@ -269,8 +278,9 @@ def mixed_derivative(cfg, grad_b, grad_a, a, b):
     derivative in a of grad_b and the PE-local derivative in b of grad_a are
     averaged.
     """
+    sc = cfg.scheme
     interior = _central_fits(cfg, a) & _central_fits(cfg, b)
-    central = _apply(grad_b, D1_CENTRAL, _axis(a)) / (12.0 * cfg.dx[a])
+    central = _apply(grad_b, sc.d1, _axis(a)) / (sc.d1_den * cfg.dx[a])
     boundary = 0.5 * (pe_local_d1(cfg, grad_b, a) + pe_local_d1(cfg, grad_a, b))
     return np.where(interior, central, boundary)
 

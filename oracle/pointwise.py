@@ -3,12 +3,13 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/ns.py``).
 
 Each derivative is written out as an explicit list of (offset, time level,
-weight) terms built from Table B (Appendix B): the standard 4th-order stencil
-repeated for l = 0, 1, 2, its points outside the PE taken at level n-k-l and
-weighted by w_l(k) -- the same rows the paper prints, read per point.  Mixed
-derivatives follow the three-step rule of Sec. 2.1.  Pure Python loops, so it
-is used on tiny grids (as a brute-force check of the vectorised oracle) and on
-a few hundred sampled points of full-size grids (parity of the CUDA path).
+weight) terms built from Table B (Appendix B): the standard stencil of the
+configured order (4 or 6) repeated for l = 0 .. T_l-1, its points outside the
+PE taken at level n-k-l and weighted by w_l(k) -- the same rows the paper
+prints, read per point.  Mixed derivatives follow the three-step rule of
+Sec. 2.1.  Pure Python loops, so it is used on tiny grids (as a brute-force
+check of the vectorised oracle) and on a few hundred sampled points of
+full-size grids (parity of the CUDA path).
 
 The right-hand side is assembled from the definitions of Sec. 2: the
 inviscid flux divergence, the viscous stress divergence
@@ -18,9 +19,6 @@ the viscous work u_i d sigma_ij/dx_j + sigma_ij S_ij, the heat conduction
 kappa lap T + (d kappa/dx_j)(dT/dx_j) and the forcing rho f_i, rho f_i u_i.
 """
 import math
-
-from .stencils import (D1_CENTRAL, D2_CENTRAL, D1_FORWARD0, D1_FORWARD1,
-                       D1_BACKWARD0, D1_BACKWARD1, HALF_WIDTH, T_LEVELS, at_weights)
 
 
 class PointOracle:
@@ -33,6 +31,7 @@ class PointOracle:
 
     def __init__(self, cfg, level, delays, fhat=None, modes=None):
         self.cfg = cfg
+        self.sc = cfg.scheme
         self.level = level
         self.delays = delays
         self.fhat = fhat
@@ -92,24 +91,25 @@ class PointOracle:
         """[(offset, level, weight)] such that the derivative is
         sum weight * q(pos + offset e_d, level)."""
         cfg = self.cfg
+        sc = self.sc
         if order == 1:
-            stencil, denom = D1_CENTRAL, 12.0 * cfg.dx[d]
+            stencil, denom = sc.d1, sc.d1_den * cfg.dx[d]
         else:
-            stencil, denom = D2_CENTRAL, 12.0 * cfg.dx[d] ** 2
+            stencil, denom = sc.d2, sc.d2_den * cfg.dx[d] ** 2
         if cfg.pes[d] == 1:
             return [(off, 0, c / denom) for off, c in stencil]
         nloc = cfg.nloc[d]
         li = self.local(pos, d)
         p = self.pe_of(pos)
-        if li < HALF_WIDTH:
+        if li < sc.M:
             k = int(self.delays[p][2 * d])
-        elif li >= nloc - HALF_WIDTH:
+        elif li >= nloc - sc.M:
             k = int(self.delays[p][2 * d + 1])
         else:
             k = 0
-        w = at_weights(k)
+        w = sc.weights(k)
         out = []
-        for l in range(T_LEVELS):
+        for l in range(sc.T):
             for off, c in stencil:
                 inside = 0 <= li + off < nloc
                 out.append((off, 0 if inside else k + l, w[l] * c / denom))
@@ -135,22 +135,12 @@ class PointOracle:
         if self.cfg.pes[d] == 1:
             return True
         li = self.local(pos, d)
-        return HALF_WIDTH <= li <= self.cfg.nloc[d] - 1 - HALF_WIDTH
+        return self.sc.M <= li <= self.cfg.nloc[d] - 1 - self.sc.M
 
     def _pe_local_stencil(self, pos, d):
         if self.cfg.pes[d] == 1:
-            return D1_CENTRAL
-        li = self.local(pos, d)
-        nloc = self.cfg.nloc[d]
-        if li == 0:
-            return D1_FORWARD0
-        if li == 1:
-            return D1_FORWARD1
-        if li == nloc - 2:
-            return D1_BACKWARD1
-        if li == nloc - 1:
-            return D1_BACKWARD0
-        return D1_CENTRAL
+            return self.sc.d1
+        return self.sc.one_sided(self.local(pos, d), self.cfg.nloc[d])
 
     def _apply_d1(self, stencil, gfun, pos, d):
         s = 0.0
@@ -158,14 +148,14 @@ class PointOracle:
             p2 = list(pos)
             p2[d] += off
             s += c * gfun(tuple(p2))
-        return s / (12.0 * self.cfg.dx[d])
+        return s / (self.sc.d1_den * self.cfg.dx[d])
 
     def mixed(self, k, a, b, pos):
         """d/dx_a (d u_k / d x_b) at pos."""
         gb = lambda p: self.grad(k, b, p)
         ga = lambda p: self.grad(k, a, p)
         if self._central_fits(pos, a) and self._central_fits(pos, b):
-            return self._apply_d1(D1_CENTRAL, gb, pos, a)
+            return self._apply_d1(self.sc.d1, gb, pos, a)
         return 0.5 * (self._apply_d1(self._pe_local_stencil(pos, a), gb, pos, a)
                       + self._apply_d1(self._pe_local_stencil(pos, b), ga, pos, b))
 
