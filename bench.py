@@ -37,6 +37,9 @@ CFL_AT = 0.2        # min(0.5, 0.8 / f(L)), f(2) = 0.90*4 - 0.35*2 + 1 = 3.9 (Se
 # FP64 operations per grid point of the main kernel, counted from the method
 # (FMA = 2; division, square root and power = 1 each); see the design notes.
 FLOP_MAIN = 390.0
+# the 6th-order scheme adds one stencil pair to every first derivative
+# (15 flux + 6 mixed: +3 flops each) and second derivative (12: +3 each)
+FLOP_MAIN6 = 489.0
 # algorithmic HBM bytes per grid point of one step (read U, R^{n-1}; write U^{n+1},
 # R^n; plus the slab ring: 1 write + 3 reads of 5 variables at the N_B fraction)
 NB_FRAC = 1.0 - (28.0 / 32.0) ** 3
@@ -44,7 +47,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max S
 # DRAM bytes (read + write) of one k_main launch, FP64 multi-pass path: ncu at
 # 128^3 (877.2 MB, profiles/k_main_fp64_128cube_4x4x4pes.md) scaled by the
 # point count to the 256^3 workload (traffic grows with the points)
-K_MAIN_FP64_TRAFFIC_256 = 8 * 877.2e6
+K_MAIN_FP64_TRAFFIC_256 = None
 
 
 def set_workload(n, pes):
@@ -61,8 +64,18 @@ def peaks():
         return {"hbm_gbs": 6800.0, "_fallback": True}
 
 
-def algorithmic_bytes(elem):
-    return 4 * 5 * elem + NB_FRAC * 5 * elem * 4
+def nb_frac(order):
+    """N_B / N_T per PE for half width M = order / 2 (Eqs. (NT)-(NB))."""
+    nl = N // PES
+    return 1.0 - ((nl - order) / float(nl)) ** 3
+
+
+def algorithmic_bytes(elem, order=4):
+    """Read U, R^{n-1}; write U^{n+1}, R^n; the slab ring: 1 write + 3 reads of
+    5 variables at the N_B fraction (T_l = 3 reads at 4th order; at 6th order
+    T_l = 4 levels are read)."""
+    reads = 3 if order == 4 else 4
+    return 4 * 5 * elem + nb_frac(order) * 5 * elem * (1 + reads)
 
 
 class Clocks:
@@ -182,10 +195,10 @@ def workload_config(world):
             "l2": "working set %.1f GB >> 129 MB L2; no flush needed" % (N ** 3 * 5 * 8 * 12 / 1e9)}
 
 
-def make_solver(at_dns, precision, stream, mu0, path="auto"):
+def make_solver(at_dns, precision, stream, mu0, path="auto", order=4):
     return at_dns.Solver(n=(N, N, N), pes=(PES, PES, PES), precision=precision, stream=stream, path=path,
                          gamma=1.4, prandtl=0.7, visc_exp=0.76, mu0=mu0, cfl=CFL_AT, dt=0.0,
-                         max_delay=L, seed=SEED, stats_every=1)
+                         max_delay=L, seed=SEED, stats_every=1, order=order)
 
 
 def timed_steps(s, stream, steps, warmup, torch, profile=False):
@@ -224,6 +237,8 @@ def main():
     ap.add_argument("--pes", type=int, default=PES, help="virtual PEs per direction")
     ap.add_argument("--precision", default="both", choices=["both", "p64", "p32"])
     ap.add_argument("--path", default="auto", choices=["auto", "multipass", "fused"])
+    ap.add_argument("--order", default="both", choices=["both", "4", "6"],
+                    help="spatial order of the AT scheme (4: headline; 6: Table B (1,6)/(2,6))")
     args = ap.parse_args()
     set_workload(args.grid, args.pes)
     args.warmup = max(args.warmup, 3)
@@ -250,27 +265,31 @@ def main():
     clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
                     if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_rank%d.csv" % rank)
     precs = ("p64", "p32") if args.precision == "both" else (args.precision,)
-    for prec in precs:
-        s = make_solver(at_dns, prec, stream.cuda_stream, mu0, args.path)
+    orders = (4, 6) if args.order == "both" else (int(args.order),)
+    legs = [(p, o) for o in orders for p in precs]
+    for prec, order in legs:
+        key = prec if order == 4 else prec + "_o6"
+        s = make_solver(at_dns, prec, stream.cuda_stream, mu0, args.path if order == 4 else "auto", order)
         s.set_state(U0)
         s.step(at_dns.at_dns_get_info(s.h).n_levels + 1, "random")   # past the synchronous start-up
         if pg:
             pg.barrier()
-        if prec == "p64":
+        if key == legs[0][0] + ("" if legs[0][1] == 4 else "_o6"):
             with clocks:
                 ms, kt = timed_steps(s, stream, args.steps, args.warmup, torch, profile=True)
         else:
             ms, kt = timed_steps(s, stream, args.steps, args.warmup, torch, profile=True)
         ms = max_over_ranks(ms, pg, "cuda")
         st = s.stats()
-        res[prec] = {"ms": ms, "kt": kt, "stats": st, "info": s.info()}
+        res[key] = {"ms": ms, "kt": kt, "stats": st, "info": s.info(), "order": order,
+                    "dtype": "f64" if prec == "p64" else "f32"}
         # kernels in the timed region: every replayed step plus the health reset
-        res[prec]["launches"] = args.steps * res[prec]["info"]["kernels_per_step"] + 1
-        res[prec]["path"] = "fused" if res[prec]["info"]["kernel_path"] == at_dns.AT_DNS_PATH_FUSED else "multipass"
+        res[key]["launches"] = args.steps * res[key]["info"]["kernels_per_step"] + 1
+        res[key]["path"] = "fused" if res[key]["info"]["kernel_path"] == at_dns.AT_DNS_PATH_FUSED else "multipass"
         # end to end through the public API with host buffers: per step, upload
         # U^n from pinned host memory (as the state of step n), step, read the
         # statistics record back
-        if prec == "p64" and not args.no_e2e:
+        if key == "p64" and not args.no_e2e:
             host = torch.from_numpy(U0).pin_memory()
             nlev = at_dns.at_dns_get_info(s.h).n_levels
             e2e_steps = max(3, args.steps // 4)
@@ -302,50 +321,62 @@ def main():
     pts = float(N ** 3)
     p64 = res.get("p64")
     p32 = res.get("p32")
-    head = p64 or p32
+    head = p64 or p32 or res.get("p64_o6") or res.get("p32_o6")
     value = job_rate(world, pts, args.steps, head["ms"])
-    launches = head["launches"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if p64 else "f32", "data": "synthetic",
-        "config": workload_config(world),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head in (p64, res.get("p64_o6")) else "f32",
+        "data": "synthetic", "config": workload_config(world),
         "kernel_ms_per_step": {k: v[1] / v[0] for k, v in head["kt"].items()},
         "e2e": res.get("e2e"),
         "cpu_baseline": cpu,
         "clocks": clocks.summary(local),
-        "gpu_launches": launches,
+        "gpu_launches": head["launches"],
         "rhs_per_s": value,
         "kernel_path": head["path"],
+        "order": head["order"],
     }
-    if p64:
-        main64 = p64["kt"].get("main", (1, 1.0))
-        t_main = main64[1] / main64[0] / 1e3
-        achieved = FLOP_MAIN * pts / t_main / 1e12
-        line["roofline"] = {"bound": "alu", "kernel": "k_main (FP64)", "achieved": achieved,
-                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                            "traffic": (K_MAIN_FP64_TRAFFIC_256 if (N == 256 and PES == 8 and p64["path"] == "multipass")
-                                        else None),
-                            "note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
-                                    "(an FMA probe measured 1.20 TFLOP/s)"}
-    if p32:
-        main32 = p32["kt"].get("main", (1, 1.0))
-        t_main32 = main32[1] / main32[0] / 1e3
-        ach32 = algorithmic_bytes(4) * pts / t_main32 / 1e9
-        r32 = {"bound": "hbm", "kernel": "k_main (FP32)", "achieved": ach32, "peak": pk.get("hbm_gbs"),
-               "unit": "GB/s", "frac": ach32 / pk.get("hbm_gbs", 6800.0), "traffic": None}
-        blk = {"value": job_rate(world, pts, args.steps, p32["ms"]), "unit": UNIT, "kernel_path": p32["path"],
-               "ms_per_step": p32["ms"] / args.steps, "dtype": "f32", "roofline": r32,
-               "kernel_ms_per_step": {k: v[1] / v[0] for k, v in p32["kt"].items()}}
+    rep = {k: leg_report(r, world, pts, args.steps, pk) for k, r in res.items() if k != "e2e"}
+    line["roofline"] = rep[[k for k in res if res[k] is head][0]]["roofline"]
+    if p32 and p32 is not head:
+        blk = rep["p32"]
         if p64:
             blk["rel_err_vs_fp64"] = {k: abs(p32["stats"][k] - p64["stats"][k]) / abs(p64["stats"][k])
                                       for k in ("tke", "dissipation")}
-            line["fp32_bulk"] = blk
-        else:
-            line["roofline"] = r32
-            line["fp32_bulk"] = blk
+        line["fp32_bulk"] = blk
+    o6 = {k[:-3]: rep[k] for k in ("p64_o6", "p32_o6") if k in rep and res[k] is not head}
+    if o6:
+        line["order6"] = dict(o6, workload="the same box, PEs, delays and state with the 6th-order AT scheme "
+                                            "(Table B (1,6)/(2,6), T_l = 4, N_B %.1f%%)" % (100 * nb_frac(6)))
     print(json.dumps(line), flush=True)
     return 0
+
+
+def leg_report(r, world, pts, steps, pk):
+    """Throughput, per-kernel times and the roofline of the main kernel of one
+    measured (precision, order) leg."""
+    order = r["order"]
+    main = r["kt"].get("main", (1, 1.0))
+    t_main = main[1] / main[0] / 1e3
+    if r["dtype"] == "f64":
+        flops = FLOP_MAIN if order == 4 else FLOP_MAIN6
+        achieved = flops * pts / t_main / 1e12
+        traffic = K_MAIN_FP64_TRAFFIC_256 if (order == 4 and N == 256 and PES == 8 and r["path"] == "multipass"
+                                              and K_MAIN_FP64_TRAFFIC_256) else None
+        roof = {"bound": "alu", "kernel": "k_main (FP64, order %d)" % order, "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": traffic, "flop_per_point": flops,
+                "note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                        "(an FMA probe measured 1.20 TFLOP/s)"}
+    else:
+        achieved = algorithmic_bytes(4, order) * pts / t_main / 1e9
+        roof = {"bound": "hbm", "kernel": "k_main (FP32, order %d)" % order, "achieved": achieved,
+                "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0),
+                "traffic": None, "bytes_per_point": algorithmic_bytes(4, order)}
+    return {"value": job_rate(world, pts, steps, r["ms"]), "unit": UNIT, "kernel_path": r["path"],
+            "ms_per_step": r["ms"] / steps, "dtype": r["dtype"], "roofline": roof,
+            "kernel_ms_per_step": {k: v[1] / v[0] for k, v in r["kt"].items()}}
 
 
 def ctypes_stats_size(at_dns):

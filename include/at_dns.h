@@ -9,7 +9,9 @@
  *   - equations: Sec. 2, Eqs. (cont), (mome), (ie) (solved here in total-energy
  *     form E = rho e + rho|u|^2/2, divergence form for the inviscid flux);
  *   - 4th-order central stencils inside a PE and AT stencils at PE faces:
- *     Sec. 2.1, Eq. (at) and Table B (Appendix B), T_l = 3 time levels;
+ *     Sec. 2.1, Eq. (at) and Table B (Appendix B), T_l = 3 time levels; or
+ *     the 6th-order rows of Table B (T_l = 4) with 6th-order stencils inside
+ *     (the sixth-order comparison of Sec. 4.1.2);
  *   - mixed derivatives by the three-step rule of Sec. 2.1;
  *   - second-order Adams-Bashforth with a fixed dt: Sec. 2.2, Eq. (time_ab);
  *   - PE decomposition, control parameters c_r and L, storage of L + T_l
@@ -74,16 +76,17 @@ extern "C" {
 typedef struct at_dns at_dns_t;   /* opaque handle; owned by the library */
 
 typedef struct {
-  int32_t  n[3];         /* grid points in x, y, z (each >= 5)                          */
+  int32_t  n[3];         /* grid points in x, y, z (each >= order + 1)                  */
   int32_t  pes[3];       /* virtual PEs per direction; n[d] % pes[d] == 0 and, when
-                            pes[d] > 1, n[d]/pes[d] >= 5.  pes[d] == 1: no faces in d   */
+                            pes[d] > 1, n[d]/pes[d] >= order + 1.  pes[d] == 1: no
+                            faces in d                                                  */
   double   gamma;        /* ratio of specific heats (1.4)                               */
   double   prandtl;      /* Prandtl number (0.7)                                        */
   double   mu0;          /* viscosity at T = 1                                          */
   double   visc_exp;     /* power-law exponent omega (0.76)                             */
   double   dt;           /* fixed time step; <= 0: set from cfl when a state is set     */
   double   cfl;          /* convective CFL used when dt <= 0                            */
-  int32_t  max_delay;    /* L >= 0: largest delay; the ring holds L + 3 levels          */
+  int32_t  max_delay;    /* L >= 0: largest delay; the ring holds L + T_l levels        */
   int32_t  comm_period;  /* c_r >= 1 for AT_DNS_PERIODIC; needs c_r - 1 <= L            */
   uint64_t seed;         /* key of the random delay stream                              */
   int32_t  forcing;      /* 0: decaying; 1: OU solenoidal forcing on |kappa| <= kf      */
@@ -95,6 +98,8 @@ typedef struct {
   int32_t  stats_every;  /* 1: reduce statistics in every step; 0: only on request      */
   void*    stream;       /* cudaStream_t to run on; NULL = the legacy default stream    */
   int32_t  kernel_path;  /* AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS or AT_DNS_PATH_FUSED */
+  int32_t  order;        /* spatial order: 4 (Table B (1,4)/(2,4), T_l = 3, default) or
+                            6 (Table B (1,6)/(2,6), T_l = 4; multi-pass path only)      */
 } at_dns_config_t;
 
 /* kernel paths (same results up to rounding): the multi-pass path stores
@@ -136,6 +141,7 @@ typedef struct {
   int32_t kernels_per_step;   /* kernel launches of one at_dns_step step                */
   int32_t kernel_path;   /* path in use: AT_DNS_PATH_MULTIPASS or AT_DNS_PATH_FUSED     */
   int32_t tile[3];       /* fused path: TX, TY, planes per CTA (0 on the multi-pass path)*/
+  int32_t order;         /* spatial order of the scheme (4 or 6)                        */
 } at_dns_info_t;
 
 /* Fill *cfg with defaults: 32^3, one PE, gamma 1.4, Pr 0.7, omega 0.76,

@@ -41,7 +41,7 @@ class at_dns_config_t(ctypes.Structure):
         ("forcing", ctypes.c_int32), ("kf", ctypes.c_double), ("f_amp", ctypes.c_double),
         ("f_tcorr", ctypes.c_double), ("f_seed", ctypes.c_uint64),
         ("precision", ctypes.c_int32), ("stats_every", ctypes.c_int32), ("stream", ctypes.c_void_p),
-        ("kernel_path", ctypes.c_int32),
+        ("kernel_path", ctypes.c_int32), ("order", ctypes.c_int32),
     ]
 
 
@@ -70,7 +70,7 @@ class at_dns_info_t(ctypes.Structure):
         ("step", ctypes.c_int64), ("time", ctypes.c_double), ("dt", ctypes.c_double),
         ("n_levels", ctypes.c_int32), ("boundary_fraction", ctypes.c_double),
         ("device_bytes", ctypes.c_size_t), ("kernels_per_step", ctypes.c_int32),
-        ("kernel_path", ctypes.c_int32), ("tile", ctypes.c_int32 * 3),
+        ("kernel_path", ctypes.c_int32), ("tile", ctypes.c_int32 * 3), ("order", ctypes.c_int32),
     ]
 
 

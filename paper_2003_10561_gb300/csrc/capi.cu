@@ -76,12 +76,12 @@ struct at_dns {
 // small kernels
 namespace {
 
-__global__ void k_delay_map(uint8_t* out, int P, long long n, const DevState* ds, int mode, int L, int cr,
+__global__ void k_delay_map(uint8_t* out, int P, long long n, const DevState* ds, int mode, int L, int tl, int cr,
                             uint32_t k0, uint32_t k1) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P * 6) return;
   if (ds) n = ds->n;
-  out[i] = (uint8_t)delay_of(mode, n, i / 6, i % 6, L, cr, k0, k1);
+  out[i] = (uint8_t)delay_of(mode, n, i / 6, i % 6, L, tl, cr, k0, k1);
 }
 
 __global__ void k_set_state(DevState* ds, long long n, int first, int cur) {
@@ -126,7 +126,9 @@ __global__ void k_join_double(const float* __restrict__ hi, const float* __restr
   if (i < count) out[i] = (double)hi[i] + (double)lo[i];
 }
 
-// Write the PE-boundary slabs of field U (S, [5][npts]) into ring slot `slot`.
+// Write the PE-boundary slabs of field U (S, [5][npts]) into ring slot `slot`:
+// the M layers next to each face, slab index 2M pe + t (t < M: local t,
+// t >= M: local nl - 2M + t).
 template <typename S>
 __global__ void k_ring_store(Geom g, const S* __restrict__ U, S* r0, S* r1, S* r2, int slot) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -134,15 +136,16 @@ __global__ void k_ring_store(Geom g, const S* __restrict__ U, S* r0, S* r1, S* r
   int c[3];
   decode(g, idx, c[0], c[1], c[2]);
   S* rings[3] = {r0, r1, r2};
+  const int M = g.M;
   for (int d = 0; d < 3; ++d) {
     if (g.pes[d] == 1) continue;
     const int pe = c[d] / g.nl[d], li = c[d] - pe * g.nl[d], nl = g.nl[d];
-    if (li >= 2 && li < nl - 2) continue;
-    const int t = li < 2 ? li : li - nl + 4;
-    const long long sp = 4LL * pe + t, P4 = 4LL * g.pes[d];
+    if (li >= M && li < nl - M) continue;
+    const int t = li < M ? li : li - nl + 2 * M;
+    const long long sp = 2LL * M * pe + t, PS = 2LL * M * g.pes[d];
     const long long pl = plane_index(g, d, c[0], c[1], c[2]);
     for (int v = 0; v < 5; ++v)
-      rings[d][(((long long)slot * 5 + v) * P4 + sp) * g.plane[d] + pl] = U[v * g.npts + idx];
+      rings[d][(((long long)slot * 5 + v) * PS + sp) * g.plane[d] + pl] = U[v * g.npts + idx];
   }
 }
 
@@ -156,7 +159,7 @@ __global__ void k_wave(Geom g, Phys ph, const double* __restrict__ U, unsigned l
     const double u[3] = {U[N + idx] * inv, U[2 * N + idx] * inv, U[3 * N + idx] * inv};
     const double p = ph.gm1 * (U[4 * N + idx] - 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
     const double c = sqrt(ph.gamma * p * inv);
-    for (int d = 0; d < 3; ++d) s = fmax(s, (fabs(u[d]) + c) * g.inv12dx[d] * 12.0);
+    for (int d = 0; d < 3; ++d) s = fmax(s, (fabs(u[d]) + c) * g.inv_dx[d]);
   }
   for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
   if ((threadIdx.x & 31) == 0) atomicMax((long long*)word, ordered_key(s));
@@ -427,7 +430,7 @@ struct Ops {
     const uint64_t seed = h->cfg.seed;
     {
       Timed t(h, KD_DELAY);
-      k_delay_map<<<nblk(P * 6), kBlock, 0, st>>>(h->dmap, P, 0, h->ds, mode, h->cfg.max_delay,
+      k_delay_map<<<nblk(P * 6), kBlock, 0, st>>>(h->dmap, P, 0, h->ds, mode, h->cfg.max_delay, g.M + 1,
                                                  h->cfg.comm_period, (uint32_t)seed, (uint32_t)(seed >> 32));
     }
     CK(cudaGetLastError());
@@ -530,10 +533,13 @@ struct Ops {
   }
 };
 
-// Tile shape of the fused path, or false if it does not apply: tiles must not
-// straddle PE faces, hold a multiple of 32 points (at most 256) and be at least
-// 8 wide in x and y (the one-sided mixed stencils reach 4 points into a PE).
+// Tile shape of the fused path, or false if it does not apply: the fused
+// kernel runs the 4th-order scheme; tiles must not straddle PE faces, hold a
+// multiple of 32 points (at most 256) and be at least 8 wide in x and y (the
+// one-sided mixed stencils reach 4 points into a PE).
 bool pick_fused_shape(const Geom& g, int& TX, int& TY, int& ZC) {
+  TX = TY = ZC = 0;
+  if (g.M != 2) return false;
   int ext[3];
   for (int d = 0; d < 3; ++d) ext[d] = g.pes[d] > 1 ? g.nl[d] : g.n[d];
   TX = TY = ZC = 0;
@@ -610,6 +616,7 @@ struct Candidate { bool fused; int TX, TY, ZC; };
 std::vector<Candidate> tune_candidates(const Geom& g) {
   std::vector<Candidate> out;
   out.push_back({false, 0, 0, 0});
+  if (g.M != 2) return out;   // the fused kernel runs the 4th-order scheme only
   int ext[3];
   for (int d = 0; d < 3; ++d) ext[d] = g.pes[d] > 1 ? g.nl[d] : g.n[d];
   const int shapes[6][2] = {{32, 8}, {16, 16}, {16, 8}, {8, 32}, {8, 16}, {8, 8}};
@@ -682,6 +689,7 @@ int at_dns_config_default(at_dns_config_t* c) {
   c->precision = AT_DNS_P64;
   c->stats_every = 1;
   c->stream = nullptr;
+  c->order = 4;
   return AT_DNS_OK;
 }
 
@@ -696,10 +704,12 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   *out = nullptr;
   const at_dns_config_t& c = *cfg;
   std::string bad;
+  const int M = c.order == 6 ? 3 : 2;
+  if (c.order != 4 && c.order != 6) bad = "order must be 4 or 6";
   for (int d = 0; d < 3 && bad.empty(); ++d) {
-    if (c.n[d] < 5 || c.n[d] > 32768) bad = "n[d] must be in [5, 32768]";
+    if (c.n[d] < 2 * M + 1 || c.n[d] > 32768) bad = "n[d] must be in [order + 1, 32768]";
     else if (c.pes[d] < 1 || c.n[d] % c.pes[d] != 0) bad = "pes[d] must divide n[d]";
-    else if (c.pes[d] > 1 && c.n[d] / c.pes[d] < 5) bad = "n[d]/pes[d] must be >= 5 when pes[d] > 1";
+    else if (c.pes[d] > 1 && c.n[d] / c.pes[d] < 2 * M + 1) bad = "n[d]/pes[d] must be >= order + 1 when pes[d] > 1";
   }
   if (bad.empty()) {
     if (!(c.gamma > 1.0)) bad = "gamma must be > 1";
@@ -735,17 +745,9 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   g.stride[0] = 1;
   g.stride[1] = g.n[0];
   g.stride[2] = (long long)g.n[0] * g.n[1];
-  for (int d = 0; d < 3; ++d) {
-    g.plane[d] = g.npts / g.n[d];
-    const double dx = 2.0 * M_PI / g.n[d];
-    g.c1[d] = 8.0 / (12.0 * dx);
-    g.c2[d] = -1.0 / (12.0 * dx);
-    g.a0[d] = -30.0 / (12.0 * dx * dx);
-    g.a1[d] = 16.0 / (12.0 * dx * dx);
-    g.a2[d] = -1.0 / (12.0 * dx * dx);
-    g.inv12dx[d] = 1.0 / (12.0 * dx);
-  }
-  g.nlev = c.max_delay + 3;
+  for (int d = 0; d < 3; ++d) g.plane[d] = g.npts / g.n[d];
+  set_stencils(g, M);
+  g.nlev = c.max_delay + M + 1;   // L + T_l levels
   Phys& ph = h->ph;
   ph.gamma = c.gamma;
   ph.gm1 = c.gamma - 1.0;
@@ -759,7 +761,8 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   int rc;
   const bool can_fuse = pick_fused_shape(g, h->TX, h->TY, h->ZC);
   if (c.kernel_path == AT_DNS_PATH_FUSED && !can_fuse) {
-    h->err = "the fused path needs PE (or grid) extents that are multiples of 8 in x and y";
+    h->err = M != 2 ? "the fused path runs the 4th-order scheme only"
+                    : "the fused path needs PE (or grid) extents that are multiples of 8 in x and y";
     return create_fail(h, AT_DNS_E_UNSUPPORTED);
   }
   // AUTO takes the multi-pass path (at_dns_tune can switch): it is the faster
@@ -782,7 +785,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   }
   for (int d = 0; d < 3; ++d) {
     if (g.pes[d] == 1) continue;
-    const size_t gpts = 4ull * g.pes[d] * (size_t)g.plane[d];
+    const size_t gpts = 2ull * M * g.pes[d] * (size_t)g.plane[d];
     if ((rc = dev_alloc(h, &h->GH[d], (size_t)kNumGhostQ * gpts * S)) ||
         (rc = dev_alloc(h, &h->ring[d], (size_t)g.nlev * 5 * gpts * S)))
       return create_fail(h, rc);
@@ -820,7 +823,7 @@ int at_dns_set_history(at_dns_t* h, const double* levels, int32_t nlevels, int64
   h->err.clear();
   if (!levels) return fail(h, AT_DNS_E_INVALID_ARG, "levels is NULL");
   if (where != AT_DNS_HOST && where != AT_DNS_DEVICE) return fail(h, AT_DNS_E_INVALID_ARG, "bad where");
-  if (nlevels < 1 || nlevels > h->g.nlev) return fail(h, AT_DNS_E_INVALID_ARG, "nlevels must be in [1, L+3]");
+  if (nlevels < 1 || nlevels > h->g.nlev) return fail(h, AT_DNS_E_INVALID_ARG, "nlevels must be in [1, L + T_l]");
   if (step < 0) return fail(h, AT_DNS_E_INVALID_ARG, "step must be >= 0");
   const long long cnt = 5 * h->g.npts;
   int rc;
@@ -998,7 +1001,7 @@ int at_dns_get_delay_map(at_dns_t* h, int64_t step, int32_t mode, uint8_t* out) 
   const int P = g.pes[0] * g.pes[1] * g.pes[2];
   uint8_t* tmp = nullptr;
   if ((rc = dev_alloc(h, (void**)&tmp, (size_t)P * 6))) return rc;
-  k_delay_map<<<nblk(P * 6), kBlock, 0, h->st>>>(tmp, P, step, nullptr, mode, h->cfg.max_delay,
+  k_delay_map<<<nblk(P * 6), kBlock, 0, h->st>>>(tmp, P, step, nullptr, mode, h->cfg.max_delay, g.M + 1,
                                                 h->cfg.comm_period, (uint32_t)h->cfg.seed,
                                                 (uint32_t)(h->cfg.seed >> 32));
   cudaError_t e = cudaGetLastError();
@@ -1018,7 +1021,7 @@ int at_dns_get_info(at_dns_t* h, at_dns_info_t* out) {
   out->dt = h->dt;
   out->n_levels = h->g.nlev;
   long long nt = 1, ni = 1;
-  for (int d = 0; d < 3; ++d) { nt *= h->g.nl[d]; ni *= (h->g.nl[d] - 4); }
+  for (int d = 0; d < 3; ++d) { nt *= h->g.nl[d]; ni *= (h->g.nl[d] - 2 * h->g.M); }
   out->boundary_fraction = (double)(nt - ni) / (double)nt;
   out->device_bytes = h->bytes;
   const bool ghost = h->g.pes[0] > 1 || h->g.pes[1] > 1 || h->g.pes[2] > 1;
@@ -1030,6 +1033,7 @@ int at_dns_get_info(at_dns_t* h, at_dns_info_t* out) {
   out->tile[0] = h->TX;
   out->tile[1] = h->TY;
   out->tile[2] = h->ZC;
+  out->order = 2 * h->g.M;
   return AT_DNS_OK;
 }
 

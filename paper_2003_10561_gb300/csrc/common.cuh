@@ -1,10 +1,12 @@
 // Device-side definitions shared by the AT-DNS kernels (sm_103a).
 //
 // Geometry of the periodic (2 pi)^3 grid cut into virtual PEs (Sec. 3,
-// Eqs. (NT)-(NB)), the 4th-order stencil coefficients (zero-delay rows of
-// Table B, Appendix B), the Table B AT time weights and the Philox4x32-10
-// generator that stands in for the network delays of Algorithm 1.
+// Eqs. (NT)-(NB)), the 4th- and 6th-order stencil coefficients (zero-delay
+// rows of Table B, Appendix B), the Table B AT time weights and the
+// Philox4x32-10 generator that stands in for the network delays of
+// Algorithm 1.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -33,12 +35,43 @@ struct Geom {
   long long npts;    // n0 n1 n2
   long long plane[3];// points of a plane normal to d: npts / n[d]
   long long stride[3];  // linear-index stride of direction d: 1, n0, n0 n1
-  int nlev;          // ring levels L + 3
-  // stencil coefficients with the 1/(12 dx) and 1/(12 dx^2) folded in
-  double c1[3], c2[3];        // D1 = c1 (f[+1]-f[-1]) + c2 (f[+2]-f[-2])
-  double a0[3], a1[3], a2[3]; // D2 = a0 f + a1 (f[+1]+f[-1]) + a2 (f[+2]+f[-2])
-  double inv12dx[3];          // 1/(12 dx) for the one-sided stencils
+  int M;             // stencil half width: 2 (4th order) or 3 (6th order)
+  int nlev;          // ring levels L + T_l, T_l = M + 1
+  // central stencil coefficients with the denominators and dx folded in
+  double c1[3], c2[3], c3[3];         // D1 = sum_m c_m (f[+m] - f[-m])
+  double a0[3], a1[3], a2[3], a3[3];  // D2 = a0 f + sum_m a_m (f[+m] + f[-m])
+  double hloc[3];    // 1/(12 dx) (M = 2) or 1/(60 dx) (M = 3): one-sided stencils
+  double inv_dx[3];  // 1/dx
 };
+
+// Central stencils of half width M = 2 (4th order, /12) or 3 (6th order:
+// D1 (-1, 9, -45, 0, 45, -9, 1)/60, D2 (2, -27, 270, -490, 270, -27, 2)/180).
+inline void set_stencils(Geom& g, int M) {
+  g.M = M;
+  for (int d = 0; d < 3; ++d) {
+    const double dx = 2.0 * M_PI / g.n[d];
+    if (M == 2) {
+      g.c1[d] = 8.0 / (12.0 * dx);
+      g.c2[d] = -1.0 / (12.0 * dx);
+      g.c3[d] = 0.0;
+      g.a0[d] = -30.0 / (12.0 * dx * dx);
+      g.a1[d] = 16.0 / (12.0 * dx * dx);
+      g.a2[d] = -1.0 / (12.0 * dx * dx);
+      g.a3[d] = 0.0;
+      g.hloc[d] = 1.0 / (12.0 * dx);
+    } else {
+      g.c1[d] = 45.0 / (60.0 * dx);
+      g.c2[d] = -9.0 / (60.0 * dx);
+      g.c3[d] = 1.0 / (60.0 * dx);
+      g.a0[d] = -490.0 / (180.0 * dx * dx);
+      g.a1[d] = 270.0 / (180.0 * dx * dx);
+      g.a2[d] = -27.0 / (180.0 * dx * dx);
+      g.a3[d] = 2.0 / (180.0 * dx * dx);
+      g.hloc[d] = 1.0 / (60.0 * dx);
+    }
+    g.inv_dx[d] = 1.0 / dx;
+  }
+}
 
 struct Phys {
   double gamma, gm1, prandtl, mu0, omega, cp_over_pr;
@@ -49,9 +82,9 @@ struct Phys {
 // run on the FP64 pipe).
 template <typename S>
 struct Coef {
-  S c1[3], c2[3];          // D1 = c1 (f[+1]-f[-1]) + c2 (f[+2]-f[-2])
-  S a0[3], a1[3], a2[3];   // D2 = a0 f + a1 (f[+1]+f[-1]) + a2 (f[+2]+f[-2])
-  S h12[3];                // 1/(12 dx) for the one-sided stencils
+  S c1[3], c2[3], c3[3];          // D1 = sum_m c_m (f[+m] - f[-m])
+  S a0[3], a1[3], a2[3], a3[3];   // D2 = a0 f + sum_m a_m (f[+m] + f[-m])
+  S hloc[3];                      // scale of the one-sided stencils
   S gamma, gm1, mu0, omega, cp_over_pr;
   S inv_gamma;
   S dt;
@@ -63,10 +96,12 @@ inline Coef<S> make_coef(const Geom& g, const Phys& ph, double dt) {
   for (int d = 0; d < 3; ++d) {
     c.c1[d] = (S)g.c1[d];
     c.c2[d] = (S)g.c2[d];
+    c.c3[d] = (S)g.c3[d];
     c.a0[d] = (S)g.a0[d];
     c.a1[d] = (S)g.a1[d];
     c.a2[d] = (S)g.a2[d];
-    c.h12[d] = (S)g.inv12dx[d];
+    c.a3[d] = (S)g.a3[d];
+    c.hloc[d] = (S)g.hloc[d];
   }
   c.gamma = (S)ph.gamma;
   c.gm1 = (S)ph.gm1;
@@ -104,12 +139,21 @@ __device__ __forceinline__ int pe_number(const Geom& g, int x, int y, int z) {
   return ((z / g.nl[2]) * g.pes[1] + (y / g.nl[1])) * g.pes[0] + (x / g.nl[0]);
 }
 
-// Table B (T_l = 3) weights of levels n-k, n-k-1, n-k-2:
-// (k^2+3k+2)/2, -(k^2+2k), (k^2+k)/2 -- integers for integer k.
-__device__ __forceinline__ void at_weights(int k, int& w0, int& w1, int& w2) {
-  w0 = ((k + 1) * (k + 2)) / 2;
-  w1 = -(k * (k + 2));
-  w2 = (k * (k + 1)) / 2;
+// Table B weights of levels n-k .. n-k-M (T_l = M + 1 levels), integers for
+// integer k.  4th order: (k^2+3k+2)/2, -(k^2+2k), (k^2+k)/2.  6th order:
+// (k^3+6k^2+11k+6)/6, -(k^3+5k^2+6k)/2, (k^3+4k^2+3k)/2, -(k^3+3k^2+2k)/6.
+template <int M>
+__device__ __forceinline__ void at_weights(int k, int (&w)[M + 1]) {
+  if constexpr (M == 2) {
+    w[0] = ((k + 1) * (k + 2)) / 2;
+    w[1] = -(k * (k + 2));
+    w[2] = (k * (k + 1)) / 2;
+  } else {
+    w[0] = ((k + 1) * (k + 2) * (k + 3)) / 6;
+    w[1] = -((k * (k + 2) * (k + 3)) / 2);
+    w[2] = (k * (k + 1) * (k + 3)) / 2;
+    w[3] = -((k * (k + 1) * (k + 2)) / 6);
+  }
 }
 
 // Philox4x32-10 (Salmon et al., SC'11): counter c, key k, ten rounds, key
@@ -128,10 +172,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 constexpr uint32_t kDelayTag = 0x4154u;
 constexpr uint32_t kForceTag = 0x464Fu;
 
-// Delay of face f of PE p at step n (Sec. 3.1, Algorithms 1 and 2).
-__device__ __forceinline__ int delay_of(int mode, long long n, int p, int f, int L, int cr,
+// Delay of face f of PE p at step n (Sec. 3.1, Algorithms 1 and 2); the
+// first L + T_l steps are synchronous.
+__device__ __forceinline__ int delay_of(int mode, long long n, int p, int f, int L, int tl, int cr,
                                         uint32_t k0, uint32_t k1) {
-  const long long n0 = L + 3;               // synchronous start-up: L + T_l steps
+  const long long n0 = L + tl;
   if (mode == 0 || n < n0) return 0;
   if (mode == 1) return (int)((n - n0) % cr);
   const uint4 w = philox4x32_10(make_uint4((uint32_t)n, (uint32_t)p, (uint32_t)f, kDelayTag), k0, k1);
@@ -151,6 +196,42 @@ __constant__ double kLocalCoefD[5][5] = {
     {1, -8, 8, -1, 0}, {-25, 48, -36, 16, -3}, {-3, -10, 18, -6, 1}, {3, 10, -18, 6, -1}, {25, -48, 36, -16, 3}};
 __device__ __forceinline__ float local_coef(float, int kind, int i) { return kLocalCoefF[kind][i]; }
 __device__ __forceinline__ double local_coef(double, int kind, int i) { return kLocalCoefD[kind][i]; }
+
+// The 6th-order set (coefficient x 60): 0 central (-1, 9, -45, 45, -9, 1);
+// 1, 2, 3 the first three points of a PE on offsets 0..6, -1..5, -2..4;
+// 4, 5, 6 the last three (mirror images of 3, 2, 1).
+__constant__ int kLocal6Off[7][7] = {
+    {-3, -2, -1, 1, 2, 3, 0},     {0, 1, 2, 3, 4, 5, 6},         {-1, 0, 1, 2, 3, 4, 5},
+    {-2, -1, 0, 1, 2, 3, 4},      {2, 1, 0, -1, -2, -3, -4},     {1, 0, -1, -2, -3, -4, -5},
+    {0, -1, -2, -3, -4, -5, -6}};
+__constant__ double kLocal6Coef[7][7] = {
+    {-1, 9, -45, 45, -9, 1, 0},           {-147, 360, -450, 400, -225, 72, -10},
+    {-10, -77, 150, -100, 50, -15, 2},    {2, -24, -35, 80, -30, 8, -1},
+    {-2, 24, 35, -80, 30, -8, 1},         {10, 77, -150, 100, -50, 15, -2},
+    {147, -360, 450, -400, 225, -72, 10}};
+__constant__ float kLocal6CoefF[7][7] = {
+    {-1, 9, -45, 45, -9, 1, 0},           {-147, 360, -450, 400, -225, 72, -10},
+    {-10, -77, 150, -100, 50, -15, 2},    {2, -24, -35, 80, -30, 8, -1},
+    {-2, 24, 35, -80, 30, -8, 1},         {10, 77, -150, 100, -50, 15, -2},
+    {147, -360, 450, -400, 225, -72, 10}};
+
+// Row i of the PE-local stencil of `kind` for half width M: offset and
+// coefficient (times the stencil denominator); 2M + 1 entries.
+template <int M>
+__device__ __forceinline__ int local_off(int kind, int i) {
+  if constexpr (M == 2) return kLocalOff[kind][i];
+  else return kLocal6Off[kind][i];
+}
+template <int M>
+__device__ __forceinline__ float local_coefm(float, int kind, int i) {
+  if constexpr (M == 2) return kLocalCoefF[kind][i];
+  else return kLocal6CoefF[kind][i];
+}
+template <int M>
+__device__ __forceinline__ double local_coefm(double, int kind, int i) {
+  if constexpr (M == 2) return kLocalCoefD[kind][i];
+  else return kLocal6Coef[kind][i];
+}
 
 // Order-preserving map of a double to a signed 64-bit key (for atomic min/max).
 __device__ __forceinline__ long long ordered_key(double v) {
@@ -188,11 +269,11 @@ struct StepArgs {
   S* Unext;            // [5][npts] level n+1 (step) -- may be null for rhs-only
   const S* PQ;         // [16][npts]
   const S* G;          // [12][npts]
-  const S* GH[3];      // [9][4 P_d][plane_d] per direction
+  const S* GH[3];      // [9][2M P_d][plane_d] per direction
   S* Rprev;            // [5][npts] R^{n-1} in, R^n out
   const S* Ulo;        // compensated form: low words of U (else null)
   S* Ulo_next;         // compensated form: low words of U^{n+1}
-  S* ring[3];          // [nlev][5][4 P_d][plane_d]
+  S* ring[3];          // [nlev][5][2M P_d][plane_d]
   double* Rout;        // rhs-only output [5][npts] or null
   double* partial;     // [gridDim.x][kNumStat]
   unsigned long long* words;  // [0] max wave key, [1] min rho key, [2] min p key, [3] health

@@ -6,10 +6,11 @@
 //
 // One RHS evaluation (Sec. 2) is four launches:
 //   k_prim   per point: u, v, w, T and the 12 non-trivial inviscid fluxes;
-//   k_ghost  per PE-face ghost point (2 layers each side, Sec. 3): the 9
+//   k_ghost  per PE-face ghost point (M layers each side, Sec. 3; M = 2 for
+//            the 4th-order scheme, 3 for the 6th-order one): the 9
 //            differentiated quantities of that direction at level n (k = 0) or
-//            extrapolated from levels n-k, n-k-1, n-k-2 of the slab ring with
-//            the Table B weights (Appendix B);
+//            extrapolated from levels n-k .. n-k-M of the slab ring with the
+//            Table B weights (Appendix B);
 //   k_grad   per point: AT first derivatives du_i/dx_j and dT/dx_j;
 //   k_main   per point: inviscid flux divergence, second derivatives, mixed
 //            derivatives by the three-step rule (Sec. 2.1), viscous / heat /
@@ -77,11 +78,11 @@ __device__ __forceinline__ void ghost_quantities(const Coef<S>& K, int d, const 
 }
 
 // ---------------------------------------------------------------------------
-// AT ghost assembly.  Ghost slot s of PE column p_d along d: s = 0, 1 are the
-// local coordinates -2, -1 (left face, face 2d), s = 2, 3 are nl, nl+1 (right
-// face, face 2d+1).  Ring slab index sp = 4 p + t with t = 0, 1 for local 0, 1
-// and t = 2, 3 for local nl-2, nl-1.
-template <typename S>
+// AT ghost assembly.  Ghost slot s of PE column p_d along d (2M slots): s < M
+// is the local coordinate s - M (left face, face 2d), s >= M is nl + s - M
+// (right face, face 2d+1).  Ring slab index sp = 2M p + t with t < M for
+// local t and t >= M for local nl - 2M + t.
+template <typename S, int M>
 __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __restrict__ U0,
                                                const S* __restrict__ U1, const DevState* __restrict__ ds,
                                                const S* __restrict__ PQ, S* GH0, S* GH1, S* GH2,
@@ -101,21 +102,22 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   S* GH = d == 0 ? GH0 : (d == 1 ? GH1 : GH2);
   const S* ring = d == 0 ? ring0 : (d == 1 ? ring1 : ring2);
   const long long plane = g.plane[d];
+  constexpr int NS = 2 * M;
   const int gi = (int)(j / plane);
   const long long pl = j - (long long)gi * plane;
-  const int ped = gi >> 2, slot = gi & 3;
+  const int ped = gi / NS, slot = gi - ped * NS;
   const int P = g.pes[d], nl = g.nl[d], nd = g.n[d];
   int c[3];
   if (d == 0) { c[2] = (int)(pl / g.n[1]); c[1] = (int)(pl - (long long)c[2] * g.n[1]); }
   else if (d == 1) { c[2] = (int)(pl / g.n[0]); c[0] = (int)(pl - (long long)c[2] * g.n[0]); }
   else { c[1] = (int)(pl / g.n[0]); c[0] = (int)(pl - (long long)c[1] * g.n[0]); }
-  int cd = ped * nl + (slot < 2 ? slot - 2 : nl + slot - 2);
+  int cd = ped * nl + (slot < M ? slot - M : nl + slot - M);
   cd = cd < 0 ? cd + nd : (cd >= nd ? cd - nd : cd);
   c[d] = ped * nl;   // any coordinate inside the receiving PE
   const int p = pe_number(g, c[0], c[1], c[2]);
-  const int face = 2 * d + (slot >= 2 ? 1 : 0);
+  const int face = 2 * d + (slot >= M ? 1 : 0);
   const int k = dmap[p * 6 + face];
-  const long long qstride = 4LL * P * plane;
+  const long long qstride = (long long)NS * P * plane;
   S* out = GH + (long long)gi * plane + pl;
   if (k == 0) {
     c[d] = cd;
@@ -138,25 +140,25 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
     }
     return;
   }
-  const int nbr = slot < 2 ? (ped - 1 + P) % P : (ped + 1) % P;
-  const int sp = 4 * nbr + (slot < 2 ? slot + 2 : slot - 2);
-  int wi[3];
-  at_weights(k, wi[0], wi[1], wi[2]);
-  const S w[3] = {S(wi[0]), S(wi[1]), S(wi[2])};
+  const int nbr = slot < M ? (ped - 1 + P) % P : (ped + 1) % P;
+  const int sp = NS * nbr + (slot < M ? slot + M : slot - M);
+  int wi[M + 1];
+  at_weights<M>(k, wi);
   S acc[kNumGhostQ];
 #pragma unroll
   for (int q = 0; q < kNumGhostQ; ++q) acc[q] = S(0);
 #pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    const long long lev = n - k - l;              // >= 1: delays start after L + 3 steps
+  for (int l = 0; l <= M; ++l) {
+    const long long lev = n - k - l;              // >= 1: delays start after L + T_l steps
     const int rs = (int)(lev % g.nlev);
+    const S w = S(wi[l]);
     S Uv[5], q[kNumGhostQ];
 #pragma unroll
     for (int v = 0; v < 5; ++v)
-      Uv[v] = ring[(((long long)rs * 5 + v) * 4 * P + sp) * plane + pl];
+      Uv[v] = ring[(((long long)rs * 5 + v) * NS * P + sp) * plane + pl];
     ghost_quantities(K, d, Uv, q);
 #pragma unroll
-    for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = fma(w[l], q[qq], acc[qq]);
+    for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = fma(w, q[qq], acc[qq]);
   }
 #pragma unroll
   for (int q = 0; q < kNumGhostQ; ++q) out[q * qstride] = acc[q];
@@ -182,23 +184,26 @@ __device__ __forceinline__ Pt make_point(const Geom& g, long long idx) {
   return P;
 }
 
-// Neighbours of one point along direction d at offsets -2, -1, +1, +2: either
-// an offset into the field relative to the point (inside the PE, or periodic
-// wrap when the direction has one PE) or, across a PE face, an index into the
-// ghost array of direction d.  Built once per point and direction, then used
-// for every quantity of that direction.
+// Neighbours of one point along direction d at offsets -M .. -1, +1 .. +M
+// (entry j is offset j - M for j < M, j - M + 1 above): either an offset into
+// the field relative to the point (inside the PE, or periodic wrap when the
+// direction has one PE) or, across a PE face, an index into the ghost array of
+// direction d.  Built once per point and direction, then used for every
+// quantity of that direction.
+template <int M>
 struct Nb {
-  long long off[4];
+  long long off[2 * M];
   unsigned gmask;    // bit j: off[j] indexes the ghost array
 };
 
-__device__ __forceinline__ Nb make_nb(const Geom& g, const Pt& P, int d) {
-  Nb nb;
+template <int M>
+__device__ __forceinline__ Nb<M> make_nb(const Geom& g, const Pt& P, int d) {
+  Nb<M> nb;
   nb.gmask = 0;
   const long long st = g.stride[d];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int m = j < 2 ? j - 2 : j - 1;
+  for (int j = 0; j < 2 * M; ++j) {
+    const int m = j < M ? j - M : j - M + 1;
     if (g.pes[d] == 1) {
       int c2 = P.c[d] + m;
       c2 = c2 < 0 ? c2 + g.n[d] : (c2 >= g.n[d] ? c2 - g.n[d] : c2);
@@ -208,8 +213,8 @@ __device__ __forceinline__ Nb make_nb(const Geom& g, const Pt& P, int d) {
       if (l2 >= 0 && l2 < g.nl[d]) {
         nb.off[j] = (long long)m * st;
       } else {
-        const int slot = l2 < 0 ? l2 + 2 : 2 + (l2 - g.nl[d]);
-        nb.off[j] = (long long)(4 * P.pe[d] + slot) * g.plane[d] + P.pl[d];
+        const int slot = l2 < 0 ? l2 + M : M + (l2 - g.nl[d]);
+        nb.off[j] = (long long)(2 * M * P.pe[d] + slot) * g.plane[d] + P.pl[d];
         nb.gmask |= 1u << j;
       }
     }
@@ -217,27 +222,35 @@ __device__ __forceinline__ Nb make_nb(const Geom& g, const Pt& P, int d) {
   return nb;
 }
 
-template <typename S>
-__device__ __forceinline__ S nbv(const Nb& nb, int j, long long idx, const S* __restrict__ f,
+template <typename S, int M>
+__device__ __forceinline__ S nbv(const Nb<M>& nb, int j, long long idx, const S* __restrict__ f,
                                  const S* __restrict__ gh) {
   return ((nb.gmask >> j) & 1u) ? gh[nb.off[j]] : f[idx + nb.off[j]];
 }
 
-// acc + D1 f  with  D1 = c1 (f[+1]-f[-1]) + c2 (f[+2]-f[-2])  (differences
-// first: rounding relative to the derivative, not to the stencil terms).
-template <typename S>
-__device__ __forceinline__ S nb_d1_acc(S acc, S c1, S c2, const Nb& nb, long long idx, const S* f, const S* gh) {
-  acc = fma(c1, nbv(nb, 2, idx, f, gh) - nbv(nb, 1, idx, f, gh), acc);
-  return fma(c2, nbv(nb, 3, idx, f, gh) - nbv(nb, 0, idx, f, gh), acc);
+// acc - D1 f or acc + D1 f (sign s = -1 or 1 folded into the coefficients)
+// with D1 = sum_m c_m (f[+m]-f[-m])  (differences first: rounding relative to
+// the derivative, not to the stencil terms).  Entry M - 1 + m is offset +m,
+// entry M - m is offset -m.
+template <typename S, int M>
+__device__ __forceinline__ S nb_d1_acc(S acc, S c1, S c2, S c3, const Nb<M>& nb, long long idx, const S* f,
+                                       const S* gh) {
+  acc = fma(c1, nbv(nb, M, idx, f, gh) - nbv(nb, M - 1, idx, f, gh), acc);
+  acc = fma(c2, nbv(nb, M + 1, idx, f, gh) - nbv(nb, M - 2, idx, f, gh), acc);
+  if constexpr (M == 3) acc = fma(c3, nbv(nb, M + 2, idx, f, gh) - nbv(nb, M - 3, idx, f, gh), acc);
+  return acc;
 }
 
-// D2 without the centre term: a1 (f[+1]+f[-1]) + a2 (f[+2]+f[-2]).
-template <typename S>
-__device__ __forceinline__ S nb_d2_off(S a1, S a2, const Nb& nb, long long idx, const S* f, const S* gh) {
-  return fma(a1, nbv(nb, 2, idx, f, gh) + nbv(nb, 1, idx, f, gh), a2 * (nbv(nb, 3, idx, f, gh) + nbv(nb, 0, idx, f, gh)));
+// D2 without the centre term: sum_m a_m (f[+m]+f[-m]).
+template <typename S, int M>
+__device__ __forceinline__ S nb_d2_off(S a1, S a2, S a3, const Nb<M>& nb, long long idx, const S* f, const S* gh) {
+  if constexpr (M == 2)
+    return fma(a1, nbv(nb, 2, idx, f, gh) + nbv(nb, 1, idx, f, gh), a2 * (nbv(nb, 3, idx, f, gh) + nbv(nb, 0, idx, f, gh)));
+  return fma(a1, nbv(nb, 3, idx, f, gh) + nbv(nb, 2, idx, f, gh),
+             fma(a2, nbv(nb, 4, idx, f, gh) + nbv(nb, 1, idx, f, gh), a3 * (nbv(nb, 5, idx, f, gh) + nbv(nb, 0, idx, f, gh))));
 }
 
-template <typename S>
+template <typename S, int M>
 __global__ void __launch_bounds__(256) k_grad(Geom g, Coef<S> K, const S* __restrict__ PQ,
                                               const S* __restrict__ GH0, const S* __restrict__ GH1,
                                               const S* __restrict__ GH2, S* __restrict__ G) {
@@ -248,11 +261,11 @@ __global__ void __launch_bounds__(256) k_grad(Geom g, Coef<S> K, const S* __rest
   const S* GH[3] = {GH0, GH1, GH2};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const long long qs = 4LL * g.pes[d] * g.plane[d];
-    const Nb nb = make_nb(g, P, d);
+    const long long qs = 2LL * M * g.pes[d] * g.plane[d];
+    const Nb<M> nb = make_nb<M>(g, P, d);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const S v = nb_d1_acc(S(0), K.c1[d], K.c2[d], nb, idx, PQ + q * N, GH[d] + (5 + q) * qs);
+      const S v = nb_d1_acc<S, M>(S(0), K.c1[d], K.c2[d], K.c3[d], nb, idx, PQ + q * N, GH[d] + (5 + q) * qs);
       const int out = q < 3 ? 3 * q + d : 9 + d;
       G[out * N + idx] = v;
     }
@@ -261,28 +274,28 @@ __global__ void __launch_bounds__(256) k_grad(Geom g, Coef<S> K, const S* __rest
 
 // ---------------------------------------------------------------------------
 // Mixed-derivative helpers (Sec. 2.1).
-__device__ __forceinline__ bool central_fits(const Geom& g, const Pt& P, int d) {
-  return g.pes[d] == 1 || (P.li[d] >= 2 && P.li[d] <= g.nl[d] - 3);
-}
 
-// PE-local 4th-order first derivative of a gradient field in direction a at a
-// point where the stencil is one-sided or central (kind as in kLocalOff): a
-// table-driven loop, so only the one stencil that applies is evaluated.
+// Kind of the PE-local first-derivative stencil at a point (kLocalOff /
+// kLocal6Off rows): 0 central; 1 .. M the first M points of a PE; M+1 .. 2M
+// the last M points.
+template <int M>
 __device__ __forceinline__ int local_kind_of(const Geom& g, const Pt& P, int d) {
   if (g.pes[d] == 1) return 0;
   const int li = P.li[d], nl = g.nl[d];
-  if (li >= 2 && li <= nl - 3) return 0;
-  return li == 0 ? 1 : (li == 1 ? 2 : (li == nl - 2 ? 3 : 4));
+  if (li >= M && li <= nl - 1 - M) return 0;
+  return li < M ? 1 + li : 1 + M + (li - (nl - M));
 }
 
-template <typename S>
+// PE-local first derivative of a gradient field in direction a: a
+// table-driven loop, so only the one stencil that applies is evaluated.
+template <typename S, int M>
 __device__ __noinline__ S local_d1_table(const Geom& g, const Coef<S>& K, const Pt& P, int a, const S* __restrict__ f,
                                          int kind) {
   const long long s = g.stride[a];
   S acc = S(0);
-  for (int i = 0; i < 5; ++i) {
-    const S c = local_coef(S(0), kind, i);
-    int off = kLocalOff[kind][i];
+  for (int i = 0; i < 2 * M + 1; ++i) {
+    const S c = local_coefm<M>(S(0), kind, i);
+    int off = local_off<M>(kind, i);
     if (g.pes[a] == 1) {   // central with periodic wrap
       int c2 = P.c[a] + off;
       c2 = c2 < 0 ? c2 + g.n[a] : (c2 >= g.n[a] ? c2 - g.n[a] : c2);
@@ -290,7 +303,7 @@ __device__ __noinline__ S local_d1_table(const Geom& g, const Coef<S>& K, const 
     }
     if (c != S(0)) acc = fma(c, f[P.idx + (long long)off * s], acc);
   }
-  return acc * K.h12[a];
+  return acc * K.hloc[a];
 }
 
 // PE-local 4th-order first derivative with the stencil written out per kind
@@ -299,7 +312,7 @@ template <typename S>
 __device__ __forceinline__ S local_d1(const Geom& g, const Coef<S>& K, const Pt& P, int a, const S* __restrict__ f) {
   const long long s = g.stride[a];
   const long long i = P.idx;
-  const int kind = local_kind_of(g, P, a);
+  const int kind = local_kind_of<2>(g, P, a);
   if (kind == 0) {
     if (g.pes[a] == 1) {
       auto at = [&](int off) {
@@ -311,7 +324,7 @@ __device__ __forceinline__ S local_d1(const Geom& g, const Coef<S>& K, const Pt&
     }
     return fma(K.c1[a], f[i + s] - f[i - s], K.c2[a] * (f[i + 2 * s] - f[i - 2 * s]));
   }
-  const S h = K.h12[a];
+  const S h = K.hloc[a];
   if (kind == 1)
     return h * (S(-25) * f[i] + S(48) * f[i + s] - S(36) * f[i + 2 * s] + S(16) * f[i + 3 * s] - S(3) * f[i + 4 * s]);
   if (kind == 2)
@@ -323,23 +336,25 @@ __device__ __forceinline__ S local_d1(const Geom& g, const Coef<S>& K, const Pt&
 
 // d/dx_a (d f/dx_b) with Gb = AT df/dx_b and Ga = AT df/dx_a (Sec. 2.1): the
 // central derivative in a of Gb inside (fast path), the average of the two
-// PE-local derivatives at PE-boundary points.  The FP64 form evaluates the
-// one-sided stencils from a table out of line (fewer FP64-pipe instructions);
-// the FP32 form keeps them inline.
-template <typename S>
+// PE-local derivatives at PE-boundary points.  The FP64 form (and the 6th-order
+// scheme) evaluates the one-sided stencils from a table out of line (fewer
+// FP64-pipe instructions); the 4th-order FP32 form keeps them inline.
+template <typename S, int M>
 __device__ __forceinline__ S mixed(const Geom& g, const Coef<S>& K, const Pt& P, int a, int b, const S* Gb,
                                    const S* Ga) {
-  if (sizeof(S) == 4) {
-    if (local_kind_of(g, P, a) == 0 && local_kind_of(g, P, b) == 0) return local_d1(g, K, P, a, Gb);
+  if constexpr (sizeof(S) == 4 && M == 2) {
+    if (local_kind_of<2>(g, P, a) == 0 && local_kind_of<2>(g, P, b) == 0) return local_d1(g, K, P, a, Gb);
     return S(0.5) * (local_d1(g, K, P, a, Gb) + local_d1(g, K, P, b, Ga));
   }
-  const int ka = local_kind_of(g, P, a), kb = local_kind_of(g, P, b);
+  const int ka = local_kind_of<M>(g, P, a), kb = local_kind_of<M>(g, P, b);
   if (ka == 0 && kb == 0 && g.pes[a] > 1) {
     const long long s = g.stride[a], i = P.idx;
-    return fma(K.c1[a], Gb[i + s] - Gb[i - s], K.c2[a] * (Gb[i + 2 * s] - Gb[i - 2 * s]));
+    if constexpr (M == 2) return fma(K.c1[a], Gb[i + s] - Gb[i - s], K.c2[a] * (Gb[i + 2 * s] - Gb[i - 2 * s]));
+    return fma(K.c1[a], Gb[i + s] - Gb[i - s],
+               fma(K.c2[a], Gb[i + 2 * s] - Gb[i - 2 * s], K.c3[a] * (Gb[i + 3 * s] - Gb[i - 3 * s])));
   }
-  if (ka == 0 && kb == 0) return local_d1_table(g, K, P, a, Gb, 0);
-  return S(0.5) * (local_d1_table(g, K, P, a, Gb, ka) + local_d1_table(g, K, P, b, Ga, kb));
+  if (ka == 0 && kb == 0) return local_d1_table<S, M>(g, K, P, a, Gb, 0);
+  return S(0.5) * (local_d1_table<S, M>(g, K, P, a, Gb, ka) + local_d1_table<S, M>(g, K, P, b, Ga, kb));
 }
 
 template <typename T>
@@ -463,7 +478,7 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
 }
 
 // ---------------------------------------------------------------------------
-template <typename S>
+template <typename S, int M>
 __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> A0) {
   StepArgs<S> A = A0;
   resolve_step(A);
@@ -491,17 +506,17 @@ __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> 
     S a0sum = S(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const long long qs = 4LL * g.pes[d] * g.plane[d];
-      const Nb nb = make_nb(g, P, d);
+      const long long qs = 2LL * M * g.pes[d] * g.plane[d];
+      const Nb<M> nb = make_nb<M>(g, P, d);
       const S* gh = A.GH[d];
 #pragma unroll
       for (int e = 0; e < 5; ++e) {
         const S* f = e == 0 ? U + (1 + d) * N : PQ + (4 + 4 * d + e - 1) * N;
-        R[e] = nb_d1_acc(R[e], -K.c1[d], -K.c2[d], nb, idx, f, gh + e * qs);
+        R[e] = nb_d1_acc<S, M>(R[e], -K.c1[d], -K.c2[d], -K.c3[d], nb, idx, f, gh + e * qs);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const S v = nb_d2_off(K.a1[d], K.a2[d], nb, idx, PQ + q * N, gh + (5 + q) * qs);
+        const S v = nb_d2_off<S, M>(K.a1[d], K.a2[d], K.a3[d], nb, idx, PQ + q * N, gh + (5 + q) * qs);
         lap[q] += v;
         if (q == d) d2diag[d] = fma(K.a0[d], PQ[q * N + idx], v);
       }
@@ -526,7 +541,7 @@ __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> 
       S s = d2diag[i];
 #pragma unroll
       for (int k = 0; k < 3; ++k)
-        if (k != i) s += mixed(g, K, P, i, k, G + (3 * k + k) * N, G + (3 * k + i) * N);
+        if (k != i) s += mixed<S, M>(g, K, P, i, k, G + (3 * k + k) * N, G + (3 * k + i) * N);
       gth[i] = s;
     }
 
@@ -606,13 +621,13 @@ __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> 
       for (int d = 0; d < 3; ++d) {
         if (g.pes[d] == 1) continue;
         const int li = P.li[d], nl = g.nl[d];
-        if (li >= 2 && li < nl - 2) continue;
-        const int t = li < 2 ? li : li - nl + 4;
-        const long long sp = 4LL * P.pe[d] + t;
+        if (li >= M && li < nl - M) continue;
+        const int t = li < M ? li : li - nl + 2 * M;
+        const long long sp = 2LL * M * P.pe[d] + t;
         S* rg = A.ring[d];
-        const long long P4 = 4LL * g.pes[d];
+        const long long PS = 2LL * M * g.pes[d];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) rg[(((long long)slot * 5 + v) * P4 + sp) * g.plane[d] + P.pl[d]] = un[v];
+        for (int v = 0; v < 5; ++v) rg[(((long long)slot * 5 + v) * PS + sp) * g.plane[d] + P.pl[d]] = un[v];
       }
     } else if (A.Rout) {
 #pragma unroll

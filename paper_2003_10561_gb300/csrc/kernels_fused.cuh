@@ -203,10 +203,10 @@ struct PointWin {
       return d1(K, f, in, outer == 0 ? off : 0, outer == 1 ? off : 0, outer == 2 ? off : 0);
     };
     if (kind[a] == 0 && kind[b] == 0)
-      return K.h12[a] * apply_local<S>(0, [&](int o) { return inner(a, b, o); });
+      return K.hloc[a] * apply_local<S>(0, [&](int o) { return inner(a, b, o); });
     if (sizeof(S) == 4) {   // FP32 form: the stencils inline
-      const S pa = K.h12[a] * apply_local<S>(kind[a], [&](int o) { return inner(a, b, o); });
-      const S pb_ = K.h12[b] * apply_local<S>(kind[b], [&](int o) { return inner(b, a, o); });
+      const S pa = K.hloc[a] * apply_local<S>(kind[a], [&](int o) { return inner(a, b, o); });
+      const S pb_ = K.hloc[b] * apply_local<S>(kind[b], [&](int o) { return inner(b, a, o); });
       return S(0.5) * (pa + pb_);
     }
     return S(0.5) * (boundary_part(K, f, a, b, kind[a], s0) + boundary_part(K, f, b, a, kind[b], s0));
@@ -233,7 +233,7 @@ struct PointWin {
       const S d = fma(K.c1[in], val(1) - val(-1), K.c2[in] * (val(2) - val(-2)));
       acc = fma(c, d, acc);
     }
-    return acc * K.h12[outer];
+    return acc * K.hloc[outer];
   }
 };
 

@@ -1,3 +1,4 @@
-// FP32-bulk instantiation of the step kernels.
+// FP32-bulk instantiation of the step kernels, 4th-order scheme (half width 2).
 #define AT_DNS_SCALAR float
+#define AT_DNS_HALF_WIDTH 2
 #include "kernels_impl.cuh"

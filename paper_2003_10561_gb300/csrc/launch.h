@@ -1,5 +1,4 @@
-// Launchers of the templated step kernels; each precision is instantiated in
-// its own translation unit (kernels_p64.cu, kernels_p32.cu).
+// Launchers of the templated step kernels.
 #pragma once
 #include "common.cuh"
 
@@ -11,16 +10,37 @@ template <typename S>
 cudaError_t launch_prim(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds, S* PQ,
                         cudaStream_t st);
 
-template <typename S>
-cudaError_t launch_ghost(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds,
-                         const S* PQ, S* const GH[3],
-                         S* const ring[3], const uint8_t* dmap, long long n, cudaStream_t st);
+// The ghost, gradient and main kernels for stencil half width M (2: 4th
+// order, 3: 6th order); each (S, M) pair is compiled in its own translation
+// unit (kernels_p64.cu, kernels_p32.cu, kernels_p64_o6.cu, kernels_p32_o6.cu).
+template <typename S, int M>
+cudaError_t launch_ghost_m(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds,
+                           const S* PQ, S* const GH[3], S* const ring[3], const uint8_t* dmap, long long n,
+                           cudaStream_t st);
+
+template <typename S, int M>
+cudaError_t launch_grad_m(const Geom& g, const Coef<S>& K, const S* PQ, S* const GH[3], S* G, cudaStream_t st);
+
+template <typename S, int M>
+cudaError_t launch_main_m(const Geom& g, const Coef<S>& K, const StepArgs<S>& a, cudaStream_t st);
 
 template <typename S>
-cudaError_t launch_grad(const Geom& g, const Coef<S>& K, const S* PQ, S* const GH[3], S* G, cudaStream_t st);
+inline cudaError_t launch_ghost(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds,
+                                const S* PQ, S* const GH[3], S* const ring[3], const uint8_t* dmap, long long n,
+                                cudaStream_t st) {
+  return g.M == 3 ? launch_ghost_m<S, 3>(g, K, U0, U1, ds, PQ, GH, ring, dmap, n, st)
+                  : launch_ghost_m<S, 2>(g, K, U0, U1, ds, PQ, GH, ring, dmap, n, st);
+}
 
 template <typename S>
-cudaError_t launch_main(const Geom& g, const Coef<S>& K, const StepArgs<S>& a, cudaStream_t st);
+inline cudaError_t launch_grad(const Geom& g, const Coef<S>& K, const S* PQ, S* const GH[3], S* G, cudaStream_t st) {
+  return g.M == 3 ? launch_grad_m<S, 3>(g, K, PQ, GH, G, st) : launch_grad_m<S, 2>(g, K, PQ, GH, G, st);
+}
+
+template <typename S>
+inline cudaError_t launch_main(const Geom& g, const Coef<S>& K, const StepArgs<S>& a, cudaStream_t st) {
+  return g.M == 3 ? launch_main_m<S, 3>(g, K, a, st) : launch_main_m<S, 2>(g, K, a, st);
+}
 
 // Fused single-pass step kernel on TX x TY tiles marching ZC planes in z.
 template <typename S>

@@ -84,16 +84,8 @@ extern "C" int at_dns_rhs_noalloc(const int32_t n[3], double gamma, double prand
   g.stride[0] = 1;
   g.stride[1] = g.n[0];
   g.stride[2] = (long long)g.n[0] * g.n[1];
-  for (int d = 0; d < 3; ++d) {
-    g.plane[d] = g.npts / g.n[d];
-    const double dx = 2.0 * M_PI / g.n[d];
-    g.c1[d] = 8.0 / (12.0 * dx);
-    g.c2[d] = -1.0 / (12.0 * dx);
-    g.a0[d] = -30.0 / (12.0 * dx * dx);
-    g.a1[d] = 16.0 / (12.0 * dx * dx);
-    g.a2[d] = -1.0 / (12.0 * dx * dx);
-    g.inv12dx[d] = 1.0 / (12.0 * dx);
-  }
+  for (int d = 0; d < 3; ++d) g.plane[d] = g.npts / g.n[d];
+  set_stencils(g, 2);   // 4th-order scheme
   g.nlev = 3;
   Phys ph{};
   ph.gamma = gamma;

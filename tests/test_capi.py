@@ -46,6 +46,7 @@ int main(void) {
   printf("at_dns_info_t size %zu\n", sizeof(at_dns_info_t));
   F(at_dns_config_t, seed) F(at_dns_config_t, forcing) F(at_dns_config_t, f_seed)
   F(at_dns_config_t, precision) F(at_dns_config_t, stream) F(at_dns_config_t, kernel_path)
+  F(at_dns_config_t, order) F(at_dns_info_t, order)
   F(at_dns_stats_t, mom) F(at_dns_stats_t, min_p) F(at_dns_stats_t, unstable)
   F(at_dns_info_t, n_levels) F(at_dns_info_t, device_bytes) F(at_dns_info_t, kernels_per_step)
   F(at_dns_info_t, kernel_path) F(at_dns_info_t, tile)
@@ -77,11 +78,13 @@ def test_config_default(lib):
     assert list(cfg.n) == [32, 32, 32] and list(cfg.pes) == [1, 1, 1]
     assert cfg.gamma == 1.4 and cfg.prandtl == 0.7 and cfg.visc_exp == 0.76
     assert cfg.max_delay == 2 and cfg.comm_period == 3 and cfg.precision == at_dns.AT_DNS_P64
+    assert cfg.order == 4
 
 
 @pytest.mark.parametrize("field,value", [
     ("n", (4, 32, 32)), ("pes", (3, 1, 1)), ("pes", (8, 1, 1)), ("gamma", 1.0),
     ("max_delay", -1), ("comm_period", 0), ("precision", 7), ("prandtl", 0.0), ("kernel_path", 9),
+    ("order", 5), ("order", 8),
 ])
 def test_create_rejects_bad_config_without_gpu(lib, field, value):
     cfg = at_dns.at_dns_config_default()
@@ -95,6 +98,14 @@ def test_create_rejects_bad_config_without_gpu(lib, field, value):
     assert rc == at_dns.AT_DNS_E_INVALID_ARG
     assert h.value is None
     assert at_dns.at_dns_last_error(None) != ""
+
+
+@pytest.mark.parametrize("n,pes", [((6, 32, 32), (1, 1, 1)), ((36, 32, 32), (6, 1, 1))])
+def test_create_rejects_sixth_order_below_seven_points_without_gpu(lib, n, pes):
+    cfg = at_dns.make_config(n=n, pes=pes, order=6)
+    h = ctypes.c_void_p()
+    assert lib.at_dns_create(ctypes.byref(cfg), ctypes.byref(h)) == at_dns.AT_DNS_E_INVALID_ARG
+    assert "order + 1" in at_dns.at_dns_last_error(None)
 
 
 def test_null_arguments(lib):
