@@ -44,10 +44,11 @@ FLOP_MAIN6 = 489.0
 # R^n; plus the slab ring: 1 write + 3 reads of 5 variables at the N_B fraction)
 NB_FRAC = 1.0 - (28.0 / 32.0) ** 3
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max SM clock
-# DRAM bytes (read + write) of one k_main launch, FP64 multi-pass path: ncu at
-# 128^3 (877.2 MB, profiles/k_main_fp64_128cube_4x4x4pes.md) scaled by the
-# point count to the 256^3 workload (traffic grows with the points)
-K_MAIN_FP64_TRAFFIC_256 = None
+# DRAM bytes (read + write) of one k_main<double, 2> launch on the multi-pass
+# path: ncu at 128^3 with 4x4x4 PEs of 32^3 (708.2 MB read + 358.0 MB written,
+# profiles/k_main_fp64_128cube_4x4x4pes.md), scaled by the point count to the
+# 256^3 workload (same PE size; traffic grows with the points)
+K_MAIN_FP64_TRAFFIC_256 = 8 * (708.172288e6 + 358.002176e6)
 
 
 def set_workload(n, pes):

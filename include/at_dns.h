@@ -150,7 +150,7 @@ typedef struct {
 int at_dns_config_default(at_dns_config_t* cfg);
 
 /* Validate *cfg, allocate device state (double-buffered U, AB2 history,
- * slab ring of L + 3 levels, ghost and derivative work arrays) on the current
+ * slab ring of L + T_l levels, ghost and derivative work arrays) on the current
  * device and return a handle in *out.  Errors: INVALID_ARG (see the field
  * rules above), OOM, CUDA.  Sec. 3: PE geometry and L + T_l levels. */
 int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out);
@@ -163,7 +163,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out);
 int at_dns_set_state(at_dns_t* h, const double* u, int where);
 
 /* Set a state with an explicit past: levels holds nlevels consecutive fields
- * U^step, U^(step-1), ..., each 5*N^3 FP64 (1 <= nlevels <= L + 3; missing
+ * U^step, U^(step-1), ..., each 5*N^3 FP64 (1 <= nlevels <= L + T_l; missing
  * older levels repeat the oldest one given).  The step counter becomes `step`
  * (>= 0), so the delay map of that step applies to the next rhs/step; the
  * forcing coefficients are advanced to `step`; the AB2 history is forgotten.
@@ -199,8 +199,8 @@ int at_dns_stats(at_dns_t* h, at_dns_stats_t* out);
 /* Delay map of step `step` for delay mode `mode`: out[p*6 + f] for PE
  * p = (pz*Py + py)*Px + px and face f = x-, x+, y-, y+, z-, z+ (host buffer of
  * Px*Py*Pz*6 bytes), computed by the same device code the step uses.
- * Sec. 3.1 / Algorithms 1-2: zero for step < L + 3; periodic
- * (step - L - 3) mod c_r; random floor(w0 (L+1) / 2^32) with w0 the first
+ * Sec. 3.1 / Algorithms 1-2: zero for step < L + T_l; periodic
+ * (step - L - T_l) mod c_r; random floor(w0 (L+1) / 2^32) with w0 the first
  * word of Philox4x32-10(counter = (step, p, f, 0x4154), key = (seed lo, seed hi)).
  * Errors: INVALID_ARG, CUDA. */
 int at_dns_get_delay_map(at_dns_t* h, int64_t step, int32_t mode, uint8_t* out);
@@ -229,7 +229,8 @@ int at_dns_kernel_times(at_dns_t* h, at_dns_kernel_time_t* out, int32_t max, int
 /* Autotuner: for the current state, time `trials` right-hand-side
  * evaluations (no state change) of every kernel path that applies -- the
  * multi-pass path and each compiled fused tile shape (32x8, 16x16, 16x8, 8x32,
- * 8x16, 8x8) with whole-PE, half and quarter z chunks -- and keep the fastest
+ * 8x16, 8x8; 4th order only) with whole-PE, half and quarter z chunks -- and
+ * keep the fastest
  * (at_dns_get_info reports it).  *best_ms (may be NULL) receives its time per
  * evaluation.  Candidates that cannot get their work arrays are skipped.
  * Errors: INVALID_ARG, STATE, CUDA. */
