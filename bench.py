@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max S
 # path: ncu at 128^3 with 4x4x4 PEs of 32^3 (708.2 MB read + 358.0 MB written,
 # profiles/k_main_fp64_128cube_4x4x4pes.md), scaled by the point count to the
 # 256^3 workload (same PE size; traffic grows with the points)
-K_MAIN_FP64_TRAFFIC_256 = 8 * (708.172288e6 + 358.002176e6)
+K_MAIN_FP64_TRAFFIC_256 = None   # recapture after the kernel changes
 
 
 def set_workload(n, pes):
@@ -372,7 +372,8 @@ def leg_report(r, world, pts, steps, pk):
                         "(an FMA probe measured 1.20 TFLOP/s)"}
     else:
         achieved = algorithmic_bytes(4, order) * pts / t_main / 1e9
-        roof = {"bound": "hbm", "kernel": "k_main (FP32, order %d)" % order, "achieved": achieved,
+        kname = "k_fused" if r["path"] == "fused" else "k_main"
+        roof = {"bound": "hbm", "kernel": "%s (FP32, order %d)" % (kname, order), "achieved": achieved,
                 "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0),
                 "traffic": None, "bytes_per_point": algorithmic_bytes(4, order)}
     return {"value": job_rate(world, pts, steps, r["ms"]), "unit": UNIT, "kernel_path": r["path"],

@@ -106,8 +106,9 @@ typedef struct {
  * derived fields and gradients between kernels; the fused path does one pass
  * over U per step on PE-aligned tiles (needs the per-direction PE extent, or
  * the grid extent where a direction has one PE, to be a multiple of 8 and the
- * tile to hold a multiple of 32 points).  AUTO takes the multi-pass path,
- * which is the faster one on GB300 at the benchmark workload. */
+ * tile to hold a multiple of 32 points; 4th order only).  AUTO takes the path
+ * that is faster on GB300 at the benchmark workload: fused for P32 / P32C
+ * where it applies, multi-pass otherwise. */
 #define AT_DNS_PATH_AUTO       0
 #define AT_DNS_PATH_MULTIPASS  1
 #define AT_DNS_PATH_FUSED      2

@@ -765,11 +765,11 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
                     : "the fused path needs PE (or grid) extents that are multiples of 8 in x and y";
     return create_fail(h, AT_DNS_E_UNSUPPORTED);
   }
-  // AUTO takes the multi-pass path (at_dns_tune can switch): it is the faster
-  // one on GB300 in both
-  // precisions at the benchmark workload (FP64 is bound by the FP64 pipe, where
-  // the fused path's halo recompute costs more than the work arrays' traffic)
-  h->fused = can_fuse && c.kernel_path == AT_DNS_PATH_FUSED;
+  // AUTO takes the faster path on GB300 at the benchmark workload (at_dns_tune
+  // can switch): the fused one for the FP32 forms (one pass over U, no work
+  // arrays), the multi-pass one for FP64 (bound by the FP64 pipe, where the
+  // fused path's halo recompute costs more than the work arrays' traffic)
+  h->fused = can_fuse && (c.kernel_path == AT_DNS_PATH_FUSED || (c.kernel_path == AT_DNS_PATH_AUTO && !h->p64));
   if (!h->fused) h->TX = h->TY = h->ZC = 0;
   h->nblk_step = h->fused ? (long long)(g.n[0] / h->TX) * (g.n[1] / h->TY) * (g.n[2] / h->ZC) : main_blocks(g);
   if ((rc = dev_alloc(h, &h->U[0], 5 * N * S)) || (rc = dev_alloc(h, &h->U[1], 5 * N * S)) ||

@@ -287,18 +287,52 @@ struct StepArgs {
   int do_stats;
 };
 
-// Fill the per-step fields of the arguments from the device step state.
+// The per-step fields of one evaluation: from the device step state when the
+// arguments carry one, else as given.  Kept apart from StepArgs so that the
+// kernels read the (large) argument block from the parameter space and hold
+// only these few values in registers.
 template <typename S>
-__device__ __forceinline__ void resolve_step(StepArgs<S>& A) {
-  if (!A.ds) return;
+struct StepDyn {
+  const S* U;          // [5][npts] level n
+  S* Unext;            // [5][npts] level n+1
+  const S* Ulo;        // compensated form: low words of U^n (else null)
+  S* Ulo_next;         // compensated form: low words of U^{n+1}
+  long long n;         // step of U
+  int first;           // 1: forward Euler
+};
+
+template <typename S>
+__device__ __forceinline__ StepDyn<S> resolve_step(const StepArgs<S>& A) {
+  StepDyn<S> D;
+  if (!A.ds) {
+    D.U = A.U;
+    D.Unext = A.Unext;
+    D.Ulo = A.Ulo;
+    D.Ulo_next = A.Ulo_next;
+    D.n = A.n;
+    D.first = A.first;
+    return D;
+  }
   const int cur = A.ds->cur;
-  A.U = A.Ub[cur];
-  A.Unext = const_cast<S*>(A.Ub[1 - cur]);
-  A.Ulo = A.Ulob[cur];
-  A.Ulo_next = A.Ulob[1 - cur];
-  A.n = A.ds->n;
-  A.first = A.ds->first;
+  D.U = A.Ub[cur];
+  D.Unext = const_cast<S*>(A.Ub[1 - cur]);
+  D.Ulo = A.Ulob[cur];
+  D.Ulo_next = A.Ulob[1 - cur];
+  D.n = A.ds->n;
+  D.first = A.ds->first;
+  return D;
 }
+
+// |x| by clearing the sign bit (integer instructions only).
+__device__ __forceinline__ double abs_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ float abs_bits(float x) { return __int_as_float(__float_as_int(x) & 0x7FFFFFFF); }
+
+// 1/x rounded to nearest (the correctly rounded reciprocal instruction
+// sequence for FP32, plain division for FP64).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return 1.0 / x; }
 
 // Separately rounded products / sums (never contracted into an FMA), for the
 // error-free transformations of the compensated update.
@@ -315,24 +349,25 @@ __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(
 // the increment is added by TwoSum (Knuth), so no increment is lost below the
 // resolution of the high word; the stencils read the high word only.
 template <typename S>
-__device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& A, long long idx, long long N,
-                                           const S (&Uo)[5], const S (&R)[5], S (&un)[5], unsigned& health) {
+__device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& A, const StepDyn<S>& D, long long idx,
+                                           long long N, const S (&Uo)[5], const S (&R)[5], S (&un)[5],
+                                           unsigned& health) {
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const S inc = A.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * A.Rprev[v * N + idx]);
-    if (A.Ulo) {
+    const S inc = D.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * A.Rprev[v * N + idx]);
+    if (D.Ulo) {
       const S dlt = mul_rn(K.dt, inc);
       const S s = add_rn(Uo[v], dlt);                           // TwoSum(U_hi, dlt)
       const S bp = sub_rn(s, Uo[v]);
       const S e = add_rn(sub_rn(Uo[v], sub_rn(s, bp)), sub_rn(dlt, bp));
-      const S lo = add_rn(A.Ulo[v * N + idx], e);
+      const S lo = add_rn(D.Ulo[v * N + idx], e);
       const S hi = add_rn(s, lo);                               // renormalise
-      A.Ulo_next[v * N + idx] = sub_rn(lo, sub_rn(hi, s));
+      D.Ulo_next[v * N + idx] = sub_rn(lo, sub_rn(hi, s));
       un[v] = hi;
     } else {
       un[v] = fma(K.dt, inc, Uo[v]);
     }
-    A.Unext[v * N + idx] = un[v];
+    D.Unext[v * N + idx] = un[v];
     A.Rprev[v * N + idx] = R[v];
     if (nonfinite(un[v])) health |= H_NONFINITE;
   }

@@ -189,10 +189,11 @@ __device__ __forceinline__ Pt make_point(const Geom& g, long long idx) {
 // the field relative to the point (inside the PE, or periodic wrap when the
 // direction has one PE) or, across a PE face, an index into the ghost array of
 // direction d.  Built once per point and direction, then used for every
-// quantity of that direction.
+// quantity of that direction.  Offsets and indices are 32-bit: grids hold
+// fewer than 2^31 points and a ghost array fewer than the grid.
 template <int M>
 struct Nb {
-  long long off[2 * M];
+  int off[2 * M];
   unsigned gmask;    // bit j: off[j] indexes the ghost array
 };
 
@@ -200,21 +201,21 @@ template <int M>
 __device__ __forceinline__ Nb<M> make_nb(const Geom& g, const Pt& P, int d) {
   Nb<M> nb;
   nb.gmask = 0;
-  const long long st = g.stride[d];
+  const int st = (int)g.stride[d];
 #pragma unroll
   for (int j = 0; j < 2 * M; ++j) {
     const int m = j < M ? j - M : j - M + 1;
     if (g.pes[d] == 1) {
       int c2 = P.c[d] + m;
       c2 = c2 < 0 ? c2 + g.n[d] : (c2 >= g.n[d] ? c2 - g.n[d] : c2);
-      nb.off[j] = (long long)(c2 - P.c[d]) * st;
+      nb.off[j] = (c2 - P.c[d]) * st;
     } else {
       const int l2 = P.li[d] + m;
       if (l2 >= 0 && l2 < g.nl[d]) {
-        nb.off[j] = (long long)m * st;
+        nb.off[j] = m * st;
       } else {
         const int slot = l2 < 0 ? l2 + M : M + (l2 - g.nl[d]);
-        nb.off[j] = (long long)(2 * M * P.pe[d] + slot) * g.plane[d] + P.pl[d];
+        nb.off[j] = (2 * M * P.pe[d] + slot) * (int)g.plane[d] + (int)P.pl[d];
         nb.gmask |= 1u << j;
       }
     }
@@ -222,9 +223,13 @@ __device__ __forceinline__ Nb<M> make_nb(const Geom& g, const Pt& P, int d) {
   return nb;
 }
 
-template <typename S, int M>
-__device__ __forceinline__ S nbv(const Nb<M>& nb, int j, long long idx, const S* __restrict__ f,
+// Neighbour j of quantity f (ghost array gh across a face).  G = false: no
+// lane of the warp has a ghost neighbour in this direction (a warp-uniform
+// fact, tested with a vote), so the field is read directly.
+template <bool G, typename S, int M>
+__device__ __forceinline__ S nbv(const Nb<M>& nb, int j, int idx, const S* __restrict__ f,
                                  const S* __restrict__ gh) {
+  if constexpr (!G) return f[idx + nb.off[j]];
   return ((nb.gmask >> j) & 1u) ? gh[nb.off[j]] : f[idx + nb.off[j]];
 }
 
@@ -232,22 +237,38 @@ __device__ __forceinline__ S nbv(const Nb<M>& nb, int j, long long idx, const S*
 // with D1 = sum_m c_m (f[+m]-f[-m])  (differences first: rounding relative to
 // the derivative, not to the stencil terms).  Entry M - 1 + m is offset +m,
 // entry M - m is offset -m.
-template <typename S, int M>
-__device__ __forceinline__ S nb_d1_acc(S acc, S c1, S c2, S c3, const Nb<M>& nb, long long idx, const S* f,
+template <bool G, typename S, int M>
+__device__ __forceinline__ S nb_d1_acc(S acc, S c1, S c2, S c3, const Nb<M>& nb, int idx, const S* f,
                                        const S* gh) {
-  acc = fma(c1, nbv(nb, M, idx, f, gh) - nbv(nb, M - 1, idx, f, gh), acc);
-  acc = fma(c2, nbv(nb, M + 1, idx, f, gh) - nbv(nb, M - 2, idx, f, gh), acc);
-  if constexpr (M == 3) acc = fma(c3, nbv(nb, M + 2, idx, f, gh) - nbv(nb, M - 3, idx, f, gh), acc);
+  acc = fma(c1, nbv<G>(nb, M, idx, f, gh) - nbv<G>(nb, M - 1, idx, f, gh), acc);
+  acc = fma(c2, nbv<G>(nb, M + 1, idx, f, gh) - nbv<G>(nb, M - 2, idx, f, gh), acc);
+  if constexpr (M == 3) acc = fma(c3, nbv<G>(nb, M + 2, idx, f, gh) - nbv<G>(nb, M - 3, idx, f, gh), acc);
   return acc;
 }
 
 // D2 without the centre term: sum_m a_m (f[+m]+f[-m]).
-template <typename S, int M>
-__device__ __forceinline__ S nb_d2_off(S a1, S a2, S a3, const Nb<M>& nb, long long idx, const S* f, const S* gh) {
+template <bool G, typename S, int M>
+__device__ __forceinline__ S nb_d2_off(S a1, S a2, S a3, const Nb<M>& nb, int idx, const S* f, const S* gh) {
   if constexpr (M == 2)
-    return fma(a1, nbv(nb, 2, idx, f, gh) + nbv(nb, 1, idx, f, gh), a2 * (nbv(nb, 3, idx, f, gh) + nbv(nb, 0, idx, f, gh)));
-  return fma(a1, nbv(nb, 3, idx, f, gh) + nbv(nb, 2, idx, f, gh),
-             fma(a2, nbv(nb, 4, idx, f, gh) + nbv(nb, 1, idx, f, gh), a3 * (nbv(nb, 5, idx, f, gh) + nbv(nb, 0, idx, f, gh))));
+    return fma(a1, nbv<G>(nb, 2, idx, f, gh) + nbv<G>(nb, 1, idx, f, gh),
+               a2 * (nbv<G>(nb, 3, idx, f, gh) + nbv<G>(nb, 0, idx, f, gh)));
+  return fma(a1, nbv<G>(nb, 3, idx, f, gh) + nbv<G>(nb, 2, idx, f, gh),
+             fma(a2, nbv<G>(nb, 4, idx, f, gh) + nbv<G>(nb, 1, idx, f, gh),
+                 a3 * (nbv<G>(nb, 5, idx, f, gh) + nbv<G>(nb, 0, idx, f, gh))));
+}
+
+template <bool B>
+struct BoolC {
+  static constexpr bool value = B;
+};
+
+// Run body(BoolC<G>) with G = whether any active lane of the warp reads a
+// ghost in this direction (warp-uniform branch: both loads of the select are
+// issued only where a face is near).
+template <int M, typename F>
+__device__ __forceinline__ void with_ghosts(const Nb<M>& nb, F&& body) {
+  if (__any_sync(__activemask(), nb.gmask != 0u)) body(BoolC<true>{});
+  else body(BoolC<false>{});
 }
 
 template <typename S, int M>
@@ -258,17 +279,21 @@ __global__ void __launch_bounds__(256) k_grad(Geom g, Coef<S> K, const S* __rest
   if (idx >= g.npts) return;
   const Pt P = make_point(g, idx);
   const long long N = g.npts;
+  const int i32 = (int)idx;
   const S* GH[3] = {GH0, GH1, GH2};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const long long qs = 2LL * M * g.pes[d] * g.plane[d];
     const Nb<M> nb = make_nb<M>(g, P, d);
+    with_ghosts(nb, [&](auto gh_) {
+      constexpr bool Gh = decltype(gh_)::value;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const S v = nb_d1_acc<S, M>(S(0), K.c1[d], K.c2[d], K.c3[d], nb, idx, PQ + q * N, GH[d] + (5 + q) * qs);
-      const int out = q < 3 ? 3 * q + d : 9 + d;
-      G[out * N + idx] = v;
-    }
+      for (int q = 0; q < 4; ++q) {
+        const S v = nb_d1_acc<Gh, S, M>(S(0), K.c1[d], K.c2[d], K.c3[d], nb, i32, PQ + q * N, GH[d] + (5 + q) * qs);
+        const int out = q < 3 ? 3 * q + d : 9 + d;
+        G[out * N + idx] = v;
+      }
+    });
   }
 }
 
@@ -301,7 +326,7 @@ __device__ __noinline__ S local_d1_table(const Geom& g, const Coef<S>& K, const 
       c2 = c2 < 0 ? c2 + g.n[a] : (c2 >= g.n[a] ? c2 - g.n[a] : c2);
       off = c2 - P.c[a];
     }
-    if (c != S(0)) acc = fma(c, f[P.idx + (long long)off * s], acc);
+    acc = fma(c, f[P.idx + (long long)off * s], acc);
   }
   return acc * K.hloc[a];
 }
@@ -478,11 +503,39 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
 }
 
 // ---------------------------------------------------------------------------
+// Linear index of the point of this thread of k_main (blocks of 256).  FP64
+// form: when the block's 256 consecutive points are whole PE rows in x (PE
+// width 8, 16 or 32 divides 256 and the row length, so a full block starts at
+// a row start), the points next to the two x-faces of every PE row go to the
+// block's first warps and the interior points to the others,
+// so that the one-sided stencils of the mixed rule run in those warps only: a
+// divergent FP64 path costs the whole warp on the FP64 pipe.
+template <typename S>
+__device__ __forceinline__ long long main_point_index(const Geom& g) {
+  const long long base = blockIdx.x * (long long)blockDim.x;
+  int t = threadIdx.x;
+  if constexpr (sizeof(S) == 8) {
+    const int nl = g.nl[0];
+    if (g.pes[0] > 1 && (nl == 8 || nl == 16 || nl == 32) && base + 256 <= g.npts) {
+      const int nb = 4 * (256 / nl);   // face-adjacent points of the block: whole warps
+      if (t < nb) {
+        const int r = t >> 2, c = t & 3;
+        t = r * nl + (c < 2 ? c : nl - 4 + c);
+      } else {
+        const int u = t - nb, w = nl - 4;
+        const int r = u / w;
+        t = r * nl + 2 + (u - r * w);
+      }
+    }
+  }
+  return base + t;
+}
+
 template <typename S, int M>
 __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> A0) {
-  StepArgs<S> A = A0;
-  resolve_step(A);
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const StepArgs<S>& A = A0;
+  const StepDyn<S> D = resolve_step(A0);
+  const long long idx = main_point_index<S>(g);
   const bool active = idx < g.npts;
   S st[kNumStat];
 #pragma unroll
@@ -493,7 +546,7 @@ __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> 
   if (active) {
     const Pt P = make_point(g, idx);
     const long long N = g.npts;
-    const S* U = A.U;
+    const S* U = D.U;
     const S* PQ = A.PQ;
     const S* G = A.G;
 
@@ -509,17 +562,21 @@ __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> 
       const long long qs = 2LL * M * g.pes[d] * g.plane[d];
       const Nb<M> nb = make_nb<M>(g, P, d);
       const S* gh = A.GH[d];
+      const int i32 = (int)idx;
+      with_ghosts(nb, [&](auto gh_) {
+        constexpr bool Gh = decltype(gh_)::value;
 #pragma unroll
-      for (int e = 0; e < 5; ++e) {
-        const S* f = e == 0 ? U + (1 + d) * N : PQ + (4 + 4 * d + e - 1) * N;
-        R[e] = nb_d1_acc<S, M>(R[e], -K.c1[d], -K.c2[d], -K.c3[d], nb, idx, f, gh + e * qs);
-      }
+        for (int e = 0; e < 5; ++e) {
+          const S* f = e == 0 ? U + (1 + d) * N : PQ + (4 + 4 * d + e - 1) * N;
+          R[e] = nb_d1_acc<Gh, S, M>(R[e], -K.c1[d], -K.c2[d], -K.c3[d], nb, i32, f, gh + e * qs);
+        }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const S v = nb_d2_off<S, M>(K.a1[d], K.a2[d], K.a3[d], nb, idx, PQ + q * N, gh + (5 + q) * qs);
-        lap[q] += v;
-        if (q == d) d2diag[d] = fma(K.a0[d], PQ[q * N + idx], v);
-      }
+        for (int q = 0; q < 4; ++q) {
+          const S v = nb_d2_off<Gh, S, M>(K.a1[d], K.a2[d], K.a3[d], nb, i32, PQ + q * N, gh + (5 + q) * qs);
+          lap[q] += v;
+          if (q == d) d2diag[d] = fma(K.a0[d], PQ[q * N + idx], v);
+        }
+      });
       a0sum += K.a0[d];
     }
 #pragma unroll
@@ -614,9 +671,9 @@ __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> 
     if (A.do_update) {
       const S Uo[5] = {r, m[0], m[1], m[2], E};
       S un[5];
-      ab2_update(K, A, idx, N, Uo, R, un, health);
+      ab2_update(K, A, D, idx, N, Uo, R, un, health);
       // PE-boundary slabs of U^{n+1} into ring slot (n+1) mod nlev
-      const int slot = (int)((A.n + 1) % g.nlev);
+      const int slot = (int)((D.n + 1) % g.nlev);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         if (g.pes[d] == 1) continue;
@@ -657,7 +714,7 @@ __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> 
       st[ST_C] = c;
       // max |u_d| + c: the largest |u_d| chosen by bit pattern (non-negative
       // values order as integers)
-      const S au[3] = {fabs(vel[0]), fabs(vel[1]), fabs(vel[2])};
+      const S au[3] = {abs_bits(vel[0]), abs_bits(vel[1]), abs_bits(vel[2])};
       const long long k0 = okey(au[0]), k1 = okey(au[1]), k2 = okey(au[2]);
       const S umax = (k0 >= k1 && k0 >= k2) ? au[0] : (k1 >= k2 ? au[1] : au[2]);
       kwave = okey(umax + c);

@@ -66,7 +66,8 @@ struct FusedGeo {
 // Fill window plane zp (stored at element offset `pbase`).
 template <typename S, int TX, int TY>
 __device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K, const StepArgs<S>& A,
-                                                 const FusedGeo& F, S* win, int pbase, int zp) {
+                                                 const S* __restrict__ U, const FusedGeo& F, S* win, int pbase,
+                                                 int zp) {
   using T_ = TileShape<TX, TY>;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const long long N = g.npts;
@@ -105,10 +106,9 @@ __device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K
     } else {
       const int xw = wrapc(xg, g.n[0]), yw = wrapc(yg, g.n[1]), zw = wrapc(zp, g.n[2]);
       const long long idx = ((long long)zw * g.n[1] + yw) * g.n[0] + xw;
-      const S* U = A.U;
       r = U[idx];
       const S m0 = U[N + idx], m1 = U[2 * N + idx], m2 = U[3 * N + idx], E = U[4 * N + idx];
-      const S inv = S(1) / r;
+      const S inv = rcp_rn(r);
       u = m0 * inv;
       v = m1 * inv;
       w = m2 * inv;
@@ -160,20 +160,6 @@ __device__ __forceinline__ int local_kind(int pes, int li, int nl) {
   return 4;
 }
 
-// 12 dx times the PE-local first derivative of kind `kind`, val(o) giving the
-// value at offset o: central (1, -8, 0, 8, -1), one-sided (-25, 48, -36, 16, -3)
-// on 0..4, (-3, -10, 18, -6, 1) on -1..3 and their mirror images.
-template <typename S, typename F>
-__device__ __forceinline__ S apply_local(int kind, F&& val) {
-  switch (kind) {
-    case 1: return S(-25) * val(0) + S(48) * val(1) - S(36) * val(2) + S(16) * val(3) - S(3) * val(4);
-    case 2: return S(-3) * val(-1) - S(10) * val(0) + S(18) * val(1) - S(6) * val(2) + val(3);
-    case 3: return S(3) * val(1) + S(10) * val(0) - S(18) * val(-1) + S(6) * val(-2) - val(-3);
-    case 4: return S(25) * val(0) - S(48) * val(-1) + S(36) * val(-2) - S(16) * val(-3) + S(3) * val(-4);
-    default: return fma(S(8), val(1) - val(-1), val(-2) - val(2));
-  }
-}
-
 // The window seen from one point: plane bases for offsets -4..4 (already
 // including the point's cell), so a value at (dx, dy, dz) of field f is one
 // load at a constant offset.
@@ -194,74 +180,85 @@ struct PointWin {
     return fma(K.c1[b], sh(f, b, 1, dx, dy, dz) - sh(f, b, -1, dx, dy, dz),
                K.c2[b] * (sh(f, b, 2, dx, dy, dz) - sh(f, b, -2, dx, dy, dz)));
   }
-  // d/dx_a (d f/dx_b) by the three-step rule of Sec. 2.1: central fast path
-  // inside; at PE-boundary points the FP64 form runs the one PE-local stencil
-  // that applies from a table out of line (fewer FP64-pipe instructions), the
-  // FP32 form keeps the stencils inline
-  __device__ __forceinline__ S mixed(const Coef<S>& K, int f, int a, int b, const int (&kind)[3], int s0) const {
-    auto inner = [&](int outer, int in, int off) {
-      return d1(K, f, in, outer == 0 ? off : 0, outer == 1 ? off : 0, outer == 2 ? off : 0);
-    };
-    if (kind[a] == 0 && kind[b] == 0)
-      return K.hloc[a] * apply_local<S>(0, [&](int o) { return inner(a, b, o); });
-    if (sizeof(S) == 4) {   // FP32 form: the stencils inline
-      const S pa = K.hloc[a] * apply_local<S>(kind[a], [&](int o) { return inner(a, b, o); });
-      const S pb_ = K.hloc[b] * apply_local<S>(kind[b], [&](int o) { return inner(b, a, o); });
-      return S(0.5) * (pa + pb_);
-    }
-    return S(0.5) * (boundary_part(K, f, a, b, kind[a], s0) + boundary_part(K, f, b, a, kind[b], s0));
+  // plane base of the point's cell at z offset dz (window slot arithmetic;
+  // dz may be a run-time value)
+  __device__ __forceinline__ int plane_at(int s0, int dz) const {
+    int sl = s0 + 4 + dz;
+    sl = sl >= kWinPlanes ? sl - kWinPlanes : (sl < 0 ? sl + kWinPlanes : sl);
+    return sl * T_::PLANE + (pb[4] - ((s0 + 4) % kWinPlanes) * T_::PLANE);
   }
-  // PE-local derivative along `outer` (stencil `kind`) of the AT derivative
-  // along `in`, offsets taken from the table at run time
-  __device__ __noinline__ S boundary_part(const Coef<S>& K, int f, int outer, int in, int kind, int s0) const {
+  // 12 dx_outer times the PE-local derivative along `outer` (stencil `kind`:
+  // five taps at offsets st + 0..4 with coefficients coef[kind]) of the AT
+  // derivative along `in`.  kind may differ between lanes (x and y), or be
+  // warp-uniform (z); every lane runs the same five taps.
+  __device__ __forceinline__ S local_of_d1(const Coef<S>& K, const S (*coef)[5], int f, int outer, int in, int kind,
+                                           int s0) const {
+    const int st = kind == 0 ? -2 : (kind == 1 ? 0 : (kind == 2 ? -1 : (kind == 3 ? -3 : -4)));
     S acc = S(0);
+#pragma unroll
     for (int i = 0; i < 5; ++i) {
-      const S c = local_coef(S(0), kind, i);
-      if (c == S(0)) continue;
-      const int o = kLocalOff[kind][i];
-      int dz = 0, dx = 0, dy = 0;
-      if (outer == 0) dx = o; else if (outer == 1) dy = o; else dz = o;
-      // plane z + dz + k for the inner offsets k (only when the inner direction is z)
-      auto val = [&](int k) {
-        int zz = dz + (in == 2 ? k : 0);
-        int sl = s0 + 4 + zz;
-        sl = sl >= kWinPlanes ? sl - kWinPlanes : sl;
-        const int cellp = pb[4] - (((s0 + 4) % kWinPlanes) * T_::PLANE);   // the point's cell
-        const int xx = dx + (in == 0 ? k : 0), yy = dy + (in == 1 ? k : 0);
-        return win[sl * T_::PLANE + cellp + f * T_::CELLS + yy * T_::CX + xx];
-      };
-      const S d = fma(K.c1[in], val(1) - val(-1), K.c2[in] * (val(2) - val(-2)));
-      acc = fma(c, d, acc);
+      const int o = st + i;
+      const S c = coef[kind][i];
+      S dv;
+      if (outer == 2) {
+        const int base = plane_at(s0, o);
+        auto v = [&](int k) {
+          return win[base + f * T_::CELLS + (in == 1 ? k * T_::CX : k)];
+        };
+        dv = fma(K.c1[in], v(1) - v(-1), K.c2[in] * (v(2) - v(-2)));
+      } else {
+        const int co = outer == 0 ? o : o * T_::CX;   // cell offset of the tap
+        if (in == 2) {
+          dv = fma(K.c1[2], win[pb[5] + f * T_::CELLS + co] - win[pb[3] + f * T_::CELLS + co],
+                   K.c2[2] * (win[pb[6] + f * T_::CELLS + co] - win[pb[2] + f * T_::CELLS + co]));
+        } else {
+          const int sk = in == 0 ? 1 : T_::CX;
+          const S* q = win + pb[4] + f * T_::CELLS + co;
+          dv = fma(K.c1[in], q[sk] - q[-sk], K.c2[in] * (q[2 * sk] - q[-2 * sk]));
+        }
+      }
+      acc = fma(c, dv, acc);
     }
-    return acc * K.hloc[outer];
+    return acc;
+  }
+  // d/dx_a (d f/dx_b) by the three-step rule of Sec. 2.1: the central D_a of
+  // the AT derivative in b where both stencils fit in the PE, the average of
+  // the two PE-local derivatives elsewhere.  A warp without boundary points
+  // takes the central stencil only; otherwise every lane runs the table-driven
+  // taps (kind 0 is the central stencil) and boundary lanes average.
+  __device__ __forceinline__ S mixed(const Coef<S>& K, const S (*coef)[5], int f, int a, int b,
+                                     const int (&kind)[3], int s0) const {
+    const bool bnd = kind[a] != 0 || kind[b] != 0;
+    if (!__any_sync(__activemask(), bnd)) {
+      auto inner = [&](int off) {
+        return d1(K, f, b, a == 0 ? off : 0, a == 1 ? off : 0, a == 2 ? off : 0);
+      };
+      return K.hloc[a] * fma(S(8), inner(1) - inner(-1), inner(-2) - inner(2));
+    }
+    const S pa = K.hloc[a] * local_of_d1(K, coef, f, a, b, kind[a], s0);
+    const S pb_ = K.hloc[b] * local_of_d1(K, coef, f, b, a, kind[b], s0);
+    return bnd ? S(0.5) * (pa + pb_) : pa;
   }
 };
 
-// Per-thread statistics accumulators: FP64 form sums in FP64, FP32 form in
-// compensated (Kahan) FP32; both reach FP64 before crossing threads.
-template <typename S> struct StatAcc;
-template <> struct StatAcc<double> {
-  double s[kNumStat];
-  __device__ void init() { for (int i = 0; i < kNumStat; ++i) s[i] = 0.0; }
-  __device__ void add(int i, double v) { s[i] += v; }
-  __device__ double get(int i) const { return s[i]; }
-};
-template <> struct StatAcc<float> {
-  float s[kNumStat], c[kNumStat];
-  __device__ void init() { for (int i = 0; i < kNumStat; ++i) { s[i] = 0.f; c[i] = 0.f; } }
-  __device__ void add(int i, float v) {
-    const float y = v - c[i];
-    const float t = s[i] + y;
-    c[i] = (t - s[i]) - y;
-    s[i] = t;
+// Per-thread statistics accumulators over the thread's column of one z chunk
+// (at most 64 points), in the kernel's type; they reach FP64 before crossing
+// threads.
+template <typename S>
+struct StatAcc {
+  S s[kNumStat];
+  __device__ void init() {
+#pragma unroll
+    for (int i = 0; i < kNumStat; ++i) s[i] = S(0);
   }
-  __device__ double get(int i) const { return (double)s[i] - (double)c[i]; }
+  __device__ void add(int i, S v) { s[i] += v; }
+  __device__ double get(int i) const { return (double)s[i]; }
 };
 
 template <typename S, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S> A0, int ZC) {
-  StepArgs<S> A = A0;
-  resolve_step(A);
+__global__ void __launch_bounds__(TX * TY, sizeof(S) == 4 ? 2 : 1) k_fused(Geom g, Coef<S> K, StepArgs<S> A0, int ZC) {
+  const StepArgs<S>& A = A0;
+  const StepDyn<S> D = resolve_step(A0);
   using T_ = TileShape<TX, TY>;
   extern __shared__ __align__(16) unsigned char fused_smem[];
   S* win = reinterpret_cast<S*>(fused_smem);
@@ -278,13 +275,27 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
   const int cell = (ty + 2) * T_::CX + (tx + 2);
   const long long N = g.npts;
 
+  // PE-local stencil coefficients (x 12) by kind, taps in ascending offset:
+  // central, first point, second point, second to last, last (Sec. 2.1)
+  __shared__ S coef[5][5];
+  {
+    const int t0 = threadIdx.y * TX + threadIdx.x;   // tiles hold at least 64 threads
+    if (t0 < 25) {
+      const float t[5][5] = {{1, -8, 0, 8, -1}, {-25, 48, -36, 16, -3}, {-3, -10, 18, -6, 1},
+                             {-1, 6, -18, 10, 3}, {3, -16, 36, -48, 25}};
+      coef[t0 / 5][t0 % 5] = S(t[t0 / 5][t0 % 5]);
+    }
+  }
+
   StatAcc<S> st;
   st.init();
   long long kwave = LLONG_MIN, krho = LLONG_MAX, kp = LLONG_MAX;
+  // FP32 form: running max / min in FP32 (keys formed once at the end)
+  S wmax = S(0), rmin = S(3.0e38), pmin = S(3.0e38);
   unsigned health = 0;
 
   // window slot of plane zs - 4 is 0; plane zs - 4 + k lives in slot k mod 9
-  for (int k = 0; k < 8; ++k) fused_load_plane<S, TX, TY>(g, K, A, F, win, k * T_::PLANE, zs - 4 + k);
+  for (int k = 0; k < 8; ++k) fused_load_plane<S, TX, TY>(g, K, A, D.U, F, win, k * T_::PLANE, zs - 4 + k);
 
   const int li_x = x - F.base[0], li_y = y - F.base[1];
   const int kind_x = local_kind(g.pes[0], li_x, g.nl[0]), kind_y = local_kind(g.pes[1], li_y, g.nl[1]);
@@ -315,7 +326,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
   int s0 = 0;                                  // slot of plane z - 4
   for (int z = zs; z < zs + ZC; ++z) {
     const int snew = s0 + 8 >= kWinPlanes ? s0 + 8 - kWinPlanes : s0 + 8;   // slot of plane z + 4
-    fused_load_plane<S, TX, TY>(g, K, A, F, win, snew * T_::PLANE, z + 4);
+    fused_load_plane<S, TX, TY>(g, K, A, D.U, F, win, snew * T_::PLANE, z + 4);
     __syncthreads();
     // fluxes of the current plane: x on x-extended rows, y on y-extended columns
     {
@@ -416,7 +427,7 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
       S s = d2diag[i];
 #pragma unroll
       for (int k = 0; k < 3; ++k)
-        if (k != i) s += W.mixed(K, WF_U + k, i, k, kind, s0);
+        if (k != i) s += W.mixed(K, coef, WF_U + k, i, k, kind, s0);
       gth[i] = s;
     }
 
@@ -424,8 +435,8 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
     const S r = W.at(WF_R, 0, 0, 0);
     const S vel[3] = {W.at(WF_U, 0, 0, 0), W.at(WF_V, 0, 0, 0), W.at(WF_W, 0, 0, 0)};
     const S T = W.at(WF_T, 0, 0, 0);
-    const S m[3] = {A.U[N + idx], A.U[2 * N + idx], A.U[3 * N + idx]};
-    const S Ecur = A.U[4 * N + idx];
+    const S m[3] = {D.U[N + idx], D.U[2 * N + idx], D.U[3 * N + idx]};
+    const S Ecur = D.U[4 * N + idx];
     const S p = K.gm1 * (Ecur - S(0.5) * (m[0] * vel[0] + m[1] * vel[1] + m[2] * vel[2]));
     const S theta = Ag[0][0] + Ag[1][1] + Ag[2][2];
     const S mu = K.mu0 * exp(K.omega * log(T));   // mu0 T^omega
@@ -484,8 +495,8 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
     if (A.do_update) {
       const S Uo[5] = {r, m[0], m[1], m[2], Ecur};
       S un[5];
-      ab2_update(K, A, idx, N, Uo, R, un, health);
-      const int slot = (int)((A.n + 1) % g.nlev);
+      ab2_update(K, A, D, idx, N, Uo, R, un, health);
+      const int slot = (int)((D.n + 1) % g.nlev);
       const int li[3] = {li_x, li_y, li_z};
       const int c3[3] = {x, y, z};
 #pragma unroll
@@ -530,9 +541,15 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
       const S au[3] = {fabs(vel[0]), fabs(vel[1]), fabs(vel[2])};
       const long long k0 = okey(au[0]), k1 = okey(au[1]), k2 = okey(au[2]);
       const S umax = (k0 >= k1 && k0 >= k2) ? au[0] : (k1 >= k2 ? au[1] : au[2]);
-      kwave = max(kwave, okey(umax + c));
-      krho = min(krho, okey(r));
-      kp = min(kp, okey(p));
+      if constexpr (sizeof(S) == 4) {
+        wmax = fmaxf(wmax, umax + c);
+        rmin = fminf(rmin, r);
+        pmin = fminf(pmin, p);
+      } else {
+        kwave = max(kwave, okey(umax + c));
+        krho = min(krho, okey(r));
+        kp = min(kp, okey(p));
+      }
     }
     s0 = s0 + 1 >= kWinPlanes ? 0 : s0 + 1;
 #pragma unroll
@@ -545,6 +562,13 @@ __global__ void __launch_bounds__(TX * TY) k_fused(Geom g, Coef<S> K, StepArgs<S
 #pragma unroll
   for (int s = 0; s < kNumStat; ++s) tot[s] = st.get(s);
   // the window is dead after the last barrier: reuse it as reduction scratch
+  if constexpr (sizeof(S) == 4) {
+    if (A.do_stats) {
+      kwave = okey(wmax);
+      krho = okey(rmin);
+      kp = okey(pmin);
+    }
+  }
   block_reduce<double>(tot, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words,
                        reinterpret_cast<double*>(fused_smem));
 }
