@@ -26,10 +26,16 @@ Readings where the paper is silent (each listed in the design notes):
 
 * Non-dimensionalisation rho_0 = T_0 = c_0 = 1, so R = 1/gamma,
   p = rho T / gamma, c^2 = T, c_p = 1/(gamma-1).
-* Energy variable: total energy E = rho e + rho |u|^2 / 2 in divergence form;
-  the viscous work and conduction terms are expanded into first, second and
-  mixed derivatives (the paper's derivative machinery).
-* Viscosity: power law mu = mu0 T^omega (Sutherland constants are not given).
+* Energy variable: total energy E = rho e + rho |u|^2 / 2 in divergence form
+  (default); the viscous work and conduction terms are expanded into first,
+  second and mixed derivatives (the paper's derivative machinery).  Or the
+  paper's own internal-energy form, Eq. (ie): the fifth variable is rho e and
+  its right-hand side is -d(rho e u_j)/dx_j - p theta + sigma_ij S_ij
+  + d(k dT/dx_j)/dx_j.
+* Viscosity: power law mu = mu0 T^omega (default), or Sutherland's law
+  mu = mu0 T^(3/2) (1 + S) / (T + S) with S the Sutherland temperature over
+  the reference temperature (the paper names the law without constants;
+  S = 110.4 K / 300 K = 0.368 is taken).
 * Only stencil points outside the PE read delayed levels; the two sides of a
   shared face have independent delays; a direction with one PE has no faces.
 * Quantity extrapolated by the AT weights: the differentiated quantity
@@ -49,6 +55,8 @@ from .philox import philox4x32_10, split_seed
 from .stencils import Scheme
 
 SYNC, PERIODIC, RANDOM = 0, 1, 2
+ENERGY_TOTAL, ENERGY_INTERNAL = 0, 1
+VISC_POWER, VISC_SUTHERLAND = 0, 1
 DELAY_STREAM_TAG = 0x4154      # 4th Philox counter word of the delay stream
 FORCING_STREAM_TAG = 0x464F    # 4th Philox counter word of the forcing stream
 
@@ -71,6 +79,9 @@ class Config:
     f_tcorr: float = 1.0
     f_seed: int = 0
     order: int = 4                   # spatial order: 4 (T_l = 3) or 6 (T_l = 4)
+    energy_form: int = ENERGY_TOTAL  # fifth variable: E (total) or rho e (Eq. (ie))
+    visc_law: int = VISC_POWER       # mu0 T^omega, or Sutherland with S = suth_s
+    suth_s: float = 0.368
 
     @property
     def scheme(self):
@@ -155,11 +166,14 @@ def delay_map(cfg, step, mode):
 # primitive variables and differentiated quantities
 # --------------------------------------------------------------------------
 def primitives(cfg, U):
-    """rho, (u, v, w), p, T from conserved (rho, rho u, rho v, rho w, E)."""
+    """rho, (u, v, w), p, T from conserved (rho, rho u, rho v, rho w, E or rho e)."""
     rho = U[0]
     vel = [U[1] / rho, U[2] / rho, U[3] / rho]
-    ke = 0.5 * rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)
-    p = (cfg.gamma - 1.0) * (U[4] - ke)
+    if cfg.energy_form == ENERGY_INTERNAL:
+        p = (cfg.gamma - 1.0) * U[4]
+    else:
+        ke = 0.5 * rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)
+        p = (cfg.gamma - 1.0) * (U[4] - ke)
     T = cfg.gamma * p / rho
     return rho, vel, p, T
 
@@ -168,7 +182,7 @@ def quantity(cfg, U, name):
     """A differentiated quantity evaluated from one time level of U.
 
     'F{d}{e}': component e of the inviscid flux in direction d
-               (rho u_d, rho u_i u_d + p delta_id, (E + p) u_d);
+               (rho u_d, rho u_i u_d + p delta_id, (E + p) u_d or rho e u_d);
     'u0','u1','u2': velocity components; 'T': temperature.
     """
     rho, vel, p, T = primitives(cfg, U)
@@ -180,6 +194,8 @@ def quantity(cfg, U, name):
     if e == 0:
         return U[1 + d]
     if e == 4:
+        if cfg.energy_form == ENERGY_INTERNAL:
+            return U[4] * vel[d]
         return (U[4] + p) * vel[d]
     i = e - 1
     return U[1 + i] * vel[d] + (p if i == d else 0.0)
@@ -348,6 +364,20 @@ def forcing_field(cfg, fhat):
 
 
 # --------------------------------------------------------------------------
+# transport coefficients (Sec. 2)
+# --------------------------------------------------------------------------
+def viscosity(cfg, T):
+    """mu(T) and d mu / dT: power law mu0 T^omega, or Sutherland
+    mu0 T^(3/2) (1 + S) / (T + S)."""
+    if cfg.visc_law == VISC_SUTHERLAND:
+        S = cfg.suth_s
+        mu = cfg.mu0 * T ** 1.5 * (1.0 + S) / (T + S)
+        return mu, mu * (1.5 / T - 1.0 / (T + S))
+    mu = cfg.mu0 * T ** cfg.visc_exp
+    return mu, cfg.visc_exp * mu / T
+
+
+# --------------------------------------------------------------------------
 # right-hand side
 # --------------------------------------------------------------------------
 def rhs(cfg, levels, delays, fhat=None, return_aux=False):
@@ -395,8 +425,7 @@ def rhs(cfg, levels, delays, fhat=None, return_aux=False):
                 s = s + mixed_derivative(cfg, A[k][k], A[k][i], i, k)
         grad_theta.append(s)
 
-    mu = cfg.mu0 * T ** cfg.visc_exp
-    dmu_dT = cfg.visc_exp * mu / T
+    mu, dmu_dT = viscosity(cfg, T)
     dmu = [dmu_dT * dT[j] for j in range(3)]
     cp = 1.0 / (g - 1.0)
     kappa = mu * cp / cfg.prandtl
@@ -423,9 +452,13 @@ def rhs(cfg, levels, delays, fhat=None, return_aux=False):
     for i in range(3):
         R[1 + i] += V[i] + rho * f[i]
     sigS = sum(sigma[i][j] * S[i][j] for i in range(3) for j in range(3))
-    R[4] += (sum(vel[i] * V[i] for i in range(3)) + sigS + kappa * lap_T
-             + sum(dkappa[j] * dT[j] for j in range(3))
-             + sum(rho * f[i] * vel[i] for i in range(3)))
+    heat = kappa * lap_T + sum(dkappa[j] * dT[j] for j in range(3))
+    if cfg.energy_form == ENERGY_INTERNAL:
+        # Eq. (ie): -p theta + sigma_ij S_ij + d(k dT/dx_j)/dx_j
+        R[4] += -p * theta + sigS + heat
+    else:
+        R[4] += (sum(vel[i] * V[i] for i in range(3)) + sigS + heat
+                 + sum(rho * f[i] * vel[i] for i in range(3)))
     if not return_aux:
         return R
     aux = dict(rho=rho, vel=vel, p=p, T=T, A=A, theta=theta, sigS=sigS, f=f)

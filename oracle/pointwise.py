@@ -11,7 +11,8 @@ Sec. 2.1.  Pure Python loops, so it is used on tiny grids (as a brute-force
 check of the vectorised oracle) and on a few hundred sampled points of
 full-size grids (parity of the CUDA path).
 
-The right-hand side is assembled from the definitions of Sec. 2: the
+The right-hand side is assembled from the definitions of Sec. 2 (total- or
+internal-energy form, power-law or Sutherland viscosity): the
 inviscid flux divergence, the viscous stress divergence
 d sigma_ij/dx_j = mu (lap u_i + d theta/dx_i / 3)
                   + (d mu/dx_j)(du_i/dx_j + du_j/dx_i - 2/3 delta_ij theta),
@@ -19,6 +20,9 @@ the viscous work u_i d sigma_ij/dx_j + sigma_ij S_ij, the heat conduction
 kappa lap T + (d kappa/dx_j)(dT/dx_j) and the forcing rho f_i, rho f_i u_i.
 """
 import math
+
+ENERGY_INTERNAL = 1     # the fifth variable is rho e (Eq. (ie)); 0: total energy E
+VISC_SUTHERLAND = 1     # mu0 T^(3/2) (1 + S) / (T + S); 0: power law mu0 T^omega
 
 
 class PointOracle:
@@ -57,7 +61,10 @@ class PointOracle:
         g = self.cfg.gamma
         rho, mx, my, mz, E = self.U(l, pos)
         u = (mx / rho, my / rho, mz / rho)
-        p = (g - 1.0) * (E - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]))
+        if self.cfg.energy_form == ENERGY_INTERNAL:
+            p = (g - 1.0) * E
+        else:
+            p = (g - 1.0) * (E - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]))
         T = g * p / rho
         return rho, u, p, T
 
@@ -72,7 +79,7 @@ class PointOracle:
         if e == 0:
             return U[1 + d]
         if e == 4:
-            return (U[4] + p) * u[d]
+            return U[4] * u[d] if self.cfg.energy_form == ENERGY_INTERNAL else (U[4] + p) * u[d]
         i = e - 1
         return U[1 + i] * u[d] + (p if i == d else 0.0)
 
@@ -195,8 +202,14 @@ class PointOracle:
                 if k != i:
                     s += self.mixed(k, i, k, pos)
             dtheta.append(s)
-        mu = cfg.mu0 * T ** cfg.visc_exp
-        dmu = [cfg.visc_exp * mu / T * dT[j] for j in range(3)]
+        if cfg.visc_law == VISC_SUTHERLAND:
+            S = cfg.suth_s
+            mu = cfg.mu0 * T * math.sqrt(T) * (1.0 + S) / (T + S)
+            dmu_dT = mu * (1.5 / T - 1.0 / (T + S))
+        else:
+            mu = cfg.mu0 * T ** cfg.visc_exp
+            dmu_dT = cfg.visc_exp * mu / T
+        dmu = [dmu_dT * dT[j] for j in range(3)]
         cp = 1.0 / (g - 1.0)
         kappa = mu * cp / cfg.prandtl
         f = self.force(pos)
@@ -212,7 +225,9 @@ class PointOracle:
             for j in range(3):
                 sig = mu * (A[i][j] + A[j][i] - (2.0 / 3.0 if i == j else 0.0) * theta)
                 sigS += sig * 0.5 * (A[i][j] + A[j][i])
-        R[4] += (work + sigS + kappa * lapT
-                 + sum(dmu[j] * cp / cfg.prandtl * dT[j] for j in range(3))
-                 + sum(rho * f[i] * u[i] for i in range(3)))
+        heat = kappa * lapT + sum(dmu[j] * cp / cfg.prandtl * dT[j] for j in range(3))
+        if cfg.energy_form == ENERGY_INTERNAL:
+            R[4] += -p * theta + sigS + heat
+        else:
+            R[4] += work + sigS + heat + sum(rho * f[i] * u[i] for i in range(3))
         return R

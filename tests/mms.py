@@ -27,14 +27,23 @@ def fields():
 
 
 @functools.lru_cache(maxsize=None)
-def exact(gamma, prandtl, mu0, omega):
-    """Return (conserved(X, Y, Z, tt), rhs(X, Y, Z, tt)) numpy callables."""
+def exact(gamma, prandtl, mu0, omega, internal=False, sutherland=None):
+    """Return (conserved(X, Y, Z, tt), rhs(X, Y, Z, tt)) numpy callables.
+
+    internal: the fifth variable is rho e with the paper's Eq. (ie),
+    d(rho e)/dt + d(rho e u_j)/dx_j = -p du_j/dx_j + d(k dT/dx_j)/dx_j
+    + sigma_ij S_ij; else total energy.  sutherland = S: Sutherland's law
+    mu0 T^(3/2) (1 + S) / (T + S) instead of the power law."""
     g = sp.nsimplify(gamma)
     rho, vel, T = fields()
     X = (x, y, z)
     p = rho * T / g
     E = p / (g - 1) + rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2) / 2
-    mu = sp.nsimplify(mu0) * T ** sp.nsimplify(omega)
+    if sutherland is None:
+        mu = sp.nsimplify(mu0) * T ** sp.nsimplify(omega)
+    else:
+        S = sp.nsimplify(sutherland)
+        mu = sp.nsimplify(mu0) * T ** sp.Rational(3, 2) * (1 + S) / (T + S)
     kap = mu / (g - 1) / sp.nsimplify(prandtl)
     dudx = [[sp.diff(vel[i], X[j]) for j in range(3)] for i in range(3)]
     theta = dudx[0][0] + dudx[1][1] + dudx[2][2]
@@ -45,10 +54,18 @@ def exact(gamma, prandtl, mu0, omega):
     for i in range(3):
         R[1 + i] = sum(-sp.diff(rho * vel[i] * vel[j] + (p if i == j else 0), X[j])
                        + sp.diff(sigma[i][j], X[j]) for j in range(3))
-    R[4] = sum(-sp.diff((E + p) * vel[j], X[j])
-               + sp.diff(sum(vel[i] * sigma[i][j] for i in range(3)), X[j])
-               + sp.diff(kap * sp.diff(T, X[j]), X[j]) for j in range(3))
-    cons = [rho, rho * vel[0], rho * vel[1], rho * vel[2], E]
+    if internal:
+        rhoe = p / (g - 1)
+        R[4] = sum(-sp.diff(rhoe * vel[j], X[j]) - p * dudx[j][j]
+                   + sp.diff(kap * sp.diff(T, X[j]), X[j]) for j in range(3)) \
+            + sum(sigma[i][j] * (dudx[i][j] + dudx[j][i]) / 2 for i in range(3) for j in range(3))
+        last = rhoe
+    else:
+        R[4] = sum(-sp.diff((E + p) * vel[j], X[j])
+                   + sp.diff(sum(vel[i] * sigma[i][j] for i in range(3)), X[j])
+                   + sp.diff(kap * sp.diff(T, X[j]), X[j]) for j in range(3))
+        last = E
+    cons = [rho, rho * vel[0], rho * vel[1], rho * vel[2], last]
     fc = sp.lambdify((x, y, z, t), cons, "numpy")
     fr = sp.lambdify((x, y, z, t), R, "numpy")
     return fc, fr
