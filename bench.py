@@ -196,10 +196,10 @@ def workload_config(world):
             "l2": "working set %.1f GB >> 129 MB L2; no flush needed" % (N ** 3 * 5 * 8 * 12 / 1e9)}
 
 
-def make_solver(at_dns, precision, stream, mu0, path="auto", order=4):
+def make_solver(at_dns, precision, stream, mu0, path="auto", order=4, **kw):
     return at_dns.Solver(n=(N, N, N), pes=(PES, PES, PES), precision=precision, stream=stream, path=path,
                          gamma=1.4, prandtl=0.7, visc_exp=0.76, mu0=mu0, cfl=CFL_AT, dt=0.0,
-                         max_delay=L, seed=SEED, stats_every=1, order=order)
+                         max_delay=L, seed=SEED, stats_every=1, order=order, **kw)
 
 
 def timed_steps(s, stream, steps, warmup, torch, profile=False):
@@ -240,6 +240,8 @@ def main():
     ap.add_argument("--path", default="auto", choices=["auto", "multipass", "fused"])
     ap.add_argument("--order", default="both", choices=["both", "4", "6"],
                     help="spatial order of the AT scheme (4: headline; 6: Table B (1,6)/(2,6))")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the internal-energy / Sutherland leg")
     args = ap.parse_args()
     set_workload(args.grid, args.pes)
     args.warmup = max(args.warmup, 3)
@@ -309,6 +311,21 @@ def main():
                           "steps": e2e_steps}
         s.close()
 
+    # the paper's own internal-energy form (Eq. (ie)) with Sutherland viscosity,
+    # FP64, same workload: its step time beside the headline form's
+    if not args.no_variants and "p64" in res:
+        s = make_solver(at_dns, "p64", stream.cuda_stream, mu0, "auto", 4, energy_form=at_dns.AT_DNS_ENERGY_INTERNAL,
+                        visc_law=at_dns.AT_DNS_VISC_SUTHERLAND)
+        Ui = U0.copy()
+        rho = U0[0]
+        Ui[4] = U0[4] - 0.5 * (U0[1] ** 2 + U0[2] ** 2 + U0[3] ** 2) / rho   # rho e
+        s.set_state(Ui)
+        s.step(at_dns.at_dns_get_info(s.h).n_levels + 1, "random")
+        ms, kt = timed_steps(s, stream, args.steps, args.warmup, torch, profile=False)
+        ms = max_over_ranks(ms, pg, "cuda")
+        res["variant"] = {"ms": ms}
+        s.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, el = oracle_rate(3, 1)
@@ -338,7 +355,12 @@ def main():
         "kernel_path": head["path"],
         "order": head["order"],
     }
-    rep = {k: leg_report(r, world, pts, args.steps, pk) for k, r in res.items() if k != "e2e"}
+    rep = {k: leg_report(r, world, pts, args.steps, pk) for k, r in res.items() if k not in ("e2e", "variant")}
+    if "variant" in res:
+        line["variant_rhoe_sutherland"] = {
+            "value": job_rate(world, pts, args.steps, res["variant"]["ms"]), "unit": UNIT, "dtype": "f64",
+            "ms_per_step": res["variant"]["ms"] / args.steps,
+            "workload": "the headline workload with the internal-energy form (Eq. (ie)) and Sutherland viscosity"}
     line["roofline"] = rep[[k for k in res if res[k] is head][0]]["roofline"]
     if p32 and p32 is not head:
         blk = rep["p32"]

@@ -22,11 +22,13 @@
  *   - large-scale solenoidal forcing on |kappa| <= kappa_f: Sec. 4.2.
  *
  * Units: rho_0 = T_0 = c_0 = 1, so p = rho T / gamma, c^2 = T and
- * c_p = 1/(gamma-1).  Viscosity mu = mu0 T^visc_exp, conductivity
+ * c_p = 1/(gamma-1).  Viscosity mu = mu0 T^visc_exp (power law, default) or
+ * Sutherland's law mu0 T^(3/2) (1 + S) / (T + S); conductivity
  * k = mu c_p / Pr.  The box is (2 pi)^3, dx_d = 2 pi / n[d].
  *
  * Field layout (every state array crossing this ABI): FP64, structure of
- * arrays [5][n[2]][n[1]][n[0]] -- variable (rho, rho u, rho v, rho w, E),
+ * arrays [5][n[2]][n[1]][n[0]] -- variable (rho, rho u, rho v, rho w, E)
+ * (with energy_form = AT_DNS_ENERGY_INTERNAL the fifth variable is rho e),
  * then z, y, x with x fastest -- i.e. 5 * n0 * n1 * n2 doubles.
  *
  * Ownership: the library owns every device allocation it makes (released by
@@ -69,6 +71,14 @@ extern "C" {
 #define AT_DNS_P32C 2        /* as P32, but the state is carried as FP32 hi + lo words and
                                 updated by TwoSum (compensated, ~48-bit accumulation) */
 
+/* energy forms (Sec. 2) */
+#define AT_DNS_ENERGY_TOTAL     0   /* fifth variable E = rho e + rho|u|^2/2, divergence form */
+#define AT_DNS_ENERGY_INTERNAL  1   /* fifth variable rho e, Eq. (ie): source -p theta + sigma S + conduction */
+
+/* viscosity laws (Sec. 2) */
+#define AT_DNS_VISC_POWER       0   /* mu0 T^visc_exp */
+#define AT_DNS_VISC_SUTHERLAND  1   /* mu0 T^(3/2) (1 + S) / (T + S), S = sutherland_s */
+
 /* pointer locations */
 #define AT_DNS_HOST    0
 #define AT_DNS_DEVICE  1
@@ -100,6 +110,10 @@ typedef struct {
   int32_t  kernel_path;  /* AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS or AT_DNS_PATH_FUSED */
   int32_t  order;        /* spatial order: 4 (Table B (1,4)/(2,4), T_l = 3, default) or
                             6 (Table B (1,6)/(2,6), T_l = 4; multi-pass path only)      */
+  int32_t  energy_form;  /* AT_DNS_ENERGY_TOTAL (default) or AT_DNS_ENERGY_INTERNAL     */
+  int32_t  visc_law;     /* AT_DNS_VISC_POWER (default) or AT_DNS_VISC_SUTHERLAND        */
+  double   sutherland_s; /* S, Sutherland temperature / reference temperature (0.368:
+                            110.4 K over 300 K; the paper gives no constants)           */
 } at_dns_config_t;
 
 /* kernel paths (same results up to rounding): the multi-pass path stores

@@ -26,6 +26,8 @@ AT_DNS_SYNC, AT_DNS_PERIODIC, AT_DNS_RANDOM = 0, 1, 2
 AT_DNS_P64, AT_DNS_P32, AT_DNS_P32C = 0, 1, 2
 AT_DNS_HOST, AT_DNS_DEVICE = 0, 1
 AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS, AT_DNS_PATH_FUSED = 0, 1, 2
+AT_DNS_ENERGY_TOTAL, AT_DNS_ENERGY_INTERNAL = 0, 1
+AT_DNS_VISC_POWER, AT_DNS_VISC_SUTHERLAND = 0, 1
 PATHS = {"auto": AT_DNS_PATH_AUTO, "multipass": AT_DNS_PATH_MULTIPASS, "fused": AT_DNS_PATH_FUSED}
 
 MODES = {"sync": AT_DNS_SYNC, "periodic": AT_DNS_PERIODIC, "random": AT_DNS_RANDOM}
@@ -42,6 +44,7 @@ class at_dns_config_t(ctypes.Structure):
         ("f_tcorr", ctypes.c_double), ("f_seed", ctypes.c_uint64),
         ("precision", ctypes.c_int32), ("stats_every", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("kernel_path", ctypes.c_int32), ("order", ctypes.c_int32),
+        ("energy_form", ctypes.c_int32), ("visc_law", ctypes.c_int32), ("sutherland_s", ctypes.c_double),
     ]
 
 

@@ -157,7 +157,8 @@ __global__ void k_wave(Geom g, Phys ph, const double* __restrict__ U, unsigned l
     const long long N = g.npts;
     const double r = U[idx], inv = 1.0 / r;
     const double u[3] = {U[N + idx] * inv, U[2 * N + idx] * inv, U[3 * N + idx] * inv};
-    const double p = ph.gm1 * (U[4 * N + idx] - 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+    const double p = ph.eform ? ph.gm1 * U[4 * N + idx]
+                              : ph.gm1 * (U[4 * N + idx] - 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
     const double c = sqrt(ph.gamma * p * inv);
     for (int d = 0; d < 3; ++d) s = fmax(s, (fabs(u[d]) + c) * g.inv_dx[d]);
   }
@@ -690,6 +691,9 @@ int at_dns_config_default(at_dns_config_t* c) {
   c->stats_every = 1;
   c->stream = nullptr;
   c->order = 4;
+  c->energy_form = AT_DNS_ENERGY_TOTAL;
+  c->visc_law = AT_DNS_VISC_POWER;
+  c->sutherland_s = 0.368;
   return AT_DNS_OK;
 }
 
@@ -724,6 +728,9 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     else if (c.forcing && !(c.f_tcorr > 0)) bad = "f_tcorr must be > 0";
     else if (c.stats_every != 0 && c.stats_every != 1) bad = "stats_every must be 0 or 1";
     else if (c.kernel_path < 0 || c.kernel_path > 2) bad = "unknown kernel_path";
+    else if (c.energy_form != AT_DNS_ENERGY_TOTAL && c.energy_form != AT_DNS_ENERGY_INTERNAL) bad = "unknown energy_form";
+    else if (c.visc_law != AT_DNS_VISC_POWER && c.visc_law != AT_DNS_VISC_SUTHERLAND) bad = "unknown visc_law";
+    else if (c.visc_law == AT_DNS_VISC_SUTHERLAND && !(c.sutherland_s > 0)) bad = "sutherland_s must be > 0";
   }
   if (bad.empty() && (long long)c.n[0] * c.n[1] * c.n[2] >= (1LL << 31)) bad = "grids must hold fewer than 2^31 points";
   if (!bad.empty()) { g_create_error = bad; return AT_DNS_E_INVALID_ARG; }
@@ -752,6 +759,9 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   ph.gamma = c.gamma;
   ph.gm1 = c.gamma - 1.0;
   ph.prandtl = c.prandtl;
+  ph.eform = c.energy_form;
+  ph.vlaw = c.visc_law;
+  ph.suth_s = c.sutherland_s;
   ph.mu0 = c.mu0;
   ph.omega = c.visc_exp;
   ph.cp_over_pr = 1.0 / ((c.gamma - 1.0) * c.prandtl);

@@ -75,6 +75,9 @@ inline void set_stencils(Geom& g, int M) {
 
 struct Phys {
   double gamma, gm1, prandtl, mu0, omega, cp_over_pr;
+  int eform;         // 0: fifth variable E (total energy); 1: rho e (Eq. (ie))
+  int vlaw;          // 0: mu0 T^omega; 1: Sutherland mu0 T^(3/2) (1 + S) / (T + S)
+  double suth_s;     // S (Sutherland temperature over the reference temperature)
 };
 
 // Stencil coefficients and physical constants in the kernel's scalar type,
@@ -88,6 +91,8 @@ struct Coef {
   S gamma, gm1, mu0, omega, cp_over_pr;
   S inv_gamma;
   S dt;
+  int eform, vlaw;                // energy form and viscosity law (Phys)
+  S suth_s, suth_c;               // Sutherland S and mu0 (1 + S)
 };
 
 template <typename S>
@@ -110,6 +115,10 @@ inline Coef<S> make_coef(const Geom& g, const Phys& ph, double dt) {
   c.cp_over_pr = (S)ph.cp_over_pr;
   c.inv_gamma = (S)(1.0 / ph.gamma);
   c.dt = (S)dt;
+  c.eform = ph.eform;
+  c.vlaw = ph.vlaw;
+  c.suth_s = (S)ph.suth_s;
+  c.suth_c = (S)(ph.mu0 * (1.0 + ph.suth_s));
   return c;
 }
 
@@ -321,6 +330,27 @@ __device__ __forceinline__ StepDyn<S> resolve_step(const StepArgs<S>& A) {
   D.n = A.ds->n;
   D.first = A.ds->first;
   return D;
+}
+
+// Pressure from the conserved variables of one point: (gamma-1)(E - rho|u|^2/2)
+// in the total-energy form, (gamma-1) rho e in the internal-energy form.
+template <typename S>
+__device__ __forceinline__ S pressure(const Coef<S>& K, S m0, S m1, S m2, S u, S v, S w, S E) {
+  return K.eform ? K.gm1 * E : K.gm1 * (E - S(0.5) * (m0 * u + m1 * v + m2 * w));
+}
+
+// Viscosity and its temperature derivative (Sec. 2): power law mu0 T^omega,
+// or Sutherland mu0 T^(3/2) (1 + S) / (T + S).
+template <typename S>
+__device__ __forceinline__ void viscosity(const Coef<S>& K, S T, S& mu, S& dmudT) {
+  if (K.vlaw) {
+    const S inv = S(1) / (T + K.suth_s);
+    mu = K.suth_c * T * sqrt(T) * inv;
+    dmudT = mu * (S(1.5) / T - inv);
+  } else {
+    mu = K.mu0 * exp(K.omega * log(T));   // mu0 T^omega
+    dmudT = K.omega * mu / T;
+  }
 }
 
 // |x| by clearing the sign bit (integer instructions only).

@@ -36,9 +36,9 @@ __global__ void __launch_bounds__(256) k_prim(Geom g, Coef<S> K, const S* __rest
   const S r = U[idx], m0 = U[N + idx], m1 = U[2 * N + idx], m2 = U[3 * N + idx], E = U[4 * N + idx];
   const S inv = S(1) / r;
   const S u = m0 * inv, v = m1 * inv, w = m2 * inv;
-  const S p = K.gm1 * (E - S(0.5) * (m0 * u + m1 * v + m2 * w));
+  const S p = pressure(K, m0, m1, m2, u, v, w, E);
   const S T = K.gamma * p * inv;
-  const S H = E + p;
+  const S H = K.eform ? E : E + p;   // fifth flux = H u_d
   PQ[0 * N + idx] = u;
   PQ[1 * N + idx] = v;
   PQ[2 * N + idx] = w;
@@ -63,14 +63,14 @@ template <typename S>
 __device__ __forceinline__ void ghost_quantities(const Coef<S>& K, int d, const S* Uv, S* q) {
   const S r = Uv[0], inv = S(1) / r;
   const S vel[3] = {Uv[1] * inv, Uv[2] * inv, Uv[3] * inv};
-  const S p = K.gm1 * (Uv[4] - S(0.5) * (Uv[1] * vel[0] + Uv[2] * vel[1] + Uv[3] * vel[2]));
+  const S p = pressure(K, Uv[1], Uv[2], Uv[3], vel[0], vel[1], vel[2], Uv[4]);
   const S T = K.gamma * p * inv;
   const S ud = vel[d];
   q[0] = Uv[1 + d];
   q[1] = Uv[1] * ud + (d == 0 ? p : S(0));
   q[2] = Uv[2] * ud + (d == 1 ? p : S(0));
   q[3] = Uv[3] * ud + (d == 2 ? p : S(0));
-  q[4] = (Uv[4] + p) * ud;
+  q[4] = (K.eform ? Uv[4] : Uv[4] + p) * ud;
   q[5] = vel[0];
   q[6] = vel[1];
   q[7] = vel[2];
@@ -607,10 +607,10 @@ __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> 
     const S E = U[4 * N + idx];
     const S vel[3] = {PQ[idx], PQ[N + idx], PQ[2 * N + idx]};
     const S T = PQ[3 * N + idx];
-    const S p = K.gm1 * (E - S(0.5) * (m[0] * vel[0] + m[1] * vel[1] + m[2] * vel[2]));
+    const S p = pressure(K, m[0], m[1], m[2], vel[0], vel[1], vel[2], E);
     const S theta = Ag[0][0] + Ag[1][1] + Ag[2][2];
-    const S mu = K.mu0 * exp(K.omega * log(T));   // mu0 T^omega
-    const S dmudT = K.omega * mu / T;
+    S mu, dmudT;
+    viscosity(K, T, mu, dmudT);
     const S kappa = mu * K.cp_over_pr;
     S dmu[3];
 #pragma unroll
@@ -657,9 +657,12 @@ __global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> 
       R[1 + i] += fma(r, fo[i], V);
       work = fma(vel[i], V, work);
     }
-    S tail = fma(kappa, lap[3], sigS + work);
-    tail = fma(K.cp_over_pr, fma(dmu[0], dT[0], fma(dmu[1], dT[1], dmu[2] * dT[2])), tail);
-    R[4] += fma(r, fma(fo[0], vel[0], fma(fo[1], vel[1], fo[2] * vel[2])), tail);
+    // conduction k lap T + grad k . grad T, then the form's energy sources:
+    // total E: viscous work u_i V_i + sigma S + forcing power; rho e (Eq. (ie)):
+    // -p theta + sigma S
+    const S heat = fma(K.cp_over_pr, fma(dmu[0], dT[0], fma(dmu[1], dT[1], dmu[2] * dT[2])), kappa * lap[3]);
+    if (K.eform) R[4] += fma(-p, theta, sigS + heat);
+    else R[4] += fma(r, fma(fo[0], vel[0], fma(fo[1], vel[1], fo[2] * vel[2])), sigS + work + heat);
 
     // health: rho <= 0, p <= 0, non-finite R (bit tests)
     if (nonpositive(r)) health |= H_RHO;

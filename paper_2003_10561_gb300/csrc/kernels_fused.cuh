@@ -2,7 +2,8 @@
 //
 // A CTA owns a TX x TY tile of one PE in x and y and marches in z through a
 // chunk of ZC planes of one PE.  A shared-memory window holds nine planes
-// (z-4 .. z+4) of six per-point fields -- u, v, w, T, rho, H = E + p -- on the
+// (z-4 .. z+4) of six per-point fields -- u, v, w, T, rho and H, the quantity
+// whose product with u_d is the fifth flux (E + p, or rho e) -- on the
 // tile plus a two-cell halo in x and y.  Halo cells beyond a PE face hold the
 // AT ghost values of that direction (Table B extrapolation done by k_ghost),
 // planes beyond a PE z-face hold the z ghosts, so every stencil of Sec. 2.1 is
@@ -112,9 +113,9 @@ __device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K
       u = m0 * inv;
       v = m1 * inv;
       w = m2 * inv;
-      const S p = K.gm1 * (E - S(0.5) * (m0 * u + m1 * v + m2 * w));
+      const S p = pressure(K, m0, m1, m2, u, v, w, E);
       T = K.gamma * p * inv;
-      H = E + p;
+      H = K.eform ? E : E + p;
     }
     if (gh) {
       u = gh[5 * qs + gi];
@@ -437,10 +438,10 @@ __global__ void __launch_bounds__(TX * TY, sizeof(S) == 4 ? 2 : 1) k_fused(Geom 
     const S T = W.at(WF_T, 0, 0, 0);
     const S m[3] = {D.U[N + idx], D.U[2 * N + idx], D.U[3 * N + idx]};
     const S Ecur = D.U[4 * N + idx];
-    const S p = K.gm1 * (Ecur - S(0.5) * (m[0] * vel[0] + m[1] * vel[1] + m[2] * vel[2]));
+    const S p = pressure(K, m[0], m[1], m[2], vel[0], vel[1], vel[2], Ecur);
     const S theta = Ag[0][0] + Ag[1][1] + Ag[2][2];
-    const S mu = K.mu0 * exp(K.omega * log(T));   // mu0 T^omega
-    const S dmudT = K.omega * mu / T;
+    S mu, dmudT;
+    viscosity(K, T, mu, dmudT);
     const S kappa = mu * K.cp_over_pr;
     S dmu[3];
 #pragma unroll
@@ -482,9 +483,9 @@ __global__ void __launch_bounds__(TX * TY, sizeof(S) == 4 ? 2 : 1) k_fused(Geom 
       R[1 + i] += fma(r, fo[i], V);
       work = fma(vel[i], V, work);
     }
-    S tail = fma(kappa, lap[3], sigS + work);
-    tail = fma(K.cp_over_pr, fma(dmu[0], dT[0], fma(dmu[1], dT[1], dmu[2] * dT[2])), tail);
-    R[4] += fma(r, fma(fo[0], vel[0], fma(fo[1], vel[1], fo[2] * vel[2])), tail);
+    const S heat = fma(K.cp_over_pr, fma(dmu[0], dT[0], fma(dmu[1], dT[1], dmu[2] * dT[2])), kappa * lap[3]);
+    if (K.eform) R[4] += fma(-p, theta, sigS + heat);
+    else R[4] += fma(r, fma(fo[0], vel[0], fma(fo[1], vel[1], fo[2] * vel[2])), sigS + work + heat);
 
     if (nonpositive(r)) health |= H_RHO;
     if (nonpositive(p)) health |= H_P;

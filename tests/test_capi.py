@@ -47,6 +47,7 @@ int main(void) {
   F(at_dns_config_t, seed) F(at_dns_config_t, forcing) F(at_dns_config_t, f_seed)
   F(at_dns_config_t, precision) F(at_dns_config_t, stream) F(at_dns_config_t, kernel_path)
   F(at_dns_config_t, order) F(at_dns_info_t, order)
+  F(at_dns_config_t, energy_form) F(at_dns_config_t, visc_law) F(at_dns_config_t, sutherland_s)
   F(at_dns_stats_t, mom) F(at_dns_stats_t, min_p) F(at_dns_stats_t, unstable)
   F(at_dns_info_t, n_levels) F(at_dns_info_t, device_bytes) F(at_dns_info_t, kernels_per_step)
   F(at_dns_info_t, kernel_path) F(at_dns_info_t, tile)
@@ -78,16 +79,19 @@ def test_config_default(lib):
     assert list(cfg.n) == [32, 32, 32] and list(cfg.pes) == [1, 1, 1]
     assert cfg.gamma == 1.4 and cfg.prandtl == 0.7 and cfg.visc_exp == 0.76
     assert cfg.max_delay == 2 and cfg.comm_period == 3 and cfg.precision == at_dns.AT_DNS_P64
-    assert cfg.order == 4
+    assert cfg.order == 4 and cfg.energy_form == at_dns.AT_DNS_ENERGY_TOTAL
+    assert cfg.visc_law == at_dns.AT_DNS_VISC_POWER and cfg.sutherland_s == 0.368
 
 
 @pytest.mark.parametrize("field,value", [
     ("n", (4, 32, 32)), ("pes", (3, 1, 1)), ("pes", (8, 1, 1)), ("gamma", 1.0),
     ("max_delay", -1), ("comm_period", 0), ("precision", 7), ("prandtl", 0.0), ("kernel_path", 9),
-    ("order", 5), ("order", 8),
+    ("order", 5), ("order", 8), ("energy_form", 2), ("visc_law", 3), ("sutherland_s", 0.0),
 ])
 def test_create_rejects_bad_config_without_gpu(lib, field, value):
     cfg = at_dns.at_dns_config_default()
+    if field == "sutherland_s":
+        cfg.visc_law = at_dns.AT_DNS_VISC_SUTHERLAND
     if isinstance(value, tuple):
         for i, v in enumerate(value):
             getattr(cfg, field)[i] = v
