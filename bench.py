@@ -240,6 +240,8 @@ def main():
     ap.add_argument("--path", default="auto", choices=["auto", "multipass", "fused"])
     ap.add_argument("--order", default="both", choices=["both", "4", "6"],
                     help="spatial order of the AT scheme (4: headline; 6: Table B (1,6)/(2,6))")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the AUTO kernel path instead of the autotuner's pick")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the internal-energy / Sutherland leg")
     args = ap.parse_args()
@@ -275,6 +277,8 @@ def main():
         s = make_solver(at_dns, prec, stream.cuda_stream, mu0, args.path if order == 4 else "auto", order)
         s.set_state(U0)
         s.step(at_dns.at_dns_get_info(s.h).n_levels + 1, "random")   # past the synchronous start-up
+        if not args.no_tune and args.path == "auto":
+            s.tune("random", trials=3)    # kernel path, tile and z chunk from the autotuner
         if pg:
             pg.barrier()
         if key == legs[0][0] + ("" if legs[0][1] == 4 else "_o6"):
@@ -289,6 +293,7 @@ def main():
         # kernels in the timed region: every replayed step plus the health reset
         res[key]["launches"] = args.steps * res[key]["info"]["kernels_per_step"] + 1
         res[key]["path"] = "fused" if res[key]["info"]["kernel_path"] == at_dns.AT_DNS_PATH_FUSED else "multipass"
+        res[key]["tile"] = res[key]["info"]["tile"]
         # end to end through the public API with host buffers: per step, upload
         # U^n from pinned host memory (as the state of step n), step, read the
         # statistics record back
@@ -353,6 +358,7 @@ def main():
         "gpu_launches": head["launches"],
         "rhs_per_s": value,
         "kernel_path": head["path"],
+        "tile": head["tile"],
         "order": head["order"],
     }
     rep = {k: leg_report(r, world, pts, args.steps, pk) for k, r in res.items() if k not in ("e2e", "variant")}
@@ -398,7 +404,7 @@ def leg_report(r, world, pts, steps, pk):
         roof = {"bound": "hbm", "kernel": "%s (FP32, order %d)" % (kname, order), "achieved": achieved,
                 "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0),
                 "traffic": None, "bytes_per_point": algorithmic_bytes(4, order)}
-    return {"value": job_rate(world, pts, steps, r["ms"]), "unit": UNIT, "kernel_path": r["path"],
+    return {"value": job_rate(world, pts, steps, r["ms"]), "unit": UNIT, "kernel_path": r["path"], "tile": r["tile"],
             "ms_per_step": r["ms"] / steps, "dtype": r["dtype"], "roofline": roof,
             "kernel_ms_per_step": {k: v[1] / v[0] for k, v in r["kt"].items()}}
 
