@@ -64,6 +64,8 @@ extern "C" {
 #define AT_DNS_SYNC      0   /* k = 0 on every face: standard scheme */
 #define AT_DNS_PERIODIC  1   /* CAA: k = (n - n0) mod c_r (Algorithm 2) */
 #define AT_DNS_RANDOM    2   /* SAA: k iid uniform on {0..L} (Algorithm 1) */
+#define AT_DNS_FIXED     3   /* k = L on every face after the start-up: the worst case
+                                of the stability analysis (Sec. 3.2) */
 
 /* precision forms */
 #define AT_DNS_P64  0        /* FP64 storage and arithmetic */

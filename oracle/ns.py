@@ -54,7 +54,7 @@ import numpy as np
 from .philox import philox4x32_10, split_seed
 from .stencils import Scheme
 
-SYNC, PERIODIC, RANDOM = 0, 1, 2
+SYNC, PERIODIC, RANDOM, FIXED = 0, 1, 2, 3
 ENERGY_TOTAL, ENERGY_INTERNAL = 0, 1
 VISC_POWER, VISC_SUTHERLAND = 0, 1
 DELAY_STREAM_TAG = 0x4154      # 4th Philox counter word of the delay stream
@@ -151,6 +151,9 @@ def delay_map(cfg, step, mode):
         return k
     if mode == PERIODIC:
         k[:] = (step - n0) % cfg.comm_period
+        return k
+    if mode == FIXED:                       # worst case of the stability analysis (Sec. 3.2)
+        k[:] = cfg.max_delay
         return k
     if mode == RANDOM:
         p = np.arange(P, dtype=np.uint64)[:, None]

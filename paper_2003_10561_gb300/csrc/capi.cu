@@ -59,8 +59,8 @@ struct at_dns {
   std::string err;
   DevState* ds = nullptr;       // device copy of (n, first, cur)
   // captured one-step graphs per delay mode (replayed by at_dns_step)
-  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
-  double gdt[3] = {0, 0, 0};    // dt the graphs were captured with
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  double gdt[4] = {0, 0, 0, 0};    // dt the graphs were captured with
   bool use_graphs = true;
   // kernel path: fused single pass on TX x TY tiles marching ZC planes, or multi-pass
   bool fused = false;
@@ -559,7 +559,7 @@ bool pick_fused_shape(const Geom& g, int& TX, int& TY, int& ZC) {
 }
 
 void drop_graphs(at_dns* h) {
-  for (int m = 0; m < 3; ++m)
+  for (int m = 0; m < 4; ++m)
     if (h->gexec[m]) {
       cudaGraphExecDestroy(h->gexec[m]);
       h->gexec[m] = nullptr;
@@ -890,7 +890,7 @@ int at_dns_get_state(at_dns_t* h, double* u_out, int where) {
 }
 
 static int check_mode(at_dns* h, int mode) {
-  if (mode != AT_DNS_SYNC && mode != AT_DNS_PERIODIC && mode != AT_DNS_RANDOM)
+  if (mode != AT_DNS_SYNC && mode != AT_DNS_PERIODIC && mode != AT_DNS_RANDOM && mode != AT_DNS_FIXED)
     return fail(h, AT_DNS_E_INVALID_ARG, "unknown delay mode");
   if (mode == AT_DNS_PERIODIC && h->cfg.comm_period - 1 > h->cfg.max_delay)
     return fail(h, AT_DNS_E_INVALID_ARG, "periodic delays need comm_period - 1 <= max_delay");
@@ -1163,8 +1163,8 @@ struct at_dns_batch {
   cudaEvent_t fork = nullptr, done = nullptr;
   cudaStream_t st = nullptr;          // batch stream
   bool own_st = false;
-  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
-  std::vector<std::string> gkey[3];   // member path + dt each graph was captured with
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<std::string> gkey[4];   // member path + dt each graph was captured with
   std::string err;
 };
 
@@ -1182,7 +1182,7 @@ int batch_fail(at_dns_batch* b, int code, const std::string& msg) {
 }
 
 void batch_drop(at_dns_batch* b) {
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 4; ++k)
     if (b->gexec[k]) { cudaGraphExecDestroy(b->gexec[k]); b->gexec[k] = nullptr; }
 }
 
@@ -1246,7 +1246,7 @@ int at_dns_batch_member(at_dns_batch_t* b, int32_t i, at_dns_t** out) {
 int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode) {
   if (!b) return AT_DNS_E_INVALID_ARG;
   b->err.clear();
-  if (nsteps < 0 || delay_mode < 0 || delay_mode > 2) return batch_fail(b, AT_DNS_E_INVALID_ARG, "bad arguments");
+  if (nsteps < 0 || delay_mode < 0 || delay_mode > 3) return batch_fail(b, AT_DNS_E_INVALID_ARG, "bad arguments");
   const int M = (int)b->m.size();
   std::vector<std::string> key(M);
   for (int i = 0; i < M; ++i) {

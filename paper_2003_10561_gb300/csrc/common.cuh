@@ -188,6 +188,7 @@ __device__ __forceinline__ int delay_of(int mode, long long n, int p, int f, int
   const long long n0 = L + tl;
   if (mode == 0 || n < n0) return 0;
   if (mode == 1) return (int)((n - n0) % cr);
+  if (mode == 3) return L;                  // fixed worst case (stability scans, Sec. 3.2)
   const uint4 w = philox4x32_10(make_uint4((uint32_t)n, (uint32_t)p, (uint32_t)f, kDelayTag), k0, k1);
   return (int)(((unsigned long long)w.x * (unsigned long long)(L + 1)) >> 32);
 }

@@ -57,7 +57,7 @@ def ocfg(n, pes, **kw):
 
 
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("mode", ["sync", "periodic", "random"])
+@pytest.mark.parametrize("mode", ["sync", "periodic", "random", "fixed"])
 def test_delay_map_bit_exact(lib, mode):
     s = make(lib, (40, 30, 20), (4, 3, 2), mu0=0.01, dt=1e-3, max_delay=3, comm_period=4,
              seed=0x0123456789ABCDEF)
@@ -80,6 +80,7 @@ CASES = [
     ((40, 24, 16), (5, 3, 2), "random", 10, 2),       # 8^3 PEs (fused tiles 8 x 8)
     ((48, 32, 24), (3, 2, 3), "periodic", 9, 2),      # 16 x 16 x 8 PEs
     ((32, 16, 24), (1, 2, 3), "random", 12, 3),       # x without faces, periodic wrap in a tile
+    ((16, 16, 16), (2, 2, 2), "fixed", 9, 2),         # the worst case of the stability scans
 ]
 
 
