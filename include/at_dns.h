@@ -246,12 +246,21 @@ int at_dns_kernel_times(at_dns_t* h, at_dns_kernel_time_t* out, int32_t max, int
 /* Autotuner: for the current state, time `trials` right-hand-side
  * evaluations (no state change) of every kernel path that applies -- the
  * multi-pass path and each compiled fused tile shape (32x8, 16x16, 16x8, 8x32,
- * 8x16, 8x8; 4th order only) with whole-PE, half and quarter z chunks -- and
+ * 8x16, 8x8, and 32x16 for P32 / P32C; 4th order only) with whole-PE, half and
+ * quarter z chunks -- and
  * keep the fastest
  * (at_dns_get_info reports it).  *best_ms (may be NULL) receives its time per
  * evaluation.  Candidates that cannot get their work arrays are skipped.
  * Errors: INVALID_ARG, STATE, CUDA. */
 int at_dns_tune(at_dns_t* h, int32_t delay_mode, int32_t trials, double* best_ms);
+
+/* Select the kernel path explicitly: AT_DNS_PATH_MULTIPASS (tile ignored) or
+ * AT_DNS_PATH_FUSED with tile = {TX, TY, ZC}, one of the candidates that
+ * at_dns_tune times for this handle (a compiled tile shape whose TX and TY
+ * divide the PE extents, ZC planes per CTA dividing the PE extent in z).
+ * Captured step graphs are dropped; the state is kept.
+ * Errors: INVALID_ARG (NULL), UNSUPPORTED (not a candidate), OOM. */
+int at_dns_set_kernel_path(at_dns_t* h, int32_t path, const int32_t tile[3]);
 
 /* Block until all work queued on the handle's stream has finished. */
 int at_dns_synchronize(at_dns_t* h);

@@ -97,6 +97,7 @@ _SIGS = {
     "at_dns_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(at_dns_kernel_time_t), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]),
     "at_dns_synchronize": (ctypes.c_int, [_P]),
+    "at_dns_set_kernel_path": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "at_dns_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "at_dns_batch_create": (ctypes.c_int, [ctypes.POINTER(at_dns_config_t), ctypes.c_int32, _P, ctypes.POINTER(_P)]),
     "at_dns_batch_member": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
@@ -234,6 +235,11 @@ def at_dns_kernel_times(h):
     cnt = ctypes.c_int32(0)
     _check(load().at_dns_kernel_times(h, arr, 16, ctypes.byref(cnt)), h)
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(cnt.value)}
+
+
+def at_dns_set_kernel_path(h, path, tile=(0, 0, 0)):
+    t = (ctypes.c_int32 * 3)(*[int(v) for v in tile])
+    _check(load().at_dns_set_kernel_path(h, int(path), t), h)
 
 
 def at_dns_synchronize(h):
@@ -420,6 +426,9 @@ class Solver:
 
     def kernel_times(self):
         return at_dns_kernel_times(self.h)
+
+    def set_kernel_path(self, path, tile=(0, 0, 0)):
+        at_dns_set_kernel_path(self.h, PATHS[path] if isinstance(path, str) else int(path), tile)
 
     def tune(self, mode="random", trials=3):
         return at_dns_tune(self.h, MODES.get(mode, mode), trials)

@@ -614,13 +614,15 @@ struct Candidate { bool fused; int TX, TY, ZC; };
 // Kernel-path candidates of the autotuner: the multi-pass path and every
 // compiled fused tile shape that fits the PE extents, with whole-PE, half and
 // quarter z chunks (at least 8 planes).
-std::vector<Candidate> tune_candidates(const Geom& g) {
+std::vector<Candidate> tune_candidates(const Geom& g, bool p64) {
   std::vector<Candidate> out;
   out.push_back({false, 0, 0, 0});
   if (g.M != 2) return out;   // the fused kernel runs the 4th-order scheme only
   int ext[3];
   for (int d = 0; d < 3; ++d) ext[d] = g.pes[d] > 1 ? g.nl[d] : g.n[d];
-  const int shapes[6][2] = {{32, 8}, {16, 16}, {16, 8}, {8, 32}, {8, 16}, {8, 8}};
+  // 32x16 (one CTA of 512 threads per SM) is compiled for the FP32 forms only:
+  // its FP64 window does not fit in shared memory
+  const int shapes[7][2] = {{32, 8}, {16, 16}, {16, 8}, {8, 32}, {8, 16}, {8, 8}, {32, 16}};
   int zmax = 0;
   if (ext[2] <= 64) zmax = ext[2];
   else
@@ -628,6 +630,7 @@ std::vector<Candidate> tune_candidates(const Geom& g) {
       if (ext[2] % t == 0) { zmax = t; break; }
   for (auto& sh : shapes) {
     if (ext[0] % sh[0] || ext[1] % sh[1]) continue;
+    if (p64 && sh[1] == 16 && sh[0] == 32) continue;
     for (int div : {1, 2, 4}) {
       const int zc = zmax / div;
       if (zc < 8 || zmax % div || ext[2] % zc) continue;
@@ -1104,7 +1107,7 @@ int at_dns_tune(at_dns_t* h, int32_t delay_mode, int32_t trials, double* best_ms
   CK(cudaEventCreate(&e1));
   double best = 1e300;
   Candidate pick{h->fused, h->TX, h->TY, h->ZC};
-  for (const Candidate& c : tune_candidates(h->g)) {
+  for (const Candidate& c : tune_candidates(h->g, h->p64)) {
     if (set_path(h, c.fused, c.TX, c.TY, c.ZC) != AT_DNS_OK) continue;   // e.g. no memory for work arrays
     // one untimed evaluation, then `trials` timed right-hand sides (no state change)
     for (int t = 0; t <= trials; ++t) {
@@ -1127,6 +1130,16 @@ int at_dns_tune(at_dns_t* h, int32_t delay_mode, int32_t trials, double* best_ms
   h->prof = was_prof;
   if (best_ms) *best_ms = best;
   return AT_DNS_OK;
+}
+
+int at_dns_set_kernel_path(at_dns_t* h, int32_t path, const int32_t tile[3]) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  if (path == AT_DNS_PATH_MULTIPASS) return set_path(h, false, 0, 0, 0);
+  if (path != AT_DNS_PATH_FUSED || !tile) return fail(h, AT_DNS_E_INVALID_ARG, "path must be MULTIPASS or FUSED with a tile");
+  for (const Candidate& c : tune_candidates(h->g, h->p64))
+    if (c.fused && c.TX == tile[0] && c.TY == tile[1] && c.ZC == tile[2]) return set_path(h, true, c.TX, c.TY, c.ZC);
+  return fail(h, AT_DNS_E_UNSUPPORTED, "tile is not a fused-path candidate for this handle");
 }
 
 int at_dns_synchronize(at_dns_t* h) {

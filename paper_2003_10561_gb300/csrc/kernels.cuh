@@ -414,19 +414,19 @@ __device__ __forceinline__ long long okey(float v) {
 
 // Per-block reduction of the kNumStat per-thread sums (fixed order) into
 // partial[block], and of the max/min keys and health bits into the global
-// words.  Blocks have a multiple of 32 threads, at most 256.  FP64 values go
-// through shared memory: each statistic in 16 partial sums of 16 threads, then
-// one sum of the 16 (a warp-shuffle tree would cost every lane 5 FP64 adds per
-// statistic).  FP32 values are summed within a warp in FP32 first.
-constexpr int kReduceScratchDoubles = kNumStat * 257;
+// words.  Blocks have a multiple of 32 threads, at most NT.  FP64 values go
+// through shared memory: each statistic in NT/16 partial sums of 16 threads,
+// then one sum of those (a warp-shuffle tree would cost every lane 5 FP64 adds
+// per statistic).  FP32 values are summed within a warp in FP32 first.
+constexpr int kReduceScratchDoubles = kNumStat * 257;   // NT = 256
 
-// scratch: at least kReduceScratchDoubles doubles of shared memory that no
+// scratch: at least kNumStat * (NT + 1) doubles of shared memory that no
 // other thread of the block still reads (k_fused passes its dead window).
-template <typename S>
+template <typename S, int NT = 256>
 __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave, long long krho, long long kp,
                                              unsigned health, bool do_stats, double* partial,
                                              unsigned long long* words, double* scratch) {
-  constexpr int kMaxThreads = 256, kMaxWarps = kMaxThreads / 32;
+  constexpr int kMaxThreads = NT, kMaxWarps = kMaxThreads / 32, kParts = kMaxThreads / 16;
   double (*sh)[kMaxThreads + 1] = reinterpret_cast<double (*)[kMaxThreads + 1]>(scratch);
   __shared__ long long shk[kMaxWarps][3];
   __shared__ unsigned shh[kMaxWarps];
@@ -478,8 +478,8 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
   if (!do_stats) return;
   if (!by_warp) {
     // 16 consecutive entries per (statistic, part), written back in place
-    for (int j = tid; j < kNumStat * 16; j += nthreads) {
-      const int s = j >> 4, part = j & 15;
+    for (int j = tid; j < kNumStat * kParts; j += nthreads) {
+      const int s = j / kParts, part = j - s * kParts;
       double a = 0.0;
 #pragma unroll
       for (int q = 0; q < 16; ++q) a += sh[s][part * 16 + q];
@@ -489,7 +489,7 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
     for (int s = tid; s < kNumStat; s += nthreads) {
       double a = 0.0;
 #pragma unroll
-      for (int part = 0; part < 16; ++part) a += sh[s][part * 16];
+      for (int part = 0; part < kParts; ++part) a += sh[s][part * 16];
       partial[blk * kNumStat + s] = a;
     }
   } else {

@@ -41,10 +41,11 @@ struct TileShape {
 template <typename S>
 inline size_t fused_smem_bytes(int TX, int TY) {
   // nine window planes, then the x fluxes of the current plane on TY rows of
-  // TX+4 cells and the y fluxes on TY+4 rows of TX cells
+  // TX+4 cells and the y fluxes on TY+4 rows of TX cells; at the end the
+  // window is the reduction scratch (kNumStat * (NT + 1) doubles)
   const size_t win = ((size_t)kWinPlanes * kWinFields * (TX + 4) * (TY + 4) +
                       5 * (size_t)TY * (TX + 4) + 5 * (size_t)(TY + 4) * TX) * sizeof(S);
-  const size_t red = (size_t)kReduceScratchDoubles * sizeof(double);
+  const size_t red = (size_t)kNumStat * ((TX * TY > 256 ? 512 : 256) + 1) * sizeof(double);
   return win > red ? win : red;
 }
 
@@ -257,7 +258,8 @@ struct StatAcc {
 };
 
 template <typename S, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, sizeof(S) == 4 ? 2 : 1) k_fused(Geom g, Coef<S> K, StepArgs<S> A0, int ZC) {
+__global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 2 : 1)
+    k_fused(Geom g, Coef<S> K, StepArgs<S> A0, int ZC) {
   const StepArgs<S>& A = A0;
   const StepDyn<S> D = resolve_step(A0);
   using T_ = TileShape<TX, TY>;
@@ -570,7 +572,7 @@ __global__ void __launch_bounds__(TX * TY, sizeof(S) == 4 ? 2 : 1) k_fused(Geom 
       kp = okey(pmin);
     }
   }
-  block_reduce<double>(tot, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words,
+  block_reduce<double, (TX * TY > 256 ? 512 : 256)>(tot, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words,
                        reinterpret_cast<double*>(fused_smem));
 }
 

@@ -405,3 +405,33 @@ def test_tuner_keeps_parity(lib):
     R = s.rhs("random")
     Rref = ns.rhs(c, hist, ns.delay_map(c, step, ns.RANDOM))
     assert max(rel_linf(R, Rref)) <= 1e-12
+
+
+FUSED_SHAPES = [(32, 8), (16, 16), (16, 8), (8, 32), (8, 16), (8, 8), (32, 16)]
+
+
+@pytest.mark.parametrize("prec", ["p64", "p32"])
+def test_every_fused_tile_keeps_parity(lib, prec):
+    """Each compiled fused tile shape and z chunk that applies (the autotuner's
+    candidates), selected explicitly, matches the oracle."""
+    n, pes = (64, 64, 32), (2, 2, 1)
+    kw = dict(mu0=0.02, dt=2e-3, max_delay=2, seed=77)
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=11)
+    c = ocfg(n, pes, **kw)
+    hist = synth.history(U0, c.n_levels, eps=2e-2, seed=5)
+    Rref = ns.rhs(c, hist, ns.delay_map(c, 9, ns.RANDOM))
+    s = make(lib, n, pes, prec, **kw)
+    s.set_history(hist, 9)
+    tried = 0
+    for tx, ty in FUSED_SHAPES:
+        for zc in (32, 16, 8):
+            try:
+                s.set_kernel_path("fused", (tx, ty, zc))
+            except lib.AtDnsError as e:
+                assert e.code == lib.AT_DNS_E_UNSUPPORTED
+                continue
+            tried += 1
+            R = s.rhs("random")
+            err = rel_linf(R, Rref)
+            assert max(err) <= (1e-12 if prec == "p64" else 2e-4), (tx, ty, zc, err)
+    assert tried >= (18 if prec == "p64" else 21)
