@@ -531,8 +531,10 @@ __device__ __forceinline__ long long main_point_index(const Geom& g) {
   return base + t;
 }
 
+// FP64: three CTAs per SM (more warps to hide the FP64 pipe's latency; a
+// few registers spill); FP32: two.
 template <typename S, int M>
-__global__ void __launch_bounds__(256, 2) k_main(Geom g, Coef<S> K, StepArgs<S> A0) {
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 3 : 2) k_main(Geom g, Coef<S> K, StepArgs<S> A0) {
   const StepArgs<S>& A = A0;
   const StepDyn<S> D = resolve_step(A0);
   const long long idx = main_point_index<S>(g);
