@@ -44,11 +44,13 @@ FLOP_MAIN6 = 489.0
 # R^n; plus the slab ring: 1 write + 3 reads of 5 variables at the N_B fraction)
 NB_FRAC = 1.0 - (28.0 / 32.0) ** 3
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max SM clock
-# DRAM bytes (read + write) of one k_main<double, 2> launch on the multi-pass
-# path: ncu at 128^3 with 4x4x4 PEs of 32^3 (708.2 MB read + 358.0 MB written,
-# profiles/k_main_fp64_128cube_4x4x4pes.md), scaled by the point count to the
-# 256^3 workload (same PE size; traffic grows with the points)
-K_MAIN_FP64_TRAFFIC_256 = None   # recapture after the kernel changes
+# DRAM bytes (read + write) of one launch of the dominant kernel, from ncu at
+# 128^3 with 4x4x4 PEs of 32^3 (profiles/k_main_fp64_128cube_4x4x4pes.md,
+# profiles/k_fused_fp32_128cube_4x4x4pes.md), scaled by the point count to the
+# 256^3 workload (same PE size; traffic grows with the points):
+# k_main<double, 2> 701.1 MB + 462.6 MB, k_fused<float, 32, 8> 113.1 MB + 53.3 MB
+K_MAIN_FP64_TRAFFIC_256 = 8 * (701.0944e6 + 462.572032e6)
+K_FUSED_FP32_TRAFFIC_256 = 8 * (113.08416e6 + 53.325824e6)
 
 
 def set_workload(n, pes):
@@ -404,9 +406,11 @@ def leg_report(r, world, pts, steps, pk):
     else:
         achieved = algorithmic_bytes(4, order) * pts / t_main / 1e9
         kname = "k_fused" if r["path"] == "fused" else "k_main"
+        traffic = K_FUSED_FP32_TRAFFIC_256 if (order == 4 and N == 256 and PES == 8 and r["path"] == "fused"
+                                               and list(r["tile"]) == [32, 8, 32]) else None
         roof = {"bound": "hbm", "kernel": "%s (FP32, order %d)" % (kname, order), "achieved": achieved,
                 "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0),
-                "traffic": None, "bytes_per_point": algorithmic_bytes(4, order)}
+                "traffic": traffic, "bytes_per_point": algorithmic_bytes(4, order)}
     return {"value": job_rate(world, pts, steps, r["ms"]), "unit": UNIT, "kernel_path": r["path"], "tile": r["tile"],
             "ms_per_step": r["ms"] / steps, "dtype": r["dtype"], "roofline": roof,
             "kernel_ms_per_step": {k: v[1] / v[0] for k, v in r["kt"].items()}}
