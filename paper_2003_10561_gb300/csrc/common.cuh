@@ -379,13 +379,15 @@ __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(
 // With low words (compensated FP32 form) the state is carried as hi + lo and
 // the increment is added by TwoSum (Knuth), so no increment is lost below the
 // resolution of the high word; the stencils read the high word only.
+// Rp: R^{n-1} of the point already loaded (null: read here).
 template <typename S>
 __device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& A, const StepDyn<S>& D, long long idx,
                                            long long N, const S (&Uo)[5], const S (&R)[5], S (&un)[5],
-                                           unsigned& health) {
+                                           unsigned& health, const S* Rp = nullptr) {
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const S inc = D.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * A.Rprev[v * N + idx]);
+    const S rp = Rp ? Rp[v] : A.Rprev[v * N + idx];
+    const S inc = D.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * rp);
     if (D.Ulo) {
       const S dlt = mul_rn(K.dt, inc);
       const S s = add_rn(Uo[v], dlt);                           // TwoSum(U_hi, dlt)

@@ -65,11 +65,21 @@ struct FusedGeo {
   }
 };
 
-// Fill window plane zp (stored at element offset `pbase`).
+// Raw values of one window plane for this thread's cells: the conserved
+// variables (kind 1), the AT ghost u, v, w, T (kind 2) or nothing (kind 0:
+// corner cells beyond two faces, planes beyond the z ghosts).  Fetching a
+// plane into registers one iteration ahead keeps its global loads in flight
+// while the current plane is computed.
 template <typename S, int TX, int TY>
-__device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K, const StepArgs<S>& A,
-                                                 const S* __restrict__ U, const FusedGeo& F, S* win, int pbase,
-                                                 int zp) {
+struct PlaneRaw {
+  static constexpr int ITER = (TileShape<TX, TY>::CELLS + TileShape<TX, TY>::THREADS - 1) / TileShape<TX, TY>::THREADS;
+  S v[ITER][5];
+  int kind[ITER];
+};
+
+template <typename S, int TX, int TY>
+__device__ __forceinline__ void fused_fetch_plane(const Geom& g, const StepArgs<S>& A, const S* __restrict__ U,
+                                                  const FusedGeo& F, int zp, PlaneRaw<S, TX, TY>& P) {
   using T_ = TileShape<TX, TY>;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const long long N = g.npts;
@@ -77,13 +87,15 @@ __device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K
   const int lz = zp - F.base[2];
   const bool zfar = bz && (lz < -2 || lz >= g.nl[2] + 2);
 #pragma unroll
-  for (int c0 = 0; c0 < T_::CELLS; c0 += T_::THREADS) {
-    const int c = c0 + tid;
-    if (c >= T_::CELLS) break;
+  for (int it = 0; it < P.ITER; ++it) {
+    const int c = it * T_::THREADS + tid;
+    P.kind[it] = 0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) P.v[it][q] = S(0);
+    if (c >= T_::CELLS) continue;
     const int cy = c / T_::CX, cx = c - cy * T_::CX;
     const int xg = F.x0 - 2 + cx, yg = F.y0 - 2 + cy;
     const bool bx = F.beyond(g, 0, xg), by = F.beyond(g, 1, yg);
-    S u = S(0), v = S(0), w = S(0), T = S(0), r = S(0), H = S(0);
     const S* gh = nullptr;
     long long gi = 0, qs = 0;
     if (bz) {
@@ -108,8 +120,32 @@ __device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K
     } else {
       const int xw = wrapc(xg, g.n[0]), yw = wrapc(yg, g.n[1]), zw = wrapc(zp, g.n[2]);
       const long long idx = ((long long)zw * g.n[1] + yw) * g.n[0] + xw;
-      r = U[idx];
-      const S m0 = U[N + idx], m1 = U[2 * N + idx], m2 = U[3 * N + idx], E = U[4 * N + idx];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) P.v[it][q] = U[q * N + idx];
+      P.kind[it] = 1;
+    }
+    if (gh) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) P.v[it][q] = gh[(5 + q) * qs + gi];
+      P.kind[it] = 2;
+    }
+  }
+}
+
+// Window plane (element offset `pbase`) from fetched raw values: u, v, w, T,
+// rho and H from the conserved variables, or the ghost values as they are.
+template <typename S, int TX, int TY>
+__device__ __forceinline__ void fused_store_plane(const Coef<S>& K, const PlaneRaw<S, TX, TY>& P, S* win, int pbase) {
+  using T_ = TileShape<TX, TY>;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+#pragma unroll
+  for (int it = 0; it < P.ITER; ++it) {
+    const int c = it * T_::THREADS + tid;
+    if (c >= T_::CELLS) break;
+    S u = S(0), v = S(0), w = S(0), T = S(0), r = S(0), H = S(0);
+    if (P.kind[it] == 1) {
+      r = P.v[it][0];
+      const S m0 = P.v[it][1], m1 = P.v[it][2], m2 = P.v[it][3], E = P.v[it][4];
       const S inv = rcp_rn(r);
       u = m0 * inv;
       v = m1 * inv;
@@ -117,12 +153,11 @@ __device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K
       const S p = pressure(K, m0, m1, m2, u, v, w, E);
       T = K.gamma * p * inv;
       H = K.eform ? E : E + p;
-    }
-    if (gh) {
-      u = gh[5 * qs + gi];
-      v = gh[6 * qs + gi];
-      w = gh[7 * qs + gi];
-      T = gh[8 * qs + gi];
+    } else if (P.kind[it] == 2) {
+      u = P.v[it][0];
+      v = P.v[it][1];
+      w = P.v[it][2];
+      T = P.v[it][3];
     }
     S* cell = win + pbase + c;
     cell[WF_U * T_::CELLS] = u;
@@ -132,6 +167,16 @@ __device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K
     cell[WF_R * T_::CELLS] = r;
     cell[WF_H * T_::CELLS] = H;
   }
+}
+
+// Fill window plane zp (stored at element offset `pbase`).
+template <typename S, int TX, int TY>
+__device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K, const StepArgs<S>& A,
+                                                 const S* __restrict__ U, const FusedGeo& F, S* win, int pbase,
+                                                 int zp) {
+  PlaneRaw<S, TX, TY> P;
+  fused_fetch_plane<S, TX, TY>(g, A, U, F, zp, P);
+  fused_store_plane<S, TX, TY>(K, P, win, pbase);
 }
 
 // Inviscid flux component e of direction d of the window cell at element
@@ -299,6 +344,8 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
 
   // window slot of plane zs - 4 is 0; plane zs - 4 + k lives in slot k mod 9
   for (int k = 0; k < 8; ++k) fused_load_plane<S, TX, TY>(g, K, A, D.U, F, win, k * T_::PLANE, zs - 4 + k);
+  PlaneRaw<S, TX, TY> pf;                       // plane z + 4, fetched one iteration ahead
+  fused_fetch_plane<S, TX, TY>(g, A, D.U, F, zs + 4, pf);
 
   const int li_x = x - F.base[0], li_y = y - F.base[1];
   const int kind_x = local_kind(g.pes[0], li_x, g.nl[0]), kind_y = local_kind(g.pes[1], li_y, g.nl[1]);
@@ -329,8 +376,17 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
   int s0 = 0;                                  // slot of plane z - 4
   for (int z = zs; z < zs + ZC; ++z) {
     const int snew = s0 + 8 >= kWinPlanes ? s0 + 8 - kWinPlanes : s0 + 8;   // slot of plane z + 4
-    fused_load_plane<S, TX, TY>(g, K, A, D.U, F, win, snew * T_::PLANE, z + 4);
+    fused_store_plane<S, TX, TY>(K, pf, win, snew * T_::PLANE);
     __syncthreads();
+    if (z + 1 < zs + ZC) fused_fetch_plane<S, TX, TY>(g, A, D.U, F, z + 5, pf);
+    // the point's conserved variables and R^{n-1}: loaded here so that the
+    // loads are in flight during the flux phase
+    const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
+    const S m[3] = {D.U[N + idx], D.U[2 * N + idx], D.U[3 * N + idx]};
+    const S Ecur = D.U[4 * N + idx];
+    S Rp[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Rp[v] = (A.do_update && !D.first) ? A.Rprev[v * N + idx] : S(0);
     // fluxes of the current plane: x on x-extended rows, y on y-extended columns
     {
       const int sz = s0 + 4 >= kWinPlanes ? s0 + 4 - kWinPlanes : s0 + 4;   // slot of plane z
@@ -385,7 +441,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     }
     const int li_z = z - F.base[2];
     const int kind[3] = {kind_x, kind_y, local_kind(g.pes[2], li_z, g.nl[2])};
-    const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
 
     // ---- inviscid flux divergence: -sum_d D_d F_d (ghost fluxes already in
     // the flux arrays / queue across PE faces)
@@ -438,8 +493,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     const S r = W.at(WF_R, 0, 0, 0);
     const S vel[3] = {W.at(WF_U, 0, 0, 0), W.at(WF_V, 0, 0, 0), W.at(WF_W, 0, 0, 0)};
     const S T = W.at(WF_T, 0, 0, 0);
-    const S m[3] = {D.U[N + idx], D.U[2 * N + idx], D.U[3 * N + idx]};
-    const S Ecur = D.U[4 * N + idx];
     const S p = pressure(K, m[0], m[1], m[2], vel[0], vel[1], vel[2], Ecur);
     const S theta = Ag[0][0] + Ag[1][1] + Ag[2][2];
     S mu, dmudT;
@@ -498,7 +551,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     if (A.do_update) {
       const S Uo[5] = {r, m[0], m[1], m[2], Ecur};
       S un[5];
-      ab2_update(K, A, D, idx, N, Uo, R, un, health);
+      ab2_update(K, A, D, idx, N, Uo, R, un, health, Rp);
       const int slot = (int)((D.n + 1) % g.nlev);
       const int li[3] = {li_x, li_y, li_z};
       const int c3[3] = {x, y, z};
