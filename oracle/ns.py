@@ -20,7 +20,11 @@ Paper passages followed, in the order of one step:
 * right-hand side of Eqs. (cont), (mome) and the energy equation with the
   stress / strain definitions of Sec. 2 (total energy form, see below);
 * large-scale solenoidal forcing in a shell |kappa| <= kappa_f (Sec. 4.2);
-* second-order Adams-Bashforth, Eq. (time_ab) with T = 2 (Sec. 2.2).
+* second-order Adams-Bashforth, Eq. (time_ab) with T = 2 (Sec. 2.2); or, for
+  synchronous runs only, a low-storage three-stage Runge-Kutta scheme
+  (Williamson, J. Comput. Phys. 35, 1980: dU = A_s dU + dt R, U = U + B_s dU,
+  A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15)) -- the paper discusses
+  RK and keeps AB2 for AT because each RK stage would need a synchronisation.
 
 Readings where the paper is silent (each listed in the design notes):
 
@@ -57,6 +61,9 @@ from .stencils import Scheme
 SYNC, PERIODIC, RANDOM, FIXED = 0, 1, 2, 3
 ENERGY_TOTAL, ENERGY_INTERNAL = 0, 1
 VISC_POWER, VISC_SUTHERLAND = 0, 1
+AB2, RK3 = 0, 1
+RK3_A = (0.0, -5.0 / 9.0, -153.0 / 128.0)
+RK3_B = (1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0)
 DELAY_STREAM_TAG = 0x4154      # 4th Philox counter word of the delay stream
 FORCING_STREAM_TAG = 0x464F    # 4th Philox counter word of the forcing stream
 
@@ -82,6 +89,7 @@ class Config:
     energy_form: int = ENERGY_TOTAL  # fifth variable: E (total) or rho e (Eq. (ie))
     visc_law: int = VISC_POWER       # mu0 T^omega, or Sutherland with S = suth_s
     suth_s: float = 0.368
+    integrator: int = AB2            # AB2, or RK3 (synchronous steps only)
 
     @property
     def scheme(self):
@@ -548,9 +556,28 @@ class Run:
         return rhs(self.cfg, self.levels, self.delays(), self.fhat(), return_aux)
 
     def step(self):
+        if self.cfg.integrator == RK3:
+            return self.step_rk3()
         R = self.rhs()
         U_new = ab2_update(self.levels[0], R, self.R_prev, self.cfg.dt)
         self.levels = [U_new] + self.levels[:-1]
         self.R_prev = R
         self.step_n += 1
         return U_new
+
+    def step_rk3(self):
+        """Three low-storage RK stages from U^n, each with the forcing of step
+        n and no delays."""
+        if self.mode != SYNC:
+            raise ValueError("RK3 steps are synchronous")
+        fhat = self.fhat()
+        zero = np.zeros((self.cfg.n_pes, 6), dtype=np.int64)
+        U = self.levels[0].copy()
+        dU = np.zeros_like(U)
+        for s in range(3):
+            R = rhs(self.cfg, [U] + self.levels[1:], zero, fhat)
+            dU = RK3_A[s] * dU + self.cfg.dt * R
+            U = U + RK3_B[s] * dU
+        self.levels = [U] + self.levels[:-1]
+        self.step_n += 1
+        return U
