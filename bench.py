@@ -321,6 +321,22 @@ def main():
                           "steps": e2e_steps}
         s.close()
 
+    # synchronous low-storage RK3 (three right-hand sides per step), FP64
+    if not args.no_variants and "p64" in res:
+        s = make_solver(at_dns, "p64", stream.cuda_stream, mu0, "auto", 4, integrator=at_dns.AT_DNS_RK3)
+        s.set_state(U0)
+        s.step(2, "sync")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        s.step(args.warmup, "sync")
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(args.steps, "sync")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res["rk3"] = {"ms": max_over_ranks(e0.elapsed_time(e1), pg, "cuda")}
+        s.close()
+
     # the paper's own internal-energy form (Eq. (ie)) with Sutherland viscosity,
     # FP64, same workload: its step time beside the headline form's
     if not args.no_variants and "p64" in res:
@@ -366,7 +382,12 @@ def main():
         "tile": head["tile"],
         "order": head["order"],
     }
-    rep = {k: leg_report(r, world, pts, args.steps, pk) for k, r in res.items() if k not in ("e2e", "variant")}
+    rep = {k: leg_report(r, world, pts, args.steps, pk) for k, r in res.items() if k not in ("e2e", "variant", "rk3")}
+    if "rk3" in res:
+        line["rk3_sync"] = {
+            "value": job_rate(world, pts, args.steps, res["rk3"]["ms"]), "unit": UNIT, "dtype": "f64",
+            "ms_per_step": res["rk3"]["ms"] / args.steps,
+            "workload": "the headline box and state, synchronous (no delays), three-stage low-storage RK3"}
     if "variant" in res:
         line["variant_rhoe_sutherland"] = {
             "value": job_rate(world, pts, args.steps, res["variant"]["ms"]), "unit": UNIT, "dtype": "f64",

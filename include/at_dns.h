@@ -81,6 +81,10 @@ extern "C" {
 #define AT_DNS_VISC_POWER       0   /* mu0 T^visc_exp */
 #define AT_DNS_VISC_SUTHERLAND  1   /* mu0 T^(3/2) (1 + S) / (T + S), S = sutherland_s */
 
+/* time integrators (Sec. 2.2) */
+#define AT_DNS_AB2  0   /* second-order Adams-Bashforth, Eq. (time_ab): the paper's integrator for AT */
+#define AT_DNS_RK3  1   /* low-storage three-stage RK3 (Williamson 1980), synchronous steps only */
+
 /* pointer locations */
 #define AT_DNS_HOST    0
 #define AT_DNS_DEVICE  1
@@ -116,6 +120,8 @@ typedef struct {
   int32_t  visc_law;     /* AT_DNS_VISC_POWER (default) or AT_DNS_VISC_SUTHERLAND        */
   double   sutherland_s; /* S, Sutherland temperature / reference temperature (0.368:
                             110.4 K over 300 K; the paper gives no constants)           */
+  int32_t  integrator;   /* AT_DNS_AB2 (default) or AT_DNS_RK3 (AT_DNS_SYNC steps only:
+                            the stages of an RK step would need a synchronisation each) */
 } at_dns_config_t;
 
 /* kernel paths (same results up to rounding): the multi-pass path stores
@@ -201,10 +207,14 @@ int at_dns_rhs(at_dns_t* h, int32_t delay_mode, double* rhs_out, int where);
  * map, assemble AT ghost values from the ring, evaluate R(U^n), update
  * U^{n+1} = U^n + dt(3/2 R^n - 1/2 R^{n-1}) (forward Euler on the first step
  * after a state is set), store U^{n+1}'s PE-boundary slabs in the ring and
- * advance the forcing.  Asynchronous on the handle's stream except that the
- * health word is read back once at the end.  Errors: INVALID_ARG, STATE,
- * CUDA, UNSTABLE (NaN/Inf, rho <= 0 or p <= 0 in any evaluated state; the
- * state is left as computed). */
+ * advance the forcing.  With integrator AT_DNS_RK3 a step is the three stages
+ * dU = A_s dU + dt R(U), U = U + B_s dU, A = (0, -5/9, -153/128),
+ * B = (1/3, 15/16, 8/15), with the forcing of step n in every stage and the
+ * statistics of U^n; only AT_DNS_SYNC is accepted.  Asynchronous on the
+ * handle's stream except that the health word is read back once at the end.
+ * Errors: INVALID_ARG, STATE, CUDA, UNSUPPORTED (RK3 with delays), UNSTABLE
+ * (NaN/Inf, rho <= 0 or p <= 0 in any evaluated state; the state is left as
+ * computed). */
 int at_dns_step(at_dns_t* h, int32_t nsteps, int32_t delay_mode);
 
 /* Statistics of the state at which the last RHS was evaluated (a step or

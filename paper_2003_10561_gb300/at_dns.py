@@ -28,6 +28,7 @@ AT_DNS_HOST, AT_DNS_DEVICE = 0, 1
 AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS, AT_DNS_PATH_FUSED = 0, 1, 2
 AT_DNS_ENERGY_TOTAL, AT_DNS_ENERGY_INTERNAL = 0, 1
 AT_DNS_VISC_POWER, AT_DNS_VISC_SUTHERLAND = 0, 1
+AT_DNS_AB2, AT_DNS_RK3 = 0, 1
 PATHS = {"auto": AT_DNS_PATH_AUTO, "multipass": AT_DNS_PATH_MULTIPASS, "fused": AT_DNS_PATH_FUSED}
 
 MODES = {"sync": AT_DNS_SYNC, "periodic": AT_DNS_PERIODIC, "random": AT_DNS_RANDOM, "fixed": AT_DNS_FIXED}
@@ -45,6 +46,7 @@ class at_dns_config_t(ctypes.Structure):
         ("precision", ctypes.c_int32), ("stats_every", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("kernel_path", ctypes.c_int32), ("order", ctypes.c_int32),
         ("energy_form", ctypes.c_int32), ("visc_law", ctypes.c_int32), ("sutherland_s", ctypes.c_double),
+        ("integrator", ctypes.c_int32),
     ]
 
 

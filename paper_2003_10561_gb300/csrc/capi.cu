@@ -90,6 +90,9 @@ __global__ void k_set_state(DevState* ds, long long n, int first, int cur) {
   ds->cur = cur;
 }
 
+// Between two RK3 stages: the stage state is in the other buffer.
+__global__ void k_flip_state(DevState* ds) { ds->cur = 1 - ds->cur; }
+
 // End of a step: level n+1 is in the other buffer and the next step is AB2.
 __global__ void k_advance_state(DevState* ds) {
   ds->n += 1;
@@ -424,8 +427,11 @@ struct Ops {
   // Queue one RHS evaluation at the device level n on stream `st`: update
   // (a step, advancing the device step state) or write R to Rout.  Touches no
   // host-side state, so it can be captured into a graph.
+  //
+  // rkstage >= 0: that stage of the low-storage RK3 (Williamson 1980; the
+  // step counter advances after stage 2).
   static int launch_step(at_dns* h, int mode, bool update, double* Rout, bool stats, bool reset_health,
-                         cudaStream_t st) {
+                         cudaStream_t st, int rkstage = -1) {
     const Geom& g = h->g;
     const int P = g.pes[0] * g.pes[1] * g.pes[2];
     const uint64_t seed = h->cfg.seed;
@@ -475,6 +481,13 @@ struct Ops {
     a.dt = h->dt;
     a.do_update = update ? 1 : 0;
     a.do_stats = stats ? 1 : 0;
+    if (rkstage >= 0) {
+      static const double kA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+      static const double kB[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+      a.rk = 1;
+      a.rkA = (S)kA[rkstage];
+      a.rkB = (S)kB[rkstage];
+    }
     if (h->fused) {
       Timed t(h, KD_MAIN);
       CK(launch_fused<S>(g, K, a, h->TX, h->TY, h->ZC, st));
@@ -486,7 +499,10 @@ struct Ops {
       { Timed t(h, KD_STATS); k_stats_final<<<kNumStat, 256, 0, st>>>(h->partial, h->nblk_step, h->sums); }
       CK(cudaGetLastError());
     }
-    if (update) {
+    if (update && rkstage >= 0 && rkstage < 2) {
+      k_flip_state<<<1, 1, 0, st>>>(h->ds);
+      CK(cudaGetLastError());
+    } else if (update) {
       k_advance_state<<<1, 1, 0, st>>>(h->ds);
       CK(cudaGetLastError());
       if (h->cfg.forcing) {
@@ -517,6 +533,24 @@ struct Ops {
       h->n += 1;
       h->t += h->dt;
     }
+  }
+
+  // One time step on `st`: one AB2 update, or the three stages of the
+  // low-storage RK3 (statistics of U^n from the first stage).
+  static int launch_update(at_dns* h, int mode, bool stats, bool reset_health, cudaStream_t st) {
+    if (h->cfg.integrator != AT_DNS_RK3) return launch_step(h, mode, true, nullptr, stats, reset_health, st);
+    for (int s = 0; s < 3; ++s) {
+      const int rc = launch_step(h, mode, true, nullptr, stats && s == 0, reset_health && s == 0, st, s);
+      if (rc) return rc;
+    }
+    return AT_DNS_OK;
+  }
+
+  static int evaluate_step(at_dns* h, int mode, bool stats, bool reset_health) {
+    int rc = launch_update(h, mode, stats, reset_health, h->st);
+    if (rc) return rc;
+    account(h, true, stats);
+    return AT_DNS_OK;
   }
 
   static int evaluate(at_dns* h, int mode, bool update, double* Rout, bool stats, bool reset_health) {
@@ -572,8 +606,8 @@ int step_graph(at_dns* h, int mode, bool stats) {
   if (h->gexec[mode]) { cudaGraphExecDestroy(h->gexec[mode]); h->gexec[mode] = nullptr; }
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
-  const int rc = h->p64 ? Ops<double>::launch_step(h, mode, true, nullptr, stats, false, h->st)
-                        : Ops<float>::launch_step(h, mode, true, nullptr, stats, false, h->st);
+  const int rc = h->p64 ? Ops<double>::launch_update(h, mode, stats, false, h->st)
+                        : Ops<float>::launch_update(h, mode, stats, false, h->st);
   const cudaError_t e = cudaStreamEndCapture(h->st, &graph);
   if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
   if (e != cudaSuccess) return fail(h, AT_DNS_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -697,6 +731,7 @@ int at_dns_config_default(at_dns_config_t* c) {
   c->energy_form = AT_DNS_ENERGY_TOTAL;
   c->visc_law = AT_DNS_VISC_POWER;
   c->sutherland_s = 0.368;
+  c->integrator = AT_DNS_AB2;
   return AT_DNS_OK;
 }
 
@@ -734,6 +769,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     else if (c.energy_form != AT_DNS_ENERGY_TOTAL && c.energy_form != AT_DNS_ENERGY_INTERNAL) bad = "unknown energy_form";
     else if (c.visc_law != AT_DNS_VISC_POWER && c.visc_law != AT_DNS_VISC_SUTHERLAND) bad = "unknown visc_law";
     else if (c.visc_law == AT_DNS_VISC_SUTHERLAND && !(c.sutherland_s > 0)) bad = "sutherland_s must be > 0";
+    else if (c.integrator != AT_DNS_AB2 && c.integrator != AT_DNS_RK3) bad = "unknown integrator";
   }
   if (bad.empty() && (long long)c.n[0] * c.n[1] * c.n[2] >= (1LL << 31)) bad = "grids must hold fewer than 2^31 points";
   if (!bad.empty()) { g_create_error = bad; return AT_DNS_E_INVALID_ARG; }
@@ -895,6 +931,8 @@ int at_dns_get_state(at_dns_t* h, double* u_out, int where) {
 static int check_mode(at_dns* h, int mode) {
   if (mode != AT_DNS_SYNC && mode != AT_DNS_PERIODIC && mode != AT_DNS_RANDOM && mode != AT_DNS_FIXED)
     return fail(h, AT_DNS_E_INVALID_ARG, "unknown delay mode");
+  if (h->cfg.integrator == AT_DNS_RK3 && mode != AT_DNS_SYNC)
+    return fail(h, AT_DNS_E_UNSUPPORTED, "the RK3 integrator runs synchronous steps only");
   if (mode == AT_DNS_PERIODIC && h->cfg.comm_period - 1 > h->cfg.max_delay)
     return fail(h, AT_DNS_E_INVALID_ARG, "periodic delays need comm_period - 1 <= max_delay");
   return AT_DNS_OK;
@@ -941,8 +979,8 @@ int at_dns_step(at_dns_t* h, int32_t nsteps, int32_t delay_mode) {
     }
   } else {
     for (int s = 0; s < nsteps; ++s) {
-      rc = h->p64 ? Ops<double>::evaluate(h, delay_mode, true, nullptr, stats, s == 0)
-                  : Ops<float>::evaluate(h, delay_mode, true, nullptr, stats, s == 0);
+      rc = h->p64 ? Ops<double>::evaluate_step(h, delay_mode, stats, s == 0)
+                  : Ops<float>::evaluate_step(h, delay_mode, stats, s == 0);
       if (rc) return rc;
     }
   }
@@ -1282,8 +1320,8 @@ int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode) {
       at_dns* h = b->m[i];
       cudaStreamWaitEvent(b->ms[i], b->fork, 0);
       const bool stats = h->cfg.stats_every == 1;
-      rc = h->p64 ? Ops<double>::launch_step(h, delay_mode, true, nullptr, stats, false, b->ms[i])
-                  : Ops<float>::launch_step(h, delay_mode, true, nullptr, stats, false, b->ms[i]);
+      rc = h->p64 ? Ops<double>::launch_update(h, delay_mode, stats, false, b->ms[i])
+                  : Ops<float>::launch_update(h, delay_mode, stats, false, b->ms[i]);
       cudaEventRecord(b->ev[i], b->ms[i]);
       cudaStreamWaitEvent(b->st, b->ev[i], 0);
     }

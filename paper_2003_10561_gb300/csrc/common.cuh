@@ -295,6 +295,8 @@ struct StepArgs {
   int first;           // 1: forward Euler (no R^{n-1})
   int do_update;       // 1: write Unext/Rprev/ring; 0: write Rout
   int do_stats;
+  int rk;              // 1: a stage of the low-storage RK3 (Rprev holds the stage register dU)
+  S rkA, rkB;          // its coefficients: dU = rkA dU + dt R, U = U + rkB dU
 };
 
 // The per-step fields of one evaluation: from the device step state when the
@@ -379,17 +381,32 @@ __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(
 // With low words (compensated FP32 form) the state is carried as hi + lo and
 // the increment is added by TwoSum (Knuth), so no increment is lost below the
 // resolution of the high word; the stencils read the high word only.
-// Rp: R^{n-1} of the point already loaded (null: read here).
+// Rp: R^{n-1} (or the RK3 stage register) of the point already loaded
+// (null: read here).  A low-storage RK3 stage (A.rk) updates the register
+// dU = rkA dU + dt R (kept in the Rprev array) and adds rkB dU to the state.
+template <typename S>
+__device__ __forceinline__ bool needs_rprev(const StepArgs<S>& A, const StepDyn<S>& D) {
+  return A.do_update && (A.rk ? A.rkA != S(0) : !D.first);
+}
+
 template <typename S>
 __device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& A, const StepDyn<S>& D, long long idx,
                                            long long N, const S (&Uo)[5], const S (&R)[5], S (&un)[5],
                                            unsigned& health, const S* Rp = nullptr) {
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const S rp = Rp ? Rp[v] : A.Rprev[v * N + idx];
-    const S inc = D.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * rp);
+    const S rp = needs_rprev(A, D) ? (Rp ? Rp[v] : A.Rprev[v * N + idx]) : S(0);
+    S inc, kept;
+    if (A.rk) {
+      kept = fma(A.rkA, rp, K.dt * R[v]);   // stage register dU
+      inc = A.rkB * kept;                   // the state grows by rkB dU
+    } else {
+      inc = D.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * rp);
+      kept = R[v];
+    }
+    const S scale = A.rk ? S(1) : K.dt;
     if (D.Ulo) {
-      const S dlt = mul_rn(K.dt, inc);
+      const S dlt = mul_rn(scale, inc);
       const S s = add_rn(Uo[v], dlt);                           // TwoSum(U_hi, dlt)
       const S bp = sub_rn(s, Uo[v]);
       const S e = add_rn(sub_rn(Uo[v], sub_rn(s, bp)), sub_rn(dlt, bp));
@@ -398,10 +415,10 @@ __device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& 
       D.Ulo_next[v * N + idx] = sub_rn(lo, sub_rn(hi, s));
       un[v] = hi;
     } else {
-      un[v] = fma(K.dt, inc, Uo[v]);
+      un[v] = fma(scale, inc, Uo[v]);
     }
     D.Unext[v * N + idx] = un[v];
-    A.Rprev[v * N + idx] = R[v];
+    A.Rprev[v * N + idx] = kept;
     if (nonfinite(un[v])) health |= H_NONFINITE;
   }
 }

@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     const S Ecur = D.U[4 * N + idx];
     S Rp[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Rp[v] = (A.do_update && !D.first) ? A.Rprev[v * N + idx] : S(0);
+    for (int v = 0; v < 5; ++v) Rp[v] = needs_rprev(A, D) ? A.Rprev[v * N + idx] : S(0);
     // fluxes of the current plane: x on x-extended rows, y on y-extended columns
     {
       const int sz = s0 + 4 >= kWinPlanes ? s0 + 4 - kWinPlanes : s0 + 4;   // slot of plane z

@@ -435,3 +435,26 @@ def test_every_fused_tile_keeps_parity(lib, prec):
             err = rel_linf(R, Rref)
             assert max(err) <= (1e-12 if prec == "p64" else 2e-4), (tx, ty, zc, err)
     assert tried >= (18 if prec == "p64" else 21)
+
+
+@pytest.mark.parametrize("prec,tol", [("p64", 1e-10), ("p32", 2e-4)])
+@pytest.mark.parametrize("path", PATHS)
+def test_rk3_steps_parity(lib, path, prec, tol):
+    """20 synchronous low-storage RK3 steps on 16^3 with 2x2x2 PEs (forced),
+    through a captured graph on a stream, against the oracle's RK3."""
+    torch = pytest.importorskip("torch")
+    n, pes = (16, 16, 16), (2, 2, 2)
+    kw = dict(mu0=0.03, dt=4e-3, max_delay=2, forcing=1, kf=2.0, f_amp=0.2, f_tcorr=0.3, f_seed=8)
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=21)
+    c = ocfg(n, pes, **{**kw, "forcing": True}, integrator=ns.RK3)
+    stream = torch.cuda.Stream()
+    s = make(lib, n, pes, prec, path=path, stream=stream.cuda_stream, integrator=lib.AT_DNS_RK3, **kw)
+    s.set_state(U0)
+    run = ns.Run.start(c, U0, ns.SYNC)
+    for _ in range(20):
+        run.step()
+    s.step(20, "sync")
+    assert max(rel_linf(s.get_state(), run.levels[0])) <= tol
+    with pytest.raises(lib.AtDnsError) as ei:
+        s.step(1, "random")
+    assert ei.value.code == lib.AT_DNS_E_UNSUPPORTED
