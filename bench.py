@@ -247,6 +247,7 @@ def main():
                     help="spatial order of the AT scheme (4: headline; 6: Table B (1,6)/(2,6))")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the AUTO kernel path instead of the autotuner's pick")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the internal-energy / Sutherland leg")
     args = ap.parse_args()
@@ -352,6 +353,39 @@ def main():
         res["variant"] = {"ms": ms}
         s.close()
 
+    # batched ensemble: 64 independent decaying runs of uneven sizes advanced by
+    # one graph launch per step (FP32-bulk, random delays, tiles from the tuner)
+    if not args.no_batch and N == 256:
+        specs, states = [], []
+        mu_of = {nb: synth.mu0_for_resolution((nb,) * 3, k0=4.0, mach_t=0.3, seed=0) for nb in (32, 48, 64, 96, 128)}
+        for i in range(64):
+            nb = (32, 48, 64, 96, 128)[i % 5]
+            k0 = (3.0, 4.0, 6.0)[i % 3]
+            mt = 0.1 + 0.4 * i / 63.0
+            specs.append(dict(n=(nb, nb, nb), pes=(nb // 16,) * 3, precision="p32", gamma=1.4, prandtl=0.7,
+                              visc_exp=0.76, mu0=mu_of[nb], cfl=CFL_AT, dt=0.0, max_delay=L, seed=i,
+                              stats_every=1))
+            states.append(synth.initial_state((nb,) * 3, k0=k0, mach_t=mt, seed=i))
+        bstream = torch.cuda.Stream()
+        batch = at_dns.Batch(specs, stream=bstream.cuda_stream)
+        for m, U in zip(batch.members, states):
+            m.set_state(U)
+        batch.step(6, "random")
+        batch.tune("random", trials=2)
+        batch.step(args.warmup, "random")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(bstream)
+        batch.step(args.steps, "random")
+        e1.record(bstream)
+        torch.cuda.synchronize()
+        bms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+        bpts = float(sum(sp["n"][0] ** 3 for sp in specs))
+        paths = [m.info()["kernel_path"] for m in batch.members]
+        res["batch"] = {"ms": bms, "pts": bpts, "fused": sum(1 for p_ in paths if p_ == at_dns.AT_DNS_PATH_FUSED)}
+        batch.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, el = oracle_rate(3, 1)
@@ -382,7 +416,16 @@ def main():
         "tile": head["tile"],
         "order": head["order"],
     }
-    rep = {k: leg_report(r, world, pts, args.steps, pk) for k, r in res.items() if k not in ("e2e", "variant", "rk3")}
+    rep = {k: leg_report(r, world, pts, args.steps, pk) for k, r in res.items()
+           if k not in ("e2e", "variant", "rk3", "batch")}
+    if "batch" in res:
+        bt = res["batch"]
+        line["batch_ensemble"] = {
+            "value": job_rate(world, bt["pts"], args.steps, bt["ms"]), "unit": UNIT, "dtype": "f32",
+            "ms_per_step": bt["ms"] / args.steps, "members": 64, "members_on_fused_path": bt["fused"],
+            "workload": "64 decaying runs, grids {32,48,64,96,128}^3 by member, PEs of 16^3, M_t 0.1..0.5, "
+                        "k0 in {3,4,6}, seeds 0..63, FP32-bulk, random delays L = 2, one graph launch per step, "
+                        "kernel paths and tiles from the autotuner"}
     if "rk3" in res:
         line["rk3_sync"] = {
             "value": job_rate(world, pts, args.steps, res["rk3"]["ms"]), "unit": UNIT, "dtype": "f64",

@@ -1,0 +1,47 @@
+"""Accuracy of the FP32-bulk forms against FP64 on a forced 512^3 run (the
+workload list's third configuration, shortened to 100 steps): 8x8x8 PEs of
+64^3, forcing on |kappa| <= 2, random delays with L = 3, AB2 from the same
+state in P64, P32 and P32C.  The relative error in the kinetic
+energy, the dissipation and the longitudinal gradient moments against the
+FP64 run must stay below 1e-4 (the target for the FP32-bulk form)."""
+import pytest
+
+from paper_2003_10561_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N, PES, STEPS = 512, 8, 100
+
+
+def test_fp32_bulk_matches_fp64_at_512():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if torch.cuda.mem_get_info()[0] < 100e9:
+        pytest.skip("needs about 100 GB of free device memory")
+    from paper_2003_10561_gb300 import at_dns
+    n = (N, N, N)
+    # kappa_max eta = 1.5 at 128^3, carried to 512^3 with nu ~ eta^(4/3) at fixed <eps>
+    mu0 = synth.mu0_for_resolution((128,) * 3, k0=4.0, mach_t=0.3, seed=3) * (128.0 / N) ** (4.0 / 3.0)
+    U0 = synth.initial_state(n, k0=4.0, mach_t=0.3, seed=3)
+    stream = torch.cuda.Stream()
+    stats = {}
+    dt = None
+    for prec in ("p64", "p32", "p32c"):
+        s = at_dns.Solver(n=n, pes=(PES,) * 3, precision=prec, stream=stream.cuda_stream, gamma=1.4, prandtl=0.7,
+                          visc_exp=0.76, mu0=mu0, cfl=0.15, dt=dt or 0.0, max_delay=3, seed=5, forcing=1,
+                          kf=2.0, f_amp=0.05, f_tcorr=0.5, f_seed=11)
+        s.set_state(U0)
+        dt = s.info()["dt"]
+        s.step(STEPS, "random")
+        stats[prec] = s.stats()
+        s.close()
+        torch.cuda.empty_cache()
+    ref = stats["p64"]
+    for prec in ("p32", "p32c"):
+        for k in ("tke", "dissipation", "grad_m2", "enstrophy"):
+            err = abs(stats[prec][k] - ref[k]) / abs(ref[k])
+            print(prec, k, err)
+            assert err <= 1e-4, (prec, k, err)
+        # the record describes U^{n} of the last step evaluated
+        assert stats[prec]["step"] == ref["step"] == STEPS - 1
