@@ -32,7 +32,10 @@
  * then z, y, x with x fastest -- i.e. 5 * n0 * n1 * n2 doubles.
  *
  * Ownership: the library owns every device allocation it makes (released by
- * at_dns_destroy).  Caller buffers are read or written only during the call;
+ * at_dns_destroy), unless the configuration hands it a device pool: then all
+ * of the handle's device memory is carved from that region, which the caller
+ * owns and must keep alive until at_dns_destroy.  Caller buffers are read or
+ * written only during the call;
  * `where` says whether a pointer is host (AT_DNS_HOST, any pageable or pinned
  * memory) or device (AT_DNS_DEVICE, memory of the handle's device).
  *
@@ -122,6 +125,10 @@ typedef struct {
                             110.4 K over 300 K; the paper gives no constants)           */
   int32_t  integrator;   /* AT_DNS_AB2 (default) or AT_DNS_RK3 (AT_DNS_SYNC steps only:
                             the stages of an RK step would need a synchronisation each) */
+  void*    pool;         /* NULL, or device memory (256-byte aligned) the handle carves all
+                            of its buffers from -- e.g. a framework tensor; OOM if too small.
+                            Each handle (and each batch member) needs its own region. */
+  size_t   pool_bytes;   /* size of the pool                                            */
 } at_dns_config_t;
 
 /* kernel paths (same results up to rounding): the multi-pass path stores

@@ -162,3 +162,25 @@ def analyze(U, mu0=0.01, visc_exp=0.76, gamma=1.4, energy_form=ENERGY_TOTAL, vis
         "pdf_gradient": normalized_pdf(A[0][0] / math.sqrt(np.mean(A[0][0] ** 2)), bins, log=False),
         "enstrophy_slice": ens_f[mid] / ens_f.mean(),
     }
+
+
+def forced_stationary_state(solver, state, block=200, max_blocks=50, tol=0.02, mode="sync"):
+    """Advance a forced solver (at_dns.Solver with forcing on) from `state`
+    until the kinetic energy is statistically stationary: the mean of K over
+    the last block of steps differs from the previous block's by less than
+    `tol` (relative).  Stands in for the paper's forced stationary fields
+    (Sec. 4.2), which are not available.  Returns (state, K history per block)."""
+    solver.set_state(state)
+    history = []
+    prev = None
+    for _ in range(max_blocks):
+        ks = []
+        for _ in range(max(1, block // 10)):
+            solver.step(10, mode)
+            ks.append(solver.stats()["tke"])
+        mean = float(np.mean(ks))
+        history.append(mean)
+        if prev is not None and abs(mean - prev) <= tol * abs(prev):
+            break
+        prev = mean
+    return solver.get_state(), history

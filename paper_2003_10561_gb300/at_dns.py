@@ -46,7 +46,7 @@ class at_dns_config_t(ctypes.Structure):
         ("precision", ctypes.c_int32), ("stats_every", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("kernel_path", ctypes.c_int32), ("order", ctypes.c_int32),
         ("energy_form", ctypes.c_int32), ("visc_law", ctypes.c_int32), ("sutherland_s", ctypes.c_double),
-        ("integrator", ctypes.c_int32),
+        ("integrator", ctypes.c_int32), ("pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t),
     ]
 
 
@@ -318,6 +318,13 @@ def make_config(n=(32, 32, 32), pes=(1, 1, 1), precision="p64", stream=None, pat
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     if stream is not None:
         cfg.stream = stream
+    pool = kw.pop("pool", None)
+    if pool is not None:
+        if hasattr(pool, "data_ptr"):        # a device tensor lends its memory
+            cfg.pool = pool.data_ptr()
+            cfg.pool_bytes = pool.numel() * pool.element_size()
+        else:
+            cfg.pool = int(pool)
     for k, v in kw.items():
         if not hasattr(cfg, k):
             raise TypeError("unknown configuration field %r" % k)
@@ -369,6 +376,7 @@ class Solver:
 
     def __init__(self, n=(32, 32, 32), pes=(1, 1, 1), precision="p64", stream=None, path="auto", handle=None,
                  **kw):
+        self._pool = kw.get("pool")            # kept alive as long as the handle
         cfg = make_config(n, pes, precision, stream, path, **kw)
         self.cfg = cfg
         self.n = tuple(int(v) for v in n)

@@ -2,6 +2,7 @@
 // transfer, step orchestration and the small kernels around the step (delay
 // map, ring fill, forcing, wave speed, final reductions).
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -56,6 +57,9 @@ struct at_dns {
   long long stats_step = 0;
   double stats_time = 0.0;
   size_t bytes = 0;
+  // caller-provided device memory: every allocation is carved from it
+  char* pool = nullptr;
+  size_t pool_size = 0, pool_used = 0;
   std::string err;
   DevState* ds = nullptr;       // device copy of (n, first, cur)
   // captured one-step graphs per delay mode (replayed by at_dns_step)
@@ -316,6 +320,18 @@ int fail(at_dns* h, int code, const std::string& msg) {
 
 int dev_alloc(at_dns* h, void** p, size_t bytes) {
   if (bytes == 0) { *p = nullptr; return AT_DNS_OK; }
+  if (h->pool) {   // bump allocation from the caller's region, 256-byte aligned
+    const size_t at = (h->pool_used + 255) & ~(size_t)255;
+    if (at + bytes > h->pool_size) {
+      *p = nullptr;
+      return fail(h, AT_DNS_E_OOM, "device pool of " + std::to_string(h->pool_size) + " bytes is too small (needs " +
+                                       std::to_string(at + bytes) + " so far)");
+    }
+    *p = h->pool + at;
+    h->pool_used = at + bytes;
+    h->bytes += bytes;
+    return AT_DNS_OK;
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -630,7 +646,8 @@ int set_path(at_dns* h, bool fused, int TX, int TY, int ZC) {
     int rc;
     if ((rc = dev_alloc(h, &h->PQ, (size_t)kNumQ * N * h->ssize)) ||
         (rc = dev_alloc(h, &h->G, (size_t)kNumGrad * N * h->ssize))) {
-      if (h->PQ) { cudaFree(h->PQ); h->PQ = nullptr; }
+      if (h->PQ && !h->pool) cudaFree(h->PQ);
+      h->PQ = nullptr;
       return rc;
     }
   }
@@ -770,12 +787,17 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     else if (c.visc_law != AT_DNS_VISC_POWER && c.visc_law != AT_DNS_VISC_SUTHERLAND) bad = "unknown visc_law";
     else if (c.visc_law == AT_DNS_VISC_SUTHERLAND && !(c.sutherland_s > 0)) bad = "sutherland_s must be > 0";
     else if (c.integrator != AT_DNS_AB2 && c.integrator != AT_DNS_RK3) bad = "unknown integrator";
+    else if (c.pool && ((uintptr_t)c.pool & 255)) bad = "pool must be 256-byte aligned";
   }
   if (bad.empty() && (long long)c.n[0] * c.n[1] * c.n[2] >= (1LL << 31)) bad = "grids must hold fewer than 2^31 points";
   if (!bad.empty()) { g_create_error = bad; return AT_DNS_E_INVALID_ARG; }
 
   at_dns* h = new at_dns();
   h->cfg = c;
+  if (c.pool) {
+    h->pool = (char*)c.pool;
+    h->pool_size = c.pool_bytes;
+  }
   h->st = (cudaStream_t)c.stream;
   h->p64 = c.precision == AT_DNS_P64;
   h->comp = c.precision == AT_DNS_P32C;
@@ -1050,16 +1072,13 @@ int at_dns_get_delay_map(at_dns_t* h, int64_t step, int32_t mode, uint8_t* out) 
   if (step < 0) return fail(h, AT_DNS_E_INVALID_ARG, "step must be >= 0");
   const Geom& g = h->g;
   const int P = g.pes[0] * g.pes[1] * g.pes[2];
-  uint8_t* tmp = nullptr;
-  if ((rc = dev_alloc(h, (void**)&tmp, (size_t)P * 6))) return rc;
-  k_delay_map<<<nblk(P * 6), kBlock, 0, h->st>>>(tmp, P, step, nullptr, mode, h->cfg.max_delay, g.M + 1,
+  // the step's own map buffer: every step rebuilds it before use
+  k_delay_map<<<nblk(P * 6), kBlock, 0, h->st>>>(h->dmap, P, step, nullptr, mode, h->cfg.max_delay, g.M + 1,
                                                 h->cfg.comm_period, (uint32_t)h->cfg.seed,
                                                 (uint32_t)(h->cfg.seed >> 32));
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, (size_t)P * 6, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->dmap, (size_t)P * 6, cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-  cudaFree(tmp);
-  h->bytes -= (size_t)P * 6;
   if (e != cudaSuccess) return fail(h, AT_DNS_E_CUDA, std::string("delay map: ") + cudaGetErrorString(e));
   return AT_DNS_OK;
 }
@@ -1197,8 +1216,9 @@ void at_dns_destroy(at_dns_t* h) {
   drop_graphs(h);
   void* ptrs[] = {h->ds, h->U[0], h->U[1], h->Ulo[0], h->Ulo[1], h->PQ, h->G, h->Rprev, h->GH[0], h->GH[1], h->GH[2], h->ring[0], h->ring[1],
                   h->ring[2], h->stage, h->dmap, h->partial, h->sums, h->words, h->modes, h->fhat, h->fB, h->fX};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  if (!h->pool)
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
   clear_recs(h);
   delete h;
 }

@@ -48,7 +48,7 @@ int main(void) {
   F(at_dns_config_t, precision) F(at_dns_config_t, stream) F(at_dns_config_t, kernel_path)
   F(at_dns_config_t, order) F(at_dns_info_t, order)
   F(at_dns_config_t, energy_form) F(at_dns_config_t, visc_law) F(at_dns_config_t, sutherland_s)
-  F(at_dns_config_t, integrator)
+  F(at_dns_config_t, integrator) F(at_dns_config_t, pool) F(at_dns_config_t, pool_bytes)
   F(at_dns_stats_t, mom) F(at_dns_stats_t, min_p) F(at_dns_stats_t, unstable)
   F(at_dns_info_t, n_levels) F(at_dns_info_t, device_bytes) F(at_dns_info_t, kernels_per_step)
   F(at_dns_info_t, kernel_path) F(at_dns_info_t, tile)

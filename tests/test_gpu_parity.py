@@ -458,3 +458,27 @@ def test_rk3_steps_parity(lib, path, prec, tol):
     with pytest.raises(lib.AtDnsError) as ei:
         s.step(1, "random")
     assert ei.value.code == lib.AT_DNS_E_UNSUPPORTED
+
+
+def test_device_pool_from_a_tensor(lib):
+    """All device buffers carved from a caller's tensor: the same steps as a
+    handle that allocates its own memory, and OOM when the pool is too small."""
+    torch = pytest.importorskip("torch")
+    n, pes = (32, 32, 32), (2, 2, 2)
+    kw = dict(mu0=0.02, dt=3e-3, max_delay=2, seed=4)
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=8)
+    ref = make(lib, n, pes, **kw)
+    need = ref.info()["device_bytes"] + 5 * n[0] * n[1] * n[2] * 8 + (1 << 16)   # + host staging
+    pool = torch.empty(need + 4096, dtype=torch.uint8, device="cuda")
+    s = make(lib, n, pes, pool=pool, **kw)
+    for h in (ref, s):
+        h.set_state(U0)
+        h.step(10, "random")
+    assert np.array_equal(s.get_state(), ref.get_state())
+    assert s.info()["device_bytes"] <= pool.numel()
+    assert np.array_equal(s.delay_map(12, "random"), ref.delay_map(12, "random"))
+    s.close()
+    small = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lib.AtDnsError) as ei:
+        make(lib, n, pes, pool=small, **kw)
+    assert ei.value.code == lib.AT_DNS_E_OOM
