@@ -503,18 +503,19 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
 }
 
 // ---------------------------------------------------------------------------
-// Linear index of the point of this thread of k_main (blocks of 256).  FP64
-// form: when the block's 256 consecutive points are whole PE rows in x (PE
-// width 8, 16 or 32 divides 256 and the row length, so a full block starts at
-// a row start), the points next to the two x-faces of every PE row go to the
-// block's first warps and the interior points to the others,
-// so that the one-sided stencils of the mixed rule run in those warps only: a
-// divergent FP64 path costs the whole warp on the FP64 pipe.
+// Linear index of the point of this thread of k_main (blocks of 256).  When
+// the block's 256 consecutive points are whole PE rows in x (PE width 8, 16
+// or 32 divides 256 and the row length, so a full block starts at a row
+// start), the points next to the two x-faces of every PE row go to the
+// block's first warps and the interior points to the others, so that the
+// one-sided stencils of the mixed rule run in those warps only instead of
+// diverging in every warp (in the FP64 form a divergent path costs the whole
+// warp on the FP64 pipe).
 template <typename S>
 __device__ __forceinline__ long long main_point_index(const Geom& g) {
   const long long base = blockIdx.x * (long long)blockDim.x;
   int t = threadIdx.x;
-  if constexpr (sizeof(S) == 8) {
+  {
     const int nl = g.nl[0];
     if (g.pes[0] > 1 && (nl == 8 || nl == 16 || nl == 32) && base + 256 <= g.npts) {
       const int nb = 4 * (256 / nl);   // face-adjacent points of the block: whole warps
