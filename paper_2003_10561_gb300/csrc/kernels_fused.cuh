@@ -1,10 +1,11 @@
 // Fused AT-DNS step kernel: one pass over U per step.
 //
 // A CTA owns a TX x TY tile of one PE in x and y and marches in z through a
-// chunk of ZC planes of one PE.  A shared-memory window holds nine planes
-// (z-4 .. z+4) of six per-point fields -- u, v, w, T, rho and H, the quantity
-// whose product with u_d is the fifth flux (E + p, or rho e) -- on the
-// tile plus a two-cell halo in x and y.  Halo cells beyond a PE face hold the
+// chunk of ZC planes of one PE.  A shared-memory window holds, on the tile
+// plus a two-cell halo in x and y, u, v, w for nine planes (z-4 .. z+4), T for
+// seven (z-2 .. z+4) and rho and H -- the quantity whose product with u_d is
+// the fifth flux (E + p, or rho e) -- for five (z .. z+4): each field for as
+// many planes as its stencils reach.  Halo cells beyond a PE face hold the
 // AT ghost values of that direction (Table B extrapolation done by k_ghost),
 // planes beyond a PE z-face hold the z ghosts, so every stencil of Sec. 2.1 is
 // a plain read of the window:
@@ -14,9 +15,12 @@
 //     the column's z fluxes are carried in a five-plane register queue;
 //   * mixed derivatives: the central cross stencil D_a(D_b f) inside, and at
 //     PE-boundary points the average of the PE-local derivative in a of the AT
-//     derivative in b and vice versa -- the inner AT derivatives are formed from
-//     the window on the fly (the one-sided reach of 4 planes in z is why the
-//     window is nine planes deep).
+//     derivative in b and vice versa.  The AT derivatives that the x- and
+//     y-stencils take are formed once per plane into shared arrays (on
+//     x-extended rows and y-extended columns, like the fluxes), so every lane
+//     runs the same five-tap stencil of its own kind; the z-stencils take the
+//     inner derivatives from the window (the one-sided reach of 4 planes in z
+//     is why u, v, w are kept for nine planes).
 // Then the assembly, forcing, AB2 update, ring write and statistics of k_main.
 // No per-point work arrays (derived fields, gradients) exist on this path.
 //
@@ -27,24 +31,36 @@
 
 namespace atdns {
 
-constexpr int kWinPlanes = 9;
-constexpr int kWinFields = 6;
+constexpr int kWinPlanes = 9;   // u, v, w: planes z-4 .. z+4
+constexpr int kWinT = 7;        // T: planes z-2 .. z+4
+constexpr int kWinR = 5;        // rho, H: planes z .. z+4
 enum WinField { WF_U = 0, WF_V, WF_W, WF_T, WF_R, WF_H };
+// per-plane AT derivatives for the mixed rule: on x-extended rows (taken by
+// the x-stencils) and on y-extended columns (taken by the y-stencils)
+enum XRField { XR_VY = 0, XR_WZ, XR_UY, XR_UZ };
+enum YCField { YC_VX = 0, YC_UX, YC_WZ, YC_VZ };
 
 template <int TX, int TY>
 struct TileShape {
   static constexpr int CX = TX + 4, CY = TY + 4, CELLS = CX * CY;
-  static constexpr int PLANE = kWinFields * CELLS;     // elements per window plane
   static constexpr int THREADS = TX * TY;
+  // element offsets of the shared-memory regions
+  static constexpr int OFF_A = 0;                                   // [9][3][CELLS]
+  static constexpr int OFF_T = OFF_A + kWinPlanes * 3 * CELLS;      // [7][CELLS]
+  static constexpr int OFF_R = OFF_T + kWinT * CELLS;               // [5][2][CELLS]
+  static constexpr int OFF_FX = OFF_R + kWinR * 2 * CELLS;          // [5][TY][CX]
+  static constexpr int OFF_FY = OFF_FX + 5 * TY * CX;               // [5][CY][TX]
+  static constexpr int OFF_XR = OFF_FY + 5 * CY * TX;               // [4][TY][CX]
+  static constexpr int OFF_YC = OFF_XR + 4 * TY * CX;               // [4][CY][TX]
+  static constexpr int TOTAL = OFF_YC + 4 * CY * TX;
 };
 
 template <typename S>
 inline size_t fused_smem_bytes(int TX, int TY) {
-  // nine window planes, then the x fluxes of the current plane on TY rows of
-  // TX+4 cells and the y fluxes on TY+4 rows of TX cells; at the end the
-  // window is the reduction scratch (kNumStat * (NT + 1) doubles)
-  const size_t win = ((size_t)kWinPlanes * kWinFields * (TX + 4) * (TY + 4) +
-                      5 * (size_t)TY * (TX + 4) + 5 * (size_t)(TY + 4) * TX) * sizeof(S);
+  // the window, the flux and derivative arrays; at the end the window is the
+  // reduction scratch (kNumStat * (NT + 1) doubles)
+  const size_t CX = TX + 4, CY = TY + 4, CELLS = CX * CY;
+  const size_t win = ((kWinPlanes * 3 + kWinT + kWinR * 2) * CELLS + 9 * (size_t)TY * CX + 9 * CY * TX) * sizeof(S);
   const size_t red = (size_t)kNumStat * ((TX * TY > 256 ? 512 : 256) + 1) * sizeof(double);
   return win > red ? win : red;
 }
@@ -132,10 +148,12 @@ __device__ __forceinline__ void fused_fetch_plane(const Geom& g, const StepArgs<
   }
 }
 
-// Window plane (element offset `pbase`) from fetched raw values: u, v, w, T,
-// rho and H from the conserved variables, or the ghost values as they are.
+// Window plane from fetched raw values: u, v, w, T, rho and H from the
+// conserved variables, or the ghost values as they are; bA, bT, bR are the
+// element offsets of the plane's slots in the three window regions.
 template <typename S, int TX, int TY>
-__device__ __forceinline__ void fused_store_plane(const Coef<S>& K, const PlaneRaw<S, TX, TY>& P, S* win, int pbase) {
+__device__ __forceinline__ void fused_store_plane(const Coef<S>& K, const PlaneRaw<S, TX, TY>& P, S* win, int bA,
+                                                  int bT, int bR) {
   using T_ = TileShape<TX, TY>;
   const int tid = threadIdx.y * TX + threadIdx.x;
 #pragma unroll
@@ -159,41 +177,49 @@ __device__ __forceinline__ void fused_store_plane(const Coef<S>& K, const PlaneR
       w = P.v[it][2];
       T = P.v[it][3];
     }
-    S* cell = win + pbase + c;
-    cell[WF_U * T_::CELLS] = u;
-    cell[WF_V * T_::CELLS] = v;
-    cell[WF_W * T_::CELLS] = w;
-    cell[WF_T * T_::CELLS] = T;
-    cell[WF_R * T_::CELLS] = r;
-    cell[WF_H * T_::CELLS] = H;
+    win[bA + c] = u;
+    win[bA + T_::CELLS + c] = v;
+    win[bA + 2 * T_::CELLS + c] = w;
+    win[bT + c] = T;
+    win[bR + c] = r;
+    win[bR + T_::CELLS + c] = H;
   }
 }
 
-// Fill window plane zp (stored at element offset `pbase`).
+// Slots of a window plane: `q` counts planes from the chunk's first window
+// plane (z_start - 4); each region is a ring of its own depth.
+template <int TX, int TY>
+__device__ __forceinline__ int slot_A(int q) { return TileShape<TX, TY>::OFF_A + (q % kWinPlanes) * 3 * TileShape<TX, TY>::CELLS; }
+template <int TX, int TY>
+__device__ __forceinline__ int slot_T(int q) { return TileShape<TX, TY>::OFF_T + (q % kWinT) * TileShape<TX, TY>::CELLS; }
+template <int TX, int TY>
+__device__ __forceinline__ int slot_R(int q) { return TileShape<TX, TY>::OFF_R + (q % kWinR) * 2 * TileShape<TX, TY>::CELLS; }
+
+// Fill window plane q (plane z_start - 4 + q).
 template <typename S, int TX, int TY>
 __device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K, const StepArgs<S>& A,
-                                                 const S* __restrict__ U, const FusedGeo& F, S* win, int pbase,
+                                                 const S* __restrict__ U, const FusedGeo& F, S* win, int q,
                                                  int zp) {
   PlaneRaw<S, TX, TY> P;
   fused_fetch_plane<S, TX, TY>(g, A, U, F, zp, P);
-  fused_store_plane<S, TX, TY>(K, P, win, pbase);
+  fused_store_plane<S, TX, TY>(K, P, win, slot_A<TX, TY>(q), slot_T<TX, TY>(q), slot_R<TX, TY>(q));
 }
 
-// Inviscid flux component e of direction d of the window cell at element
-// offset `at` (plane base + cell): rho u_d, rho u_i u_d + p delta_id, H u_d,
-// with p = rho T / gamma.
+// Inviscid flux component e of direction d of one window cell (aA, aT, aR:
+// element offsets of the cell in its plane's slots): rho u_d,
+// rho u_i u_d + p delta_id, H u_d, with p = rho T / gamma.
 template <typename S, int TX, int TY>
-__device__ __forceinline__ S cell_flux(const Coef<S>& K, const S* win, int at, int d, int e) {
+__device__ __forceinline__ S cell_flux(const Coef<S>& K, const S* win, int aA, int aT, int aR, int d, int e) {
   using T_ = TileShape<TX, TY>;
-  const S r = win[at + WF_R * T_::CELLS];
-  const S ud = win[at + (WF_U + d) * T_::CELLS];
+  const S r = win[aR];
+  const S ud = win[aA + d * T_::CELLS];
   if (e == 0) return r * ud;
-  if (e == 4) return win[at + WF_H * T_::CELLS] * ud;
+  if (e == 4) return win[aR + T_::CELLS] * ud;
   const int i = e - 1;
   const S rud = r * ud;
-  const S ui = win[at + (WF_U + i) * T_::CELLS];
+  const S ui = win[aA + i * T_::CELLS];
   if (i != d) return rud * ui;
-  return fma(rud, ui, r * win[at + WF_T * T_::CELLS] * K.inv_gamma);
+  return fma(rud, ui, r * win[aT] * K.inv_gamma);
 }
 
 // PE-local first-derivative stencil kind of the Sec. 2.1 mixed rule at local
@@ -207,16 +233,23 @@ __device__ __forceinline__ int local_kind(int pes, int li, int nl) {
   return 4;
 }
 
-// The window seen from one point: plane bases for offsets -4..4 (already
-// including the point's cell), so a value at (dx, dy, dz) of field f is one
-// load at a constant offset.
+// The window seen from one point: element offsets of the point's cell in the
+// u, v, w planes z-4 .. z+4, the T planes z-2 .. z+2 and the rho, H plane z,
+// so that a value at (dx, dy, dz) of a field is one load at a constant offset.
 template <typename S, int TX, int TY>
 struct PointWin {
   using T_ = TileShape<TX, TY>;
   const S* win;                 // the shared-memory window
-  int pb[kWinPlanes];           // element offsets of the point's cell in planes z-4 .. z+4
+  int pA[kWinPlanes];           // u (v, w at + CELLS, + 2 CELLS) in planes z-4 .. z+4
+  int pT[5];                    // T in planes z-2 .. z+2
+  int pR;                       // rho (H at + CELLS) in plane z
+  int qa0;                      // window-plane count of plane z-4 (slot arithmetic)
+  int cell;                     // the point's cell within a plane
   __device__ __forceinline__ S at(int f, int dx, int dy, int dz) const {
-    return win[pb[4 + dz] + f * T_::CELLS + dy * T_::CX + dx];
+    const int o = dy * T_::CX + dx;
+    if (f <= WF_W) return win[pA[4 + dz] + f * T_::CELLS + o];
+    if (f == WF_T) return win[pT[2 + dz] + o];
+    return win[pR + (f - WF_R) * T_::CELLS + o];
   }
   // value shifted by m along direction d
   __device__ __forceinline__ S sh(int f, int d, int m, int dx = 0, int dy = 0, int dz = 0) const {
@@ -227,66 +260,36 @@ struct PointWin {
     return fma(K.c1[b], sh(f, b, 1, dx, dy, dz) - sh(f, b, -1, dx, dy, dz),
                K.c2[b] * (sh(f, b, 2, dx, dy, dz) - sh(f, b, -2, dx, dy, dz)));
   }
-  // plane base of the point's cell at z offset dz (window slot arithmetic;
-  // dz may be a run-time value)
-  __device__ __forceinline__ int plane_at(int s0, int dz) const {
-    int sl = s0 + 4 + dz;
-    sl = sl >= kWinPlanes ? sl - kWinPlanes : (sl < 0 ? sl + kWinPlanes : sl);
-    return sl * T_::PLANE + (pb[4] - ((s0 + 4) % kWinPlanes) * T_::PLANE);
-  }
-  // 12 dx_outer times the PE-local derivative along `outer` (stencil `kind`:
-  // five taps at offsets st + 0..4 with coefficients coef[kind]) of the AT
-  // derivative along `in`.  kind may differ between lanes (x and y), or be
-  // warp-uniform (z); every lane runs the same five taps.
-  __device__ __forceinline__ S local_of_d1(const Coef<S>& K, const S (*coef)[5], int f, int outer, int in, int kind,
-                                           int s0) const {
-    const int st = kind == 0 ? -2 : (kind == 1 ? 0 : (kind == 2 ? -1 : (kind == 3 ? -3 : -4)));
+  // 12 dz times the PE-local derivative along z (stencil `kind`, warp-uniform:
+  // five taps at planes st + 0..4) of the AT derivative of u, v or w along
+  // `in` (x or y); the central kind runs its four nonzero taps only.
+  __device__ __forceinline__ S zlocal_of_d1(const Coef<S>& K, const S (*coef)[5], int f, int in, int kind) const {
+    const int sk = in == 0 ? 1 : T_::CX;
+    auto dv = [&](int o) {   // inner derivative at plane z + o (o may be a run-time value)
+      const S* q = win + slot_A<TX, TY>(qa0 + 4 + o) + f * T_::CELLS + cell;
+      return fma(K.c1[in], q[sk] - q[-sk], K.c2[in] * (q[2 * sk] - q[-2 * sk]));
+    };
+    if (kind == 0) return fma(S(8), dv(1) - dv(-1), dv(-2) - dv(2));
+    const int st = kind == 1 ? 0 : (kind == 2 ? -1 : (kind == 3 ? -3 : -4));
     S acc = S(0);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      const int o = st + i;
-      const S c = coef[kind][i];
-      S dv;
-      if (outer == 2) {
-        const int base = plane_at(s0, o);
-        auto v = [&](int k) {
-          return win[base + f * T_::CELLS + (in == 1 ? k * T_::CX : k)];
-        };
-        dv = fma(K.c1[in], v(1) - v(-1), K.c2[in] * (v(2) - v(-2)));
-      } else {
-        const int co = outer == 0 ? o : o * T_::CX;   // cell offset of the tap
-        if (in == 2) {
-          dv = fma(K.c1[2], win[pb[5] + f * T_::CELLS + co] - win[pb[3] + f * T_::CELLS + co],
-                   K.c2[2] * (win[pb[6] + f * T_::CELLS + co] - win[pb[2] + f * T_::CELLS + co]));
-        } else {
-          const int sk = in == 0 ? 1 : T_::CX;
-          const S* q = win + pb[4] + f * T_::CELLS + co;
-          dv = fma(K.c1[in], q[sk] - q[-sk], K.c2[in] * (q[2 * sk] - q[-2 * sk]));
-        }
-      }
-      acc = fma(c, dv, acc);
-    }
+    for (int i = 0; i < 5; ++i) acc = fma(coef[kind][i], dv(st + i), acc);
     return acc;
   }
-  // d/dx_a (d f/dx_b) by the three-step rule of Sec. 2.1: the central D_a of
-  // the AT derivative in b where both stencils fit in the PE, the average of
-  // the two PE-local derivatives elsewhere.  A warp without boundary points
-  // takes the central stencil only; otherwise every lane runs the table-driven
-  // taps (kind 0 is the central stencil) and boundary lanes average.
-  __device__ __forceinline__ S mixed(const Coef<S>& K, const S (*coef)[5], int f, int a, int b,
-                                     const int (&kind)[3], int s0) const {
-    const bool bnd = kind[a] != 0 || kind[b] != 0;
-    if (!__any_sync(__activemask(), bnd)) {
-      auto inner = [&](int off) {
-        return d1(K, f, b, a == 0 ? off : 0, a == 1 ? off : 0, a == 2 ? off : 0);
-      };
-      return K.hloc[a] * fma(S(8), inner(1) - inner(-1), inner(-2) - inner(2));
-    }
-    const S pa = K.hloc[a] * local_of_d1(K, coef, f, a, b, kind[a], s0);
-    const S pb_ = K.hloc[b] * local_of_d1(K, coef, f, b, a, kind[b], s0);
-    return bnd ? S(0.5) * (pa + pb_) : pa;
-  }
 };
+
+// Five-tap PE-local stencil (kind as in the coefficient table, taps in
+// ascending offset from st) applied to a per-plane derivative array with
+// stride `step` between taps, centred at element `at`.
+template <typename S>
+__device__ __forceinline__ S local_taps(const S (*coef)[5], const S* arr, int at, int step, int kind) {
+  const int st = kind == 0 ? -2 : (kind == 1 ? 0 : (kind == 2 ? -1 : (kind == 3 ? -3 : -4)));
+  const S* q = arr + at + st * step;
+  S acc = S(0);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) acc = fma(coef[kind][i], q[i * step], acc);
+  return acc;
+}
 
 // Per-thread statistics accumulators over the thread's column of one z chunk
 // (at most 64 points), in the kernel's type; they reach FP64 before crossing
@@ -342,41 +345,47 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
   S wmax = S(0), rmin = S(3.0e38), pmin = S(3.0e38);
   unsigned health = 0;
 
-  // window slot of plane zs - 4 is 0; plane zs - 4 + k lives in slot k mod 9
-  for (int k = 0; k < 8; ++k) fused_load_plane<S, TX, TY>(g, K, A, D.U, F, win, k * T_::PLANE, zs - 4 + k);
-  PlaneRaw<S, TX, TY> pf;                       // plane z + 4, fetched one iteration ahead
-  fused_fetch_plane<S, TX, TY>(g, A, D.U, F, zs + 4, pf);
-
   const int li_x = x - F.base[0], li_y = y - F.base[1];
   const int kind_x = local_kind(g.pes[0], li_x, g.nl[0]), kind_y = local_kind(g.pes[1], li_y, g.nl[1]);
   const S a0sum = K.a0[0] + K.a0[1] + K.a0[2];
   const int tid = ty * TX + tx;
-  S* FX = win + kWinPlanes * T_::PLANE;        // [5][TY][TX+4]
-  S* FY = FX + 5 * TY * T_::CX;                // [5][TY+4][TX]
+  S* FX = win + T_::OFF_FX;                    // [5][TY][CX]
+  S* FY = win + T_::OFF_FY;                    // [5][CY][TX]
+  S* XR = win + T_::OFF_XR;                    // [4][TY][CX]
+  S* YC = win + T_::OFF_YC;                    // [4][CY][TX]
   const long long qsx = 4LL * g.pes[0] * g.plane[0], qsy = 4LL * g.pes[1] * g.plane[1];
   const long long qsz = 4LL * g.pes[2] * g.plane[2];
 
-  // z fluxes of this column at one plane (z ghosts beyond a PE z-face)
-  auto zflux = [&](int zp, int slot, S (&out)[5]) {
+  // z fluxes of this column at window plane q = zp - zs + 4 (z ghosts beyond
+  // a PE z-face)
+  auto zflux = [&](int zp, int q, S (&out)[5]) {
     if (F.beyond(g, 2, zp)) {
       const long long gi = (long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] + (long long)y * g.n[0] + x;
 #pragma unroll
       for (int e = 0; e < 5; ++e) out[e] = A.GH[2][e * qsz + gi];
     } else {
+      const int aA = slot_A<TX, TY>(q) + cell, aT = slot_T<TX, TY>(q) + cell, aR = slot_R<TX, TY>(q) + cell;
 #pragma unroll
-      for (int e = 0; e < 5; ++e) out[e] = cell_flux<S, TX, TY>(K, win, slot * T_::PLANE + cell, 2, e);
+      for (int e = 0; e < 5; ++e) out[e] = cell_flux<S, TX, TY>(K, win, aA, aT, aR, 2, e);
     }
   };
+
+  // window planes q = 0 .. 7 (z = zs-4 .. zs+3); the z-flux queue needs rho
+  // and H of planes 2 .. 5 before planes 6 and 7 reuse their slots
+  for (int q = 0; q < 6; ++q) fused_load_plane<S, TX, TY>(g, K, A, D.U, F, win, q, zs - 4 + q);
   // queue of the z fluxes at planes z-2, z-1, z, z+1, z+2
   S qz[5][5];
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < 4; ++k) zflux(zs - 2 + k, 2 + k, qz[k]);
+  __syncthreads();
+  for (int q = 6; q < 8; ++q) fused_load_plane<S, TX, TY>(g, K, A, D.U, F, win, q, zs - 4 + q);
+  PlaneRaw<S, TX, TY> pf;                       // plane z + 4, fetched one iteration ahead
+  fused_fetch_plane<S, TX, TY>(g, A, D.U, F, zs + 4, pf);
 
-  int s0 = 0;                                  // slot of plane z - 4
   for (int z = zs; z < zs + ZC; ++z) {
-    const int snew = s0 + 8 >= kWinPlanes ? s0 + 8 - kWinPlanes : s0 + 8;   // slot of plane z + 4
-    fused_store_plane<S, TX, TY>(K, pf, win, snew * T_::PLANE);
+    const int q = z - zs + 4;                  // window-plane count of plane z
+    fused_store_plane<S, TX, TY>(K, pf, win, slot_A<TX, TY>(q + 4), slot_T<TX, TY>(q + 4), slot_R<TX, TY>(q + 4));
     __syncthreads();
     if (z + 1 < zs + ZC) fused_fetch_plane<S, TX, TY>(g, A, D.U, F, z + 5, pf);
     // the point's conserved variables and R^{n-1}: loaded here so that the
@@ -387,26 +396,41 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     S Rp[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) Rp[v] = needs_rprev(A, D) ? A.Rprev[v * N + idx] : S(0);
-    // fluxes of the current plane: x on x-extended rows, y on y-extended columns
+    // fluxes of the current plane (x on x-extended rows, y on y-extended
+    // columns), and on the same cells the AT derivatives the mixed rule's x-
+    // and y-stencils take
     {
-      const int sz = s0 + 4 >= kWinPlanes ? s0 + 4 - kWinPlanes : s0 + 4;   // slot of plane z
-      const int pbz = sz * T_::PLANE;
+      const int bA = slot_A<TX, TY>(q), bT = slot_T<TX, TY>(q), bR = slot_R<TX, TY>(q);
+      const int bAm1 = slot_A<TX, TY>(q - 1), bAp1 = slot_A<TX, TY>(q + 1);
+      const int bAm2 = slot_A<TX, TY>(q - 2), bAp2 = slot_A<TX, TY>(q + 2);
+      // d/dz of field f (0 u, 2 w) at window cell cw of plane z
+      auto ddz = [&](int f, int cw) {
+        const int o = f * T_::CELLS + cw;
+        return fma(K.c1[2], win[bAp1 + o] - win[bAm1 + o], K.c2[2] * (win[bAp2 + o] - win[bAm2 + o]));
+      };
 #pragma unroll
       for (int c0 = 0; c0 < TY * T_::CX; c0 += T_::THREADS) {
         const int c = c0 + tid;
         if (c < TY * T_::CX) {
           const int r = c / T_::CX, cxw = c - r * T_::CX;
           const int xg = F.x0 - 2 + cxw, yg = F.y0 + r;
+          const int cw = (r + 2) * T_::CX + cxw;
           if (F.beyond(g, 0, xg)) {
             const long long gi = (long long)(4 * F.pe[0] + F.ghost_slot(g, 0, xg)) * g.plane[0] +
                                  (long long)z * g.n[1] + yg;
 #pragma unroll
             for (int e = 0; e < 5; ++e) FX[e * TY * T_::CX + c] = A.GH[0][e * qsx + gi];
           } else {
-            const int at = pbz + (r + 2) * T_::CX + cxw;
 #pragma unroll
-            for (int e = 0; e < 5; ++e) FX[e * TY * T_::CX + c] = cell_flux<S, TX, TY>(K, win, at, 0, e);
+            for (int e = 0; e < 5; ++e) FX[e * TY * T_::CX + c] = cell_flux<S, TX, TY>(K, win, bA + cw, bT + cw, bR + cw, 0, e);
           }
+          // (cells beyond the x-face are never read by the PE-local x-stencils)
+          const S* vq = win + bA + T_::CELLS + cw;
+          const S* uq = win + bA + cw;
+          XR[XR_VY * TY * T_::CX + c] = fma(K.c1[1], vq[T_::CX] - vq[-T_::CX], K.c2[1] * (vq[2 * T_::CX] - vq[-2 * T_::CX]));
+          XR[XR_UY * TY * T_::CX + c] = fma(K.c1[1], uq[T_::CX] - uq[-T_::CX], K.c2[1] * (uq[2 * T_::CX] - uq[-2 * T_::CX]));
+          XR[XR_WZ * TY * T_::CX + c] = ddz(2, cw);
+          XR[XR_UZ * TY * T_::CX + c] = ddz(0, cw);
         }
       }
 #pragma unroll
@@ -415,32 +439,39 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
         if (c < (TY + 4) * TX) {
           const int r = c / TX, cxl = c - r * TX;
           const int xg = F.x0 + cxl, yg = F.y0 - 2 + r;
+          const int cw = r * T_::CX + cxl + 2;
           if (F.beyond(g, 1, yg)) {
             const long long gi = (long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] +
                                  (long long)z * g.n[0] + xg;
 #pragma unroll
             for (int e = 0; e < 5; ++e) FY[e * (TY + 4) * TX + c] = A.GH[1][e * qsy + gi];
           } else {
-            const int at = pbz + r * T_::CX + cxl + 2;
 #pragma unroll
-            for (int e = 0; e < 5; ++e) FY[e * (TY + 4) * TX + c] = cell_flux<S, TX, TY>(K, win, at, 1, e);
+            for (int e = 0; e < 5; ++e) FY[e * (TY + 4) * TX + c] = cell_flux<S, TX, TY>(K, win, bA + cw, bT + cw, bR + cw, 1, e);
           }
+          const S* vq = win + bA + T_::CELLS + cw;
+          const S* uq = win + bA + cw;
+          YC[YC_VX * (TY + 4) * TX + c] = fma(K.c1[0], vq[1] - vq[-1], K.c2[0] * (vq[2] - vq[-2]));
+          YC[YC_UX * (TY + 4) * TX + c] = fma(K.c1[0], uq[1] - uq[-1], K.c2[0] * (uq[2] - uq[-2]));
+          YC[YC_WZ * (TY + 4) * TX + c] = ddz(2, cw);
+          YC[YC_VZ * (TY + 4) * TX + c] = ddz(1, cw);
         }
       }
       // z fluxes of this column at plane z+2 enter the queue
-      const int s2 = s0 + 6 >= kWinPlanes ? s0 + 6 - kWinPlanes : s0 + 6;
-      zflux(z + 2, s2, qz[4]);
+      zflux(z + 2, q + 2, qz[4]);
     }
     __syncthreads();
     PointWin<S, TX, TY> W;
     W.win = win;
+    W.cell = cell;
+    W.qa0 = q - 4;
 #pragma unroll
-    for (int k = 0; k < kWinPlanes; ++k) {
-      const int sl = s0 + k >= kWinPlanes ? s0 + k - kWinPlanes : s0 + k;
-      W.pb[k] = sl * T_::PLANE + cell;
-    }
+    for (int k = 0; k < kWinPlanes; ++k) W.pA[k] = slot_A<TX, TY>(q - 4 + k) + cell;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) W.pT[k] = slot_T<TX, TY>(q - 2 + k) + cell;
+    W.pR = slot_R<TX, TY>(q) + cell;
     const int li_z = z - F.base[2];
-    const int kind[3] = {kind_x, kind_y, local_kind(g.pes[2], li_z, g.nl[2])};
+    const int kind_z = local_kind(g.pes[2], li_z, g.nl[2]);
 
     // ---- inviscid flux divergence: -sum_d D_d F_d (ghost fluxes already in
     // the flux arrays / queue across PE faces)
@@ -478,15 +509,39 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
       lap[q] = accq;
     }
 
-    // ---- d theta/dx_i = d2 u_i/dx_i^2 + sum_{k != i} d/dx_i (d u_k/dx_k)
+    // ---- d theta/dx_i = d2 u_i/dx_i^2 + sum_{k != i} d/dx_i (d u_k/dx_k), the
+    // mixed terms by the three-step rule (Sec. 2.1): part a is the PE-local
+    // derivative along a of the AT derivative along b, part b the one along b
+    // of the derivative along a; inside both stencils' reach the term is the
+    // central part a, elsewhere the average of the two parts
     S gth[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      S s = d2diag[i];
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (k != i) s += W.mixed(K, coef, WF_U + k, i, k, kind, s0);
-      gth[i] = s;
+    {
+      const int ax = ty * T_::CX + tx + 2;          // the point in the x-row arrays
+      const int ay = (ty + 2) * TX + tx;            // the point in the y-column arrays
+      const int sxr = TY * T_::CX, syc = (TY + 4) * TX;
+      auto mix = [&](S pa, S pb, bool bnd) { return bnd ? S(0.5) * (pa + pb) : pa; };
+      const bool bxy = kind_x != 0 || kind_y != 0, bxz = kind_x != 0 || kind_z != 0, byz = kind_y != 0 || kind_z != 0;
+      // d/dx (dv/dy)
+      const S m_xy = mix(K.hloc[0] * local_taps(coef, XR + XR_VY * sxr, ax, 1, kind_x),
+                         K.hloc[1] * local_taps(coef, YC + YC_VX * syc, ay, TX, kind_y), bxy);
+      // d/dy (du/dx)
+      const S m_yx = mix(K.hloc[1] * local_taps(coef, YC + YC_UX * syc, ay, TX, kind_y),
+                         K.hloc[0] * local_taps(coef, XR + XR_UY * sxr, ax, 1, kind_x), bxy);
+      // d/dx (dw/dz): part b along z needs the window (planes z-4 .. z+4)
+      const S pa_xz = K.hloc[0] * local_taps(coef, XR + XR_WZ * sxr, ax, 1, kind_x);
+      const S pb_xz = __any_sync(__activemask(), bxz) ? K.hloc[2] * W.zlocal_of_d1(K, coef, WF_W, 0, kind_z) : S(0);
+      // d/dz (du/dx)
+      const S pa_zx = K.hloc[2] * W.zlocal_of_d1(K, coef, WF_U, 0, kind_z);
+      const S pb_zx = K.hloc[0] * local_taps(coef, XR + XR_UZ * sxr, ax, 1, kind_x);
+      // d/dy (dw/dz)
+      const S pa_yz = K.hloc[1] * local_taps(coef, YC + YC_WZ * syc, ay, TX, kind_y);
+      const S pb_yz = __any_sync(__activemask(), byz) ? K.hloc[2] * W.zlocal_of_d1(K, coef, WF_W, 1, kind_z) : S(0);
+      // d/dz (dv/dy)
+      const S pa_zy = K.hloc[2] * W.zlocal_of_d1(K, coef, WF_V, 1, kind_z);
+      const S pb_zy = K.hloc[1] * local_taps(coef, YC + YC_VZ * syc, ay, TX, kind_y);
+      gth[0] = d2diag[0] + m_xy + mix(pa_xz, pb_xz, bxz);
+      gth[1] = d2diag[1] + m_yx + mix(pa_yz, pb_yz, byz);
+      gth[2] = d2diag[2] + mix(pa_zx, pb_zx, bxz) + mix(pa_zy, pb_zy, byz);
     }
 
     // ---- point values
@@ -607,7 +662,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
         kp = min(kp, okey(p));
       }
     }
-    s0 = s0 + 1 >= kWinPlanes ? 0 : s0 + 1;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
