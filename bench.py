@@ -48,9 +48,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max S
 # 128^3 with 4x4x4 PEs of 32^3 (profiles/k_main_fp64_128cube_4x4x4pes.md,
 # profiles/k_fused_fp32_128cube_4x4x4pes.md), scaled by the point count to the
 # 256^3 workload (same PE size; traffic grows with the points):
-# k_main<double, 2> 701.1 MB + 462.6 MB, k_fused<float, 32, 8> 113.1 MB + 53.3 MB
+# k_main<double, 2> 701.1 MB + 462.6 MB, k_fused<float, 32, 8> 112.5 MB + 49.8 MB
 K_MAIN_FP64_TRAFFIC_256 = 8 * (701.0944e6 + 462.572032e6)
-K_FUSED_FP32_TRAFFIC_256 = 8 * (113.08416e6 + 53.325824e6)
+K_FUSED_FP32_TRAFFIC_256 = 8 * (112.545536e6 + 49.810176e6)
 
 
 def set_workload(n, pes):
@@ -471,7 +471,7 @@ def leg_report(r, world, pts, steps, pk):
         achieved = algorithmic_bytes(4, order) * pts / t_main / 1e9
         kname = "k_fused" if r["path"] == "fused" else "k_main"
         traffic = K_FUSED_FP32_TRAFFIC_256 if (order == 4 and N == 256 and PES == 8 and r["path"] == "fused"
-                                               and list(r["tile"]) == [32, 8, 32]) else None
+                                               and list(r["tile"]) == [32, 8, 32] and K_FUSED_FP32_TRAFFIC_256) else None
         roof = {"bound": "hbm", "kernel": "%s (FP32, order %d)" % (kname, order), "achieved": achieved,
                 "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0),
                 "traffic": traffic, "bytes_per_point": algorithmic_bytes(4, order)}

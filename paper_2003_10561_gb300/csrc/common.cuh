@@ -93,6 +93,12 @@ struct Coef {
   S dt;
   int eform, vlaw;                // energy form and viscosity law (Phys)
   S suth_s, suth_c;               // Sutherland S and mu0 (1 + S)
+  // power law with omega = p/q (q <= 64): g = T^(omega - 1) is the root of
+  // g^q T^(q - p) = 1 (vq = q, va = q - p); vrat = 0 when omega is no such
+  // fraction
+  int vrat, vq, va;
+  float vexpm1;                   // omega - 1 (FP32 start value)
+  S vinvq, vc2, mu0omega;         // 1/q, (q + 1)/(2 q^2), mu0 omega
 };
 
 template <typename S>
@@ -119,6 +125,22 @@ inline Coef<S> make_coef(const Geom& g, const Phys& ph, double dt) {
   c.vlaw = ph.vlaw;
   c.suth_s = (S)ph.suth_s;
   c.suth_c = (S)(ph.mu0 * (1.0 + ph.suth_s));
+  c.vrat = 0;
+  c.vq = 1;
+  c.va = 0;
+  for (int q = 1; q <= 64 && !ph.vlaw; ++q) {
+    const double pq = ph.omega * q, pr = std::nearbyint(pq);
+    if (std::fabs(pq - pr) <= 2e-15 * q && pr >= 0.0 && pr <= q) {
+      c.vrat = 1;
+      c.vq = q;
+      c.va = q - (int)pr;
+      break;
+    }
+  }
+  c.vexpm1 = (float)(ph.omega - 1.0);
+  c.vinvq = (S)(1.0 / c.vq);
+  c.vc2 = (S)((c.vq + 1.0) / (2.0 * c.vq * c.vq));
+  c.mu0omega = (S)(ph.mu0 * ph.omega);
   return c;
 }
 
@@ -344,12 +366,36 @@ __device__ __forceinline__ S pressure(const Coef<S>& K, S m0, S m1, S m2, S u, S
 
 // Viscosity and its temperature derivative (Sec. 2): power law mu0 T^omega,
 // or Sutherland mu0 T^(3/2) (1 + S) / (T + S).
+// x^e for a small non-negative integer e (uniform over the grid), by squaring.
+template <typename S>
+__device__ __forceinline__ S ipow(S x, int e) {
+  S r = S(1);
+  while (e) {
+    if (e & 1) r *= x;
+    e >>= 1;
+    if (e) x *= x;
+  }
+  return r;
+}
+
 template <typename S>
 __device__ __forceinline__ void viscosity(const Coef<S>& K, S T, S& mu, S& dmudT) {
   if (K.vlaw) {
     const S inv = S(1) / (T + K.suth_s);
     mu = K.suth_c * T * sqrt(T) * inv;
     dmudT = mu * (S(1.5) / T - inv);
+  } else if (sizeof(S) == 8 && K.vrat && T > S(1e-3) && T < S(1e3)) {
+    // omega = p/q: g = T^(omega - 1) from an FP32 start g0, corrected as
+    // g = g0 r^(-1/q) with r = g0^q T^(q - p) = 1 + d, taking two terms of the
+    // binomial series (1 + d)^(-1/q) = 1 - d/q + (q + 1)/(2 q^2) d^2 - ...
+    // (|d| < 1e-4, so the next term is below FP64 rounding).  Then
+    // mu = mu0 T g and dmu/dT = mu0 omega g, with no division and no FP64
+    // logarithm or exponential.
+    const S g0 = (S)powf((float)T, K.vexpm1);
+    const S d = ipow(g0, K.vq) * ipow(T, K.va) - S(1);
+    const S gg = g0 * fma(d, fma(d, K.vc2, -K.vinvq), S(1));
+    mu = K.mu0 * T * gg;
+    dmudT = K.mu0omega * gg;
   } else {
     mu = K.mu0 * exp(K.omega * log(T));   // mu0 T^omega
     dmudT = K.omega * mu / T;
@@ -389,22 +435,25 @@ __device__ __forceinline__ bool needs_rprev(const StepArgs<S>& A, const StepDyn<
   return A.do_update && (A.rk ? A.rkA != S(0) : !D.first);
 }
 
-template <typename S>
-__device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& A, const StepDyn<S>& D, long long idx,
-                                           long long N, const S (&Uo)[5], const S (&R)[5], S (&un)[5],
-                                           unsigned& health, const S* Rp = nullptr) {
+// F: 0 AB2 step, 1 RK3 stage, 2 either (A.rk read per point).
+template <int F, typename S>
+__device__ __forceinline__ void ab2_update_v(const Coef<S>& K, const StepArgs<S>& A, const StepDyn<S>& D, long long idx,
+                                             long long N, const S (&Uo)[5], const S (&R)[5], S (&un)[5],
+                                             unsigned& health, const S* Rp) {
+  const bool ld = needs_rprev(A, D);
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const S rp = needs_rprev(A, D) ? (Rp ? Rp[v] : A.Rprev[v * N + idx]) : S(0);
-    S inc, kept;
-    if (A.rk) {
+    const S rp = ld ? (Rp ? Rp[v] : A.Rprev[v * N + idx]) : S(0);
+    S inc, kept, scale;
+    if (F == 2 ? A.rk != 0 : F == 1) {
       kept = fma(A.rkA, rp, K.dt * R[v]);   // stage register dU
       inc = A.rkB * kept;                   // the state grows by rkB dU
+      scale = S(1);
     } else {
       inc = D.first ? R[v] : fma(S(1.5), R[v], S(-0.5) * rp);
       kept = R[v];
+      scale = K.dt;
     }
-    const S scale = A.rk ? S(1) : K.dt;
     if (D.Ulo) {
       const S dlt = mul_rn(scale, inc);
       const S s = add_rn(Uo[v], dlt);                           // TwoSum(U_hi, dlt)
@@ -420,6 +469,22 @@ __device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& 
     D.Unext[v * N + idx] = un[v];
     A.Rprev[v * N + idx] = kept;
     if (nonfinite(un[v])) health |= H_NONFINITE;
+  }
+}
+
+// In FP64 the RK3 and AB2 forms are separate code paths under one uniform
+// branch, so that an AB2 step does not also issue the stage arithmetic on the
+// FP64 pipe (the bound of the FP64 kernels); in FP32 one path for both keeps
+// the register count down.
+template <typename S>
+__device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& A, const StepDyn<S>& D, long long idx,
+                                           long long N, const S (&Uo)[5], const S (&R)[5], S (&un)[5],
+                                           unsigned& health, const S* Rp = nullptr) {
+  if constexpr (sizeof(S) == 8) {
+    if (A.rk) ab2_update_v<1>(K, A, D, idx, N, Uo, R, un, health, Rp);
+    else ab2_update_v<0>(K, A, D, idx, N, Uo, R, un, health, Rp);
+  } else {
+    ab2_update_v<2>(K, A, D, idx, N, Uo, R, un, health, Rp);
   }
 }
 

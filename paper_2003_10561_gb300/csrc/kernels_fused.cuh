@@ -205,21 +205,44 @@ __device__ __forceinline__ void fused_load_plane(const Geom& g, const Coef<S>& K
   fused_store_plane<S, TX, TY>(K, P, win, slot_A<TX, TY>(q), slot_T<TX, TY>(q), slot_R<TX, TY>(q));
 }
 
-// Inviscid flux component e of direction d of one window cell (aA, aT, aR:
-// element offsets of the cell in its plane's slots): rho u_d,
-// rho u_i u_d + p delta_id, H u_d, with p = rho T / gamma.
+// The five inviscid flux components of direction d of one window cell (aA,
+// aT, aR: element offsets of the cell in its plane's slots): rho u_d,
+// rho u_i u_d + p delta_id, H u_d, with p = rho T / gamma.  The cell's values
+// are read once for all five.
 template <typename S, int TX, int TY>
-__device__ __forceinline__ S cell_flux(const Coef<S>& K, const S* win, int aA, int aT, int aR, int d, int e) {
+__device__ __forceinline__ void cell_fluxes(const Coef<S>& K, const S* win, int aA, int aT, int aR, int d,
+                                            S (&f)[5]) {
   using T_ = TileShape<TX, TY>;
   const S r = win[aR];
-  const S ud = win[aA + d * T_::CELLS];
-  if (e == 0) return r * ud;
-  if (e == 4) return win[aR + T_::CELLS] * ud;
-  const int i = e - 1;
+  const S H = win[aR + T_::CELLS];
+  const S u[3] = {win[aA], win[aA + T_::CELLS], win[aA + 2 * T_::CELLS]};
+  const S ud = u[d];
   const S rud = r * ud;
-  const S ui = win[aA + i * T_::CELLS];
-  if (i != d) return rud * ui;
-  return fma(rud, ui, r * win[aT] * K.inv_gamma);
+  f[0] = rud;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) f[1 + i] = i == d ? fma(rud, ud, r * win[aT] * K.inv_gamma) : rud * u[i];
+  f[4] = H * ud;
+}
+
+// First tap (offset from the point) of the PE-local stencil of each kind.
+__device__ __forceinline__ constexpr int local_first(int kind) {
+  return kind == 0 ? -2 : (kind == 1 ? 0 : (kind == 2 ? -1 : (kind == 3 ? -3 : -4)));
+}
+
+// 12 dx times the PE-local first-derivative stencil of kind KIND (Sec. 2.1),
+// taps in ascending offset from local_first(KIND), applied to dv(offset).
+template <int KIND, typename S, typename DV>
+__device__ __forceinline__ S local_taps_c(DV dv) {
+  constexpr float c[5][5] = {{1, -8, 0, 8, -1}, {-25, 48, -36, 16, -3}, {-3, -10, 18, -6, 1},
+                             {-1, 6, -18, 10, 3}, {3, -16, 36, -48, 25}};
+  if constexpr (KIND == 0) {
+    return fma(S(8), dv(1) - dv(-1), dv(-2) - dv(2));
+  } else {
+    S acc = S(0);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) acc = fma(S(c[KIND][i]), dv(local_first(KIND) + i), acc);
+    return acc;
+  }
 }
 
 // PE-local first-derivative stencil kind of the Sec. 2.1 mixed rule at local
@@ -243,7 +266,6 @@ struct PointWin {
   int pA[kWinPlanes];           // u (v, w at + CELLS, + 2 CELLS) in planes z-4 .. z+4
   int pT[5];                    // T in planes z-2 .. z+2
   int pR;                       // rho (H at + CELLS) in plane z
-  int qa0;                      // window-plane count of plane z-4 (slot arithmetic)
   int cell;                     // the point's cell within a plane
   __device__ __forceinline__ S at(int f, int dx, int dy, int dz) const {
     const int o = dy * T_::CX + dx;
@@ -260,34 +282,33 @@ struct PointWin {
     return fma(K.c1[b], sh(f, b, 1, dx, dy, dz) - sh(f, b, -1, dx, dy, dz),
                K.c2[b] * (sh(f, b, 2, dx, dy, dz) - sh(f, b, -2, dx, dy, dz)));
   }
-  // 12 dz times the PE-local derivative along z (stencil `kind`, warp-uniform:
-  // five taps at planes st + 0..4) of the AT derivative of u, v or w along
-  // `in` (x or y); the central kind runs its four nonzero taps only.
-  __device__ __forceinline__ S zlocal_of_d1(const Coef<S>& K, const S (*coef)[5], int f, int in, int kind) const {
+  // 12 dz times the PE-local derivative along z (stencil `kind`, uniform over
+  // the CTA) of the AT derivative of u, v or w along `in` (x or y); each kind
+  // is its own code path, so every tap reads a window plane at a constant slot.
+  __device__ __forceinline__ S zlocal_of_d1(const Coef<S>& K, int f, int in, int kind) const {
     const int sk = in == 0 ? 1 : T_::CX;
-    auto dv = [&](int o) {   // inner derivative at plane z + o (o may be a run-time value)
-      const S* q = win + slot_A<TX, TY>(qa0 + 4 + o) + f * T_::CELLS + cell;
+    auto dv = [&](int o) {   // inner derivative at plane z + o
+      const S* q = win + pA[4 + o] + f * T_::CELLS;
       return fma(K.c1[in], q[sk] - q[-sk], K.c2[in] * (q[2 * sk] - q[-2 * sk]));
     };
-    if (kind == 0) return fma(S(8), dv(1) - dv(-1), dv(-2) - dv(2));
-    const int st = kind == 1 ? 0 : (kind == 2 ? -1 : (kind == 3 ? -3 : -4));
-    S acc = S(0);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) acc = fma(coef[kind][i], dv(st + i), acc);
-    return acc;
+    switch (kind) {
+      case 0: return local_taps_c<0, S>(dv);
+      case 1: return local_taps_c<1, S>(dv);
+      case 2: return local_taps_c<2, S>(dv);
+      case 3: return local_taps_c<3, S>(dv);
+      default: return local_taps_c<4, S>(dv);
+    }
   }
 };
 
-// Five-tap PE-local stencil (kind as in the coefficient table, taps in
-// ascending offset from st) applied to a per-plane derivative array with
-// stride `step` between taps, centred at element `at`.
-template <typename S>
-__device__ __forceinline__ S local_taps(const S (*coef)[5], const S* arr, int at, int step, int kind) {
-  const int st = kind == 0 ? -2 : (kind == 1 ? 0 : (kind == 2 ? -1 : (kind == 3 ? -3 : -4)));
-  const S* q = arr + at + st * step;
+// Five-tap PE-local stencil with the thread's own coefficients (kind fixed
+// for the thread's column; registers, or a row of the shared table), taps
+// STEP elements apart from q.
+template <int STEP, typename S, typename C>
+__device__ __forceinline__ S local_taps(const C& c, const S* q) {
   S acc = S(0);
 #pragma unroll
-  for (int i = 0; i < 5; ++i) acc = fma(coef[kind][i], q[i * step], acc);
+  for (int i = 0; i < 5; ++i) acc = fma(c[i], q[i * STEP], acc);
   return acc;
 }
 
@@ -366,7 +387,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     } else {
       const int aA = slot_A<TX, TY>(q) + cell, aT = slot_T<TX, TY>(q) + cell, aR = slot_R<TX, TY>(q) + cell;
 #pragma unroll
-      for (int e = 0; e < 5; ++e) out[e] = cell_flux<S, TX, TY>(K, win, aA, aT, aR, 2, e);
+      cell_fluxes<S, TX, TY>(K, win, aA, aT, aR, 2, out);
     }
   };
 
@@ -376,6 +397,14 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
   // queue of the z fluxes at planes z-2, z-1, z, z+1, z+2
   S qz[5][5];
   __syncthreads();
+  // the PE-local x- and y-stencils of this thread's column, and their first
+  // taps in the x-row and y-column arrays; the x coefficients vary across a
+  // warp and are kept in registers, the y ones are read from the table (one
+  // row per warp where a warp spans one tile row)
+  const S* lcx = coef[kind_x];
+  const S* lcy = coef[kind_y];
+  const int ax0 = ty * T_::CX + tx + 2 + local_first(kind_x);
+  const int ay0 = (ty + 2 + local_first(kind_y)) * TX + tx;
 #pragma unroll
   for (int k = 0; k < 4; ++k) zflux(zs - 2 + k, 2 + k, qz[k]);
   __syncthreads();
@@ -421,8 +450,10 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
 #pragma unroll
             for (int e = 0; e < 5; ++e) FX[e * TY * T_::CX + c] = A.GH[0][e * qsx + gi];
           } else {
+            S f[5];
+            cell_fluxes<S, TX, TY>(K, win, bA + cw, bT + cw, bR + cw, 0, f);
 #pragma unroll
-            for (int e = 0; e < 5; ++e) FX[e * TY * T_::CX + c] = cell_flux<S, TX, TY>(K, win, bA + cw, bT + cw, bR + cw, 0, e);
+            for (int e = 0; e < 5; ++e) FX[e * TY * T_::CX + c] = f[e];
           }
           // (cells beyond the x-face are never read by the PE-local x-stencils)
           const S* vq = win + bA + T_::CELLS + cw;
@@ -446,8 +477,10 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
 #pragma unroll
             for (int e = 0; e < 5; ++e) FY[e * (TY + 4) * TX + c] = A.GH[1][e * qsy + gi];
           } else {
+            S f[5];
+            cell_fluxes<S, TX, TY>(K, win, bA + cw, bT + cw, bR + cw, 1, f);
 #pragma unroll
-            for (int e = 0; e < 5; ++e) FY[e * (TY + 4) * TX + c] = cell_flux<S, TX, TY>(K, win, bA + cw, bT + cw, bR + cw, 1, e);
+            for (int e = 0; e < 5; ++e) FY[e * (TY + 4) * TX + c] = f[e];
           }
           const S* vq = win + bA + T_::CELLS + cw;
           const S* uq = win + bA + cw;
@@ -464,7 +497,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     PointWin<S, TX, TY> W;
     W.win = win;
     W.cell = cell;
-    W.qa0 = q - 4;
 #pragma unroll
     for (int k = 0; k < kWinPlanes; ++k) W.pA[k] = slot_A<TX, TY>(q - 4 + k) + cell;
 #pragma unroll
@@ -516,29 +548,27 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     // central part a, elsewhere the average of the two parts
     S gth[3];
     {
-      const int ax = ty * T_::CX + tx + 2;          // the point in the x-row arrays
-      const int ay = (ty + 2) * TX + tx;            // the point in the y-column arrays
       const int sxr = TY * T_::CX, syc = (TY + 4) * TX;
       auto mix = [&](S pa, S pb, bool bnd) { return bnd ? S(0.5) * (pa + pb) : pa; };
       const bool bxy = kind_x != 0 || kind_y != 0, bxz = kind_x != 0 || kind_z != 0, byz = kind_y != 0 || kind_z != 0;
+      auto tx_ = [&](int fld) { return local_taps<1>(lcx, XR + fld * sxr + ax0); };
+      auto ty_ = [&](int fld) { return local_taps<TX>(lcy, YC + fld * syc + ay0); };
       // d/dx (dv/dy)
-      const S m_xy = mix(K.hloc[0] * local_taps(coef, XR + XR_VY * sxr, ax, 1, kind_x),
-                         K.hloc[1] * local_taps(coef, YC + YC_VX * syc, ay, TX, kind_y), bxy);
+      const S m_xy = mix(K.hloc[0] * tx_(XR_VY), K.hloc[1] * ty_(YC_VX), bxy);
       // d/dy (du/dx)
-      const S m_yx = mix(K.hloc[1] * local_taps(coef, YC + YC_UX * syc, ay, TX, kind_y),
-                         K.hloc[0] * local_taps(coef, XR + XR_UY * sxr, ax, 1, kind_x), bxy);
+      const S m_yx = mix(K.hloc[1] * ty_(YC_UX), K.hloc[0] * tx_(XR_UY), bxy);
       // d/dx (dw/dz): part b along z needs the window (planes z-4 .. z+4)
-      const S pa_xz = K.hloc[0] * local_taps(coef, XR + XR_WZ * sxr, ax, 1, kind_x);
-      const S pb_xz = __any_sync(__activemask(), bxz) ? K.hloc[2] * W.zlocal_of_d1(K, coef, WF_W, 0, kind_z) : S(0);
+      const S pa_xz = K.hloc[0] * tx_(XR_WZ);
+      const S pb_xz = __any_sync(__activemask(), bxz) ? K.hloc[2] * W.zlocal_of_d1(K, WF_W, 0, kind_z) : S(0);
       // d/dz (du/dx)
-      const S pa_zx = K.hloc[2] * W.zlocal_of_d1(K, coef, WF_U, 0, kind_z);
-      const S pb_zx = K.hloc[0] * local_taps(coef, XR + XR_UZ * sxr, ax, 1, kind_x);
+      const S pa_zx = K.hloc[2] * W.zlocal_of_d1(K, WF_U, 0, kind_z);
+      const S pb_zx = K.hloc[0] * tx_(XR_UZ);
       // d/dy (dw/dz)
-      const S pa_yz = K.hloc[1] * local_taps(coef, YC + YC_WZ * syc, ay, TX, kind_y);
-      const S pb_yz = __any_sync(__activemask(), byz) ? K.hloc[2] * W.zlocal_of_d1(K, coef, WF_W, 1, kind_z) : S(0);
+      const S pa_yz = K.hloc[1] * ty_(YC_WZ);
+      const S pb_yz = __any_sync(__activemask(), byz) ? K.hloc[2] * W.zlocal_of_d1(K, WF_W, 1, kind_z) : S(0);
       // d/dz (dv/dy)
-      const S pa_zy = K.hloc[2] * W.zlocal_of_d1(K, coef, WF_V, 1, kind_z);
-      const S pb_zy = K.hloc[1] * local_taps(coef, YC + YC_VZ * syc, ay, TX, kind_y);
+      const S pa_zy = K.hloc[2] * W.zlocal_of_d1(K, WF_V, 1, kind_z);
+      const S pb_zy = K.hloc[1] * ty_(YC_VZ);
       gth[0] = d2diag[0] + m_xy + mix(pa_xz, pb_xz, bxz);
       gth[1] = d2diag[1] + m_yx + mix(pa_yz, pb_yz, byz);
       gth[2] = d2diag[2] + mix(pa_zx, pb_zx, bxz) + mix(pa_zy, pb_zy, byz);

@@ -50,6 +50,32 @@ def test_rhs_parity_fp64_variants(lib, name, path):
     assert max(rel_linf(R, Rref)) <= 1e-12, rel_linf(R, Rref)
 
 
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("omega", [0.76, 0.5, 0.7, 1.0, 0.0, 0.7123456789])
+def test_rhs_parity_fp64_power_law_exponents(lib, omega, path):
+    """The power law mu0 T^omega for exponents that are fractions p/q with
+    q <= 64 (0.76 = 19/25, 1/2, 7/10, 1, 0: the FP64 kernels take the
+    root-correction form) and one that is not (the exponential form), on a
+    field whose temperature spans a wide range (T from about 0.3 to 3)."""
+    n, pes = (16, 16, 16), (2, 2, 2)
+    kw = dict(mu0=0.02, dt=2e-3, max_delay=2, seed=77, visc_exp=omega)
+    c = ocfg(n, pes, **kw)
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=11)
+    x = np.arange(n[0]) * 2 * np.pi / n[0]
+    U0 = U0.copy()
+    # E raised and lowered along x: T = gamma (gamma - 1) (E - K) / rho
+    K = 0.5 * (U0[1] ** 2 + U0[2] ** 2 + U0[3] ** 2) / U0[0]
+    U0[4] = K + (U0[4] - K) * (1.0 + 0.82 * np.sin(x))[None, None, :] * 1.6
+    hist = synth.history(U0, c.n_levels, eps=2e-2, seed=5)
+    _, _, _, T = ns.primitives(c, hist[0])
+    assert T.min() < 0.5 and T.max() > 2.5
+    s = make(lib, n, pes, path=path, **kw)
+    s.set_history(hist, 9)
+    R = s.rhs("random")
+    Rref = ns.rhs(c, hist, ns.delay_map(c, 9, ns.RANDOM))
+    assert max(rel_linf(R, Rref)) <= 1e-12, rel_linf(R, Rref)
+
+
 @pytest.mark.parametrize("prec", ["p32", "p32c"])
 @pytest.mark.parametrize("path", PATHS)
 def test_rhs_parity_fp32_variant(lib, path, prec):

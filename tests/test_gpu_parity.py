@@ -44,8 +44,8 @@ def make(lib, n, pes, precision="p64", path="auto", **kw):
     """A solver on the requested kernel path; skips when the fused path does not
     apply to this grid / PE shape."""
     try:
-        return lib.Solver(n=n, pes=pes, precision=precision, path=path, gamma=GAMMA, prandtl=PR,
-                          visc_exp=OMEGA, **kw)
+        return lib.Solver(n=n, pes=pes, precision=precision, path=path, **{"gamma": GAMMA, "prandtl": PR,
+                                                                          "visc_exp": OMEGA, **kw})
     except lib.AtDnsError as e:
         if path == "fused" and e.code == lib.AT_DNS_E_UNSUPPORTED:
             pytest.skip("fused path does not apply to n=%s pes=%s" % (n, pes))
@@ -53,7 +53,7 @@ def make(lib, n, pes, precision="p64", path="auto", **kw):
 
 
 def ocfg(n, pes, **kw):
-    return ns.Config(n=tuple(n), pes=tuple(pes), gamma=GAMMA, prandtl=PR, visc_exp=OMEGA, **kw)
+    return ns.Config(n=tuple(n), pes=tuple(pes), **{"gamma": GAMMA, "prandtl": PR, "visc_exp": OMEGA, **kw})
 
 
 # --------------------------------------------------------------------------
