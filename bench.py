@@ -48,9 +48,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max S
 # 128^3 with 4x4x4 PEs of 32^3 (profiles/k_main_fp64_128cube_4x4x4pes.md,
 # profiles/k_fused_fp32_128cube_4x4x4pes.md), scaled by the point count to the
 # 256^3 workload (same PE size; traffic grows with the points):
-# k_main<double, 2> 701.1 MB + 462.6 MB, k_fused<float, 32, 8> 112.5 MB + 49.8 MB
-K_MAIN_FP64_TRAFFIC_256 = 8 * (701.0944e6 + 462.572032e6)
-K_FUSED_FP32_TRAFFIC_256 = 8 * (112.545536e6 + 49.810176e6)
+# k_main<double, 2> 700.8 MB + 443.7 MB, k_fused<float, 32, 8> 112.5 MB + 50.0 MB
+K_MAIN_FP64_TRAFFIC_256 = 8 * (700.768256e6 + 443.693824e6)
+K_FUSED_FP32_TRAFFIC_256 = 8 * (112.545536e6 + 50.034688e6)
 
 
 def set_workload(n, pes):

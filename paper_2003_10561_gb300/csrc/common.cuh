@@ -384,7 +384,14 @@ __device__ __forceinline__ void viscosity(const Coef<S>& K, S T, S& mu, S& dmudT
     const S inv = S(1) / (T + K.suth_s);
     mu = K.suth_c * T * sqrt(T) * inv;
     dmudT = mu * (S(1.5) / T - inv);
-  } else if (sizeof(S) == 8 && K.vrat && T > S(1e-3) && T < S(1e3)) {
+  } else if (sizeof(S) == 4) {
+    // FP32 forms: g = T^(omega - 1) by the hardware base-2 logarithm and
+    // exponential (a few ulp for the temperatures of a flow); mu = mu0 T g,
+    // dmu/dT = mu0 omega g
+    const S gg = (S)__powf((float)T, K.vexpm1);
+    mu = K.mu0 * T * gg;
+    dmudT = K.mu0omega * gg;
+  } else if (K.vrat && T > S(1e-3) && T < S(1e3)) {
     // omega = p/q: g = T^(omega - 1) from an FP32 start g0, corrected as
     // g = g0 r^(-1/q) with r = g0^q T^(q - p) = 1 + d, taking two terms of the
     // binomial series (1 + d)^(-1/q) = 1 - d/q + (q + 1)/(2 q^2) d^2 - ...

@@ -2,17 +2,19 @@
 //
 // A CTA owns a TX x TY tile of one PE in x and y and marches in z through a
 // chunk of ZC planes of one PE.  A shared-memory window holds, on the tile
-// plus a two-cell halo in x and y, u, v, w for nine planes (z-4 .. z+4), T for
-// seven (z-2 .. z+4) and rho and H -- the quantity whose product with u_d is
-// the fifth flux (E + p, or rho e) -- for five (z .. z+4): each field for as
-// many planes as its stencils reach.  Halo cells beyond a PE face hold the
+// plus a two-cell halo in x and y, u, v, w for nine planes (z-4 .. z+4), and
+// T, rho and H -- the quantity whose product with u_d is the fifth flux
+// (E + p, or rho e) -- for seven (z-2 .. z+4): each field for as many planes
+// as its stencils reach.  Halo cells beyond a PE face hold the
 // AT ghost values of that direction (Table B extrapolation done by k_ghost),
 // planes beyond a PE z-face hold the z ghosts, so every stencil of Sec. 2.1 is
 // a plain read of the window:
 //   * first / second derivatives of u, v, w, T in x, y, z;
 //   * inviscid fluxes: each plane's x and y fluxes are formed once into shared
-//     arrays (from the window, or from the ghost arrays across a PE face) and
-//     the column's z fluxes are carried in a five-plane register queue;
+//     arrays (from the window, or from the ghost arrays across a PE face); the
+//     column's z fluxes at z-2 .. z+2 are formed from the window (or the z
+//     ghost arrays) at each plane, which keeps 25 registers free that a queue
+//     carried across planes would hold;
 //   * mixed derivatives: the central cross stencil D_a(D_b f) inside, and at
 //     PE-boundary points the average of the PE-local derivative in a of the AT
 //     derivative in b and vice versa.  The AT derivatives that the x- and
@@ -33,7 +35,7 @@ namespace atdns {
 
 constexpr int kWinPlanes = 9;   // u, v, w: planes z-4 .. z+4
 constexpr int kWinT = 7;        // T: planes z-2 .. z+4
-constexpr int kWinR = 5;        // rho, H: planes z .. z+4
+constexpr int kWinR = 7;        // rho, H: planes z-2 .. z+4
 enum WinField { WF_U = 0, WF_V, WF_W, WF_T, WF_R, WF_H };
 // per-plane AT derivatives for the mixed rule: on x-extended rows (taken by
 // the x-stencils) and on y-extended columns (taken by the y-stencils)
@@ -378,7 +380,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
   const long long qsz = 4LL * g.pes[2] * g.plane[2];
 
   // z fluxes of this column at window plane q = zp - zs + 4 (z ghosts beyond
-  // a PE z-face)
+  // a PE z-face), formed afresh each plane for z-2 .. z+2
   auto zflux = [&](int zp, int q, S (&out)[5]) {
     if (F.beyond(g, 2, zp)) {
       const long long gi = (long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] + (long long)y * g.n[0] + x;
@@ -391,24 +393,19 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     }
   };
 
-  // window planes q = 0 .. 7 (z = zs-4 .. zs+3); the z-flux queue needs rho
-  // and H of planes 2 .. 5 before planes 6 and 7 reuse their slots
-  for (int q = 0; q < 6; ++q) fused_load_plane<S, TX, TY>(g, K, A, D.U, F, win, q, zs - 4 + q);
-  // queue of the z fluxes at planes z-2, z-1, z, z+1, z+2
-  S qz[5][5];
+  // window planes q = 0 .. 7 (z = zs-4 .. zs+3)
+  for (int q = 0; q < 8; ++q) fused_load_plane<S, TX, TY>(g, K, A, D.U, F, win, q, zs - 4 + q);
   __syncthreads();
   // the PE-local x- and y-stencils of this thread's column, and their first
   // taps in the x-row and y-column arrays; the x coefficients vary across a
   // warp and are kept in registers, the y ones are read from the table (one
   // row per warp where a warp spans one tile row)
-  const S* lcx = coef[kind_x];
+  S lcx[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) lcx[i] = coef[kind_x][i];
   const S* lcy = coef[kind_y];
   const int ax0 = ty * T_::CX + tx + 2 + local_first(kind_x);
   const int ay0 = (ty + 2 + local_first(kind_y)) * TX + tx;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) zflux(zs - 2 + k, 2 + k, qz[k]);
-  __syncthreads();
-  for (int q = 6; q < 8; ++q) fused_load_plane<S, TX, TY>(g, K, A, D.U, F, win, q, zs - 4 + q);
   PlaneRaw<S, TX, TY> pf;                       // plane z + 4, fetched one iteration ahead
   fused_fetch_plane<S, TX, TY>(g, A, D.U, F, zs + 4, pf);
 
@@ -490,8 +487,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
           YC[YC_VZ * (TY + 4) * TX + c] = ddz(1, cw);
         }
       }
-      // z fluxes of this column at plane z+2 enter the queue
-      zflux(z + 2, q + 2, qz[4]);
     }
     __syncthreads();
     PointWin<S, TX, TY> W;
@@ -507,6 +502,18 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
 
     // ---- inviscid flux divergence: -sum_d D_d F_d (ghost fluxes already in
     // the flux arrays / queue across PE faces)
+    S dz1[5], dz2[5];   // F_z(z+1) - F_z(z-1), F_z(z+2) - F_z(z-2) of this column
+    {
+      S fa[5], fb[5];
+      zflux(z + 1, q + 1, fa);
+      zflux(z - 1, q - 1, fb);
+#pragma unroll
+      for (int e = 0; e < 5; ++e) dz1[e] = fa[e] - fb[e];
+      zflux(z + 2, q + 2, fa);
+      zflux(z - 2, q - 2, fb);
+#pragma unroll
+      for (int e = 0; e < 5; ++e) dz2[e] = fa[e] - fb[e];
+    }
     S R[5];
 #pragma unroll
     for (int e = 0; e < 5; ++e) {
@@ -517,8 +524,8 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
       acc = fma(-K.c2[0], fx[2] - fx[-2], acc);
       acc = fma(-K.c1[1], fy[TX] - fy[-TX], acc);
       acc = fma(-K.c2[1], fy[2 * TX] - fy[-2 * TX], acc);
-      acc = fma(-K.c1[2], qz[3][e] - qz[1][e], acc);
-      acc = fma(-K.c2[2], qz[4][e] - qz[0][e], acc);
+      acc = fma(-K.c1[2], dz1[e], acc);
+      acc = fma(-K.c2[2], dz2[e], acc);
       R[e] = acc;
     }
 
@@ -680,22 +687,18 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
       st.add(ST_U2, uu);
       st.add(ST_C, c);
       const S au[3] = {fabs(vel[0]), fabs(vel[1]), fabs(vel[2])};
-      const long long k0 = okey(au[0]), k1 = okey(au[1]), k2 = okey(au[2]);
-      const S umax = (k0 >= k1 && k0 >= k2) ? au[0] : (k1 >= k2 ? au[1] : au[2]);
       if constexpr (sizeof(S) == 4) {
-        wmax = fmaxf(wmax, umax + c);
+        wmax = fmaxf(wmax, fmaxf(fmaxf(au[0], au[1]), au[2]) + c);
         rmin = fminf(rmin, r);
         pmin = fminf(pmin, p);
       } else {
+        const long long k0 = okey(au[0]), k1 = okey(au[1]), k2 = okey(au[2]);
+        const S umax = (k0 >= k1 && k0 >= k2) ? au[0] : (k1 >= k2 ? au[1] : au[2]);
         kwave = max(kwave, okey(umax + c));
         krho = min(krho, okey(r));
         kp = min(kp, okey(p));
       }
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int e = 0; e < 5; ++e) qz[k][e] = qz[k + 1][e];
     __syncthreads();
   }
   double tot[kNumStat];
