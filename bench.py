@@ -467,6 +467,10 @@ def leg_report(r, world, pts, steps, pk):
                 "traffic": traffic, "flop_per_point": flops,
                 "note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
                         "(an FMA probe measured 1.20 TFLOP/s)"}
+        # the same kernel against the HBM roof, at the step's algorithmic bytes
+        gbs = algorithmic_bytes(8, order) * pts / t_main / 1e9
+        roof["hbm"] = {"achieved": gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                       "frac": gbs / pk.get("hbm_gbs", 6800.0), "bytes_per_point": algorithmic_bytes(8, order)}
     else:
         achieved = algorithmic_bytes(4, order) * pts / t_main / 1e9
         kname = "k_fused" if r["path"] == "fused" else "k_main"
