@@ -189,13 +189,14 @@ __device__ __forceinline__ void fused_store_plane(const Coef<S>& K, const PlaneR
 }
 
 // Slots of a window plane: `q` counts planes from the chunk's first window
-// plane (z_start - 4); each region is a ring of its own depth.
+// plane (z_start - 4), so it is never negative (unsigned remainder); each
+// region is a ring of its own depth.
 template <int TX, int TY>
-__device__ __forceinline__ int slot_A(int q) { return TileShape<TX, TY>::OFF_A + (q % kWinPlanes) * 3 * TileShape<TX, TY>::CELLS; }
+__device__ __forceinline__ int slot_A(int q) { return TileShape<TX, TY>::OFF_A + (int)((unsigned)q % (unsigned)kWinPlanes) * 3 * TileShape<TX, TY>::CELLS; }
 template <int TX, int TY>
-__device__ __forceinline__ int slot_T(int q) { return TileShape<TX, TY>::OFF_T + (q % kWinT) * TileShape<TX, TY>::CELLS; }
+__device__ __forceinline__ int slot_T(int q) { return TileShape<TX, TY>::OFF_T + (int)((unsigned)q % (unsigned)kWinT) * TileShape<TX, TY>::CELLS; }
 template <int TX, int TY>
-__device__ __forceinline__ int slot_R(int q) { return TileShape<TX, TY>::OFF_R + (q % kWinR) * 2 * TileShape<TX, TY>::CELLS; }
+__device__ __forceinline__ int slot_R(int q) { return TileShape<TX, TY>::OFF_R + (int)((unsigned)q % (unsigned)kWinR) * 2 * TileShape<TX, TY>::CELLS; }
 
 // Fill window plane q (plane z_start - 4 + q).
 template <typename S, int TX, int TY>
