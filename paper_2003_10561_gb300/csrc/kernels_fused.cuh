@@ -435,9 +435,17 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
         const int o = f * T_::CELLS + cw;
         return fma(K.c1[2], win[bAp1 + o] - win[bAm1 + o], K.c2[2] * (win[bAp2 + o] - win[bAm2 + o]));
       };
+      // The cells of the last, partial pass of each loop go to warps that the
+      // other loop's partial pass leaves idle (y: the top warps, x: the warps
+      // just below them), so the warps reach the next barrier together; the
+      // rotation is by whole warps, which keeps each warp on consecutive cells.
+      constexpr int kNT = T_::THREADS;
+      constexpr int kRemY = ((TY + 4) * TX % kNT + 31) / 32 * 32;
+      constexpr int kRemX = (TY * T_::CX % kNT + 31) / 32 * 32;
+      const int tid_x = (tid + kRemY + kRemX) % kNT, tid_y = (tid + kRemY) % kNT;
 #pragma unroll
       for (int c0 = 0; c0 < TY * T_::CX; c0 += T_::THREADS) {
-        const int c = c0 + tid;
+        const int c = c0 + tid_x;
         if (c < TY * T_::CX) {
           const int r = c / T_::CX, cxw = c - r * T_::CX;
           const int xg = F.x0 - 2 + cxw, yg = F.y0 + r;
@@ -464,7 +472,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
       }
 #pragma unroll
       for (int c0 = 0; c0 < (TY + 4) * TX; c0 += T_::THREADS) {
-        const int c = c0 + tid;
+        const int c = c0 + tid_y;
         if (c < (TY + 4) * TX) {
           const int r = c / TX, cxl = c - r * TX;
           const int xg = F.x0 + cxl, yg = F.y0 - 2 + r;
