@@ -50,7 +50,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max S
 # 256^3 workload (same PE size; traffic grows with the points):
 # k_main<double, 2> 700.8 MB + 443.7 MB, k_fused<float, 32, 8> 112.5 MB + 50.0 MB
 K_MAIN_FP64_TRAFFIC_256 = 8 * (700.768256e6 + 443.693824e6)
-K_FUSED_FP32_TRAFFIC_256 = 8 * (112.545536e6 + 50.034688e6)
+K_FUSED_FP32_TRAFFIC_256 = 8 * (112.54272e6 + 50.045696e6)
 
 
 def set_workload(n, pes):
