@@ -23,7 +23,8 @@
 //     runs the same five-tap stencil of its own kind; the z-stencils take the
 //     inner derivatives from the window (the one-sided reach of 4 planes in z
 //     is why u, v, w are kept for nine planes).
-// Then the assembly, forcing, AB2 update, ring write and statistics of k_main.
+// Then the assembly, forcing, AB2 (or RK3 stage) update, ring write and
+// statistics of k_main.
 // No per-point work arrays (derived fields, gradients) exist on this path.
 //
 // The tile shape is a template parameter so that every window access is one
@@ -49,7 +50,7 @@ struct TileShape {
   // element offsets of the shared-memory regions
   static constexpr int OFF_A = 0;                                   // [9][3][CELLS]
   static constexpr int OFF_T = OFF_A + kWinPlanes * 3 * CELLS;      // [7][CELLS]
-  static constexpr int OFF_R = OFF_T + kWinT * CELLS;               // [5][2][CELLS]
+  static constexpr int OFF_R = OFF_T + kWinT * CELLS;               // [7][2][CELLS]
   static constexpr int OFF_FX = OFF_R + kWinR * 2 * CELLS;          // [5][TY][CX]
   static constexpr int OFF_FY = OFF_FX + 5 * TY * CX;               // [5][CY][TX]
   static constexpr int OFF_XR = OFF_FY + 5 * CY * TX;               // [4][TY][CX]
