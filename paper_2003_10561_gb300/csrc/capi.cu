@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/at_dns.h"
@@ -1330,13 +1331,20 @@ int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode) {
   cudaGraphExec_t& ge = b->gexec[delay_mode];
   if (!ge || b->gkey[delay_mode] != key) {
     if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
-    // one step of every member, each on its own branch of the graph
+    // one step of every member, each on its own branch of the graph; the
+    // branches are captured largest member first, so that the small members'
+    // kernels fill the SMs the large ones leave idle rather than the reverse
+    std::vector<int> order(M);
+    for (int i = 0; i < M; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b->m[x]->g.npts > b->m[y]->g.npts; });
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeRelaxed) != cudaSuccess)
       return batch_fail(b, AT_DNS_E_CUDA, "graph capture failed to start");
     int rc = AT_DNS_OK;
     cudaEventRecord(b->fork, b->st);
-    for (int i = 0; i < M && !rc; ++i) {
+    for (int k = 0; k < M && !rc; ++k) {
+      const int i = order[k];
       at_dns* h = b->m[i];
       cudaStreamWaitEvent(b->ms[i], b->fork, 0);
       const bool stats = h->cfg.stats_every == 1;
