@@ -281,11 +281,6 @@ struct PointWin {
   __device__ __forceinline__ S sh(int f, int d, int m, int dx = 0, int dy = 0, int dz = 0) const {
     return at(f, dx + (d == 0 ? m : 0), dy + (d == 1 ? m : 0), dz + (d == 2 ? m : 0));
   }
-  // AT first derivative in direction b at the cell (dx, dy, dz) from the point
-  __device__ __forceinline__ S d1(const Coef<S>& K, int f, int b, int dx, int dy, int dz) const {
-    return fma(K.c1[b], sh(f, b, 1, dx, dy, dz) - sh(f, b, -1, dx, dy, dz),
-               K.c2[b] * (sh(f, b, 2, dx, dy, dz) - sh(f, b, -2, dx, dy, dz)));
-  }
   // 12 dz times the PE-local derivative along z (stencil `kind`, uniform over
   // the CTA) of the AT derivative of u, v or w along `in` (x or y); each kind
   // is its own code path, so every tap reads a window plane at a constant slot.
