@@ -385,7 +385,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
       for (int e = 0; e < 5; ++e) out[e] = A.GH[2][e * qsz + gi];
     } else {
       const int aA = slot_A<TX, TY>(q) + cell, aT = slot_T<TX, TY>(q) + cell, aR = slot_R<TX, TY>(q) + cell;
-#pragma unroll
       cell_fluxes<S, TX, TY>(K, win, aA, aT, aR, 2, out);
     }
   };
