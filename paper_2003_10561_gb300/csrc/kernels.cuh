@@ -101,16 +101,23 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   else return;
   S* GH = d == 0 ? GH0 : (d == 1 ? GH1 : GH2);
   const S* ring = d == 0 ? ring0 : (d == 1 ? ring1 : ring2);
-  const long long plane = g.plane[d];
+  // j < 2M P_d plane_d < npts < 2^31 (grids hold fewer than 2^31 points), so
+  // the index arithmetic below runs in 32 bits (no 64-bit division)
+  const unsigned plane = (unsigned)g.plane[d];
   constexpr int NS = 2 * M;
-  const int gi = (int)(j / plane);
-  const long long pl = j - (long long)gi * plane;
+  const unsigned ju = (unsigned)j;
+  const int gi = (int)(ju / plane);
+  const unsigned pl = ju - (unsigned)gi * plane;
   const int ped = gi / NS, slot = gi - ped * NS;
   const int P = g.pes[d], nl = g.nl[d], nd = g.n[d];
   int c[3];
-  if (d == 0) { c[2] = (int)(pl / g.n[1]); c[1] = (int)(pl - (long long)c[2] * g.n[1]); }
-  else if (d == 1) { c[2] = (int)(pl / g.n[0]); c[0] = (int)(pl - (long long)c[2] * g.n[0]); }
-  else { c[1] = (int)(pl / g.n[0]); c[0] = (int)(pl - (long long)c[1] * g.n[0]); }
+  {
+    const unsigned row = (unsigned)(d == 0 ? g.n[1] : g.n[0]);   // fastest extent of the face plane
+    const int hi = (int)(pl / row), lo = (int)(pl - (unsigned)hi * row);
+    if (d == 0) { c[2] = hi; c[1] = lo; }
+    else if (d == 1) { c[2] = hi; c[0] = lo; }
+    else { c[1] = hi; c[0] = lo; }
+  }
   int cd = ped * nl + (slot < M ? slot - M : nl + slot - M);
   cd = cd < 0 ? cd + nd : (cd >= nd ? cd - nd : cd);
   c[d] = ped * nl;   // any coordinate inside the receiving PE
@@ -147,10 +154,13 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   S acc[kNumGhostQ];
 #pragma unroll
   for (int q = 0; q < kNumGhostQ; ++q) acc[q] = S(0);
+  // ring slot of level n - k - l (>= 1: delays start after L + T_l steps);
+  // k + l <= L + M < nlev, so one wrap of (n mod nlev) - k - l suffices
+  const int nm = (int)(n % g.nlev);
 #pragma unroll
   for (int l = 0; l <= M; ++l) {
-    const long long lev = n - k - l;              // >= 1: delays start after L + T_l steps
-    const int rs = (int)(lev % g.nlev);
+    int rs = nm - k - l;
+    if (rs < 0) rs += g.nlev;
     const S w = S(wi[l]);
     S Uv[5], q[kNumGhostQ];
 #pragma unroll
