@@ -166,6 +166,12 @@ __device__ __forceinline__ long long plane_index(const Geom& g, int d, int x, in
   return (long long)y * g.n[0] + x;
 }
 
+// Ring slot of level m (m >= 0): m mod nlev, in 32 bits while the step count
+// fits (a uniform branch; the 64-bit remainder is a long instruction sequence).
+__device__ __forceinline__ int ring_slot(const Geom& g, long long m) {
+  return m < 0x7fffffffLL ? (int)((unsigned)m % (unsigned)g.nlev) : (int)(m % g.nlev);
+}
+
 __device__ __forceinline__ int pe_number(const Geom& g, int x, int y, int z) {
   return ((z / g.nl[2]) * g.pes[1] + (y / g.nl[1])) * g.pes[0] + (x / g.nl[0]);
 }

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   for (int q = 0; q < kNumGhostQ; ++q) acc[q] = S(0);
   // ring slot of level n - k - l (>= 1: delays start after L + T_l steps);
   // k + l <= L + M < nlev, so one wrap of (n mod nlev) - k - l suffices
-  const int nm = (int)(n % g.nlev);
+  const int nm = ring_slot(g, n);
 #pragma unroll
   for (int l = 0; l <= M; ++l) {
     int rs = nm - k - l;
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 3 : 2) k_main(Geom g, Co
       S un[5];
       ab2_update(K, A, D, idx, N, Uo, R, un, health);
       // PE-boundary slabs of U^{n+1} into ring slot (n+1) mod nlev
-      const int slot = (int)((D.n + 1) % g.nlev);
+      const int slot = ring_slot(g, D.n + 1);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         if (g.pes[d] == 1) continue;

@@ -405,6 +405,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
   PlaneRaw<S, TX, TY> pf;                       // plane z + 4, fetched one iteration ahead
   fused_fetch_plane<S, TX, TY>(g, A, D.U, F, zs + 4, pf);
 
+  const int slot = ring_slot(g, D.n + 1);      // ring slot of level n+1
   for (int z = zs; z < zs + ZC; ++z) {
     const int q = z - zs + 4;                  // window-plane count of plane z
     fused_store_plane<S, TX, TY>(K, pf, win, slot_A<TX, TY>(q + 4), slot_T<TX, TY>(q + 4), slot_R<TX, TY>(q + 4));
@@ -648,7 +649,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
       const S Uo[5] = {r, m[0], m[1], m[2], Ecur};
       S un[5];
       ab2_update(K, A, D, idx, N, Uo, R, un, health, Rp);
-      const int slot = (int)((D.n + 1) % g.nlev);
       const int li[3] = {li_x, li_y, li_z};
       const int c3[3] = {x, y, z};
 #pragma unroll
