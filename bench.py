@@ -48,9 +48,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max S
 # 128^3 with 4x4x4 PEs of 32^3 (profiles/k_main_fp64_128cube_4x4x4pes.md,
 # profiles/k_fused_fp32_128cube_4x4x4pes.md), scaled by the point count to the
 # 256^3 workload (same PE size; traffic grows with the points):
-# k_main<double, 2> 700.8 MB + 443.7 MB, k_fused<float, 32, 8> 112.5 MB + 50.0 MB
+# k_main<double, 2> 700.8 MB + 443.7 MB.  k_fused<float, 32, 8> measured
+# 112.5 MB + 50.0 MB before its ring-slot index moved out of the plane loop;
+# the kernel has changed since, so its traffic is reported as unmeasured.
 K_MAIN_FP64_TRAFFIC_256 = 8 * (700.768256e6 + 443.693824e6)
-K_FUSED_FP32_TRAFFIC_256 = 8 * (112.54272e6 + 50.045696e6)
+K_FUSED_FP32_TRAFFIC_256 = None
 
 
 def set_workload(n, pes):

@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 3 : 2) k_main(Geom g, Co
       S un[5];
       ab2_update(K, A, D, idx, N, Uo, R, un, health);
       // PE-boundary slabs of U^{n+1} into ring slot (n+1) mod nlev
-      const int slot = ring_slot(g, D.n + 1);
+      const int slot = (int)((D.n + 1) % g.nlev);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         if (g.pes[d] == 1) continue;
