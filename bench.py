@@ -24,6 +24,7 @@ import os
 import statistics as pystats
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -250,6 +251,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the AUTO kernel path instead of the autotuner's pick")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory for the raw nvidia-smi clock samples (default: the system temp directory)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the internal-energy / Sutherland leg")
     args = ap.parse_args()
@@ -275,8 +278,7 @@ def main():
     U0 = synth.initial_state((N, N, N), k0=4.0, mach_t=0.3, seed=0)
     stream = torch.cuda.Stream()
     res = {}
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
-                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_rank%d.csv" % rank)
+    clocks = Clocks(os.path.join(args.clocks_dir or tempfile.gettempdir(), "bench_clocks_rank%d.csv" % rank))
     precs = ("p64", "p32") if args.precision == "both" else (args.precision,)
     orders = (4, 6) if args.order == "both" else (int(args.order),)
     legs = [(p, o) for o in orders for p in precs]
