@@ -101,3 +101,42 @@ def test_analyze_snapshot_runs_on_both_forms():
     assert abs(np.mean(a["enstrophy_slice"]) - 1.0) < 0.5
     # dissipation ~ nu <omega^2> for a nearly incompressible field at rho = 1
     assert abs(a["eps"] - a["nu"] * a["enstrophy"]) < 0.2 * a["eps"]
+
+
+class _FakeForced:
+    """Stands in for a forced solver: the kinetic energy relaxes towards 1 as
+    1 - exp(-t / 300) over the steps taken (a stationary state is approached
+    from rest)."""
+
+    def __init__(self):
+        self.t = 0
+        self.modes = set()
+
+    def set_state(self, state):
+        self.t = 0
+
+    def step(self, n, mode):
+        self.t += n
+        self.modes.add(mode)
+
+    def stats(self):
+        return {"tke": 1.0 - math.exp(-self.t / 300.0)}
+
+    def get_state(self):
+        return ("state at step", self.t)
+
+
+def test_forced_stationary_state_stops_when_block_means_settle():
+    """Blocks of 200 steps: the helper stops at the first block whose mean
+    kinetic energy is within 2 % of the previous block's, i.e. when the
+    relaxation has decayed enough, and returns the state of that step."""
+    s = _FakeForced()
+    state, hist = analysis.forced_stationary_state(s, None, block=200, max_blocks=50, tol=0.02)
+    assert s.modes == {"sync"}
+    assert len(hist) >= 3 and abs(hist[-1] - hist[-2]) <= 0.02 * abs(hist[-2])
+    assert all(abs(hist[i] - hist[i - 1]) > 0.02 * abs(hist[i - 1]) for i in range(1, len(hist) - 1))
+    assert state == ("state at step", 200 * len(hist))
+    # a block limit ends the search even when the energy has not settled
+    s2 = _FakeForced()
+    _, hist2 = analysis.forced_stationary_state(s2, None, block=10, max_blocks=4, tol=1e-9)
+    assert len(hist2) == 4

@@ -53,3 +53,48 @@ def test_fixed_delay_map():
     cfg = ns.Config(n=(16, 16, 16), pes=(2, 2, 2), max_delay=3)
     assert not ns.delay_map(cfg, cfg.n_levels - 1, ns.FIXED).any()
     assert (ns.delay_map(cfg, cfg.n_levels, ns.FIXED) == 3).all()
+
+
+class _FakeSolver:
+    """Stands in for a library handle: a run is stable when its CFL is at most
+    `limit`; above it the kinetic energy grows, or (far above) the library
+    reports an unstable state."""
+
+    def __init__(self, cfl, limit, log):
+        self.cfl, self.limit, self.log = cfl, limit, log
+        self.k = 1.0
+
+    def set_state(self, state):
+        self.k = 1.0
+
+    def stats(self):
+        return {"tke": self.k}
+
+    def step(self, n, mode):
+        self.log.append(mode)
+        if self.cfl > 2.0 * self.limit:
+            from paper_2003_10561_gb300 import at_dns
+            raise at_dns.AtDnsError(at_dns.AT_DNS_E_UNSTABLE, "non-finite")
+        if self.cfl > self.limit:
+            self.k *= 10.0
+
+    def close(self):
+        pass
+
+
+@pytest.mark.parametrize("limit", [0.07, 0.2, 0.55])
+def test_ns_cfl_limit_bisects_to_the_threshold(limit):
+    """The bisection brackets the stability threshold within its tolerance,
+    runs the fixed worst-case delay for L > 0 (sync for L = 0), and treats
+    the library's unstable-state error as instability."""
+    log = []
+    got = st.ns_cfl_limit(lambda cfl: _FakeSolver(cfl, limit, log), None, L=2, lo=0.05, hi=2.0, tol=0.01)
+    assert limit - 0.01 <= got <= limit
+    assert set(log) == {"fixed"}
+    log.clear()
+    st.ns_cfl_limit(lambda cfl: _FakeSolver(cfl, limit, log), None, L=0, lo=0.05, hi=2.0, tol=0.01)
+    assert set(log) == {"sync"}
+
+
+def test_ns_cfl_limit_zero_when_even_the_lower_bound_fails():
+    assert st.ns_cfl_limit(lambda cfl: _FakeSolver(cfl, 0.01, []), None, L=1, lo=0.05) == 0.0
