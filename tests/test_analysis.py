@@ -140,3 +140,43 @@ def test_forced_stationary_state_stops_when_block_means_settle():
     s2 = _FakeForced()
     _, hist2 = analysis.forced_stationary_state(s2, None, block=10, max_blocks=4, tol=1e-9)
     assert len(hist2) == 4
+
+
+def test_synth_viscosity_meets_resolution_target():
+    """mu0_for_resolution: with rho = T = 1 (nu = mu0) the initial field's
+    dissipation nu <omega^2>, computed here through the analysis module's own
+    spectral derivatives, gives kappa_max eta = 1.5, kappa_max = sqrt(2) N / 3."""
+    n = (32, 32, 32)
+    mu0 = synth.mu0_for_resolution(n, k0=4.0, mach_t=0.3, seed=3)
+    U = synth.initial_state(n, k0=4.0, mach_t=0.3, seed=3)
+    rho, vel, p, T = analysis.primitives(U)
+    om2 = float(analysis.enstrophy_field(analysis.gradients(vel)).mean())
+    eta = (mu0 ** 3 / (mu0 * om2)) ** 0.25
+    assert abs(math.sqrt(2.0) * 32 / 3.0 * eta - 1.5) < 1e-10
+
+
+def test_synth_spectrum_shape():
+    """The shell energy of the initial velocity follows k^4 exp(-2 (k/k0)^2)
+    up to the sampling scatter of random amplitudes (shells 2..12 at 48^3)."""
+    n = (48, 48, 48)
+    U = synth.initial_state(n, k0=4.0, mach_t=0.3, seed=11)
+    rho, vel, p, T = analysis.primitives(U)
+    E = analysis.energy_spectrum(vel)
+    k = np.arange(2, 13, dtype=float)
+    ratio = E[2:13] / (k ** 4 * np.exp(-2.0 * (k / 4.0) ** 2))
+    assert np.all(np.abs(ratio / np.median(ratio) - 1.0) < 0.35)
+    assert E[20:].sum() < 1e-6 * E.sum()
+
+
+def test_synth_history_levels():
+    """history(): level l is U0 + (l + 1) eps dU, with a compressive dU (its
+    velocity has a non-zero divergence) and a density perturbation."""
+    n = (16, 12, 20)
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=2)
+    h = synth.history(U0, 4, eps=1e-2, seed=5)
+    d1, d2, d3 = h[1] - h[0], h[2] - h[1], h[3] - h[2]
+    assert np.allclose(d1, d2, atol=1e-14) and np.allclose(d2, d3, atol=1e-14)
+    assert np.allclose(h[0] - U0, d1, atol=1e-14)
+    dvel = d1[1:4]
+    div = sum(analysis.spectral_gradient(dvel[i])[i] for i in range(3))
+    assert np.max(np.abs(div)) > 1e-4 and np.max(np.abs(d1[0])) > 1e-4
