@@ -14,7 +14,7 @@ flush is needed between steps.
 Arms:
   default            the CUDA library (FP64 headline, FP32-bulk variant);
   --impl reference   the FP64 numpy oracle on the host cores, on a bounded
-                     sample of the same workload (64^3 with 2x2x2 PEs of 32^3).
+                     sample of the same workload (48^3 with 2x2x2 PEs of 24^3).
 
 Prints one JSON line (rank 0).
 """
@@ -36,7 +36,10 @@ N, PES, L, SEED = 256, 8, 2, 2024
 MU0 = None          # set from the resolution rule kappa_max eta = 1.5 at t = 0
 CFL_AT = 0.2        # min(0.5, 0.8 / f(L)), f(2) = 0.90*4 - 0.35*2 + 1 = 3.9 (Sec. 3.2)
 # FP64 operations per grid point of the main kernel, counted from the method
-# (FMA = 2; division, square root and power = 1 each); see the design notes.
+# (FMA = 2; division, square root and power = 1 each): 90 for the flux
+# divergence (15 first derivatives x 6), 84 for the second derivatives (12 x 7),
+# 36 for the mixed derivatives (6 x 6), ~100 for the assembly, 25 for the
+# update and ~40 for the statistics.
 FLOP_MAIN = 390.0
 # the 6th-order scheme adds one stencil pair to every first derivative
 # (15 flux + 6 mixed: +3 flops each) and second derivative (12: +3 each)
@@ -46,8 +49,7 @@ FLOP_MAIN6 = 489.0
 NB_FRAC = 1.0 - (28.0 / 32.0) ** 3
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max SM clock
 # DRAM bytes (read + write) of one launch of the dominant kernel, from ncu at
-# 128^3 with 4x4x4 PEs of 32^3 (profiles/k_main_fp64_128cube_4x4x4pes.md,
-# profiles/k_fused_fp32_128cube_4x4x4pes.md), scaled by the point count to the
+# 128^3 with 4x4x4 PEs of 32^3, scaled by the point count to the
 # 256^3 workload (same PE size; traffic grows with the points):
 # k_main<double, 2> 700.8 MB + 443.7 MB.  k_fused<float, 32, 8> measured
 # 112.5 MB + 50.0 MB before its ring-slot index moved out of the plane loop;

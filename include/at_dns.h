@@ -322,21 +322,27 @@ void at_dns_batch_destroy(at_dns_batch_t* b);
  * must not allocate or synchronise, plugins in processes that forbid new
  * allocations after start-up).
  *
- * Computes, in FP64 on the current device, the same right-hand side as
- * at_dns_rhs for a single PE (periodic box, no PE faces, hence no delays), no
- * forcing, with the physics parameters given here: u_dev is the state and
+ * Computes, in FP64 on the current device, the right-hand side that
+ * at_dns_rhs gives for a single PE (periodic box, no PE faces, hence no
+ * delays) of a handle with order 4, the total-energy form, the power-law
+ * viscosity mu0 T^visc_exp and no forcing: the call always uses the
+ * 4th-order central stencils, whatever scheme other handles use.  The
+ * physics parameters are given here (all finite): u_dev is the state and
  * rhs_dev receives R, both device pointers to 5*n0*n1*n2 doubles in the
  * layout above; stream is a cudaStream_t (NULL = legacy default stream).
  * The work is queued on that stream and the call returns without waiting.
  *
  * Work arrays come from one file-scope device array of fixed size (about
  * 59 MB, held by every GPU that loads the library until the process exits);
- * no allocation is made.  Its device address is looked up on the first call
- * on each device (make that first call before any stream capture).  All
+ * no allocation is made.  Its device address is looked up, with the
+ * caller's device current, on every call; the first call on a device also
+ * loads the library's device code there, so make that first call before any
+ * stream capture.  All
  * calls on a device share that array and it keeps the last call's contents:
  * calls whose work can overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.
- * Errors: INVALID_ARG (NULL pointer, n[d] < 5, bad physics values),
+ * Errors: INVALID_ARG (NULL pointer, n[d] < 5, gamma <= 1, prandtl <= 0,
+ * mu0 < 0, or a non-finite gamma, prandtl, mu0 or visc_exp),
  * TOO_LARGE (n0*n1*n2 > AT_DNS_NOALLOC_MAX_POINTS), CUDA. */
 int at_dns_rhs_noalloc(const int32_t n[3], double gamma, double prandtl, double mu0, double visc_exp,
                        const double* u_dev, double* rhs_dev, void* stream);

@@ -26,7 +26,7 @@ Paper passages followed, in the order of one step:
   A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15)) -- the paper discusses
   RK and keeps AB2 for AT because each RK stage would need a synchronisation.
 
-Readings where the paper is silent (each listed in the design notes):
+Readings where the paper is silent:
 
 * Non-dimensionalisation rho_0 = T_0 = c_0 = 1, so R = 1/gamma,
   p = rho T / gamma, c^2 = T, c_p = 1/(gamma-1).

@@ -18,7 +18,7 @@ Everything here is a plain restatement of the paper's formulas:
 * One-sided 4th-order first derivatives used for mixed derivatives at PE
   boundary points (Sec. 2.1, mixed-derivative paragraph; the paper says
   "standard one sided" without the order -- the 4th-order textbook stencils are
-  taken here, the reading recorded in the design notes):
+  taken here):
   at the first point   (-25, 48, -36, 16, -3)/12   on offsets 0..4
   at the second point  (-3, -10, 18, -6, 1)/12     on offsets -1..3
   and their mirror images at the right end of a PE.

@@ -775,6 +775,9 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     if (!(c.gamma > 1.0)) bad = "gamma must be > 1";
     else if (!(c.prandtl > 0)) bad = "prandtl must be > 0";
     else if (!(c.mu0 >= 0)) bad = "mu0 must be >= 0";
+    else if (!std::isfinite(c.gamma) || !std::isfinite(c.prandtl) || !std::isfinite(c.mu0) ||
+             !std::isfinite(c.visc_exp))
+      bad = "gamma, prandtl, mu0 and visc_exp must be finite";
     else if (c.max_delay < 0 || c.max_delay > 64) bad = "max_delay must be in [0, 64]";
     else if (c.comm_period < 1) bad = "comm_period must be >= 1";
     else if (c.precision != AT_DNS_P64 && c.precision != AT_DNS_P32 && c.precision != AT_DNS_P32C)

@@ -11,8 +11,8 @@
 // file-scope __device__ array of fixed size, so every GPU that loads this
 // library holds it (about 59 MB) until the process exits.
 #include <climits>
+#include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/at_dns.h"
 #include "common.cuh"
@@ -36,25 +36,17 @@ __global__ void k_noalloc_reset(unsigned long long* w) {
   w[3] = 0ULL;
 }
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_ptr[kMaxDevices] = {};   // device address of the array, per device
-
-// Device address of the scratch array on the current device, looked up once
-// per device with that device current (host code only sees a stand-in).
+// Device address of the scratch array on the current device (host code only
+// sees a stand-in for it).  Looked up on every call, with the caller's device
+// current: the lookup is a host-side query, not a stream operation, and it
+// stays right after a cudaDeviceReset has rebuilt the device's context (the
+// array can then sit at another address).  The first call on a device loads
+// the library's device code there.
 cudaError_t scratch_on_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_ptr[dev] = (double*)p;
-  }
-  *out = g_ptr[dev];
+  *out = (double*)p;
   return cudaSuccess;
 }
 
@@ -69,7 +61,9 @@ extern "C" int at_dns_rhs_noalloc(const int32_t n[3], double gamma, double prand
     npts *= n[d];
   }
   if (npts > kMaxPts) return AT_DNS_E_TOO_LARGE;
-  if (!(gamma > 1.0) || !(prandtl > 0) || !(mu0 >= 0)) return AT_DNS_E_INVALID_ARG;
+  if (!(gamma > 1.0) || !(prandtl > 0) || !(mu0 >= 0) || !std::isfinite(gamma) || !std::isfinite(prandtl) ||
+      !std::isfinite(mu0) || !std::isfinite(visc_exp))
+    return AT_DNS_E_INVALID_ARG;
   double* base = nullptr;
   if (scratch_on_current_device(&base) != cudaSuccess) return AT_DNS_E_CUDA;
 
