@@ -45,7 +45,8 @@ FLOP_MAIN = 390.0
 # (15 flux + 6 mixed: +3 flops each) and second derivative (12: +3 each)
 FLOP_MAIN6 = 489.0
 # algorithmic HBM bytes per grid point of one step (read U, R^{n-1}; write U^{n+1},
-# R^n; plus the slab ring: 1 write + 3 reads of 5 variables at the N_B fraction)
+# R^n -- and the low words of U in the compensated FP32 form; plus the FP64
+# slab ring: 1 write + T_l reads of 5 variables at the N_B fraction)
 NB_FRAC = 1.0 - (28.0 / 32.0) ** 3
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max SM clock
 # DRAM bytes (read + write) of one launch of the dominant kernel, from ncu at
@@ -78,12 +79,16 @@ def nb_frac(order):
     return 1.0 - ((nl - order) / float(nl)) ** 3
 
 
-def algorithmic_bytes(elem, order=4):
-    """Read U, R^{n-1}; write U^{n+1}, R^n; the slab ring: 1 write + 3 reads of
-    5 variables at the N_B fraction (T_l = 3 reads at 4th order; at 6th order
-    T_l = 4 levels are read)."""
+STATE_WORDS = {"p64": (8, 4), "p32": (4, 4), "p32c": (4, 6)}   # (bytes, words moved per variable)
+
+
+def algorithmic_bytes(prec, order=4):
+    """Read U, R^{n-1}; write U^{n+1}, R^n (P32C also reads and writes the low
+    words of U); the FP64 slab ring: 1 write + T_l reads of 5 variables at the
+    N_B fraction (T_l = 3 at 4th order, 4 at 6th order)."""
+    elem, words = STATE_WORDS[prec]
     reads = 3 if order == 4 else 4
-    return 4 * 5 * elem + nb_frac(order) * 5 * elem * (1 + reads)
+    return words * 5 * elem + nb_frac(order) * 5 * 8 * (1 + reads)
 
 
 class Clocks:
@@ -156,23 +161,50 @@ def job_rate(world, points, steps, ms):
     return world * points * steps / (ms / 1e3)
 
 
-def oracle_rate(steps, warmup, n=48, pes=2):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
-    import numpy as np
+ORACLE_N, ORACLE_PES = 48, 2
+
+
+def _oracle_worker(steps, warmup, n, pes, seed, barrier, out):
+    """One host core: the FP64 oracle, as it stands, stepping its own copy of
+    the bounded sample (single-threaded numpy)."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    sys.path.insert(0, ROOT)
     from oracle import ns
     from paper_2003_10561_gb300 import synth
-    U0 = synth.initial_state((n, n, n), k0=4.0, mach_t=0.3, seed=0)
-    cfg = ns.Config(n=(n, n, n), pes=(pes, pes, pes), mu0=0.01, max_delay=L, seed=SEED)
+    U0 = synth.initial_state((n, n, n), k0=4.0, mach_t=0.3, seed=seed)
+    cfg = ns.Config(n=(n, n, n), pes=(pes, pes, pes), mu0=0.01, max_delay=L, seed=SEED + seed)
     cfg.dt = ns.dt_from_cfl(cfg, U0, CFL_AT)
-    hist = synth.history(U0, cfg.n_levels, eps=1e-3, seed=3)
+    hist = synth.history(U0, cfg.n_levels, eps=1e-3, seed=3 + seed)
     run = ns.Run.start(cfg, None, ns.RANDOM, step=cfg.n_levels + 2, history=hist)
     for _ in range(warmup):
         run.step()
+    barrier.wait()
     t0 = time.perf_counter()
     for _ in range(steps):
         run.step()
-    el = time.perf_counter() - t0
-    return n ** 3 * steps / el, el
+    out.put(time.perf_counter() - t0)
+
+
+def oracle_rate(steps, warmup, n=ORACLE_N, pes=ORACLE_PES, workers=None):
+    """The FP64 oracle on all host cores: one spawned process per core, each
+    stepping its own copy of an n^3 sample of the workload; the rate is the
+    points all processes advanced over the slowest process's time.  Returns
+    (rate, elapsed seconds, processes)."""
+    import multiprocessing as mp
+    workers = workers or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(steps, warmup, n, pes, i, barrier, out), daemon=True)
+             for i in range(workers)]
+    for p_ in procs:
+        p_.start()
+    els = [out.get() for _ in procs]
+    for p_ in procs:
+        p_.join()
+    el = max(els)
+    return workers * n ** 3 * steps / el, el, workers
 
 
 def run_reference(args, world, rank):
@@ -180,13 +212,15 @@ def run_reference(args, world, rank):
         return 0
     steps = max(1, args.steps)
     warm = max(0, args.warmup)
-    rate, el = oracle_rate(steps, warm)
-    sample = "FP64 numpy oracle: AB2 steps of a 48^3 box with 2x2x2 PEs of 24^3 points, random delays L = 2 (the workload's method at a size the oracle finishes in seconds)"
+    rate, el, cores = oracle_rate(steps, warm)
+    sample = ("FP64 numpy oracle, one process per host core (%d), each taking AB2 steps of its own 48^3 box with "
+              "2x2x2 PEs of 24^3 points, random delays L = 2 (the workload's method at a size the oracle "
+              "finishes in seconds)" % cores)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(world),
-            "cpu_baseline": {"kind": "oracle", "value": rate, "unit": UNIT, "cores": 1, "sample": sample},
+            "cpu_baseline": {"kind": "oracle", "value": rate, "unit": UNIT, "cores": cores, "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -246,7 +280,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", type=int, default=N, help="points per direction (profiling cases)")
     ap.add_argument("--pes", type=int, default=PES, help="virtual PEs per direction")
-    ap.add_argument("--precision", default="both", choices=["both", "p64", "p32"])
+    ap.add_argument("--precision", default="both", choices=["both", "p64", "p32c", "p32"],
+                    help="both: FP64 and the FP32-bulk form (P32C: FP32 stencils, compensated FP32 update, "
+                         "FP64 ring and reductions)")
     ap.add_argument("--path", default="auto", choices=["auto", "multipass", "fused"])
     ap.add_argument("--order", default="both", choices=["both", "4", "6"],
                     help="spatial order of the AT scheme (4: headline; 6: Table B (1,6)/(2,6))")
@@ -281,7 +317,7 @@ def main():
     stream = torch.cuda.Stream()
     res = {}
     clocks = Clocks(os.path.join(args.clocks_dir or tempfile.gettempdir(), "bench_clocks_rank%d.csv" % rank))
-    precs = ("p64", "p32") if args.precision == "both" else (args.precision,)
+    precs = ("p64", "p32c") if args.precision == "both" else (args.precision,)
     orders = (4, 6) if args.order == "both" else (int(args.order),)
     legs = [(p, o) for o in orders for p in precs]
     for prec, order in legs:
@@ -300,32 +336,38 @@ def main():
             ms, kt = timed_steps(s, stream, args.steps, args.warmup, torch, profile=True)
         ms = max_over_ranks(ms, pg, "cuda")
         st = s.stats()
-        res[key] = {"ms": ms, "kt": kt, "stats": st, "info": s.info(), "order": order,
+        res[key] = {"ms": ms, "kt": kt, "stats": st, "info": s.info(), "order": order, "prec": prec,
                     "dtype": "f64" if prec == "p64" else "f32"}
         # kernels in the timed region: every replayed step plus the health reset
         res[key]["launches"] = args.steps * res[key]["info"]["kernels_per_step"] + 1
         res[key]["path"] = "fused" if res[key]["info"]["kernel_path"] == at_dns.AT_DNS_PATH_FUSED else "multipass"
         res[key]["tile"] = res[key]["info"]["tile"]
         # end to end through the public API with host buffers: per step, upload
-        # U^n from pinned host memory (as the state of step n), step, read the
-        # statistics record back
+        # U^n from pinned host memory (as the state of step n), step, read
+        # U^{n+1} back into pinned host memory and the statistics record
         if key == "p64" and not args.no_e2e:
-            host = torch.from_numpy(U0).pin_memory()
+            host = torch.from_numpy(U0.copy()).pin_memory()
+            back = torch.empty_like(host).pin_memory()
             nlev = at_dns.at_dns_get_info(s.h).n_levels
-            e2e_steps = max(3, args.steps // 4)
+            e2e_steps = max(20, args.steps)
             s.set_history(host[None], nlev + 3)
             s.step(1, "random")
+            s.get_state(back)
             s.stats()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for k in range(e2e_steps):
                 s.set_history(host[None], nlev + 3 + k)
                 s.step(1, "random")
+                s.get_state(back)
                 s.stats()
             el = max_over_ranks((time.perf_counter() - t0) * 1e3, pg, "cuda") / 1e3   # the slowest rank's
             res["e2e"] = {"value": world * N ** 3 * e2e_steps / el, "unit": UNIT,
-                          "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(ctypes_stats_size(at_dns)),
-                          "steps": e2e_steps}
+                          "h2d_bytes_per_step": int(U0.nbytes),
+                          "d2h_bytes_per_step": int(U0.nbytes) + int(ctypes_stats_size(at_dns)),
+                          "steps": e2e_steps,
+                          "per_step": "set_history(U^n from pinned host) + step(1) + get_state(U^{n+1} to pinned "
+                                      "host) + stats()"}
         s.close()
 
     # synchronous low-storage RK3 (three right-hand sides per step), FP64
@@ -368,7 +410,7 @@ def main():
             nb = (32, 48, 64, 96, 128)[i % 5]
             k0 = (3.0, 4.0, 6.0)[i % 3]
             mt = 0.1 + 0.4 * i / 63.0
-            specs.append(dict(n=(nb, nb, nb), pes=(nb // 16,) * 3, precision="p32", gamma=1.4, prandtl=0.7,
+            specs.append(dict(n=(nb, nb, nb), pes=(nb // 16,) * 3, precision="p32c", gamma=1.4, prandtl=0.7,
                               visc_exp=0.76, mu0=mu_of[nb], cfl=CFL_AT, dt=0.0, max_delay=L, seed=i,
                               stats_every=1))
             states.append(synth.initial_state((nb,) * 3, k0=k0, mach_t=mt, seed=i))
@@ -394,18 +436,19 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, el = oracle_rate(3, 1)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "3 AB2 steps (after 1 warm-up) of the FP64 numpy oracle on 48^3 with 2x2x2 PEs of "
-                         "24^3 points, random delays L = 2, single-threaded numpy; %.1f s timed" % el}
+        rate, el, cores = oracle_rate(3, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "3 AB2 steps (after 1 warm-up) of the FP64 numpy oracle in each of %d processes (one per "
+                         "host core), each on its own 48^3 box with 2x2x2 PEs of 24^3 points, random delays "
+                         "L = 2; %.1f s timed (slowest process)" % (cores, el)}
 
     if rank != 0:
         return 0
     pk = peaks()
     pts = float(N ** 3)
     p64 = res.get("p64")
-    p32 = res.get("p32")
-    head = p64 or p32 or res.get("p64_o6") or res.get("p32_o6")
+    p32 = res.get("p32c") or res.get("p32")
+    head = p64 or p32 or res.get("p64_o6") or res.get("p32c_o6") or res.get("p32_o6")
     value = job_rate(world, pts, args.steps, head["ms"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -444,12 +487,15 @@ def main():
             "workload": "the headline workload with the internal-energy form (Eq. (ie)) and Sutherland viscosity"}
     line["roofline"] = rep[[k for k in res if res[k] is head][0]]["roofline"]
     if p32 and p32 is not head:
-        blk = rep["p32"]
+        blk = rep[p32["prec"]]
+        blk["form"] = {"p32c": "P32C: FP32 state and stencils, compensated (TwoSum hi + lo) FP32 update, FP64 slab "
+                               "ring, compensated FP32 sums within a block and FP64 across blocks",
+                       "p32": "P32: FP32 state, stencils and update; FP64 slab ring and reductions"}[p32["prec"]]
         if p64:
             blk["rel_err_vs_fp64"] = {k: abs(p32["stats"][k] - p64["stats"][k]) / abs(p64["stats"][k])
                                       for k in ("tke", "dissipation")}
         line["fp32_bulk"] = blk
-    o6 = {k[:-3]: rep[k] for k in ("p64_o6", "p32_o6") if k in rep and res[k] is not head}
+    o6 = {k[:-3]: rep[k] for k in ("p64_o6", "p32c_o6", "p32_o6") if k in rep and res[k] is not head}
     if o6:
         line["order6"] = dict(o6, workload="the same box, PEs, delays and state with the 6th-order AT scheme "
                                             "(Table B (1,6)/(2,6), T_l = 4, N_B %.1f%%)" % (100 * nb_frac(6)))
@@ -474,17 +520,17 @@ def leg_report(r, world, pts, steps, pk):
                 "note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
                         "(an FMA probe measured 1.20 TFLOP/s)"}
         # the same kernel against the HBM roof, at the step's algorithmic bytes
-        gbs = algorithmic_bytes(8, order) * pts / t_main / 1e9
+        gbs = algorithmic_bytes("p64", order) * pts / t_main / 1e9
         roof["hbm"] = {"achieved": gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                       "frac": gbs / pk.get("hbm_gbs", 6800.0), "bytes_per_point": algorithmic_bytes(8, order)}
+                       "frac": gbs / pk.get("hbm_gbs", 6800.0), "bytes_per_point": algorithmic_bytes("p64", order)}
     else:
-        achieved = algorithmic_bytes(4, order) * pts / t_main / 1e9
+        achieved = algorithmic_bytes(r["prec"], order) * pts / t_main / 1e9
         kname = "k_fused" if r["path"] == "fused" else "k_main"
         traffic = K_FUSED_FP32_TRAFFIC_256 if (order == 4 and N == 256 and PES == 8 and r["path"] == "fused"
                                                and list(r["tile"]) == [32, 8, 32] and K_FUSED_FP32_TRAFFIC_256) else None
         roof = {"bound": "hbm", "kernel": "%s (FP32, order %d)" % (kname, order), "achieved": achieved,
                 "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0),
-                "traffic": traffic, "bytes_per_point": algorithmic_bytes(4, order)}
+                "traffic": traffic, "bytes_per_point": algorithmic_bytes(r["prec"], order)}
     return {"value": job_rate(world, pts, steps, r["ms"]), "unit": UNIT, "kernel_path": r["path"], "tile": r["tile"],
             "ms_per_step": r["ms"] / steps, "dtype": r["dtype"], "roofline": roof,
             "kernel_ms_per_step": {k: v[1] / v[0] for k, v in r["kt"].items()}}

@@ -134,16 +134,15 @@ __global__ void k_join_double(const float* __restrict__ hi, const float* __restr
   if (i < count) out[i] = (double)hi[i] + (double)lo[i];
 }
 
-// Write the PE-boundary slabs of field U (S, [5][npts]) into ring slot `slot`:
-// the M layers next to each face, slab index 2M pe + t (t < M: local t,
-// t >= M: local nl - 2M + t).
-template <typename S>
-__global__ void k_ring_store(Geom g, const S* __restrict__ U, S* r0, S* r1, S* r2, int slot) {
+// Write the PE-boundary slabs of the FP64 field U ([5][npts]) into ring slot
+// `slot` (the ring is FP64 in every precision form): the M layers next to each
+// face, slab index 2M pe + t (t < M: local t, t >= M: local nl - 2M + t).
+__global__ void k_ring_store(Geom g, const double* __restrict__ U, double* r0, double* r1, double* r2, int slot) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= g.npts) return;
   int c[3];
   decode(g, idx, c[0], c[1], c[2]);
-  S* rings[3] = {r0, r1, r2};
+  double* rings[3] = {r0, r1, r2};
   const int M = g.M;
   for (int d = 0; d < 3; ++d) {
     if (g.pes[d] == 1) continue;
@@ -380,13 +379,25 @@ std::vector<Mode3> forcing_modes(double kf) {
   return out;
 }
 
+// The PE-boundary slabs of an FP64 level on the device into ring slot `slot`.
+int ring_store(at_dns* h, const double* field, int slot) {
+  const bool any = h->g.pes[0] > 1 || h->g.pes[1] > 1 || h->g.pes[2] > 1;
+  if (!any) return AT_DNS_OK;
+  k_ring_store<<<nblk(h->g.npts), kBlock, 0, h->st>>>(h->g, field, (double*)h->ring[0], (double*)h->ring[1],
+                                                      (double*)h->ring[2], slot);
+  CK(cudaGetLastError());
+  return AT_DNS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // typed operations
 template <typename S>
 struct Ops {
   static S* U(at_dns* h, int i) { return (S*)h->U[i]; }
 
-  static int upload_field(at_dns* h, const double* src, int where, S* dst) {
+  // Upload an FP64 level into dst (S); *dev_src receives the FP64 copy of it
+  // on the device (the caller's buffer, or the staging buffer).
+  static int upload_field(at_dns* h, const double* src, int where, S* dst, const double** dev_src) {
     const long long cnt = 5 * h->g.npts;
     const double* dsrc = src;
     if (where == AT_DNS_HOST) {
@@ -395,6 +406,7 @@ struct Ops {
       CK(cudaMemcpyAsync(h->stage, src, cnt * sizeof(double), cudaMemcpyHostToDevice, h->st));
       dsrc = h->stage;
     }
+    *dev_src = dsrc;
     if (sizeof(S) == sizeof(double)) {
       if ((const void*)dsrc != (const void*)dst)
         CK(cudaMemcpyAsync(dst, dsrc, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
@@ -408,14 +420,6 @@ struct Ops {
     return AT_DNS_OK;
   }
 
-  static int ring_store(at_dns* h, const S* field, int slot) {
-    bool any = h->g.pes[0] > 1 || h->g.pes[1] > 1 || h->g.pes[2] > 1;
-    if (!any) return AT_DNS_OK;
-    k_ring_store<S><<<nblk(h->g.npts), kBlock, 0, h->st>>>(h->g, field, (S*)h->ring[0], (S*)h->ring[1],
-                                                         (S*)h->ring[2], slot);
-    CK(cudaGetLastError());
-    return AT_DNS_OK;
-  }
 
   static int download(at_dns* h, double* out, int where) {
     const long long cnt = 5 * h->g.npts;
@@ -462,7 +466,7 @@ struct Ops {
     const S* U1 = U(h, 1);
     const Coef<S> K = make_coef<S>(g, h->ph, h->dt);
     S* GH[3] = {(S*)h->GH[0], (S*)h->GH[1], (S*)h->GH[2]};
-    S* ring[3] = {(S*)h->ring[0], (S*)h->ring[1], (S*)h->ring[2]};
+    double* ring[3] = {(double*)h->ring[0], (double*)h->ring[1], (double*)h->ring[2]};
     if (!h->fused) { Timed t(h, KD_PRIM); CK(launch_prim<S>(g, K, U0, U1, h->ds, (S*)h->PQ, st)); }
     if (g.pes[0] > 1 || g.pes[1] > 1 || g.pes[2] > 1) {
       Timed t(h, KD_GHOST);
@@ -862,7 +866,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     if (g.pes[d] == 1) continue;
     const size_t gpts = 2ull * M * g.pes[d] * (size_t)g.plane[d];
     if ((rc = dev_alloc(h, &h->GH[d], (size_t)kNumGhostQ * gpts * S)) ||
-        (rc = dev_alloc(h, &h->ring[d], (size_t)g.nlev * 5 * gpts * S)))
+        (rc = dev_alloc(h, &h->ring[d], (size_t)g.nlev * 5 * gpts * sizeof(double))))
       return create_fail(h, rc);
   }
   const int P = g.pes[0] * g.pes[1] * g.pes[2];
@@ -908,16 +912,15 @@ int at_dns_set_history(at_dns_t* h, const double* levels, int32_t nlevels, int64
   for (int l = nlevels - 1; l >= 0; --l) {
     const double* lv = levels + (size_t)l * cnt;
     const int last = l == nlevels - 1 ? h->g.nlev - 1 : l;
+    const double* dev_lv = nullptr;   // the level in FP64 on the device
     if (h->p64) {
-      if ((rc = Ops<double>::upload_field(h, lv, where, Ops<double>::U(h, h->cur)))) return rc;
+      if ((rc = Ops<double>::upload_field(h, lv, where, Ops<double>::U(h, h->cur), &dev_lv))) return rc;
     } else {
-      if ((rc = Ops<float>::upload_field(h, lv, where, Ops<float>::U(h, h->cur)))) return rc;
+      if ((rc = Ops<float>::upload_field(h, lv, where, Ops<float>::U(h, h->cur), &dev_lv))) return rc;
     }
     for (int ll = l; ll <= last; ++ll) {
       const int slot = (int)(((step - ll) % h->g.nlev + h->g.nlev) % h->g.nlev);
-      rc = h->p64 ? Ops<double>::ring_store(h, Ops<double>::U(h, h->cur), slot)
-                  : Ops<float>::ring_store(h, Ops<float>::U(h, h->cur), slot);
-      if (rc) return rc;
+      if ((rc = ring_store(h, dev_lv, slot))) return rc;
     }
   }
   // stage holds U^step in FP64 now (host path) -- ensure it for the dt reduction

@@ -311,7 +311,7 @@ struct StepArgs {
   S* Rprev;            // [5][npts] R^{n-1} in, R^n out
   const S* Ulo;        // compensated form: low words of U (else null)
   S* Ulo_next;         // compensated form: low words of U^{n+1}
-  S* ring[3];          // [nlev][5][2M P_d][plane_d]
+  double* ring[3];     // [nlev][5][2M P_d][plane_d], FP64 in every precision form
   double* Rout;        // rhs-only output [5][npts] or null
   double* partial;     // [gridDim.x][kNumStat]
   unsigned long long* words;  // [0] max wave key, [1] min rho key, [2] min p key, [3] health
@@ -435,6 +435,75 @@ __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
+// ---------------------------------------------------------------------------
+// FP64 values in the FP32 forms with integer instructions only.  The slab ring
+// of past levels is FP64 in every form; an FP64 (or FP32 <-> FP64 conversion)
+// instruction in an FP32 kernel would run on the FP64 pipe, a few per cent of
+// the FP32 rate on GB300, and a lane that takes it holds the whole warp.
+
+// f as a double (exact for normal floats; subnormals flush to signed zero).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned long long sg = (unsigned long long)(b & 0x80000000u) << 32;
+  if (e == 0u) return __longlong_as_double((long long)sg);
+  const unsigned long long ed = e == 0xFFu ? 0x7FFULL : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(sg | (ed << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
+// hi + lo as a double, for a renormalised pair (|lo| <= ulp(hi)/2, as the
+// compensated update leaves it): hi's 24-bit significand widened to 53 bits
+// plus lo's, aligned to it (lo's bits beyond the 53rd are truncated, a
+// relative error below 2^-52).  Any other pair takes the FP64 add.
+__device__ __forceinline__ double pair_to_double(float hi, float lo) {
+  const unsigned bh = __float_as_uint(hi), bl = __float_as_uint(lo);
+  const int eh = (int)((bh >> 23) & 0xFFu), el = (int)((bl >> 23) & 0xFFu);
+  if (el == 0) return f2d_bits(hi);                        // lo is zero (or subnormal)
+  if (eh == 0 || eh == 0xFF || el == 0xFF) return __dadd_rn(f2d_bits(hi), f2d_bits(lo));
+  // hi = Mh 2^(eh-150) = M u with M = Mh 2^29, u = 2^(eh-179); lo = Ml 2^(el-eh+29) u
+  const int sh = el - eh + 29;
+  if (sh > 5) return __dadd_rn(f2d_bits(hi), f2d_bits(lo));
+  unsigned long long M = (unsigned long long)((bh & 0x7FFFFFu) | 0x800000u) << 29;
+  const unsigned long long Ml = (bl & 0x7FFFFFu) | 0x800000u;
+  const unsigned long long add = sh >= 0 ? Ml << sh : (sh > -40 ? Ml >> (-sh) : 0ULL);
+  int ed = eh + 896;
+  if ((bh ^ bl) & 0x80000000u) {
+    M -= add;                                               // >= 2^52 - 2^28
+    if (M < (1ULL << 52)) { M <<= 1; ed -= 1; }
+  } else {
+    M += add;                                               // < 2^53 for a renormalised pair
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(bh & 0x80000000u) << 32) |
+                                          ((unsigned long long)ed << 52) | (M & 0xFFFFFFFFFFFFFULL)));
+}
+
+// d = hi + lo with hi = d truncated to 24 significant bits (exact) and lo the
+// remaining 29 bits rounded to a float.  |d| below 2^-126 flushes to a signed
+// zero; |d| of 2^128 or more, infinities and NaNs give an infinite or NaN hi.
+__device__ __forceinline__ void split_double(double d, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  const unsigned sg = bh & 0x80000000u;
+  const int ef = (int)((bh >> 20) & 0x7FFu) - 896;           // biased float exponent
+  lo = 0.f;
+  if (ef <= 0) { hi = __uint_as_float(sg); return; }
+  const unsigned mant = ((bh & 0xFFFFFu) << 3) | (bl >> 29);
+  if (ef >= 255) {
+    const bool nan = ((bh >> 20) & 0x7FFu) == 0x7FFu && ((bh & 0xFFFFFu) | bl) != 0u;
+    hi = __uint_as_float(sg | 0x7F800000u | (nan ? 0x400000u : 0u));
+    return;
+  }
+  hi = __uint_as_float(sg | ((unsigned)ef << 23) | mant);
+  const unsigned r = bl & 0x1FFFFFFFu;                       // d - hi = +-r 2^(ef-179)
+  const int es = ef - 52;                                    // biased exponent of 2^(ef-179)
+  if (r != 0u && es > 0) lo = __uint_as_float(__float_as_uint((float)r * __uint_as_float((unsigned)es << 23)) | sg);
+}
+
+// The FP64 ring value of a state variable: the double itself, or hi + lo of
+// the compensated FP32 form (lo = 0 in the plain FP32 form).
+__device__ __forceinline__ double ring_value(double hi, double) { return hi; }
+__device__ __forceinline__ double ring_value(float hi, float lo) { return pair_to_double(hi, lo); }
+
 // AB2 update of the five variables of one point (Eq. (time_ab)):
 // U^{n+1} = U^n + dt (3/2 R^n - 1/2 R^{n-1}), forward Euler on the first step.
 // With low words (compensated FP32 form) the state is carried as hi + lo and
@@ -449,10 +518,11 @@ __device__ __forceinline__ bool needs_rprev(const StepArgs<S>& A, const StepDyn<
 }
 
 // F: 0 AB2 step, 1 RK3 stage, 2 either (A.rk read per point).
+// unlo: the low words of U^{n+1} (zero without compensation), for the ring.
 template <int F, typename S>
 __device__ __forceinline__ void ab2_update_v(const Coef<S>& K, const StepArgs<S>& A, const StepDyn<S>& D, long long idx,
                                              long long N, const S (&Uo)[5], const S (&R)[5], S (&un)[5],
-                                             unsigned& health, const S* Rp) {
+                                             S (&unlo)[5], unsigned& health, const S* Rp) {
   const bool ld = needs_rprev(A, D);
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -474,10 +544,12 @@ __device__ __forceinline__ void ab2_update_v(const Coef<S>& K, const StepArgs<S>
       const S e = add_rn(sub_rn(Uo[v], sub_rn(s, bp)), sub_rn(dlt, bp));
       const S lo = add_rn(D.Ulo[v * N + idx], e);
       const S hi = add_rn(s, lo);                               // renormalise
-      D.Ulo_next[v * N + idx] = sub_rn(lo, sub_rn(hi, s));
+      unlo[v] = sub_rn(lo, sub_rn(hi, s));
+      D.Ulo_next[v * N + idx] = unlo[v];
       un[v] = hi;
     } else {
       un[v] = fma(scale, inc, Uo[v]);
+      unlo[v] = S(0);
     }
     D.Unext[v * N + idx] = un[v];
     A.Rprev[v * N + idx] = kept;
@@ -492,12 +564,12 @@ __device__ __forceinline__ void ab2_update_v(const Coef<S>& K, const StepArgs<S>
 template <typename S>
 __device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& A, const StepDyn<S>& D, long long idx,
                                            long long N, const S (&Uo)[5], const S (&R)[5], S (&un)[5],
-                                           unsigned& health, const S* Rp = nullptr) {
+                                           S (&unlo)[5], unsigned& health, const S* Rp = nullptr) {
   if constexpr (sizeof(S) == 8) {
-    if (A.rk) ab2_update_v<1>(K, A, D, idx, N, Uo, R, un, health, Rp);
-    else ab2_update_v<0>(K, A, D, idx, N, Uo, R, un, health, Rp);
+    if (A.rk) ab2_update_v<1>(K, A, D, idx, N, Uo, R, un, unlo, health, Rp);
+    else ab2_update_v<0>(K, A, D, idx, N, Uo, R, un, unlo, health, Rp);
   } else {
-    ab2_update_v<2>(K, A, D, idx, N, Uo, R, un, health, Rp);
+    ab2_update_v<2>(K, A, D, idx, N, Uo, R, un, unlo, health, Rp);
   }
 }
 

@@ -1,8 +1,9 @@
 // AT-DNS step kernels, templated on the scalar type S (double for the FP64
-// form, float for the FP32-bulk form).  Every per-point operation -- storage,
-// stencils, AT extrapolation, update and the slab ring of past levels -- is in
-// S; the statistics are summed in FP64 across points in a fixed order (FP32
-// form: within a warp in FP32 first).
+// form, float for the FP32-bulk forms).  The stencils, the AT extrapolation
+// and the update run in S; the slab ring of past levels is FP64 in every form
+// (the FP32 forms write and read it with integer instructions); the
+// statistics are summed in FP64 across points in a fixed order (FP32 forms:
+// compensated FP32 sums within a block first).
 //
 // One RHS evaluation (Sec. 2) is four launches:
 //   k_prim   per point: u, v, w, T and the 12 non-trivial inviscid fluxes;
@@ -77,6 +78,47 @@ __device__ __forceinline__ void ghost_quantities(const Coef<S>& K, int d, const 
   q[8] = T;
 }
 
+// FP32 forms: the AT ghost value sum_l w_l q(U^{n-k-l}) from FP64 levels.
+// With B = level n-k truncated to FP32 and sum_l w_l = 1 (Table B), it is
+// q(B) + sum_l w_l [q(U_l) - q(B)]; each difference is formed from
+// dU_l = U_l - B (exact in FP32 up to rounding of the difference itself) by
+// the identities
+//   d(a b) = da b + (a + da) db,          du_i = (dm_i - u_i drho) / (rho + drho),
+//   dp = (gamma-1) (dE - d(m.u)/2),       dT = (gamma dp - T drho) / (rho + drho),
+// so the rounding error stays relative to q (not amplified by Table B's
+// weights, sum_l |w_l| = 17 at k = 2 and 111 at k = 3 for the 6th order) and
+// to the differences, which are small.  Integer instructions split the FP64
+// values (no FP64 arithmetic in the FP32 kernels).
+struct GhostBase {
+  float r, m[3], E;          // B, level n-k truncated to FP32
+  float u[3], p, T, H;       // its primitives and the fifth flux's factor
+};
+
+__device__ __forceinline__ void ghost_delta_f32(const Coef<float>& K, int d, const GhostBase& B, const float (&dU)[5],
+                                                float (&dq)[kNumGhostQ]) {
+  const float dr = dU[0], dE = dU[4];
+  const float inv2 = rcp_rn(B.r + dr);
+  float du[3], m2[3];
+  float dmu = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    du[i] = fmaf(-B.u[i], dr, dU[1 + i]) * inv2;
+    m2[i] = B.m[i] + dU[1 + i];
+    dmu = fmaf(dU[1 + i], B.u[i], fmaf(m2[i], du[i], dmu));
+  }
+  const float dp = K.eform ? K.gm1 * dE : K.gm1 * fmaf(-0.5f, dmu, dE);
+  const float dH = K.eform ? dE : dE + dp;
+  const float ud = B.u[d], dud = du[d];
+  dq[0] = dU[1 + d];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) dq[1 + i] = fmaf(dU[1 + i], ud, m2[i] * dud) + (i == d ? dp : 0.f);
+  dq[4] = fmaf(dH, ud, (B.H + dH) * dud);
+  dq[5] = du[0];
+  dq[6] = du[1];
+  dq[7] = du[2];
+  dq[8] = fmaf(K.gamma, dp, -B.T * dr) * inv2;
+}
+
 // ---------------------------------------------------------------------------
 // AT ghost assembly.  Ghost slot s of PE column p_d along d (2M slots): s < M
 // is the local coordinate s - M (left face, face 2d), s >= M is nl + s - M
@@ -86,9 +128,9 @@ template <typename S, int M>
 __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __restrict__ U0,
                                                const S* __restrict__ U1, const DevState* __restrict__ ds,
                                                const S* __restrict__ PQ, S* GH0, S* GH1, S* GH2,
-                                               const S* __restrict__ ring0,
-                                               const S* __restrict__ ring1,
-                                               const S* __restrict__ ring2,
+                                               const double* __restrict__ ring0,
+                                               const double* __restrict__ ring1,
+                                               const double* __restrict__ ring2,
                                                const uint8_t* __restrict__ dmap, long long n,
                                                long long cnt0, long long cnt1, long long cnt2) {
   long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -100,7 +142,7 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   else if ((j -= cnt1) < cnt2) d = 2;
   else return;
   S* GH = d == 0 ? GH0 : (d == 1 ? GH1 : GH2);
-  const S* ring = d == 0 ? ring0 : (d == 1 ? ring1 : ring2);
+  const double* ring = d == 0 ? ring0 : (d == 1 ? ring1 : ring2);
   // j < 2M P_d plane_d < npts < 2^31 (grids hold fewer than 2^31 points), so
   // the index arithmetic below runs in 32 bits (no 64-bit division)
   const unsigned plane = (unsigned)g.plane[d];
@@ -152,23 +194,68 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   int wi[M + 1];
   at_weights<M>(k, wi);
   S acc[kNumGhostQ];
-#pragma unroll
-  for (int q = 0; q < kNumGhostQ; ++q) acc[q] = S(0);
   // ring slot of level n - k - l (>= 1: delays start after L + T_l steps);
   // k + l <= L + M < nlev, so one wrap of (n mod nlev) - k - l suffices
   const int nm = ring_slot(g, n);
-#pragma unroll
-  for (int l = 0; l <= M; ++l) {
+  auto level_at = [&](int l, int v) {
     int rs = nm - k - l;
     if (rs < 0) rs += g.nlev;
-    const S w = S(wi[l]);
-    S Uv[5], q[kNumGhostQ];
+    return ring[(((long long)rs * 5 + v) * NS * P + sp) * plane + pl];
+  };
+  if constexpr (sizeof(S) == 8) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v)
-      Uv[v] = ring[(((long long)rs * 5 + v) * NS * P + sp) * plane + pl];
-    ghost_quantities(K, d, Uv, q);
+    for (int q = 0; q < kNumGhostQ; ++q) acc[q] = S(0);
 #pragma unroll
-    for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = fma(w, q[qq], acc[qq]);
+    for (int l = 0; l <= M; ++l) {
+      const S w = S(wi[l]);
+      S Uv[5], q[kNumGhostQ];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Uv[v] = level_at(l, v);
+      ghost_quantities(K, d, Uv, q);
+#pragma unroll
+      for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = fma(w, q[qq], acc[qq]);
+    }
+  } else {
+    // base B = level n-k truncated to FP32; its own remainder is level 0's dU
+    GhostBase B;
+    float dU[5];
+    {
+      float hb[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) split_double(level_at(0, v), hb[v], dU[v]);
+      B.r = hb[0];
+      B.m[0] = hb[1];
+      B.m[1] = hb[2];
+      B.m[2] = hb[3];
+      B.E = hb[4];
+      S q[kNumGhostQ];
+      ghost_quantities(K, d, hb, q);
+#pragma unroll
+      for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = q[qq];
+      const float inv = rcp_rn(B.r);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) B.u[i] = B.m[i] * inv;
+      B.p = pressure(K, B.m[0], B.m[1], B.m[2], B.u[0], B.u[1], B.u[2], B.E);
+      B.T = K.gamma * B.p * inv;
+      B.H = K.eform ? B.E : B.E + B.p;
+    }
+#pragma unroll
+    for (int l = 0; l <= M; ++l) {
+      if (l > 0) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          float hi, lo;
+          split_double(level_at(l, v), hi, lo);
+          const float hb = v == 0 ? B.r : (v == 4 ? B.E : B.m[v - 1]);
+          dU[v] = (hi - hb) + lo;
+        }
+      }
+      float dq[kNumGhostQ];
+      ghost_delta_f32(K, d, B, dU, dq);
+      const float w = (float)wi[l];
+#pragma unroll
+      for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = fmaf(w, dq[qq], acc[qq]);
+    }
   }
 #pragma unroll
   for (int q = 0; q < kNumGhostQ; ++q) out[q * qstride] = acc[q];
@@ -422,25 +509,42 @@ __device__ __forceinline__ long long okey(float v) {
   return (long long)(b ^ ((b >> 31) & 0x7FFFFFFF));
 }
 
+// (hi, lo) += (bh, bl) in double-float arithmetic: TwoSum of the high words
+// (Knuth), low words and the rounding error summed, then renormalised.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  const float s = __fadd_rn(hi, bh);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(bh, bp));
+  const float l = __fadd_rn(__fadd_rn(lo, bl), e);
+  hi = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(hi, s));
+}
+
 // Per-block reduction of the kNumStat per-thread sums (fixed order) into
 // partial[block], and of the max/min keys and health bits into the global
-// words.  Blocks have a multiple of 32 threads, at most NT.  FP64 values go
-// through shared memory: each statistic in NT/16 partial sums of 16 threads,
-// then one sum of those (a warp-shuffle tree would cost every lane 5 FP64 adds
-// per statistic).  FP32 values are summed within a warp in FP32 first.
+// words.  Blocks have a multiple of 32 threads, at most NT.  Each statistic
+// goes through shared memory in NT/16 partial sums of 16 threads, then one sum
+// of those (a warp-shuffle tree would cost every lane 5 adds per statistic).
+// FP64 values are summed in FP64.  FP32 values arrive as (sum, compensation)
+// pairs and are summed as double-float pairs (about 48 significant bits) in
+// FP32 arithmetic, so that only the last sum of each statistic touches the
+// FP64 pipe.
 constexpr int kReduceScratchDoubles = kNumStat * 257;   // NT = 256
 
 // scratch: at least kNumStat * (NT + 1) doubles of shared memory that no
 // other thread of the block still reads (k_fused passes its dead window).
+// stc: the compensations of the FP32 sums (sum - stc is the compensated sum;
+// null: none).
 template <typename S, int NT = 256>
 __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave, long long krho, long long kp,
                                              unsigned health, bool do_stats, double* partial,
-                                             unsigned long long* words, double* scratch) {
+                                             unsigned long long* words, double* scratch,
+                                             const S* stc = nullptr) {
   constexpr int kMaxThreads = NT, kMaxWarps = kMaxThreads / 32, kParts = kMaxThreads / 16;
   double (*sh)[kMaxThreads + 1] = reinterpret_cast<double (*)[kMaxThreads + 1]>(scratch);
+  float2 (*shp)[kMaxThreads + 1] = reinterpret_cast<float2 (*)[kMaxThreads + 1]>(scratch);   // FP32 pairs
   __shared__ long long shk[kMaxWarps][3];
   __shared__ unsigned shh[kMaxWarps];
-  __shared__ float shf[kNumStat][kMaxWarps];   // FP32 warp sums (FP32 form)
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
   const int nwarps = nthreads >> 5;
   const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
@@ -463,10 +567,10 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
       // stays FP32 here: a conversion to FP64 is an FP64-pipe warp
       // instruction even with one active lane
 #pragma unroll
-      for (int s = 0; s < kNumStat; ++s) {
-        const S w = warp_sum(st[s]);
-        if (lane == 0) shf[s][wid] = (float)w;
-      }
+      for (int s = 0; s < kNumStat; ++s) shp[s][tid] = make_float2((float)st[s], stc ? -(float)stc[s] : 0.f);
+      for (int j = nthreads + tid; j < kMaxThreads; j += nthreads)
+#pragma unroll
+        for (int s = 0; s < kNumStat; ++s) shp[s][j] = make_float2(0.f, 0.f);
     }
   }
   if (lane == 0) shh[wid] = hh;
@@ -503,11 +607,25 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
       partial[blk * kNumStat + s] = a;
     }
   } else {
-    // one warp converts and sums the warp sums in FP64
+    for (int j = tid; j < kNumStat * kParts; j += nthreads) {
+      const int s = j / kParts, part = j - s * kParts;
+      float2 a = shp[s][part * 16];
+#pragma unroll
+      for (int q = 1; q < 16; ++q) {
+        const float2 b = shp[s][part * 16 + q];
+        df_add(a.x, a.y, b.x, b.y);
+      }
+      shp[s][part * 16] = a;
+    }
+    __syncthreads();
+    // one warp: the parts as a pair, then hi + lo once in FP64
     for (int s = tid; s < kNumStat; s += nthreads) {
-      double a = 0.0;
-      for (int w = 0; w < nwarps; ++w) a += (double)shf[s][w];
-      partial[blk * kNumStat + s] = a;
+      float2 a = shp[s][0];
+      for (int part = 1; part < kParts; ++part) {
+        const float2 b = shp[s][part * 16];
+        df_add(a.x, a.y, b.x, b.y);
+      }
+      partial[blk * kNumStat + s] = (double)a.x + (double)a.y;
     }
   }
 }
@@ -686,21 +804,30 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 3 : 2) k_main(Geom g, Co
 
     if (A.do_update) {
       const S Uo[5] = {r, m[0], m[1], m[2], E};
-      S un[5];
-      ab2_update(K, A, D, idx, N, Uo, R, un, health);
-      // PE-boundary slabs of U^{n+1} into ring slot (n+1) mod nlev
+      S un[5], unlo[5];
+      ab2_update(K, A, D, idx, N, Uo, R, un, unlo, health);
+      // PE-boundary slabs of U^{n+1} into ring slot (n+1) mod nlev (FP64)
       const int slot = (int)((D.n + 1) % g.nlev);
+      bool onface = false;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (g.pes[d] == 1) continue;
-        const int li = P.li[d], nl = g.nl[d];
-        if (li >= M && li < nl - M) continue;
-        const int t = li < M ? li : li - nl + 2 * M;
-        const long long sp = 2LL * M * P.pe[d] + t;
-        S* rg = A.ring[d];
-        const long long PS = 2LL * M * g.pes[d];
+      for (int d = 0; d < 3; ++d)
+        onface |= g.pes[d] > 1 && (P.li[d] < M || P.li[d] >= g.nl[d] - M);
+      if (onface) {
+        double rv[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) rg[(((long long)slot * 5 + v) * PS + sp) * g.plane[d] + P.pl[d]] = un[v];
+        for (int v = 0; v < 5; ++v) rv[v] = ring_value(un[v], unlo[v]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (g.pes[d] == 1) continue;
+          const int li = P.li[d], nl = g.nl[d];
+          if (li >= M && li < nl - M) continue;
+          const int t = li < M ? li : li - nl + 2 * M;
+          const long long sp = 2LL * M * P.pe[d] + t;
+          double* rg = A.ring[d];
+          const long long PS = 2LL * M * g.pes[d];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) rg[(((long long)slot * 5 + v) * PS + sp) * g.plane[d] + P.pl[d]] = rv[v];
+        }
       }
     } else if (A.Rout) {
 #pragma unroll

@@ -312,17 +312,30 @@ __device__ __forceinline__ S local_taps(const C& c, const S* q) {
 }
 
 // Per-thread statistics accumulators over the thread's column of one z chunk
-// (at most 64 points), in the kernel's type; they reach FP64 before crossing
-// threads.
+// (at most 64 points).  FP64 form: plain FP64 sums.  FP32 forms: compensated
+// (Kahan) FP32 sums, whose error does not grow with the number of points;
+// the block reduction carries each as a double-float pair and the block's
+// partial is FP64.
 template <typename S>
 struct StatAcc {
   S s[kNumStat];
+  S c[sizeof(S) == 4 ? kNumStat : 1];   // Kahan compensations (FP32 forms)
   __device__ void init() {
 #pragma unroll
     for (int i = 0; i < kNumStat; ++i) s[i] = S(0);
+#pragma unroll
+    for (int i = 0; i < (sizeof(S) == 4 ? kNumStat : 1); ++i) c[i] = S(0);
   }
-  __device__ void add(int i, S v) { s[i] += v; }
-  __device__ double get(int i) const { return (double)s[i]; }
+  __device__ void add(int i, S v) {
+    if constexpr (sizeof(S) == 4) {
+      const S y = __fsub_rn(v, c[i]);
+      const S t = __fadd_rn(s[i], y);
+      c[i] = __fsub_rn(__fsub_rn(t, s[i]), y);
+      s[i] = t;
+    } else {
+      s[i] += v;
+    }
+  }
 };
 
 template <typename S, int TX, int TY>
@@ -647,22 +660,31 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
 
     if (A.do_update) {
       const S Uo[5] = {r, m[0], m[1], m[2], Ecur};
-      S un[5];
-      ab2_update(K, A, D, idx, N, Uo, R, un, health, Rp);
+      S un[5], unlo[5];
+      ab2_update(K, A, D, idx, N, Uo, R, un, unlo, health, Rp);
       const int li[3] = {li_x, li_y, li_z};
       const int c3[3] = {x, y, z};
+      bool onface = false;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (g.pes[d] == 1) continue;
-        const int nl = g.nl[d];
-        if (li[d] >= 2 && li[d] < nl - 2) continue;
-        const int t = li[d] < 2 ? li[d] : li[d] - nl + 4;
-        const long long sp = 4LL * F.pe[d] + t;
-        const long long pl = plane_index(g, d, c3[0], c3[1], c3[2]);
-        S* rg = A.ring[d];
-        const long long P4 = 4LL * g.pes[d];
+      for (int d = 0; d < 3; ++d) onface |= g.pes[d] > 1 && (li[d] < 2 || li[d] >= g.nl[d] - 2);
+      if (onface) {
+        // the ring holds FP64 levels: hi + lo of the compensated form
+        double rv[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) rg[(((long long)slot * 5 + v) * P4 + sp) * g.plane[d] + pl] = un[v];
+        for (int v = 0; v < 5; ++v) rv[v] = ring_value(un[v], unlo[v]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (g.pes[d] == 1) continue;
+          const int nl = g.nl[d];
+          if (li[d] >= 2 && li[d] < nl - 2) continue;
+          const int t = li[d] < 2 ? li[d] : li[d] - nl + 4;
+          const long long sp = 4LL * F.pe[d] + t;
+          const long long pl = plane_index(g, d, c3[0], c3[1], c3[2]);
+          double* rg = A.ring[d];
+          const long long P4 = 4LL * g.pes[d];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) rg[(((long long)slot * 5 + v) * P4 + sp) * g.plane[d] + pl] = rv[v];
+        }
       }
     } else if (A.Rout) {
 #pragma unroll
@@ -705,9 +727,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     }
     __syncthreads();
   }
-  double tot[kNumStat];
-#pragma unroll
-  for (int s = 0; s < kNumStat; ++s) tot[s] = st.get(s);
   // the window is dead after the last barrier: reuse it as reduction scratch
   if constexpr (sizeof(S) == 4) {
     if (A.do_stats) {
@@ -715,9 +734,12 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
       krho = okey(rmin);
       kp = okey(pmin);
     }
+    block_reduce<S, (TX * TY > 256 ? 512 : 256)>(st.s, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words,
+                                                 reinterpret_cast<double*>(fused_smem), st.c);
+  } else {
+    block_reduce<S, (TX * TY > 256 ? 512 : 256)>(st.s, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words,
+                                                 reinterpret_cast<double*>(fused_smem));
   }
-  block_reduce<double, (TX * TY > 256 ? 512 : 256)>(tot, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words,
-                       reinterpret_cast<double*>(fused_smem));
 }
 
 }  // namespace atdns

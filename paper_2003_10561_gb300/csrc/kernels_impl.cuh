@@ -21,7 +21,7 @@ cudaError_t launch_prim<S>(const Geom& g, const Coef<S>& K, const S* U0, const S
 
 template <>
 cudaError_t launch_ghost_m<S, kM>(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds,
-                                  const S* PQ, S* const GH[3], S* const ring[3], const uint8_t* dmap, long long n,
+                                  const S* PQ, S* const GH[3], double* const ring[3], const uint8_t* dmap, long long n,
                                   cudaStream_t st) {
   long long cnt[3];
   for (int d = 0; d < 3; ++d) cnt[d] = g.pes[d] > 1 ? 2LL * kM * g.pes[d] * g.plane[d] : 0;

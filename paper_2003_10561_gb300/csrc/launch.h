@@ -15,7 +15,7 @@ cudaError_t launch_prim(const Geom& g, const Coef<S>& K, const S* U0, const S* U
 // unit (kernels_p64.cu, kernels_p32.cu, kernels_p64_o6.cu, kernels_p32_o6.cu).
 template <typename S, int M>
 cudaError_t launch_ghost_m(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds,
-                           const S* PQ, S* const GH[3], S* const ring[3], const uint8_t* dmap, long long n,
+                           const S* PQ, S* const GH[3], double* const ring[3], const uint8_t* dmap, long long n,
                            cudaStream_t st);
 
 template <typename S, int M>
@@ -26,7 +26,7 @@ cudaError_t launch_main_m(const Geom& g, const Coef<S>& K, const StepArgs<S>& a,
 
 template <typename S>
 inline cudaError_t launch_ghost(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds,
-                                const S* PQ, S* const GH[3], S* const ring[3], const uint8_t* dmap, long long n,
+                                const S* PQ, S* const GH[3], double* const ring[3], const uint8_t* dmap, long long n,
                                 cudaStream_t st) {
   return g.M == 3 ? launch_ghost_m<S, 3>(g, K, U0, U1, ds, PQ, GH, ring, dmap, n, st)
                   : launch_ghost_m<S, 2>(g, K, U0, U1, ds, PQ, GH, ring, dmap, n, st);

@@ -1,16 +1,18 @@
 """Accuracy of the FP32-bulk forms against FP64 on a forced 512^3 run (the
-workload list's third configuration, shortened to 100 steps): 8x8x8 PEs of
+workload list's third configuration, its full 1000 steps): 8x8x8 PEs of
 64^3, forcing on |kappa| <= 2, random delays with L = 3, AB2 from the same
-state in P64, P32 and P32C.  The relative error in the kinetic
-energy, the dissipation and the longitudinal gradient moments against the
-FP64 run must stay below 1e-4 (the target for the FP32-bulk form)."""
+state in P64, P32 and P32C (the FP32-bulk form: FP32 stencils, compensated
+update, FP64 ring and reductions).  The relative error in the kinetic
+energy, the dissipation, the longitudinal gradient moments and the enstrophy
+against the FP64 run must stay below 1e-4 (the target for the FP32-bulk
+form); the skewness and flatness errors are reported beside them."""
 import pytest
 
 from paper_2003_10561_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-N, PES, STEPS = 512, 8, 100
+N, PES, STEPS = 512, 8, 1000
 
 
 def test_fp32_bulk_matches_fp64_at_512():
@@ -39,9 +41,10 @@ def test_fp32_bulk_matches_fp64_at_512():
         torch.cuda.empty_cache()
     ref = stats["p64"]
     for prec in ("p32", "p32c"):
-        for k in ("tke", "dissipation", "grad_m2", "enstrophy"):
+        for k in ("tke", "dissipation", "grad_m2", "enstrophy", "skewness", "flatness"):
             err = abs(stats[prec][k] - ref[k]) / abs(ref[k])
-            print(prec, k, err)
-            assert err <= 1e-4, (prec, k, err)
+            print(prec, k, stats[prec][k], ref[k], err)
+            if k not in ("skewness", "flatness"):
+                assert err <= 1e-4, (prec, k, err)
         # the record describes U^{n} of the last step evaluated
         assert stats[prec]["step"] == ref["step"] == STEPS - 1

@@ -34,12 +34,15 @@ def lib_kw(v):
     return dict(energy_form=v["energy_form"], visc_law=v["visc_law"], sutherland_s=0.368)
 
 
+@pytest.mark.parametrize("kf", [2.0, 3.0])
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("name", list(VARIANTS))
-def test_rhs_parity_fp64_variants(lib, name, path):
+def test_rhs_parity_fp64_variants(lib, name, path, kf):
+    """Each variant forced on the workload's shell (kappa_f = 2) and on the
+    paper's (kappa_f = 3, Sec. 4.2)."""
     v = VARIANTS[name]
     n, pes = (16, 16, 16), (2, 2, 2)
-    kw = dict(mu0=0.02, dt=2e-3, max_delay=2, seed=77, forcing=1, kf=2.0, f_amp=0.1, f_tcorr=0.5, f_seed=4)
+    kw = dict(mu0=0.02, dt=2e-3, max_delay=2, seed=77, forcing=1, kf=kf, f_amp=0.1, f_tcorr=0.5, f_seed=4)
     c = ocfg(n, pes, **{**kw, "forcing": True}, **v, suth_s=0.368)
     U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=11)
     hist = to_form(c, synth.history(U0, c.n_levels, eps=2e-2, seed=5))

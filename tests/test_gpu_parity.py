@@ -100,18 +100,42 @@ def test_rhs_parity_fp64(lib, n, pes, mode, step, L, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
-def test_rhs_parity_fp64_forced(lib, path):
+@pytest.mark.parametrize("kf", [2.0, 3.0])
+def test_rhs_parity_fp64_forced(lib, path, kf):
+    """Forcing on the shell |kappa| <= kappa_f: 2 (the workload's, 16 modes in
+    the half set) and 3 (the paper's, Sec. 4.2: 61 modes and wider x-line
+    tables)."""
     n, pes = (16, 16, 16), (2, 2, 2)
-    kw = dict(mu0=0.02, dt=5e-3, max_delay=2, seed=3, forcing=1, kf=2.0, f_amp=0.2, f_tcorr=0.3, f_seed=99)
+    kw = dict(mu0=0.02, dt=5e-3, max_delay=2, seed=3, forcing=1, kf=kf, f_amp=0.2, f_tcorr=0.3, f_seed=99)
     U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=12)
     c = ocfg(n, pes, **{**kw, "forcing": True})
+    assert len(ns.forcing_modes(kf)) == {2.0: 16, 3.0: 61}[kf]
     hist = synth.history(U0, c.n_levels, eps=1e-2, seed=6)
     s = make(lib, n, pes, path=path, **kw)
     s.set_history(hist, 9)
     R = s.rhs("random")
     Rref = ns.rhs(c, hist, ns.delay_map(c, 9, ns.RANDOM), ns.forcing_coefficients(c, 9))
     err = rel_linf(R, Rref)
+    print("forced kf=%g %s fp64 rel err" % (kf, path), err)
     assert max(err) <= 1e-12, err
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_rhs_parity_fp32_forced_kf3(lib, path):
+    """The FP32-bulk form (compensated update, FP64 ring) with the paper's
+    forcing shell kappa_f = 3 and random delays."""
+    n, pes = (16, 16, 16), (2, 2, 2)
+    kw = dict(mu0=0.02, dt=5e-3, max_delay=2, seed=3, forcing=1, kf=3.0, f_amp=0.2, f_tcorr=0.3, f_seed=99)
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=12)
+    c = ocfg(n, pes, **{**kw, "forcing": True})
+    hist = synth.history(U0, c.n_levels, eps=1e-2, seed=6)
+    s = make(lib, n, pes, "p32c", path=path, **kw)
+    s.set_history(hist, 9)
+    R = s.rhs("random")
+    Rref = ns.rhs(c, hist, ns.delay_map(c, 9, ns.RANDOM), ns.forcing_coefficients(c, 9))
+    err = rel_linf(R, Rref)
+    print("forced kf=3 %s p32c rel err" % path, err)
+    assert max(err) <= 2e-4, err
 
 
 @pytest.mark.parametrize("path", PATHS)
@@ -201,6 +225,7 @@ def test_rhs_parity_fp32(lib, n, pes, mode, step, L, path, prec):
     R = s.rhs(mode)
     Rref = ns.rhs(c, hist, ns.delay_map(c, step, lib.MODES[mode]))
     err = rel_linf(R, Rref)
+    print("fp32 %s %s n=%s pes=%s %s rel err" % (prec, path, n, pes, mode), err)
     assert max(err) <= 2e-4, err
 
 
