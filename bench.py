@@ -283,7 +283,7 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "p64", "p32c", "p32"],
                     help="both: FP64 and the FP32-bulk form (P32C: FP32 stencils, compensated FP32 update, "
                          "FP64 ring and reductions)")
-    ap.add_argument("--path", default="auto", choices=["auto", "multipass", "fused"])
+    ap.add_argument("--path", default="auto", choices=["auto", "multipass", "fused", "paired"])
     ap.add_argument("--order", default="both", choices=["both", "4", "6"],
                     help="spatial order of the AT scheme (4: headline; 6: Table B (1,6)/(2,6))")
     ap.add_argument("--no-tune", action="store_true",
@@ -340,7 +340,8 @@ def main():
                     "dtype": "f64" if prec == "p64" else "f32"}
         # kernels in the timed region: every replayed step plus the health reset
         res[key]["launches"] = args.steps * res[key]["info"]["kernels_per_step"] + 1
-        res[key]["path"] = "fused" if res[key]["info"]["kernel_path"] == at_dns.AT_DNS_PATH_FUSED else "multipass"
+        res[key]["path"] = {at_dns.AT_DNS_PATH_FUSED: "fused", at_dns.AT_DNS_PATH_PAIRED: "paired"}.get(
+            res[key]["info"]["kernel_path"], "multipass")
         res[key]["tile"] = res[key]["info"]["tile"]
         # end to end through the public API with host buffers: per step, upload
         # U^n from pinned host memory (as the state of step n), step, read
@@ -525,7 +526,7 @@ def leg_report(r, world, pts, steps, pk):
                        "frac": gbs / pk.get("hbm_gbs", 6800.0), "bytes_per_point": algorithmic_bytes("p64", order)}
     else:
         achieved = algorithmic_bytes(r["prec"], order) * pts / t_main / 1e9
-        kname = "k_fused" if r["path"] == "fused" else "k_main"
+        kname = {"fused": "k_fused", "paired": "k_fused2"}.get(r["path"], "k_main")
         traffic = K_FUSED_FP32_TRAFFIC_256 if (order == 4 and N == 256 and PES == 8 and r["path"] == "fused"
                                                and list(r["tile"]) == [32, 8, 32] and K_FUSED_FP32_TRAFFIC_256) else None
         roof = {"bound": "hbm", "kernel": "%s (FP32, order %d)" % (kname, order), "achieved": achieved,

@@ -116,7 +116,7 @@ typedef struct {
   int32_t  precision;    /* AT_DNS_P64, AT_DNS_P32 or AT_DNS_P32C                       */
   int32_t  stats_every;  /* 1: reduce statistics in every step; 0: only on request      */
   void*    stream;       /* cudaStream_t to run on; NULL = the legacy default stream    */
-  int32_t  kernel_path;  /* AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS or AT_DNS_PATH_FUSED */
+  int32_t  kernel_path;  /* AT_DNS_PATH_AUTO, _MULTIPASS, _FUSED or _PAIRED              */
   int32_t  order;        /* spatial order: 4 (Table B (1,4)/(2,4), T_l = 3, default) or
                             6 (Table B (1,6)/(2,6), T_l = 4; multi-pass path only)      */
   int32_t  energy_form;  /* AT_DNS_ENERGY_TOTAL (default) or AT_DNS_ENERGY_INTERNAL     */
@@ -141,6 +141,10 @@ typedef struct {
 #define AT_DNS_PATH_AUTO       0
 #define AT_DNS_PATH_MULTIPASS  1
 #define AT_DNS_PATH_FUSED      2
+/* the fused pass with two x-adjacent points per thread carried through packed
+ * FP32 (f32x2) arithmetic: P32 / P32C only, tiles 32x8, 32x16, 16x16, 16x8
+ * (PE extents multiples of 16 in x and 8 in y) */
+#define AT_DNS_PATH_PAIRED     3
 
 typedef struct {
   int64_t step;          /* n of the state the statistics describe                      */
@@ -169,7 +173,7 @@ typedef struct {
   double  boundary_fraction;  /* N_B / N_T per PE, Eqs. (NT)-(NB)                       */
   size_t  device_bytes;  /* device memory held by the handle                            */
   int32_t kernels_per_step;   /* kernel launches of one at_dns_step step                */
-  int32_t kernel_path;   /* path in use: AT_DNS_PATH_MULTIPASS or AT_DNS_PATH_FUSED     */
+  int32_t kernel_path;   /* path in use: AT_DNS_PATH_MULTIPASS, _FUSED or _PAIRED       */
   int32_t tile[3];       /* fused path: TX, TY, planes per CTA (0 on the multi-pass path)*/
   int32_t order;         /* spatial order of the scheme (4 or 6)                        */
 } at_dns_info_t;
@@ -272,7 +276,7 @@ int at_dns_kernel_times(at_dns_t* h, at_dns_kernel_time_t* out, int32_t max, int
 int at_dns_tune(at_dns_t* h, int32_t delay_mode, int32_t trials, double* best_ms);
 
 /* Select the kernel path explicitly: AT_DNS_PATH_MULTIPASS (tile ignored) or
- * AT_DNS_PATH_FUSED with tile = {TX, TY, ZC}, one of the candidates that
+ * AT_DNS_PATH_FUSED / AT_DNS_PATH_PAIRED with tile = {TX, TY, ZC}, one of the candidates that
  * at_dns_tune times for this handle (a compiled tile shape whose TX and TY
  * divide the PE extents, ZC planes per CTA dividing the PE extent in z).
  * Captured step graphs are dropped; the state is kept.

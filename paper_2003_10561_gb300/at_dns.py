@@ -25,11 +25,12 @@ AT_DNS_NOALLOC_MAX_POINTS = 262144
 AT_DNS_SYNC, AT_DNS_PERIODIC, AT_DNS_RANDOM, AT_DNS_FIXED = 0, 1, 2, 3
 AT_DNS_P64, AT_DNS_P32, AT_DNS_P32C = 0, 1, 2
 AT_DNS_HOST, AT_DNS_DEVICE = 0, 1
-AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS, AT_DNS_PATH_FUSED = 0, 1, 2
+AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS, AT_DNS_PATH_FUSED, AT_DNS_PATH_PAIRED = 0, 1, 2, 3
 AT_DNS_ENERGY_TOTAL, AT_DNS_ENERGY_INTERNAL = 0, 1
 AT_DNS_VISC_POWER, AT_DNS_VISC_SUTHERLAND = 0, 1
 AT_DNS_AB2, AT_DNS_RK3 = 0, 1
-PATHS = {"auto": AT_DNS_PATH_AUTO, "multipass": AT_DNS_PATH_MULTIPASS, "fused": AT_DNS_PATH_FUSED}
+PATHS = {"auto": AT_DNS_PATH_AUTO, "multipass": AT_DNS_PATH_MULTIPASS, "fused": AT_DNS_PATH_FUSED,
+         "paired": AT_DNS_PATH_PAIRED}
 
 MODES = {"sync": AT_DNS_SYNC, "periodic": AT_DNS_PERIODIC, "random": AT_DNS_RANDOM, "fixed": AT_DNS_FIXED}
 PRECISIONS = {"p64": AT_DNS_P64, "p32": AT_DNS_P32, "p32c": AT_DNS_P32C}

@@ -69,6 +69,7 @@ struct at_dns {
   bool use_graphs = true;
   // kernel path: fused single pass on TX x TY tiles marching ZC planes, or multi-pass
   bool fused = false;
+  bool paired = false;         // fused pass with two points per thread (FP32 forms)
   int TX = 0, TY = 0, ZC = 0;
   long long nblk_step = 0;     // blocks of the kernel that writes the statistics partials
   // per-kernel event timing
@@ -511,7 +512,12 @@ struct Ops {
     }
     if (h->fused) {
       Timed t(h, KD_MAIN);
-      CK(launch_fused<S>(g, K, a, h->TX, h->TY, h->ZC, st));
+      if constexpr (sizeof(S) == 4) {
+        if (h->paired) CK(launch_fused2(g, K, a, h->TX, h->TY, h->ZC, st));
+        else CK(launch_fused<S>(g, K, a, h->TX, h->TY, h->ZC, st));
+      } else {
+        CK(launch_fused<S>(g, K, a, h->TX, h->TY, h->ZC, st));
+      }
     } else {
       Timed t(h, KD_MAIN);
       CK(launch_main<S>(g, K, a, st));
@@ -644,7 +650,7 @@ int step_graph(at_dns* h, int mode, bool stats) {
 
 // Switch the kernel path of a handle (allocating the multi-pass work arrays
 // on first use); captured graphs are dropped.
-int set_path(at_dns* h, bool fused, int TX, int TY, int ZC) {
+int set_path(at_dns* h, bool fused, int TX, int TY, int ZC, bool paired = false) {
   const Geom& g = h->g;
   if (!fused && !h->PQ) {
     const size_t N = (size_t)g.npts;
@@ -657,6 +663,7 @@ int set_path(at_dns* h, bool fused, int TX, int TY, int ZC) {
     }
   }
   h->fused = fused;
+  h->paired = fused && paired;
   h->TX = fused ? TX : 0;
   h->TY = fused ? TY : 0;
   h->ZC = fused ? ZC : 0;
@@ -665,14 +672,14 @@ int set_path(at_dns* h, bool fused, int TX, int TY, int ZC) {
   return AT_DNS_OK;
 }
 
-struct Candidate { bool fused; int TX, TY, ZC; };
+struct Candidate { bool fused; int TX, TY, ZC; bool paired; };
 
 // Kernel-path candidates of the autotuner: the multi-pass path and every
 // compiled fused tile shape that fits the PE extents, with whole-PE, half and
 // quarter z chunks (at least 8 planes).
 std::vector<Candidate> tune_candidates(const Geom& g, bool p64) {
   std::vector<Candidate> out;
-  out.push_back({false, 0, 0, 0});
+  out.push_back({false, 0, 0, 0, false});
   if (g.M != 2) return out;   // the fused kernel runs the 4th-order scheme only
   int ext[3];
   for (int d = 0; d < 3; ++d) ext[d] = g.pes[d] > 1 ? g.nl[d] : g.n[d];
@@ -690,7 +697,17 @@ std::vector<Candidate> tune_candidates(const Geom& g, bool p64) {
     for (int div : {1, 2, 4}) {
       const int zc = zmax / div;
       if (zc < 8 || zmax % div || ext[2] % zc) continue;
-      out.push_back({true, sh[0], sh[1], zc});
+      out.push_back({true, sh[0], sh[1], zc, false});
+    }
+  }
+  // the paired kernel (FP32 forms): two points per thread, packed arithmetic
+  const int pshapes[4][2] = {{32, 8}, {32, 16}, {16, 16}, {16, 8}};
+  for (auto& sh : pshapes) {
+    if (p64 || ext[0] % sh[0] || ext[1] % sh[1]) continue;
+    for (int div : {1, 2, 4}) {
+      const int zc = zmax / div;
+      if (zc < 8 || zmax % div || ext[2] % zc) continue;
+      out.push_back({true, sh[0], sh[1], zc, true});
     }
   }
   return out;
@@ -790,7 +807,9 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     else if (c.forcing && (!(c.kf >= 1.0) || c.kf > kMaxKf)) bad = "kf must be in [1, 4]";
     else if (c.forcing && !(c.f_tcorr > 0)) bad = "f_tcorr must be > 0";
     else if (c.stats_every != 0 && c.stats_every != 1) bad = "stats_every must be 0 or 1";
-    else if (c.kernel_path < 0 || c.kernel_path > 2) bad = "unknown kernel_path";
+    else if (c.kernel_path < 0 || c.kernel_path > 3) bad = "unknown kernel_path";
+    else if (c.kernel_path == AT_DNS_PATH_PAIRED && c.precision == AT_DNS_P64)
+      bad = "the paired path runs the FP32 forms only";
     else if (c.energy_form != AT_DNS_ENERGY_TOTAL && c.energy_form != AT_DNS_ENERGY_INTERNAL) bad = "unknown energy_form";
     else if (c.visc_law != AT_DNS_VISC_POWER && c.visc_law != AT_DNS_VISC_SUTHERLAND) bad = "unknown visc_law";
     else if (c.visc_law == AT_DNS_VISC_SUTHERLAND && !(c.sutherland_s > 0)) bad = "sutherland_s must be > 0";
@@ -844,11 +863,24 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
                     : "the fused path needs PE (or grid) extents that are multiples of 8 in x and y";
     return create_fail(h, AT_DNS_E_UNSUPPORTED);
   }
+  if (c.kernel_path == AT_DNS_PATH_PAIRED) {
+    // the first paired candidate of the tuner's list (largest tile, whole-PE z chunk)
+    bool found = false;
+    for (const Candidate& cd : tune_candidates(g, h->p64))
+      if (cd.paired) { h->TX = cd.TX; h->TY = cd.TY; h->ZC = cd.ZC; found = true; break; }
+    if (!found) {
+      h->err = M != 2 ? "the paired path runs the 4th-order scheme only"
+                      : "the paired path needs PE (or grid) extents that are multiples of 16 in x and 8 in y";
+      return create_fail(h, AT_DNS_E_UNSUPPORTED);
+    }
+    h->paired = true;
+  }
   // AUTO takes the faster path on GB300 at the benchmark workload (at_dns_tune
   // can switch): the fused one for the FP32 forms (one pass over U, no work
   // arrays), the multi-pass one for FP64 (bound by the FP64 pipe, where the
   // fused path's halo recompute costs more than the work arrays' traffic)
-  h->fused = can_fuse && (c.kernel_path == AT_DNS_PATH_FUSED || (c.kernel_path == AT_DNS_PATH_AUTO && !h->p64));
+  h->fused = h->paired ||
+             (can_fuse && (c.kernel_path == AT_DNS_PATH_FUSED || (c.kernel_path == AT_DNS_PATH_AUTO && !h->p64)));
   if (!h->fused) h->TX = h->TY = h->ZC = 0;
   h->nblk_step = h->fused ? (long long)(g.n[0] / h->TX) * (g.n[1] / h->TY) * (g.n[2] / h->ZC) : main_blocks(g);
   if ((rc = dev_alloc(h, &h->U[0], 5 * N * S)) || (rc = dev_alloc(h, &h->U[1], 5 * N * S)) ||
@@ -1106,7 +1138,7 @@ int at_dns_get_info(at_dns_t* h, at_dns_info_t* out) {
   // and gradients on the multi-pass path)
   out->kernels_per_step = (h->fused ? 4 : 6) + (ghost ? 1 : 0) + (h->cfg.stats_every ? 1 : 0) +
                           (h->cfg.forcing ? 2 : 0);
-  out->kernel_path = h->fused ? AT_DNS_PATH_FUSED : AT_DNS_PATH_MULTIPASS;
+  out->kernel_path = h->paired ? AT_DNS_PATH_PAIRED : (h->fused ? AT_DNS_PATH_FUSED : AT_DNS_PATH_MULTIPASS);
   out->tile[0] = h->TX;
   out->tile[1] = h->TY;
   out->tile[2] = h->ZC;
@@ -1170,9 +1202,9 @@ int at_dns_tune(at_dns_t* h, int32_t delay_mode, int32_t trials, double* best_ms
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   double best = 1e300;
-  Candidate pick{h->fused, h->TX, h->TY, h->ZC};
+  Candidate pick{h->fused, h->TX, h->TY, h->ZC, h->paired};
   for (const Candidate& c : tune_candidates(h->g, h->p64)) {
-    if (set_path(h, c.fused, c.TX, c.TY, c.ZC) != AT_DNS_OK) continue;   // e.g. no memory for work arrays
+    if (set_path(h, c.fused, c.TX, c.TY, c.ZC, c.paired) != AT_DNS_OK) continue;   // e.g. no memory for work arrays
     // one untimed evaluation, then `trials` timed right-hand sides (no state change)
     for (int t = 0; t <= trials; ++t) {
       if (t == 1) CK(cudaEventRecord(e0, h->st));
@@ -1189,7 +1221,7 @@ int at_dns_tune(at_dns_t* h, int32_t delay_mode, int32_t trials, double* best_ms
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if ((rc = set_path(h, pick.fused, pick.TX, pick.TY, pick.ZC))) return rc;
+  if ((rc = set_path(h, pick.fused, pick.TX, pick.TY, pick.ZC, pick.paired))) return rc;
   h->stats_valid = false;
   h->prof = was_prof;
   if (best_ms) *best_ms = best;
@@ -1200,9 +1232,12 @@ int at_dns_set_kernel_path(at_dns_t* h, int32_t path, const int32_t tile[3]) {
   if (!h) return AT_DNS_E_INVALID_ARG;
   h->err.clear();
   if (path == AT_DNS_PATH_MULTIPASS) return set_path(h, false, 0, 0, 0);
-  if (path != AT_DNS_PATH_FUSED || !tile) return fail(h, AT_DNS_E_INVALID_ARG, "path must be MULTIPASS or FUSED with a tile");
+  if ((path != AT_DNS_PATH_FUSED && path != AT_DNS_PATH_PAIRED) || !tile)
+    return fail(h, AT_DNS_E_INVALID_ARG, "path must be MULTIPASS, or FUSED or PAIRED with a tile");
+  const bool paired = path == AT_DNS_PATH_PAIRED;
   for (const Candidate& c : tune_candidates(h->g, h->p64))
-    if (c.fused && c.TX == tile[0] && c.TY == tile[1] && c.ZC == tile[2]) return set_path(h, true, c.TX, c.TY, c.ZC);
+    if (c.fused && c.paired == paired && c.TX == tile[0] && c.TY == tile[1] && c.ZC == tile[2])
+      return set_path(h, true, c.TX, c.TY, c.ZC, paired);
   return fail(h, AT_DNS_E_UNSUPPORTED, "tile is not a fused-path candidate for this handle");
 }
 

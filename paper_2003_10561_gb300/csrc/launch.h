@@ -47,6 +47,11 @@ template <typename S>
 cudaError_t launch_fused(const Geom& g, const Coef<S>& K, const StepArgs<S>& a, int TX, int TY, int ZC,
                          cudaStream_t st);
 
+// Paired fused step kernel (two x-adjacent points per thread, packed FP32
+// arithmetic; FP32 forms only): tiles 32x8, 32x16, 16x16, 16x8.
+cudaError_t launch_fused2(const Geom& g, const Coef<float>& K, const StepArgs<float>& a, int TX, int TY, int ZC,
+                          cudaStream_t st);
+
 // Number of blocks k_main is launched with (size of the partial-sum array).
 inline long long main_blocks(const Geom& g) { return (g.npts + kBlock - 1) / kBlock; }
 

@@ -38,17 +38,20 @@ def rel_linf(a, b):
 
 
 PATHS = ["multipass", "fused"]
+PATHS32 = PATHS + ["paired"]   # the paired kernel runs the FP32 forms only
 
 
 def make(lib, n, pes, precision="p64", path="auto", **kw):
-    """A solver on the requested kernel path; skips when the fused path does not
-    apply to this grid / PE shape."""
+    """A solver on the requested kernel path; skips when the fused (or paired)
+    path does not apply to this grid / PE shape or precision."""
+    if path == "paired" and precision == "p64":
+        pytest.skip("the paired kernel runs the FP32 forms only")
     try:
         return lib.Solver(n=n, pes=pes, precision=precision, path=path, **{"gamma": GAMMA, "prandtl": PR,
                                                                           "visc_exp": OMEGA, **kw})
     except lib.AtDnsError as e:
-        if path == "fused" and e.code == lib.AT_DNS_E_UNSUPPORTED:
-            pytest.skip("fused path does not apply to n=%s pes=%s" % (n, pes))
+        if path in ("fused", "paired") and e.code == lib.AT_DNS_E_UNSUPPORTED:
+            pytest.skip("%s path does not apply to n=%s pes=%s" % (path, n, pes))
         raise
 
 
@@ -120,7 +123,7 @@ def test_rhs_parity_fp64_forced(lib, path, kf):
     assert max(err) <= 1e-12, err
 
 
-@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("path", PATHS32)
 def test_rhs_parity_fp32_forced_kf3(lib, path):
     """The FP32-bulk form (compensated update, FP64 ring) with the paper's
     forcing shell kappa_f = 3 and random delays."""
@@ -214,7 +217,7 @@ def test_zero_delay_equals_sync_fp64(lib):
 
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", ["p32", "p32c"])
-@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("path", PATHS32)
 @pytest.mark.parametrize("n,pes,mode,step,L", CASES[:3] + CASES[5:7])
 def test_rhs_parity_fp32(lib, n, pes, mode, step, L, path, prec):
     U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=11)
@@ -250,8 +253,8 @@ def _sample_points(n, nloc, rng, count):
 # derivatives as 1/dx^2 but carry the small coefficients mu and k; the bounds
 # are scaled by the 8x of the first derivatives plus margin: 1e-11 (FP64) and
 # 2e-3 (FP32).
-@pytest.mark.parametrize("path", PATHS)
-@pytest.mark.parametrize("precision,tol", [("p64", 1e-11), ("p32", 2e-3)])
+@pytest.mark.parametrize("path", PATHS32)
+@pytest.mark.parametrize("precision,tol", [("p64", 1e-11), ("p32", 2e-3), ("p32c", 2e-3)])
 def test_full_size_sampled_parity(lib, precision, tol, path):
     """256^3 with 8x8x8 PEs (the benchmark workload), random delays with L = 2,
     at a step past the start-up: sampled points against the brute-force
@@ -267,11 +270,14 @@ def test_full_size_sampled_parity(lib, precision, tol, path):
     s.close()
     delays = ns.delay_map(c, step, ns.RANDOM)
     po = PointOracle(c, lambda l: hist[l], delays)
+    if path == "paired" and precision == "p64":
+        pytest.skip("the paired kernel runs the FP32 forms only")
     pts = _sample_points(n, 32, np.random.default_rng(4), 120)
     ref = np.array([po.rhs(p) for p in pts])
     got = np.array([[R[v, z, y, x] for v in range(5)] for (x, y, z) in pts])
     scale = np.max(np.abs(ref), axis=0)
     err = np.max(np.abs(got - ref), axis=0) / scale
+    print("256^3 sampled %s %s rel err per variable" % (precision, path), err)
     assert np.max(err) <= tol, err
 
 
@@ -462,8 +468,85 @@ def test_every_fused_tile_keeps_parity(lib, prec):
     assert tried >= (18 if prec == "p64" else 21)
 
 
-@pytest.mark.parametrize("prec,tol", [("p64", 1e-10), ("p32", 2e-4)])
-@pytest.mark.parametrize("path", PATHS)
+PAIRED_SHAPES = [(32, 8), (32, 16), (16, 16), (16, 8)]
+
+
+@pytest.mark.parametrize("prec", ["p32", "p32c"])
+def test_every_paired_tile_keeps_parity(lib, prec):
+    """Each paired tile shape and z chunk (two points per thread, packed FP32
+    arithmetic), selected explicitly, matches the oracle with random delays;
+    a grid direction without PE faces (z) is covered too."""
+    n, pes = (64, 64, 32), (2, 2, 1)
+    kw = dict(mu0=0.02, dt=2e-3, max_delay=2, seed=77)
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=11)
+    c = ocfg(n, pes, **kw)
+    hist = synth.history(U0, c.n_levels, eps=2e-2, seed=5)
+    Rref = ns.rhs(c, hist, ns.delay_map(c, 9, ns.RANDOM))
+    s = make(lib, n, pes, prec, **kw)
+    s.set_history(hist, 9)
+    tried = 0
+    for tx, ty in PAIRED_SHAPES:
+        for zc in (32, 16, 8):
+            s.set_kernel_path("paired", (tx, ty, zc))
+            assert s.info()["kernel_path"] == lib.AT_DNS_PATH_PAIRED
+            tried += 1
+            R = s.rhs("random")
+            err = rel_linf(R, Rref)
+            print("paired %s tile %dx%dx%d rel err" % (prec, tx, ty, zc), err)
+            assert max(err) <= 2e-4, (tx, ty, zc, err)
+    assert tried == 12
+    with pytest.raises(lib.AtDnsError) as ei:
+        s.set_kernel_path("paired", (8, 8, 8))
+    assert ei.value.code == lib.AT_DNS_E_UNSUPPORTED
+
+
+def test_paired_graph_replay_matches_direct_launches(lib):
+    """The paired kernel: graph-replayed steps equal kernel-by-kernel steps
+    bit for bit (compensated form, random and periodic delays, forcing)."""
+    import torch
+    n, pes = (32, 32, 32), (2, 2, 2)
+    U0 = synth.initial_state(n, k0=3.0, seed=40)
+    kw = dict(mu0=0.02, dt=3e-3, max_delay=2, seed=11, forcing=1, kf=2.0, f_amp=0.05, f_tcorr=0.4, f_seed=5)
+    stream = torch.cuda.Stream()
+    a = make(lib, n, pes, "p32c", path="paired", stream=stream.cuda_stream, **kw)
+    b = make(lib, n, pes, "p32c", path="paired", **kw)
+    for s in (a, b):
+        s.set_state(U0)
+        s.step(9, "random")
+        s.step(3, "periodic")
+    a.synchronize()
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert a.stats()["tke"] == b.stats()["tke"]
+
+
+@pytest.mark.parametrize("prec", ["p32", "p32c"])
+def test_paired_agrees_with_fused_and_fp64_over_steps(lib, prec):
+    """30 AB2 steps with random delays and forcing from one state on the
+    paired and the one-point-per-thread fused kernel (same arithmetic in a
+    different instruction order) and in FP64: the two FP32 kernels agree to
+    FP32 rounding, and both stay within the FP32 bound of the FP64 run."""
+    n, pes = (32, 32, 32), (2, 2, 2)
+    U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=44)
+    kw = dict(mu0=0.02, dt=2e-3, max_delay=2, seed=12, forcing=1, kf=2.0, f_amp=0.1, f_tcorr=0.5, f_seed=6)
+    out = {}
+    for key, pr, path in (("p64", "p64", "multipass"), ("fused", prec, "fused"), ("paired", prec, "paired")):
+        s = make(lib, n, pes, pr, path=path, **kw)
+        s.set_state(U0)
+        s.step(30, "random")
+        out[key] = (s.get_state(), s.stats())
+        s.close()
+    d = max(rel_linf(out["paired"][0], out["fused"][0]))
+    e_p = max(rel_linf(out["paired"][0], out["p64"][0]))
+    e_f = max(rel_linf(out["fused"][0], out["p64"][0]))
+    print("paired vs fused %.3e, paired vs fp64 %.3e, fused vs fp64 %.3e" % (d, e_p, e_f))
+    assert d <= 1e-5 and e_p <= 2e-4 and e_f <= 2e-4
+    for k in ("tke", "dissipation", "enstrophy"):
+        ref = out["p64"][1][k]
+        assert abs(out["paired"][1][k] - ref) <= 1e-4 * abs(ref), k
+
+
+@pytest.mark.parametrize("prec,tol", [("p64", 1e-10), ("p32", 2e-4), ("p32c", 2e-4)])
+@pytest.mark.parametrize("path", PATHS32)
 def test_rk3_steps_parity(lib, path, prec, tol):
     """20 synchronous low-storage RK3 steps on 16^3 with 2x2x2 PEs (forced),
     through a captured graph on a stream, against the oracle's RK3."""
