@@ -40,6 +40,8 @@ struct at_dns {
   void* Rprev = nullptr;
   void* GH[3] = {nullptr, nullptr, nullptr};
   void* ring[3] = {nullptr, nullptr, nullptr};
+  void* xst = nullptr;         // FP32 forms: x-face slabs of the state [hi, lo][5][2M P_x][plane_x]
+  long long xst_half = 0;      // elements from its hi half to its lo half (compensated form; else 0)
   double* stage = nullptr;     // [5][npts] FP64 staging / rhs output
   uint8_t* dmap = nullptr;     // [P][6]
   double* partial = nullptr;   // [main_blocks][kNumStat]
@@ -380,6 +382,25 @@ std::vector<Mode3> forcing_modes(double kf) {
   return out;
 }
 
+// The x-face slabs of the current FP32 state (and its low words) into the
+// staging buffer the ghost kernel reads: slab sp = 2M pe + t (t < M: local t,
+// t >= M: local nl - 2M + t), plane index z n1 + y.
+template <typename S>
+__global__ void k_xstage_fill(Geom g, const S* __restrict__ U, const S* __restrict__ Ulo, S* xst, long long half) {
+  const long long P2 = 2LL * g.M * g.pes[0], cnt = P2 * g.plane[0];
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= cnt) return;
+  const int sp = (int)(j / g.plane[0]);
+  const long long pl = j - (long long)sp * g.plane[0];
+  const int pe = sp / (2 * g.M), t = sp - pe * 2 * g.M;
+  const int x = pe * g.nl[0] + (t < g.M ? t : g.nl[0] - 2 * g.M + t);
+  const long long src = pl * g.n[0] + x;   // pl = z n1 + y
+  for (int v = 0; v < 5; ++v) {
+    xst[v * cnt + j] = U[v * g.npts + src];
+    if (half) xst[half + v * cnt + j] = Ulo ? Ulo[v * g.npts + src] : S(0);
+  }
+}
+
 // The PE-boundary slabs of an FP64 level on the device into ring slot `slot`.
 int ring_store(at_dns* h, const double* field, int slot) {
   const bool any = h->g.pes[0] > 1 || h->g.pes[1] > 1 || h->g.pes[2] > 1;
@@ -471,7 +492,8 @@ struct Ops {
     if (!h->fused) { Timed t(h, KD_PRIM); CK(launch_prim<S>(g, K, U0, U1, h->ds, (S*)h->PQ, st)); }
     if (g.pes[0] > 1 || g.pes[1] > 1 || g.pes[2] > 1) {
       Timed t(h, KD_GHOST);
-      CK(launch_ghost<S>(g, K, U0, U1, h->ds, h->fused ? nullptr : (S*)h->PQ, GH, ring, h->dmap, 0, st));
+      CK(launch_ghost<S>(g, K, U0, U1, h->comp ? (S*)h->Ulo[0] : nullptr, h->comp ? (S*)h->Ulo[1] : nullptr, h->ds,
+                         h->fused ? nullptr : (S*)h->PQ, GH, ring, (const S*)h->xst, h->xst_half, h->dmap, 0, st));
     }
     if (!h->fused) { Timed t(h, KD_GRAD); CK(launch_grad<S>(g, K, (S*)h->PQ, GH, (S*)h->G, st)); }
     if (h->cfg.forcing) {
@@ -492,7 +514,9 @@ struct Ops {
     a.ds = h->ds;
     a.PQ = (S*)h->PQ;
     a.G = (S*)h->G;
-    for (int d = 0; d < 3; ++d) { a.GH[d] = GH[d]; a.ring[d] = ring[d]; }
+    for (int d = 0; d < 3; ++d) a.GH[d] = GH[d];
+    a.xst = (S*)h->xst;
+    a.xst_half = h->xst_half;
     a.Rprev = (S*)h->Rprev;
     a.Rout = Rout;
     a.partial = h->partial;
@@ -584,6 +608,16 @@ struct Ops {
     int rc = launch_step(h, mode, update, Rout, stats, reset_health, h->st);
     if (rc) return rc;
     account(h, update, stats);
+    return AT_DNS_OK;
+  }
+
+  // Stage the x-face slabs of the current state (FP32 forms with x-faces).
+  static int xstage_fill(at_dns* h) {
+    if (!h->xst) return AT_DNS_OK;
+    const long long cnt = 2LL * h->g.M * h->g.pes[0] * h->g.plane[0];
+    k_xstage_fill<S><<<nblk(cnt), kBlock, 0, h->st>>>(h->g, U(h, h->cur), h->comp ? (const S*)h->Ulo[h->cur] : nullptr,
+                                                      (S*)h->xst, h->xst_half);
+    CK(cudaGetLastError());
     return AT_DNS_OK;
   }
 
@@ -900,6 +934,12 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     if ((rc = dev_alloc(h, &h->GH[d], (size_t)kNumGhostQ * gpts * S)) ||
         (rc = dev_alloc(h, &h->ring[d], (size_t)g.nlev * 5 * gpts * sizeof(double))))
       return create_fail(h, rc);
+    if (d == 0 && !h->p64) {
+      // x-face slabs staged by the step kernels for the next ghost kernel
+      const size_t halves = h->comp ? 2 : 1;
+      if ((rc = dev_alloc(h, &h->xst, halves * 5 * gpts * S))) return create_fail(h, rc);
+      h->xst_half = h->comp ? (long long)(5 * gpts) : 0;
+    }
   }
   const int P = g.pes[0] * g.pes[1] * g.pes[2];
   if ((rc = dev_alloc(h, (void**)&h->ds, sizeof(DevState))) || (rc = dev_alloc(h, (void**)&h->dmap, (size_t)P * 6)) ||
@@ -955,6 +995,9 @@ int at_dns_set_history(at_dns_t* h, const double* levels, int32_t nlevels, int64
       if ((rc = ring_store(h, dev_lv, slot))) return rc;
     }
   }
+  // the x-face slabs of U^step for the first ghost kernel (FP32 forms)
+  rc = h->p64 ? AT_DNS_OK : Ops<float>::xstage_fill(h);
+  if (rc) return rc;
   // stage holds U^step in FP64 now (host path) -- ensure it for the dt reduction
   // U^step in FP64 on the device for the CFL reduction: the caller's level 0,
   // or the staging buffer the host path just filled with it
@@ -1256,8 +1299,9 @@ void at_dns_destroy(at_dns_t* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
   drop_graphs(h);
-  void* ptrs[] = {h->ds, h->U[0], h->U[1], h->Ulo[0], h->Ulo[1], h->PQ, h->G, h->Rprev, h->GH[0], h->GH[1], h->GH[2], h->ring[0], h->ring[1],
-                  h->ring[2], h->stage, h->dmap, h->partial, h->sums, h->words, h->modes, h->fhat, h->fB, h->fX};
+  void* ptrs[] = {h->ds, h->U[0], h->U[1], h->Ulo[0], h->Ulo[1], h->PQ, h->G, h->Rprev, h->GH[0], h->GH[1], h->GH[2],
+                  h->ring[0], h->ring[1], h->ring[2], h->xst, h->stage, h->dmap, h->partial, h->sums, h->words,
+                  h->modes, h->fhat, h->fB, h->fX};
   if (!h->pool)
     for (void* p : ptrs)
       if (p) cudaFree(p);

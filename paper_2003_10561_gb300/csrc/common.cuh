@@ -311,8 +311,9 @@ struct StepArgs {
   S* Rprev;            // [5][npts] R^{n-1} in, R^n out
   const S* Ulo;        // compensated form: low words of U (else null)
   S* Ulo_next;         // compensated form: low words of U^{n+1}
-  double* ring[3];     // [nlev][5][2M P_d][plane_d], FP64 in every precision form
   double* Rout;        // rhs-only output [5][npts] or null
+  S* xst;              // FP32 forms: U^{n+1} at the x-face slabs [hi, lo][5][2M P_x][plane_x] (else null)
+  long long xst_half;  // elements from the hi half of xst to the lo half (0: no lo half)
   double* partial;     // [gridDim.x][kNumStat]
   unsigned long long* words;  // [0] max wave key, [1] min rho key, [2] min p key, [3] health
   const vec2_t<S>* fB; // forcing lines [(K+1)][3][n2][n1] or null
@@ -499,6 +500,26 @@ __device__ __forceinline__ void split_double(double d, float& hi, float& lo) {
   if (r != 0u && es > 0) lo = __uint_as_float(__float_as_uint((float)r * __uint_as_float((unsigned)es << 23)) | sg);
 }
 
+// x-face slabs of U^{n+1} staged in FP32 by the step kernels (FP32 forms): the
+// next step's ghost kernel reads them, in the ring's slab layout, for its
+// x-face work instead of strided loads of the state.  li: local x index of the
+// point in its PE (nl points), pe: its PE in x, pl = z n1 + y; un / unlo: the
+// new state and its low words.
+template <typename S>
+__device__ __forceinline__ void stage_xface(const Geom& g, const StepArgs<S>& A, int li, int pe, long long pl,
+                                            const S (&un)[5], const S (&unlo)[5]) {
+  const int M = g.M, nl = g.nl[0];
+  if (!A.xst || g.pes[0] == 1 || (li >= M && li < nl - M)) return;
+  const int t = li < M ? li : li - nl + 2 * M;
+  const long long P2 = 2LL * M * g.pes[0];
+  S* o = A.xst + (2LL * M * pe + t) * g.plane[0] + pl;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    o[v * P2 * g.plane[0]] = un[v];
+    if (A.xst_half) o[A.xst_half + v * P2 * g.plane[0]] = unlo[v];
+  }
+}
+
 // The FP64 ring value of a state variable: the double itself, or hi + lo of
 // the compensated FP32 form (lo = 0 in the plain FP32 form).
 __device__ __forceinline__ double ring_value(double hi, double) { return hi; }
@@ -519,10 +540,11 @@ __device__ __forceinline__ bool needs_rprev(const StepArgs<S>& A, const StepDyn<
 
 // F: 0 AB2 step, 1 RK3 stage, 2 either (A.rk read per point).
 // unlo: the low words of U^{n+1} (zero without compensation), for the ring.
+// Lp: the low words of U^n of the point already loaded (null: read here).
 template <int F, typename S>
 __device__ __forceinline__ void ab2_update_v(const Coef<S>& K, const StepArgs<S>& A, const StepDyn<S>& D, long long idx,
                                              long long N, const S (&Uo)[5], const S (&R)[5], S (&un)[5],
-                                             S (&unlo)[5], unsigned& health, const S* Rp) {
+                                             S (&unlo)[5], unsigned& health, const S* Rp, const S* Lp) {
   const bool ld = needs_rprev(A, D);
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -542,7 +564,7 @@ __device__ __forceinline__ void ab2_update_v(const Coef<S>& K, const StepArgs<S>
       const S s = add_rn(Uo[v], dlt);                           // TwoSum(U_hi, dlt)
       const S bp = sub_rn(s, Uo[v]);
       const S e = add_rn(sub_rn(Uo[v], sub_rn(s, bp)), sub_rn(dlt, bp));
-      const S lo = add_rn(D.Ulo[v * N + idx], e);
+      const S lo = add_rn(Lp ? Lp[v] : D.Ulo[v * N + idx], e);
       const S hi = add_rn(s, lo);                               // renormalise
       unlo[v] = sub_rn(lo, sub_rn(hi, s));
       D.Ulo_next[v * N + idx] = unlo[v];
@@ -564,12 +586,13 @@ __device__ __forceinline__ void ab2_update_v(const Coef<S>& K, const StepArgs<S>
 template <typename S>
 __device__ __forceinline__ void ab2_update(const Coef<S>& K, const StepArgs<S>& A, const StepDyn<S>& D, long long idx,
                                            long long N, const S (&Uo)[5], const S (&R)[5], S (&un)[5],
-                                           S (&unlo)[5], unsigned& health, const S* Rp = nullptr) {
+                                           S (&unlo)[5], unsigned& health, const S* Rp = nullptr,
+                                           const S* Lp = nullptr) {
   if constexpr (sizeof(S) == 8) {
-    if (A.rk) ab2_update_v<1>(K, A, D, idx, N, Uo, R, un, unlo, health, Rp);
-    else ab2_update_v<0>(K, A, D, idx, N, Uo, R, un, unlo, health, Rp);
+    if (A.rk) ab2_update_v<1>(K, A, D, idx, N, Uo, R, un, unlo, health, Rp, Lp);
+    else ab2_update_v<0>(K, A, D, idx, N, Uo, R, un, unlo, health, Rp, Lp);
   } else {
-    ab2_update_v<2>(K, A, D, idx, N, Uo, R, un, unlo, health, Rp);
+    ab2_update_v<2>(K, A, D, idx, N, Uo, R, un, unlo, health, Rp, Lp);
   }
 }
 

@@ -59,6 +59,11 @@ __global__ void __launch_bounds__(256) k_prim(Geom g, Coef<S> K, const S* __rest
   PQ[15 * N + idx] = H * w;
 }
 
+// a, b or c for direction d = 0, 1, 2 (selects: no dynamically indexed
+// arrays, which the compiler would place in local memory).
+template <typename S>
+__device__ __forceinline__ S sel3(int d, S a, S b, S c) { return d == 0 ? a : (d == 1 ? b : c); }
+
 // The 9 quantities of direction d from one level of U (same arithmetic as k_prim).
 template <typename S>
 __device__ __forceinline__ void ghost_quantities(const Coef<S>& K, int d, const S* Uv, S* q) {
@@ -66,8 +71,8 @@ __device__ __forceinline__ void ghost_quantities(const Coef<S>& K, int d, const 
   const S vel[3] = {Uv[1] * inv, Uv[2] * inv, Uv[3] * inv};
   const S p = pressure(K, Uv[1], Uv[2], Uv[3], vel[0], vel[1], vel[2], Uv[4]);
   const S T = K.gamma * p * inv;
-  const S ud = vel[d];
-  q[0] = Uv[1 + d];
+  const S ud = sel3(d, vel[0], vel[1], vel[2]);
+  q[0] = sel3(d, Uv[1], Uv[2], Uv[3]);
   q[1] = Uv[1] * ud + (d == 0 ? p : S(0));
   q[2] = Uv[2] * ud + (d == 1 ? p : S(0));
   q[3] = Uv[3] * ud + (d == 2 ? p : S(0));
@@ -90,33 +95,48 @@ __device__ __forceinline__ void ghost_quantities(const Coef<S>& K, int d, const 
 // to the differences, which are small.  Integer instructions split the FP64
 // values (no FP64 arithmetic in the FP32 kernels).
 struct GhostBase {
-  float r, m[3], E;          // B, level n-k truncated to FP32
-  float u[3], p, T, H;       // its primitives and the fifth flux's factor
+  float r, m0, m1, m2, E;    // B, level n-k truncated to FP32
+  float u0, u1, u2, p, T, H; // its primitives and the fifth flux's factor
 };
 
-__device__ __forceinline__ void ghost_delta_f32(const Coef<float>& K, int d, const GhostBase& B, const float (&dU)[5],
-                                                float (&dq)[kNumGhostQ]) {
-  const float dr = dU[0], dE = dU[4];
+__device__ __forceinline__ GhostBase ghost_base(const Coef<float>& K, float r, float m0, float m1, float m2, float E) {
+  GhostBase B;
+  B.r = r;
+  B.m0 = m0;
+  B.m1 = m1;
+  B.m2 = m2;
+  B.E = E;
+  const float inv = rcp_rn(r);
+  B.u0 = m0 * inv;
+  B.u1 = m1 * inv;
+  B.u2 = m2 * inv;
+  B.p = pressure(K, m0, m1, m2, B.u0, B.u1, B.u2, E);
+  B.T = K.gamma * B.p * inv;
+  B.H = K.eform ? E : E + B.p;
+  return B;
+}
+
+// acc += w (q(B + dU) - q(B)) for the 9 quantities of direction d.
+__device__ __forceinline__ void ghost_delta_f32(const Coef<float>& K, int d, const GhostBase& B, float dr, float dm0,
+                                                float dm1, float dm2, float dE, float w, float* acc) {
   const float inv2 = rcp_rn(B.r + dr);
-  float du[3], m2[3];
-  float dmu = 0.f;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    du[i] = fmaf(-B.u[i], dr, dU[1 + i]) * inv2;
-    m2[i] = B.m[i] + dU[1 + i];
-    dmu = fmaf(dU[1 + i], B.u[i], fmaf(m2[i], du[i], dmu));
-  }
+  const float du0 = fmaf(-B.u0, dr, dm0) * inv2;
+  const float du1 = fmaf(-B.u1, dr, dm1) * inv2;
+  const float du2 = fmaf(-B.u2, dr, dm2) * inv2;
+  const float n0 = B.m0 + dm0, n1 = B.m1 + dm1, n2 = B.m2 + dm2;   // m + dm
+  const float dmu = fmaf(dm0, B.u0, fmaf(n0, du0, fmaf(dm1, B.u1, fmaf(n1, du1, fmaf(dm2, B.u2, n2 * du2)))));
   const float dp = K.eform ? K.gm1 * dE : K.gm1 * fmaf(-0.5f, dmu, dE);
   const float dH = K.eform ? dE : dE + dp;
-  const float ud = B.u[d], dud = du[d];
-  dq[0] = dU[1 + d];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) dq[1 + i] = fmaf(dU[1 + i], ud, m2[i] * dud) + (i == d ? dp : 0.f);
-  dq[4] = fmaf(dH, ud, (B.H + dH) * dud);
-  dq[5] = du[0];
-  dq[6] = du[1];
-  dq[7] = du[2];
-  dq[8] = fmaf(K.gamma, dp, -B.T * dr) * inv2;
+  const float ud = sel3(d, B.u0, B.u1, B.u2), dud = sel3(d, du0, du1, du2);
+  acc[0] = fmaf(w, sel3(d, dm0, dm1, dm2), acc[0]);
+  acc[1] = fmaf(w, fmaf(dm0, ud, n0 * dud) + (d == 0 ? dp : 0.f), acc[1]);
+  acc[2] = fmaf(w, fmaf(dm1, ud, n1 * dud) + (d == 1 ? dp : 0.f), acc[2]);
+  acc[3] = fmaf(w, fmaf(dm2, ud, n2 * dud) + (d == 2 ? dp : 0.f), acc[3]);
+  acc[4] = fmaf(w, fmaf(dH, ud, (B.H + dH) * dud), acc[4]);
+  acc[5] = fmaf(w, du0, acc[5]);
+  acc[6] = fmaf(w, du1, acc[6]);
+  acc[7] = fmaf(w, du2, acc[7]);
+  acc[8] = fmaf(w, fmaf(K.gamma, dp, -B.T * dr) * inv2, acc[8]);
 }
 
 // ---------------------------------------------------------------------------
@@ -126,15 +146,16 @@ __device__ __forceinline__ void ghost_delta_f32(const Coef<float>& K, int d, con
 // local t and t >= M for local nl - 2M + t.
 template <typename S, int M>
 __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __restrict__ U0,
-                                               const S* __restrict__ U1, const DevState* __restrict__ ds,
+                                               const S* __restrict__ U1, const S* __restrict__ Ulo0,
+                                               const S* __restrict__ Ulo1, const DevState* __restrict__ ds,
                                                const S* __restrict__ PQ, S* GH0, S* GH1, S* GH2,
-                                               const double* __restrict__ ring0,
-                                               const double* __restrict__ ring1,
-                                               const double* __restrict__ ring2,
-                                               const uint8_t* __restrict__ dmap, long long n,
-                                               long long cnt0, long long cnt1, long long cnt2) {
+                                               double* __restrict__ ring0, double* __restrict__ ring1,
+                                               double* __restrict__ ring2, const S* __restrict__ xst,
+                                               long long xst_half, const uint8_t* __restrict__ dmap,
+                                               long long n, long long cnt0, long long cnt1, long long cnt2) {
   long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const S* __restrict__ U = (ds && ds->cur) ? U1 : U0;
+  const S* __restrict__ Ulo = (ds && ds->cur) ? Ulo1 : Ulo0;   // compensated form: low words (else null)
   if (ds) n = ds->n;
   int d;
   if (j < cnt0) d = 0;
@@ -142,7 +163,7 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   else if ((j -= cnt1) < cnt2) d = 2;
   else return;
   S* GH = d == 0 ? GH0 : (d == 1 ? GH1 : GH2);
-  const double* ring = d == 0 ? ring0 : (d == 1 ? ring1 : ring2);
+  double* ring = d == 0 ? ring0 : (d == 1 ? ring1 : ring2);
   // j < 2M P_d plane_d < npts < 2^31 (grids hold fewer than 2^31 points), so
   // the index arithmetic below runs in 32 bits (no 64-bit division)
   const unsigned plane = (unsigned)g.plane[d];
@@ -168,10 +189,33 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   const int k = dmap[p * 6 + face];
   const long long qstride = (long long)NS * P * plane;
   S* out = GH + (long long)gi * plane + pl;
+  // the source point (in the neighbouring PE) and its slab of the ring
+  c[d] = cd;
+  const long long src = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
+  const long long N = g.npts;
+  const int nbr = slot < M ? (ped - 1 + P) % P : (ped + 1) % P;
+  const int sp = NS * nbr + (slot < M ? slot + M : slot - M);
+  const int nm = ring_slot(g, n);
+  // Level n of the source point into its ring slot: every slab point of the
+  // ring is the source of exactly one ghost slot, and no ghost reads the slot
+  // of level n from the ring (delay 0 reads the state), so this kernel keeps
+  // the ring current for the later steps that read level n with a delay.
+  // (x-faces of the FP32 forms: from the slabs the step kernel staged, which
+  // lie in this kernel's order; the state itself would be read a grid row apart)
+  const S* xs = (d == 0 && xst) ? xst + (long long)sp * plane + pl : nullptr;
+  const long long xv = (long long)NS * P * plane;   // stride of a variable in xst
+  S src_hi[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) src_hi[v] = xs ? xs[v * xv] : U[v * N + src];
+  {
+    double* rw = ring + ((long long)nm * 5 * NS * P + sp) * plane + pl;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const S lo = xs ? (xst_half ? xs[xst_half + v * xv] : S(0)) : (Ulo ? Ulo[v * N + src] : S(0));
+      rw[(long long)v * NS * P * plane] = ring_value(src_hi[v], lo);
+    }
+  }
   if (k == 0) {
-    c[d] = cd;
-    const long long src = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
-    const long long N = g.npts;
     if (PQ) {
       // the derived fields of level n already exist (multi-pass path)
       out[0] = U[(1 + d) * N + src];
@@ -180,23 +224,18 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
 #pragma unroll
       for (int q = 0; q < 4; ++q) out[(5 + q) * qstride] = PQ[q * N + src];
     } else {
-      S Uv[5], q[kNumGhostQ];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Uv[v] = U[v * N + src];
-      ghost_quantities(K, d, Uv, q);
+      S q[kNumGhostQ];
+      ghost_quantities(K, d, src_hi, q);
 #pragma unroll
       for (int qq = 0; qq < kNumGhostQ; ++qq) out[qq * qstride] = q[qq];
     }
     return;
   }
-  const int nbr = slot < M ? (ped - 1 + P) % P : (ped + 1) % P;
-  const int sp = NS * nbr + (slot < M ? slot + M : slot - M);
   int wi[M + 1];
   at_weights<M>(k, wi);
   S acc[kNumGhostQ];
   // ring slot of level n - k - l (>= 1: delays start after L + T_l steps);
   // k + l <= L + M < nlev, so one wrap of (n mod nlev) - k - l suffices
-  const int nm = ring_slot(g, n);
   auto level_at = [&](int l, int v) {
     int rs = nm - k - l;
     if (rs < 0) rs += g.nlev;
@@ -206,55 +245,54 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
 #pragma unroll
     for (int q = 0; q < kNumGhostQ; ++q) acc[q] = S(0);
 #pragma unroll
+    double lv[M + 1][5];
+#pragma unroll
+    for (int l = 0; l <= M; ++l)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) lv[l][v] = level_at(l, v);
+#pragma unroll
     for (int l = 0; l <= M; ++l) {
       const S w = S(wi[l]);
       S Uv[5], q[kNumGhostQ];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) Uv[v] = level_at(l, v);
+      for (int v = 0; v < 5; ++v) Uv[v] = lv[l][v];
       ghost_quantities(K, d, Uv, q);
 #pragma unroll
       for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = fma(w, q[qq], acc[qq]);
     }
   } else {
-    // base B = level n-k truncated to FP32; its own remainder is level 0's dU
-    GhostBase B;
-    float dU[5];
-    {
-      float hb[5];
+    // every ring value of the T_l levels first (all loads in flight together)
+    double lv[M + 1][5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) split_double(level_at(0, v), hb[v], dU[v]);
-      B.r = hb[0];
-      B.m[0] = hb[1];
-      B.m[1] = hb[2];
-      B.m[2] = hb[3];
-      B.E = hb[4];
+    for (int l = 0; l <= M; ++l)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) lv[l][v] = level_at(l, v);
+    // base B = level n-k truncated to FP32; its own remainder is level 0's dU
+    float h0, h1, h2, h3, h4, l0, l1, l2, l3, l4;
+    split_double(lv[0][0], h0, l0);
+    split_double(lv[0][1], h1, l1);
+    split_double(lv[0][2], h2, l2);
+    split_double(lv[0][3], h3, l3);
+    split_double(lv[0][4], h4, l4);
+    const GhostBase B = ghost_base(K, h0, h1, h2, h3, h4);
+    {
+      const float hb[5] = {h0, h1, h2, h3, h4};
       S q[kNumGhostQ];
       ghost_quantities(K, d, hb, q);
 #pragma unroll
       for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = q[qq];
-      const float inv = rcp_rn(B.r);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) B.u[i] = B.m[i] * inv;
-      B.p = pressure(K, B.m[0], B.m[1], B.m[2], B.u[0], B.u[1], B.u[2], B.E);
-      B.T = K.gamma * B.p * inv;
-      B.H = K.eform ? B.E : B.E + B.p;
     }
+    ghost_delta_f32(K, d, B, l0, l1, l2, l3, l4, (float)wi[0], acc);
 #pragma unroll
-    for (int l = 0; l <= M; ++l) {
-      if (l > 0) {
+    for (int l = 1; l <= M; ++l) {
+      float hi, lo, dv[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          float hi, lo;
-          split_double(level_at(l, v), hi, lo);
-          const float hb = v == 0 ? B.r : (v == 4 ? B.E : B.m[v - 1]);
-          dU[v] = (hi - hb) + lo;
-        }
+      for (int v = 0; v < 5; ++v) {
+        split_double(lv[l][v], hi, lo);
+        const float hb = v == 0 ? h0 : (v == 1 ? h1 : (v == 2 ? h2 : (v == 3 ? h3 : h4)));
+        dv[v] = (hi - hb) + lo;
       }
-      float dq[kNumGhostQ];
-      ghost_delta_f32(K, d, B, dU, dq);
-      const float w = (float)wi[l];
-#pragma unroll
-      for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = fmaf(w, dq[qq], acc[qq]);
+      ghost_delta_f32(K, d, B, dv[0], dv[1], dv[2], dv[3], dv[4], (float)wi[l], acc);
     }
   }
 #pragma unroll
@@ -806,29 +844,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 3 : 2) k_main(Geom g, Co
       const S Uo[5] = {r, m[0], m[1], m[2], E};
       S un[5], unlo[5];
       ab2_update(K, A, D, idx, N, Uo, R, un, unlo, health);
-      // PE-boundary slabs of U^{n+1} into ring slot (n+1) mod nlev (FP64)
-      const int slot = (int)((D.n + 1) % g.nlev);
-      bool onface = false;
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-        onface |= g.pes[d] > 1 && (P.li[d] < M || P.li[d] >= g.nl[d] - M);
-      if (onface) {
-        double rv[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) rv[v] = ring_value(un[v], unlo[v]);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          if (g.pes[d] == 1) continue;
-          const int li = P.li[d], nl = g.nl[d];
-          if (li >= M && li < nl - M) continue;
-          const int t = li < M ? li : li - nl + 2 * M;
-          const long long sp = 2LL * M * P.pe[d] + t;
-          double* rg = A.ring[d];
-          const long long PS = 2LL * M * g.pes[d];
-#pragma unroll
-          for (int v = 0; v < 5; ++v) rg[(((long long)slot * 5 + v) * PS + sp) * g.plane[d] + P.pl[d]] = rv[v];
-        }
-      }
+      // (the ring slabs of level n+1 are written by the next step's ghost kernel)
+      stage_xface(g, A, P.li[0], P.pe[0], P.pl[0], un, unlo);
     } else if (A.Rout) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) A.Rout[v * N + idx] = (double)R[v];

@@ -418,7 +418,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
   PlaneRaw<S, TX, TY> pf;                       // plane z + 4, fetched one iteration ahead
   fused_fetch_plane<S, TX, TY>(g, A, D.U, F, zs + 4, pf);
 
-  const int slot = ring_slot(g, D.n + 1);      // ring slot of level n+1
   for (int z = zs; z < zs + ZC; ++z) {
     const int q = z - zs + 4;                  // window-plane count of plane z
     fused_store_plane<S, TX, TY>(K, pf, win, slot_A<TX, TY>(q + 4), slot_T<TX, TY>(q + 4), slot_R<TX, TY>(q + 4));
@@ -429,9 +428,12 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
     const S m[3] = {D.U[N + idx], D.U[2 * N + idx], D.U[3 * N + idx]};
     const S Ecur = D.U[4 * N + idx];
-    S Rp[5];
+    S Rp[5], Lp[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) Rp[v] = needs_rprev(A, D) ? A.Rprev[v * N + idx] : S(0);
+    // the compensated form's low words of U^n, loaded with R^{n-1}
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Lp[v] = (A.do_update && D.Ulo) ? D.Ulo[v * N + idx] : S(0);
     // fluxes of the current plane (x on x-extended rows, y on y-extended
     // columns), and on the same cells the AT derivatives the mixed rule's x-
     // and y-stencils take
@@ -661,31 +663,9 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(S) == 4 && TX * TY <= 256) ? 
     if (A.do_update) {
       const S Uo[5] = {r, m[0], m[1], m[2], Ecur};
       S un[5], unlo[5];
-      ab2_update(K, A, D, idx, N, Uo, R, un, unlo, health, Rp);
-      const int li[3] = {li_x, li_y, li_z};
-      const int c3[3] = {x, y, z};
-      bool onface = false;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) onface |= g.pes[d] > 1 && (li[d] < 2 || li[d] >= g.nl[d] - 2);
-      if (onface) {
-        // the ring holds FP64 levels: hi + lo of the compensated form
-        double rv[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) rv[v] = ring_value(un[v], unlo[v]);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          if (g.pes[d] == 1) continue;
-          const int nl = g.nl[d];
-          if (li[d] >= 2 && li[d] < nl - 2) continue;
-          const int t = li[d] < 2 ? li[d] : li[d] - nl + 4;
-          const long long sp = 4LL * F.pe[d] + t;
-          const long long pl = plane_index(g, d, c3[0], c3[1], c3[2]);
-          double* rg = A.ring[d];
-          const long long P4 = 4LL * g.pes[d];
-#pragma unroll
-          for (int v = 0; v < 5; ++v) rg[(((long long)slot * 5 + v) * P4 + sp) * g.plane[d] + pl] = rv[v];
-        }
-      }
+      ab2_update(K, A, D, idx, N, Uo, R, un, unlo, health, Rp, D.Ulo ? Lp : nullptr);
+      // (the ring slabs of level n+1 are written by the next step's ghost kernel)
+      stage_xface(g, A, li_x, F.pe[0], (long long)z * g.n[1] + y, un, unlo);
     } else if (A.Rout) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) A.Rout[v * N + idx] = (double)R[v];

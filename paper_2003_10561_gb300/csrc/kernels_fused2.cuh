@@ -292,10 +292,12 @@ __global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
   pair_xwindow(kind_x, lx0, lx1, xstart);
   f2 lcy[5];
   {
-    const float t[5][5] = {{1, -8, 0, 8, -1}, {-25, 48, -36, 16, -3}, {-3, -10, 18, -6, 1},
-                           {-1, 6, -18, 10, 3}, {3, -16, 36, -48, 25}};
-#pragma unroll
-    for (int i = 0; i < 5; ++i) lcy[i] = bc(t[kind_y][i]);
+    float t0 = 1, t1 = -8, t2 = 0, t3 = 8, t4 = -1;      // kind 0: central
+    if (kind_y == 1) { t0 = -25; t1 = 48; t2 = -36; t3 = 16; t4 = -3; }
+    else if (kind_y == 2) { t0 = -3; t1 = -10; t2 = 18; t3 = -6; t4 = 1; }
+    else if (kind_y == 3) { t0 = -1; t1 = 6; t2 = -18; t3 = 10; t4 = 3; }
+    else if (kind_y == 4) { t0 = 3; t1 = -16; t2 = 36; t3 = -48; t4 = 25; }
+    lcy[0] = bc(t0); lcy[1] = bc(t1); lcy[2] = bc(t2); lcy[3] = bc(t3); lcy[4] = bc(t4);
   }
   const int ax0 = ty * CX + 2 + 2 * txh + xstart;             // window start in an x-row array
   const int ay0 = (ty + 2 + local_first(kind_y)) * TX + 2 * txh;
@@ -320,7 +322,6 @@ __global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
   PlaneRaw2<TX, TY> pf;                                       // plane z + 4, fetched one iteration ahead
   fetch_plane2<TX, TY>(g, A, D.U, F, zs + 4, pf);
 
-  const int slot = ring_slot(g, D.n + 1);                     // ring slot of level n+1
   for (int z = zs; z < zs + ZC; ++z) {
     const int q = z - zs + 4;
     store_plane2<TX, TY>(K, KP, pf, win, slot_A<TX, TY>(q + 4), slot_T<TX, TY>(q + 4), slot_R<TX, TY>(q + 4));
@@ -329,10 +330,13 @@ __global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
     const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
     const f2 m[3] = {ld2(D.U + N + idx), ld2(D.U + 2 * N + idx), ld2(D.U + 3 * N + idx)};
     const f2 Ecur = ld2(D.U + 4 * N + idx);
-    f2 Rp[5];
-    const bool ldrp = needs_rprev(A, D);
+    f2 Rp[5], Lp[5];
+    const bool ldrp = needs_rprev(A, D), ldlo = A.do_update && D.Ulo;
 #pragma unroll
     for (int v = 0; v < 5; ++v) Rp[v] = ldrp ? ld2(A.Rprev + v * N + idx) : bc(0.f);
+    // the compensated form's low words of U^n, loaded with R^{n-1}
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Lp[v] = ldlo ? ld2(D.Ulo + v * N + idx) : bc(0.f);
 
     // ---- per-plane flux arrays and AT derivative arrays, on cell pairs
     {
@@ -353,7 +357,9 @@ __global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
       };
       constexpr int XPR = CX / 2, XP = TY * XPR;        // x-row pairs
       constexpr int YPR = TX / 2, YP = (TY + 4) * YPR;  // y-column pairs
-      for (int p = tid; p < XP; p += PS::NT) {
+      // one loop over both kinds of pair, so the passes spread evenly over the threads
+      for (int p = tid; p < XP + YP; p += PS::NT) {
+        if (p < XP) {
         const int r = p / XPR, cxw = 2 * (p - r * XPR);
         const int c = r * CX + cxw;
         const int xg = F.x0 - 2 + cxw, yg = F.y0 + r;
@@ -375,9 +381,9 @@ __global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
         st2(XR + XR_UY * TY * CX + c, ddy(win + bA + cw));
         st2(XR + XR_WZ * TY * CX + c, ddz(2, cw));
         st2(XR + XR_UZ * TY * CX + c, ddz(0, cw));
-      }
-      for (int p = tid; p < YP; p += PS::NT) {
-        const int r = p / YPR, cxl = 2 * (p - r * YPR);
+        } else {
+        const int py = p - XP;
+        const int r = py / YPR, cxl = 2 * (py - r * YPR);
         const int c = r * TX + cxl;
         const int xg = F.x0 + cxl, yg = F.y0 - 2 + r;
         const int cw = r * CX + cxl + 2;
@@ -396,6 +402,7 @@ __global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
         st2(YC + YC_UX * (TY + 4) * TX + c, ddx(win + bA + cw));
         st2(YC + YC_WZ * (TY + 4) * TX + c, ddz(2, cw));
         st2(YC + YC_VZ * (TY + 4) * TX + c, ddz(1, cw));
+        }
       }
     }
     __syncthreads();
@@ -631,7 +638,7 @@ __global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
           const f2 s = Uo[v] + dlt;
           const f2 bp = s - Uo[v];
           const f2 e = (Uo[v] - (s - bp)) + (dlt - bp);
-          const f2 lo = ld2(D.Ulo + v * N + idx) + e;
+          const f2 lo = Lp[v] + e;
           const f2 hi = s + lo;
           unlo[v] = lo - (hi - s);
           un[v] = hi;
@@ -644,42 +651,19 @@ __global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
         st2(A.Rprev + v * N + idx, kept);
         if (nonfinite(un[v].x) || nonfinite(un[v].y)) health |= H_NONFINITE;
       }
-      // FP64 ring of level n+1 at PE-boundary points (a pair is on a face
-      // together: PE extents are even and pairs start at even x)
-      const int li[3] = {li_x, li_y, li_z};
-      bool onface = false;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) onface |= g.pes[d] > 1 && (li[d] < 2 || li[d] >= g.nl[d] - 2);
-      if (onface) {
-        double rv0[5], rv1[5];
+      // (the ring slabs of level n+1 are written by the next step's ghost kernel)
+      if (A.xst && g.pes[0] > 1 && (li_x < 2 || li_x >= g.nl[0] - 2)) {
+        // the pair is x-face slabs t and t + 1 of its PE
+        const int t = li_x < 2 ? li_x : li_x - g.nl[0] + 4;
+        const long long pv = 4LL * g.pes[0] * g.plane[0];
+        float* o = A.xst + (4LL * F.pe[0] + t) * g.plane[0] + (long long)z * g.n[1] + y;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          rv0[v] = ring_value(un[v].x, unlo[v].x);
-          rv1[v] = ring_value(un[v].y, unlo[v].y);
-        }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          if (g.pes[d] == 1) continue;
-          const int nl = g.nl[d];
-          if (li[d] >= 2 && li[d] < nl - 2) continue;
-          const int t = li[d] < 2 ? li[d] : li[d] - nl + 4;
-          double* rg = A.ring[d];
-          const long long P4 = 4LL * g.pes[d];
-          if (d == 0) {
-            // the two points are consecutive slabs t, t + 1 of the x-face
-            const long long pl = (long long)z * g.n[1] + y;
-#pragma unroll
-            for (int v = 0; v < 5; ++v) {
-              rg[(((long long)slot * 5 + v) * P4 + 4LL * F.pe[0] + t) * g.plane[0] + pl] = rv0[v];
-              rg[(((long long)slot * 5 + v) * P4 + 4LL * F.pe[0] + t + 1) * g.plane[0] + pl] = rv1[v];
-            }
-          } else {
-            const long long pl = d == 1 ? (long long)z * g.n[0] + x : (long long)y * g.n[0] + x;
-            const long long sp = 4LL * F.pe[d] + t;
-#pragma unroll
-            for (int v = 0; v < 5; ++v)
-              *reinterpret_cast<double2*>(rg + (((long long)slot * 5 + v) * P4 + sp) * g.plane[d] + pl) =
-                  make_double2(rv0[v], rv1[v]);
+          o[v * pv] = un[v].x;
+          o[v * pv + g.plane[0]] = un[v].y;
+          if (A.xst_half) {
+            o[A.xst_half + v * pv] = unlo[v].x;
+            o[A.xst_half + v * pv + g.plane[0]] = unlo[v].y;
           }
         }
       }

@@ -20,16 +20,17 @@ cudaError_t launch_prim<S>(const Geom& g, const Coef<S>& K, const S* U0, const S
 #endif
 
 template <>
-cudaError_t launch_ghost_m<S, kM>(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const DevState* ds,
-                                  const S* PQ, S* const GH[3], double* const ring[3], const uint8_t* dmap, long long n,
-                                  cudaStream_t st) {
+cudaError_t launch_ghost_m<S, kM>(const Geom& g, const Coef<S>& K, const S* U0, const S* U1, const S* Ulo0,
+                                  const S* Ulo1, const DevState* ds, const S* PQ, S* const GH[3],
+                                  double* const ring[3], const S* xst, long long xst_half, const uint8_t* dmap,
+                                  long long n, cudaStream_t st) {
   long long cnt[3];
   for (int d = 0; d < 3; ++d) cnt[d] = g.pes[d] > 1 ? 2LL * kM * g.pes[d] * g.plane[d] : 0;
   const long long tot = cnt[0] + cnt[1] + cnt[2];
   if (tot == 0) return cudaSuccess;
   const unsigned nb = (unsigned)((tot + kBlock - 1) / kBlock);
-  k_ghost<S, kM><<<nb, kBlock, 0, st>>>(g, K, U0, U1, ds, PQ, GH[0], GH[1], GH[2], ring[0], ring[1], ring[2], dmap,
-                                        n, cnt[0], cnt[1], cnt[2]);
+  k_ghost<S, kM><<<nb, kBlock, 0, st>>>(g, K, U0, U1, Ulo0, Ulo1, ds, PQ, GH[0], GH[1], GH[2], ring[0], ring[1],
+                                        ring[2], xst, xst_half, dmap, n, cnt[0], cnt[1], cnt[2]);
   return cudaGetLastError();
 }
 

@@ -233,18 +233,7 @@ def test_rhs_parity_fp32(lib, n, pes, mode, step, L, path, prec):
 
 
 # --------------------------------------------------------------------------
-def _sample_points(n, nloc, rng, count):
-    """Random points plus PE face, edge and corner points and the ragged ends."""
-    pts = set()
-    for _ in range(count):
-        pts.add(tuple(int(rng.integers(0, n[d])) for d in range(3)))
-    special = [0, 1, nloc - 2, nloc - 1, nloc, nloc + 1, 2, nloc // 2]
-    for a in special:
-        for b in (0, 1, nloc - 1, 5):
-            pts.add((a % n[0], b % n[1], (a + b) % n[2]))
-            pts.add((b % n[0], a % n[1], 3 % n[2]))
-    pts.add((n[0] - 1, n[1] - 1, n[2] - 1))
-    return sorted(pts)
+from tests.sampling import sample_points as _sample_points  # noqa: E402
 
 
 # Tolerance at 256^3: the per-RHS bounds above hold at the 32^3 parity grid.
