@@ -136,8 +136,9 @@ typedef struct {
  * over U per step on PE-aligned tiles (needs the per-direction PE extent, or
  * the grid extent where a direction has one PE, to be a multiple of 8 and the
  * tile to hold a multiple of 32 points; 4th order only).  AUTO takes the path
- * that is faster on GB300 at the benchmark workload: fused for P32 / P32C
- * where it applies, multi-pass otherwise. */
+ * that is faster on GB300 at the benchmark workload: for P32 / P32C the paired
+ * fused kernel where its tiles fit, else the fused one where it applies;
+ * multi-pass otherwise. */
 #define AT_DNS_PATH_AUTO       0
 #define AT_DNS_PATH_MULTIPASS  1
 #define AT_DNS_PATH_FUSED      2

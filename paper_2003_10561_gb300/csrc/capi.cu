@@ -910,9 +910,16 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     h->paired = true;
   }
   // AUTO takes the faster path on GB300 at the benchmark workload (at_dns_tune
-  // can switch): the fused one for the FP32 forms (one pass over U, no work
-  // arrays), the multi-pass one for FP64 (bound by the FP64 pipe, where the
-  // fused path's halo recompute costs more than the work arrays' traffic)
+  // can switch): a fused one for the FP32 forms (one pass over U, no work
+  // arrays; the paired kernel where its tiles fit), the multi-pass one for
+  // FP64 (bound by the FP64 pipe, where the fused path's halo recompute costs
+  // more than the work arrays' traffic)
+  if (c.kernel_path == AT_DNS_PATH_AUTO && !h->p64 && M == 2) {
+    // AUTO for the FP32 forms: the paired fused kernel where its tiles fit
+    // (faster than the one-point kernel at the benchmark workload on GB300)
+    for (const Candidate& cd : tune_candidates(g, h->p64))
+      if (cd.paired) { h->TX = cd.TX; h->TY = cd.TY; h->ZC = cd.ZC; h->paired = true; break; }
+  }
   h->fused = h->paired ||
              (can_fuse && (c.kernel_path == AT_DNS_PATH_FUSED || (c.kernel_path == AT_DNS_PATH_AUTO && !h->p64)));
   if (!h->fused) h->TX = h->TY = h->ZC = 0;

@@ -1,7 +1,8 @@
-"""Full-size check of the memory-lean FP32 configuration: 1024^3 with 16x16x16
-virtual PEs of 64^3 (N_B = 17.6 %), random AT delays with L = 4 (seven ring
-levels), forcing on |kappa| <= 2, FP32 state and stencils with FP64
-reductions, on the fused path (no per-point work arrays).
+"""Full-size check of the memory-lean FP32-bulk configuration (the workload
+list's fifth): 1024^3 with 16x16x16 virtual PEs of 64^3 (N_B = 17.6 %),
+random AT delays with L = 4 (seven FP64 ring levels), forcing on
+|kappa| <= 2, FP32 state and stencils with compensated FP32 accumulation and
+FP64 reductions (P32C), on the paired fused path (no per-point work arrays).
 
 The state is a smooth analytic, time-dependent field: the library receives it
 as two device-resident levels (U^n and U^{n-1}; older ring levels repeat the
@@ -10,7 +11,9 @@ points (no 1024^3 array ever reaches the host).  The RHS at step n, with that
 step's random delay map and forcing, must match at the sampled points within
 the FP32 tolerance scaled to this grid (2e-4 at 32^3, times 32 for the 1/dx
 growth of the first-derivative stencil terms), and the handle must fit in
-180 GB of device memory.
+180 GB of device memory.  Then the run's 200 steps, timed, must stay healthy,
+and are reported against the FP64 plain (synchronous, one PE) method on the
+same analytic field at 512^3 on the same GPU.
 """
 import math
 
@@ -55,20 +58,22 @@ class AnalyticLevel:
         return _conserved(x * h, y * h, z * h, self.t, math)[v]
 
 
-def test_config5_1024_fp32_fused_memory_and_parity():
+def test_config5_1024_fp32_bulk_memory_parity_and_200_steps():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     free, total = torch.cuda.mem_get_info()
-    if free < 230e9:
-        pytest.skip("needs about 230 GB of free device memory")
+    if free < 265e9:
+        pytest.skip("needs about 265 GB of free device memory (the handle and two FP64 levels)")
     from paper_2003_10561_gb300 import at_dns
     kw = dict(gamma=GAMMA, prandtl=PR, visc_exp=OMEGA, mu0=MU0, dt=DT, max_delay=L, seed=97,
               forcing=1, kf=2.0, f_amp=0.02, f_tcorr=0.5, f_seed=13)
-    s = at_dns.Solver(n=(N, N, N), pes=(PES, PES, PES), precision="p32", path="fused", **kw)
+    stream = torch.cuda.Stream()
+    s = at_dns.Solver(n=(N, N, N), pes=(PES, PES, PES), precision="p32c", path="paired", stream=stream.cuda_stream,
+                      **kw)
     info = s.info()
     assert info["device_bytes"] <= 180e9, info["device_bytes"]
-    assert info["tile"] == [32, 8, 64]
+    assert info["tile"] == [32, 8, 64] and info["kernel_path"] == at_dns.AT_DNS_PATH_PAIRED
 
     # two levels on the device, filled plane block by plane block
     lv = torch.empty((2, 5, N, N, N), dtype=torch.float64, device="cuda")
@@ -105,10 +110,38 @@ def test_config5_1024_fp32_fused_memory_and_parity():
     err = np.max(np.abs(got - ref), axis=0) / np.max(np.abs(ref), axis=0)
     assert np.max(err) <= TOL, err
 
-    # a few steps run healthy on the memory-lean path
+    # the configuration's 200 steps, timed, stay healthy
     del R
     torch.cuda.empty_cache()
-    s.step(2, "random")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(200, "random")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rate32 = N ** 3 * 200 / (e0.elapsed_time(e1) / 1e3)
     st = s.stats()
-    assert st["unstable"] == 0 and st["step"] == STEP + 1
+    assert st["unstable"] == 0 and st["step"] == STEP + 199
     s.close()
+    torch.cuda.empty_cache()
+
+    # the FP64 plain method (synchronous, no PE faces) at 512^3 on the same field
+    n2 = 512
+    p = at_dns.Solver(n=(n2, n2, n2), pes=(1, 1, 1), precision="p64", stream=stream.cuda_stream,
+                      **{**kw, "max_delay": 0})
+    ax2 = torch.arange(n2, dtype=torch.float64, device="cuda") * (2 * math.pi / n2)
+    U2 = torch.stack(_conserved(ax2.view(1, 1, n2), ax2.view(1, n2, 1), ax2.view(n2, 1, 1), 0.0, torch))
+    p.set_state(U2.contiguous())
+    del U2
+    p.step(3, "sync")
+    torch.cuda.synchronize()
+    e0.record(stream)
+    p.step(20, "sync")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rate64 = n2 ** 3 * 20 / (e0.elapsed_time(e1) / 1e3)
+    assert p.stats()["unstable"] == 0
+    p.close()
+    print("config 5: 1024^3 FP32-bulk AT (L = 4) %.3e updates/s; 512^3 FP64 plain %.3e updates/s; ratio %.2f"
+          % (rate32, rate64, rate32 / rate64))
+    assert rate32 > rate64
