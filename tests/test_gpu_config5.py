@@ -87,6 +87,7 @@ def test_config5_1024_fp32_bulk_memory_parity_and_200_steps():
             vals = _conserved(X, Y, Z, t, torch)
             for var in range(5):
                 lv[l, var, z0:z0 + 64] = vals[var]
+    torch.cuda.synchronize()   # the levels were built on torch's stream, the handle runs on its own
     s.set_history(lv, STEP)
     del lv, vals
     torch.cuda.empty_cache()
@@ -131,7 +132,9 @@ def test_config5_1024_fp32_bulk_memory_parity_and_200_steps():
                       **{**kw, "max_delay": 0})
     ax2 = torch.arange(n2, dtype=torch.float64, device="cuda") * (2 * math.pi / n2)
     U2 = torch.stack(_conserved(ax2.view(1, 1, n2), ax2.view(1, n2, 1), ax2.view(n2, 1, 1), 0.0, torch))
-    p.set_state(U2.contiguous())
+    U2 = U2.contiguous()
+    torch.cuda.synchronize()
+    p.set_state(U2)
     del U2
     p.step(3, "sync")
     torch.cuda.synchronize()
