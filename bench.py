@@ -403,7 +403,8 @@ def main():
         s.close()
 
     # batched ensemble: 64 independent decaying runs of uneven sizes advanced by
-    # one graph launch per step (FP32-bulk, random delays, tiles from the tuner)
+    # one graph launch per step (FP32-bulk, random delays, each member on its
+    # default path), and by the opt-in persistent single launch per step
     if not args.no_batch and N == 256:
         specs, states = [], []
         mu_of = {nb: synth.mu0_for_resolution((nb,) * 3, k0=4.0, mach_t=0.3, seed=0) for nb in (32, 48, 64, 96, 128)}
@@ -420,19 +421,20 @@ def main():
         for m, U in zip(batch.members, states):
             m.set_state(U)
         batch.step(6, "random")
-        batch.tune("random", trials=2)
-        batch.step(args.warmup, "random")
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(bstream)
-        batch.step(args.steps, "random")
-        e1.record(bstream)
-        torch.cuda.synchronize()
-        bms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+        timed = {}
+        for persistent in (False, True):   # the graph of member branches, then the persistent launch
+            batch.set_persistent(persistent)
+            batch.step(args.warmup, "random")
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(bstream)
+            batch.step(args.steps, "random")
+            e1.record(bstream)
+            torch.cuda.synchronize()
+            timed[persistent] = (max_over_ranks(e0.elapsed_time(e1), pg, "cuda"), batch.persistent)
         bpts = float(sum(sp["n"][0] ** 3 for sp in specs))
-        paths = [m.info()["kernel_path"] for m in batch.members]
-        res["batch"] = {"ms": bms, "pts": bpts, "fused": sum(1 for p_ in paths if p_ == at_dns.AT_DNS_PATH_FUSED)}
+        res["batch"] = {"ms": timed[True][0], "pts": bpts, "persistent": timed[True][1], "ms_graph": timed[False][0]}
         batch.close()
 
     cpu = None
@@ -471,11 +473,16 @@ def main():
     if "batch" in res:
         bt = res["batch"]
         line["batch_ensemble"] = {
-            "value": job_rate(world, bt["pts"], args.steps, bt["ms"]), "unit": UNIT, "dtype": "f32",
-            "ms_per_step": bt["ms"] / args.steps, "members": 64, "members_on_fused_path": bt["fused"],
+            "value": job_rate(world, bt["pts"], args.steps, bt["ms_graph"]), "unit": UNIT, "dtype": "f32",
+            "ms_per_step": bt["ms_graph"] / args.steps, "members": 64,
+            "form": "one graph launch per step, each member on its own branch and default path",
+            "persistent_form": {"value": job_rate(world, bt["pts"], args.steps, bt["ms"]),
+                                "ms_per_step": bt["ms"] / args.steps,
+                                "one_persistent_launch_per_step": bt["persistent"],
+                                "note": "opt-in: one cooperative kernel launch per step over the members' ghost "
+                                        "items and paired-kernel tiles"},
             "workload": "64 decaying runs, grids {32,48,64,96,128}^3 by member, PEs of 16^3, M_t 0.1..0.5, "
-                        "k0 in {3,4,6}, seeds 0..63, FP32-bulk, random delays L = 2, one graph launch per step, "
-                        "kernel paths and tiles from the autotuner"}
+                        "k0 in {3,4,6}, seeds 0..63, FP32-bulk (P32C), random delays L = 2"}
     if "rk3" in res:
         line["rk3_sync"] = {
             "value": job_rate(world, pts, args.steps, res["rk3"]["ms"]), "unit": UNIT, "dtype": "f64",

@@ -62,6 +62,7 @@ extern "C" {
 #define AT_DNS_E_UNSUPPORTED  -5   /* a combination the library does not run */
 #define AT_DNS_E_STATE        -6   /* no state has been set yet */
 #define AT_DNS_E_TOO_LARGE    -7   /* problem above a fixed size limit (at_dns_rhs_noalloc) */
+#define AT_DNS_E_TIMEOUT      -8   /* a bounded wait inside a kernel gave up (persistent batch step) */
 
 /* delay modes (Sec. 3.1) */
 #define AT_DNS_SYNC      0   /* k = 0 on every face: standard scheme */
@@ -289,11 +290,32 @@ int at_dns_synchronize(at_dns_t* h);
 
 /* ---- batched ensembles --------------------------------------------------
  * Independent members (own grid, PEs, physics, precision, delays) advance
- * together: each at_dns_batch_step step is one launch of a captured graph
- * holding one step of every member on its own branch, so members of uneven
- * size run concurrently.  Members are ordinary handles (set their state, read
- * them back through at_dns_batch_member); each runs on a stream the batch
- * owns, and a batch step is ordered after earlier work on those streams. */
+ * together.  Each batch step is one launch of a captured graph holding one
+ * step of every member on its own branch (each member on its own kernels and
+ * tuned path, bit-identical to the member stepped alone).  Members are
+ * ordinary handles (set their state, read them back through
+ * at_dns_batch_member); each runs on a stream the batch owns, and a batch
+ * step is ordered after earlier work on those streams.
+ *
+ * Opt-in (at_dns_batch_persistent): when the batch has at most 64 members,
+ * every member runs an FP32 form (P32 / P32C), the 4th-order scheme, AB2 and
+ * no forcing, and the members' PE extents (grid extents where a direction
+ * has one PE) fit one paired tile shape (16x16, or 32x8), a batch step can
+ * instead be ONE persistent cooperative kernel launch over work items dealt
+ * round-robin to the CTAs: the members' ghost assembly in chunks, then their
+ * tiles of the paired fused kernel (each member's description in constant
+ * memory), each tile waiting (bounded) for its own member's ghost items
+ * only; the CTA that finishes a member's last tile sums its statistics and
+ * advances its step.  Each member then takes the arithmetic of the paired
+ * kernel with the batch's tile, and agrees with the member stepped alone to
+ * about one FP32 rounding of the right-hand side (the same operations,
+ * compiled into another kernel: P32C states within the low words).  Constant
+ * memory holds one batch's descriptions at a time: stepping another batch
+ * re-uploads them, ordered after the earlier batch's last persistent launch.
+ * The graph form is the default because it is the faster of the two on
+ * GB300: inside one kernel, the tile body reads its coefficients through a
+ * table instead of as kernel parameters, and the ghost assembly runs at the
+ * tile's occupancy. */
 typedef struct at_dns_batch at_dns_batch_t;
 
 /* Create `count` members from cfgs[0..count-1] (their `stream` fields are
@@ -306,8 +328,24 @@ int at_dns_batch_member(at_dns_batch_t* b, int32_t i, at_dns_t** out);
 
 /* Advance every member nsteps AB2 steps with delay mode `delay_mode`; blocks
  * until done.  Errors: INVALID_ARG, STATE (a member without state), CUDA,
- * UNSTABLE (a member saw NaN/Inf, rho <= 0 or p <= 0). */
+ * UNSTABLE (a member saw NaN/Inf, rho <= 0 or p <= 0), TIMEOUT (a bounded
+ * wait of the persistent step for a member's ghost items gave up; the
+ * members' states are then not valid). */
 int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode);
+
+/* Allow (enable > 0) or forbid (enable == 0, the default) the persistent
+ * single-launch step for eligible batches; enable < 0 changes nothing.
+ * *persistent (may be NULL) receives 1 if the next at_dns_batch_step runs as
+ * one persistent launch per step, 0 if as a graph launch.
+ * Errors: INVALID_ARG. */
+int at_dns_batch_persistent(at_dns_batch_t* b, int32_t enable, int32_t* persistent);
+
+/* Self-test of the persistent step's bounded wait: one GPU thread waits for
+ * a device counter that nothing advances, giving up after at most
+ * 2^log2_polls polls about 64 ns apart (log2_polls in [0, 26]); *gave_up
+ * receives 1 when the wait returned unsatisfied (the expected result) and
+ * the context stays usable.  Errors: INVALID_ARG, CUDA. */
+int at_dns_wait_selftest(int32_t log2_polls, int32_t* gave_up);
 
 /* at_dns_tune on every member. */
 int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials);

@@ -20,6 +20,7 @@ AT_DNS_E_UNSTABLE = -4
 AT_DNS_E_UNSUPPORTED = -5
 AT_DNS_E_STATE = -6
 AT_DNS_E_TOO_LARGE = -7
+AT_DNS_E_TIMEOUT = -8
 AT_DNS_NOALLOC_MAX_POINTS = 262144
 
 AT_DNS_SYNC, AT_DNS_PERIODIC, AT_DNS_RANDOM, AT_DNS_FIXED = 0, 1, 2, 3
@@ -106,6 +107,8 @@ _SIGS = {
     "at_dns_batch_member": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     "at_dns_batch_step": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "at_dns_batch_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "at_dns_batch_persistent": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "at_dns_wait_selftest": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "at_dns_batch_last_error": (ctypes.c_char_p, [_P]),
     "at_dns_batch_destroy": (None, [_P]),
     "at_dns_rhs_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_double,
@@ -297,6 +300,14 @@ def at_dns_batch_tune(b, delay_mode, trials=3):
     _bcheck(load().at_dns_batch_tune(b, delay_mode, trials), b)
 
 
+def at_dns_wait_selftest(log2_polls=20):
+    """Run the persistent step's bounded wait on a counter nothing advances;
+    True when it gave up (the expected result)."""
+    out = ctypes.c_int32(-1)
+    _check(load().at_dns_wait_selftest(log2_polls, ctypes.byref(out)))
+    return out.value == 1
+
+
 def at_dns_batch_destroy(b):
     load().at_dns_batch_destroy(b)
 
@@ -334,10 +345,14 @@ def make_config(n=(32, 32, 32), pes=(1, 1, 1), precision="p64", stream=None, pat
 
 
 class Batch:
-    """Independent members advancing together (one graph launch per step).
-    `members` is a list of dicts of Solver arguments (n, pes, precision, ...)."""
+    """Independent members advancing together: one graph launch per step (each
+    member on its own branch), or, opted into with set_persistent(True) when
+    every member is eligible (at most 64 members, FP32 forms, 4th order, AB2,
+    unforced, PE extents fitting one paired tile), one persistent kernel
+    launch per step.  `members` is a list of dicts of Solver arguments (n,
+    pes, precision, ...); `persistent` sets the step form at creation."""
 
-    def __init__(self, members, stream=None):
+    def __init__(self, members, stream=None, persistent=False):
         self.specs = [dict(m) for m in members]
         cfgs = [make_config(**m) for m in self.specs]
         self.b = at_dns_batch_create(cfgs, stream)
@@ -345,6 +360,8 @@ class Batch:
         for i, m in enumerate(self.specs):
             h = at_dns_batch_member(self.b, i)
             self.members.append(Solver(n=m.get("n", (32, 32, 32)), pes=m.get("pes", (1, 1, 1)), handle=h))
+        if persistent:
+            self.set_persistent(True)
 
     def __len__(self):
         return len(self.members)
@@ -357,6 +374,20 @@ class Batch:
 
     def tune(self, mode="random", trials=3):
         at_dns_batch_tune(self.b, MODES.get(mode, mode), trials)
+
+    def set_persistent(self, enable=True):
+        """Allow or forbid the persistent single-launch step; returns whether
+        the next step uses it."""
+        out = ctypes.c_int32(0)
+        _bcheck(load().at_dns_batch_persistent(self.b, 1 if enable else 0, ctypes.byref(out)), self.b)
+        return bool(out.value)
+
+    @property
+    def persistent(self):
+        """Whether the next step runs as one persistent kernel launch."""
+        out = ctypes.c_int32(0)
+        _bcheck(load().at_dns_batch_persistent(self.b, -1, ctypes.byref(out)), self.b)
+        return bool(out.value)
 
     def close(self):
         if self.b:

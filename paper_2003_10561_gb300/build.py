@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libat_dns.so")
 SOURCES = ["capi.cu", "kernels_p64.cu", "kernels_p32.cu", "kernels_p64_o6.cu", "kernels_p32_o6.cu",
-           "kernels_fused_p64.cu", "kernels_fused_p32.cu", "kernels_fused2_p32.cu",
+           "kernels_fused_p64.cu", "kernels_fused_p32.cu", "kernels_fused2_p32.cu", "kernels_batch_p32.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]

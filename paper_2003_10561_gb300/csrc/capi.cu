@@ -7,9 +7,12 @@
 #include <cstring>
 #include <string>
 #include <algorithm>
+#include <array>
+#include <mutex>
 #include <vector>
 
 #include "../../include/at_dns.h"
+#include "batch.h"
 #include "common.cuh"
 #include "launch.h"
 
@@ -1330,9 +1333,33 @@ struct at_dns_batch {
   cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<std::string> gkey[4];   // member path + dt each graph was captured with
   std::string err;
+  // persistent single-launch step (eligible FP32 batches)
+  bool allow_persistent = false;      // the persistent single-launch step is opt-in
+  int ptx = 0, pty = 0;               // its tile (0: not eligible)
+  int ctas = 0;                       // CTAs resident together (the cooperative grid)
+  atdns::BatchMember* dmem = nullptr; // device member table
+  unsigned* dctr = nullptr;           // [2][count]: ghost items, tiles finished per member
+  unsigned epoch = 0;                 // persistent launches since the counters were cleared
+  int* derr = nullptr;                // a wait gave up
+  std::string pkey;                   // mode + members' dt the table was built with
+  // the members' tile descriptions for constant memory (uploaded when this
+  // batch is not the one whose tables are there)
+  std::vector<atdns::TileDesc> htiles;
+  std::vector<std::array<int, 4>> hshape;
+  std::vector<long long> hgitems, hitems;   // prefix sums of the ghost items and of the tiles
+  unsigned long long table_gen = 0;
 };
 
 namespace {
+
+// Constant memory holds the tile descriptions of one batch at a time: the
+// batch (and table generation) whose tables are there, and an event after
+// the last persistent launch that read them (an upload for another batch
+// waits for it).
+std::mutex g_const_mu;
+const at_dns_batch* g_const_owner = nullptr;
+unsigned long long g_const_gen = 0;
+cudaEvent_t g_const_last = nullptr;
 
 std::string member_key(const at_dns* h) {
   char buf[128];
@@ -1348,6 +1375,142 @@ int batch_fail(at_dns_batch* b, int code, const std::string& msg) {
 void batch_drop(at_dns_batch* b) {
   for (int k = 0; k < 4; ++k)
     if (b->gexec[k]) { cudaGraphExecDestroy(b->gexec[k]); b->gexec[k] = nullptr; }
+}
+
+// z chunk of a paired tile: the z extent itself up to 64 planes, else its
+// largest divisor in [8, 64] (0: none)
+int z_chunk(const at_dns* h) {
+  const int ext = h->g.pes[2] > 1 ? h->g.nl[2] : h->g.n[2];
+  if (ext <= 64) return ext;
+  for (int t = 64; t >= 8; --t)
+    if (ext % t == 0) return t;
+  return 0;
+}
+
+// The paired tile every member can run (16x16 preferred, then 32x8), or
+// false when some member cannot take the persistent step (FP64, 6th order,
+// RK3, forcing, extents that fit no common tile).
+bool batch_persistent_tile(const at_dns_batch* b, int& TX, int& TY) {
+  const int shapes[2][2] = {{16, 16}, {32, 8}};
+  for (auto& sh : shapes) {
+    bool ok = true;
+    for (const at_dns* h : b->m) {
+      int ext[3];
+      for (int d = 0; d < 3; ++d) ext[d] = h->g.pes[d] > 1 ? h->g.nl[d] : h->g.n[d];
+      if (b->m.size() > (size_t)atdns::kBatchConstMembers || h->p64 || h->g.M != 2 ||
+          h->cfg.integrator != AT_DNS_AB2 || h->cfg.forcing || ext[0] % sh[0] || ext[1] % sh[1] || !z_chunk(h)) {
+        ok = false;
+        break;
+      }
+    }
+    if (ok) { TX = sh[0]; TY = sh[1]; return true; }
+  }
+  return false;
+}
+
+// Build (or keep) the device member table of the persistent step for mode.
+int batch_table(at_dns_batch* b, int mode) {
+  const int M = (int)b->m.size();
+  std::string key = std::to_string(mode) + "/" + std::to_string(b->ptx) + "x" + std::to_string(b->pty);
+  for (const at_dns* h : b->m) key += ":" + std::to_string(h->dt);
+  if (b->dmem && key == b->pkey) return AT_DNS_OK;
+  if (!b->dmem) {
+    if (cudaMalloc(&b->dmem, M * sizeof(atdns::BatchMember)) != cudaSuccess ||
+        cudaMalloc(&b->dctr, 2 * M * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->derr, sizeof(int)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return batch_fail(b, AT_DNS_E_OOM, "cannot allocate the persistent step's tables");
+    }
+    if (cudaMemsetAsync(b->derr, 0, sizeof(int), b->st) != cudaSuccess)
+      return batch_fail(b, AT_DNS_E_CUDA, "cannot clear the persistent step's error flag");
+  }
+  // the table and counters are rewritten after every earlier launch that read
+  // them has finished; the counters restart with the table
+  if (cudaStreamSynchronize(b->st) != cudaSuccess ||
+      cudaMemsetAsync(b->dctr, 0, 2 * M * sizeof(unsigned), b->st) != cudaSuccess)
+    return batch_fail(b, AT_DNS_E_CUDA, "cannot clear the persistent step's counters");
+  b->epoch = 0;
+  std::vector<atdns::BatchMember> hm(M);
+  b->htiles.assign(M, atdns::TileDesc{});
+  b->hshape.assign(M, std::array<int, 4>{0, 0, 0, 0});
+  b->hgitems.assign(M + 1, 0);
+  b->hitems.assign(M + 1, 0);
+  for (int i = 0; i < M; ++i) {
+    const at_dns* h = b->m[i];
+    const Geom& g = h->g;
+    atdns::BatchMember& m = hm[i];
+    std::memset(&m, 0, sizeof(m));
+    m.g = g;
+    m.K = make_coef<float>(g, h->ph, h->dt);
+    m.KP = make_coef_pair(m.K);
+    StepArgs<float>& a = m.A;
+    a.Ub[0] = (const float*)h->U[0];
+    a.Ub[1] = (const float*)h->U[1];
+    a.Ulob[0] = h->comp ? (float*)h->Ulo[0] : nullptr;
+    a.Ulob[1] = h->comp ? (float*)h->Ulo[1] : nullptr;
+    a.ds = h->ds;
+    for (int d = 0; d < 3; ++d) a.GH[d] = (const float*)h->GH[d];
+    a.Rprev = (float*)h->Rprev;
+    a.partial = h->partial;
+    a.words = h->words;
+    a.fB = nullptr;
+    a.fX = (const vec2_t<float>*)h->fX;
+    a.dt = h->dt;
+    a.do_update = 1;
+    a.do_stats = h->cfg.stats_every == 1 ? 1 : 0;
+    a.xst = (float*)h->xst;
+    a.xst_half = h->xst_half;
+    const int ZC = z_chunk(h), tiles_x = g.n[0] / b->ptx, tiles_y = g.n[1] / b->pty;
+    m.nblk = (long long)tiles_x * tiles_y * (g.n[2] / ZC);
+    m.mode = mode;
+    m.L = h->cfg.max_delay;
+    m.tl = g.M + 1;
+    m.cr = h->cfg.comm_period;
+    m.k0 = (uint32_t)h->cfg.seed;
+    m.k1 = (uint32_t)(h->cfg.seed >> 32);
+    for (int d = 0; d < 3; ++d) {
+      m.GH[d] = (float*)h->GH[d];
+      m.ring[d] = (double*)h->ring[d];
+      m.ghost_cnt[d] = g.pes[d] > 1 ? 2LL * g.M * g.pes[d] * g.plane[d] : 0;
+    }
+    m.xst = (const float*)h->xst;
+    m.xst_half = h->xst_half;
+    m.sums = h->sums;
+    // ghost items (at least one: it also resets the step's max/min keys)
+    const long long gtot = m.ghost_cnt[0] + m.ghost_cnt[1] + m.ghost_cnt[2];
+    const long long gitems = std::max(1LL, (gtot + atdns::kBatchGhostChunk - 1) / atdns::kBatchGhostChunk);
+    b->htiles[i].g = m.g;
+    b->htiles[i].K = m.K;
+    b->htiles[i].KP = m.KP;
+    b->htiles[i].A = m.A;
+    b->hshape[i] = {ZC, tiles_x, tiles_y, (int)gitems};
+    b->hgitems[i + 1] = b->hgitems[i] + gitems;
+    b->hitems[i + 1] = b->hitems[i] + m.nblk;
+  }
+  if (cudaMemcpy(b->dmem, hm.data(), M * sizeof(atdns::BatchMember), cudaMemcpyHostToDevice) != cudaSuccess)
+    return batch_fail(b, AT_DNS_E_CUDA, "cannot upload the persistent step's tables");
+  b->pkey = key;
+  ++b->table_gen;
+  return AT_DNS_OK;
+}
+
+// Whether the next batch step runs as the persistent single launch (and its tile).
+bool batch_uses_persistent(at_dns_batch* b) {
+  if (!b->allow_persistent) return false;
+  int TX = 0, TY = 0;
+  if (!batch_persistent_tile(b, TX, TY)) return false;
+  if (TX != b->ptx || TY != b->pty || !b->ctas) {
+    int ctas = 0;
+    if (batch_resident_ctas(TX, TY, &ctas) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return false;
+    }
+    b->ptx = TX;
+    b->pty = TY;
+    b->ctas = ctas;
+    b->pkey.clear();
+  }
+  return true;
 }
 
 }  // namespace
@@ -1420,6 +1583,60 @@ int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode) {
     key[i] = member_key(h);
   }
   if (nsteps == 0) return AT_DNS_OK;
+  if (batch_uses_persistent(b)) {
+    int rc;
+    if ((rc = batch_table(b, delay_mode))) return rc;
+    // order after each member's own stream; reset the health words
+    for (int i = 0; i < M; ++i) {
+      k_reset_words<<<1, 1, 0, b->ms[i]>>>(b->m[i]->words, 1);
+      cudaEventRecord(b->ev[i], b->ms[i]);
+      cudaStreamWaitEvent(b->st, b->ev[i], 0);
+    }
+    atdns::BatchSched S;
+    S.m = b->dmem;
+    S.count = M;
+    S.gdone = b->dctr;
+    S.tdone = b->dctr + M;
+    S.err = b->derr;
+    {
+      std::lock_guard<std::mutex> lock(g_const_mu);
+      if (g_const_owner != b || g_const_gen != b->table_gen) {
+        if (!g_const_last && cudaEventCreateWithFlags(&g_const_last, cudaEventDisableTiming) != cudaSuccess)
+          return batch_fail(b, AT_DNS_E_CUDA, "cannot create the constant-table event");
+        if (g_const_owner) cudaStreamWaitEvent(b->st, g_const_last, 0);
+        const cudaError_t e = atdns::upload_batch_tiles(
+            b->htiles.data(), reinterpret_cast<const int(*)[4]>(b->hshape.data()), b->hgitems.data(), b->hitems.data(), M,
+            b->st);
+        if (e != cudaSuccess) {
+          g_const_owner = nullptr;
+          return batch_fail(b, AT_DNS_E_CUDA, std::string("persistent step tables: ") + cudaGetErrorString(e));
+        }
+        g_const_owner = b;
+        g_const_gen = b->table_gen;
+      }
+      for (int s = 0; s < nsteps; ++s) {
+        S.epoch = ++b->epoch;
+        const cudaError_t e = launch_batch_step(b->ptx, b->pty, S, b->ctas, b->st);
+        if (e != cudaSuccess) {
+          cudaEventRecord(g_const_last, b->st);
+          return batch_fail(b, AT_DNS_E_CUDA, std::string("persistent step: ") + cudaGetErrorString(e));
+        }
+        for (int i = 0; i < M; ++i) {
+          at_dns* h = b->m[i];
+          Ops<float>::account(h, true, h->cfg.stats_every == 1);
+        }
+      }
+      cudaEventRecord(g_const_last, b->st);
+    }
+    int gave_up = 0;
+    if (cudaMemcpyAsync(&gave_up, b->derr, sizeof(int), cudaMemcpyDeviceToHost, b->st) != cudaSuccess ||
+        cudaStreamSynchronize(b->st) != cudaSuccess)
+      return batch_fail(b, AT_DNS_E_CUDA, "persistent step failed");
+    if (gave_up) {
+      cudaMemsetAsync(b->derr, 0, sizeof(int), b->st);
+      return batch_fail(b, AT_DNS_E_TIMEOUT, "a wait of the persistent step for a member's ghost items gave up");
+    }
+  } else {
   cudaGraphExec_t& ge = b->gexec[delay_mode];
   if (!ge || b->gkey[delay_mode] != key) {
     if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
@@ -1468,6 +1685,7 @@ int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode) {
       if (h->p64) Ops<double>::account(h, true, stats); else Ops<float>::account(h, true, stats);
     }
   }
+  }
   cudaEventRecord(b->done, b->st);
   std::vector<unsigned long long> w(M, 0);
   for (int i = 0; i < M; ++i) {
@@ -1494,12 +1712,34 @@ int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials) {
   return AT_DNS_OK;
 }
 
+int at_dns_batch_persistent(at_dns_batch_t* b, int32_t enable, int32_t* persistent) {
+  if (!b) return AT_DNS_E_INVALID_ARG;
+  b->err.clear();
+  if (enable >= 0) b->allow_persistent = enable != 0;
+  if (persistent) *persistent = batch_uses_persistent(b) ? 1 : 0;
+  return AT_DNS_OK;
+}
+
+int at_dns_wait_selftest(int32_t log2_polls, int32_t* gave_up) {
+  if (!gave_up || log2_polls < 0 || log2_polls > 26) return AT_DNS_E_INVALID_ARG;
+  int g = -1;
+  if (atdns::batch_wait_selftest(log2_polls, &g) != cudaSuccess) return AT_DNS_E_CUDA;
+  *gave_up = g;
+  return AT_DNS_OK;
+}
+
 const char* at_dns_batch_last_error(const at_dns_batch_t* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
 
 void at_dns_batch_destroy(at_dns_batch_t* b) {
   if (!b) return;
   if (b->st) cudaStreamSynchronize(b->st);
+  {
+    std::lock_guard<std::mutex> lock(g_const_mu);
+    if (g_const_owner == b) g_const_owner = nullptr;   // a later batch at this address uploads its own
+  }
   batch_drop(b);
+  for (void* p : {(void*)b->dmem, (void*)b->dctr, (void*)b->derr})
+    if (p) cudaFree(p);
   for (at_dns* h : b->m) at_dns_destroy(h);
   for (cudaStream_t s : b->ms) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);

@@ -144,6 +144,41 @@ inline Coef<S> make_coef(const Geom& g, const Phys& ph, double dt) {
   return c;
 }
 
+// Stencil coefficients and constants duplicated into both lanes of a pair
+// (converted on the host, read from the parameter space).
+struct CoefPair {
+  float2 c1[3], c2[3];        // D1 = c1 (f[+1] - f[-1]) + c2 (f[+2] - f[-2])
+  float2 nc1[3], nc2[3];      // -c1, -c2 (flux divergence)
+  float2 a1[3], a2[3];        // D2 = a0 f + a1 (f[+1] + f[-1]) + a2 (f[+2] + f[-2])
+  float2 a0[3], a0sum;        // a0 per direction, and their sum (Laplacian)
+  float2 hloc[3];             // scale of the PE-local stencils (1 / (12 dx))
+  float2 gamma, gm1, inv_gamma, cp_over_pr, mu0, mu0omega, dt;
+};
+
+inline CoefPair make_coef_pair(const Coef<float>& K) {
+  CoefPair P;
+  auto d2 = [](float a) { return make_float2(a, a); };
+  for (int d = 0; d < 3; ++d) {
+    P.c1[d] = d2(K.c1[d]);
+    P.c2[d] = d2(K.c2[d]);
+    P.nc1[d] = d2(-K.c1[d]);
+    P.nc2[d] = d2(-K.c2[d]);
+    P.a1[d] = d2(K.a1[d]);
+    P.a2[d] = d2(K.a2[d]);
+    P.a0[d] = d2(K.a0[d]);
+    P.hloc[d] = d2(K.hloc[d]);
+  }
+  P.a0sum = d2(K.a0[0] + K.a0[1] + K.a0[2]);
+  P.gamma = d2(K.gamma);
+  P.gm1 = d2(K.gm1);
+  P.inv_gamma = d2(K.inv_gamma);
+  P.cp_over_pr = d2(K.cp_over_pr);
+  P.mu0 = d2(K.mu0);
+  P.mu0omega = d2(K.mu0omega);
+  P.dt = d2(K.dt);
+  return P;
+}
+
 // Sign/zero test on the bit pattern (no floating-point instruction).
 __device__ __forceinline__ bool nonpositive(double v) { return __double_as_longlong(v) <= 0; }
 __device__ __forceinline__ bool nonpositive(float v) { return __float_as_int(v) <= 0; }
@@ -366,9 +401,11 @@ __device__ __forceinline__ StepDyn<S> resolve_step(const StepArgs<S>& A) {
 
 // Pressure from the conserved variables of one point: (gamma-1)(E - rho|u|^2/2)
 // in the total-energy form, (gamma-1) rho e in the internal-energy form.
+// The multiply-adds are explicit, so every kernel that inlines this gets the
+// same rounding (an implicit contraction may differ between call sites).
 template <typename S>
 __device__ __forceinline__ S pressure(const Coef<S>& K, S m0, S m1, S m2, S u, S v, S w, S E) {
-  return K.eform ? K.gm1 * E : K.gm1 * (E - S(0.5) * (m0 * u + m1 * v + m2 * w));
+  return K.eform ? K.gm1 * E : K.gm1 * fma(S(-0.5), fma(m0, u, fma(m1, v, m2 * w)), E);
 }
 
 // Viscosity and its temperature derivative (Sec. 2): power law mu0 T^omega,

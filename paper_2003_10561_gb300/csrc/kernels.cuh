@@ -45,17 +45,17 @@ __global__ void __launch_bounds__(256) k_prim(Geom g, Coef<S> K, const S* __rest
   PQ[2 * N + idx] = w;
   PQ[3 * N + idx] = T;
   // flux of direction d, components e = 1..4: rho u_i u_d + p delta_id, (E+p) u_d
-  PQ[4 * N + idx] = m0 * u + p;
+  PQ[4 * N + idx] = fma(m0, u, p);
   PQ[5 * N + idx] = m1 * u;
   PQ[6 * N + idx] = m2 * u;
   PQ[7 * N + idx] = H * u;
   PQ[8 * N + idx] = m0 * v;
-  PQ[9 * N + idx] = m1 * v + p;
+  PQ[9 * N + idx] = fma(m1, v, p);
   PQ[10 * N + idx] = m2 * v;
   PQ[11 * N + idx] = H * v;
   PQ[12 * N + idx] = m0 * w;
   PQ[13 * N + idx] = m1 * w;
-  PQ[14 * N + idx] = m2 * w + p;
+  PQ[14 * N + idx] = fma(m2, w, p);
   PQ[15 * N + idx] = H * w;
 }
 
@@ -73,9 +73,9 @@ __device__ __forceinline__ void ghost_quantities(const Coef<S>& K, int d, const 
   const S T = K.gamma * p * inv;
   const S ud = sel3(d, vel[0], vel[1], vel[2]);
   q[0] = sel3(d, Uv[1], Uv[2], Uv[3]);
-  q[1] = Uv[1] * ud + (d == 0 ? p : S(0));
-  q[2] = Uv[2] * ud + (d == 1 ? p : S(0));
-  q[3] = Uv[3] * ud + (d == 2 ? p : S(0));
+  q[1] = fma(Uv[1], ud, d == 0 ? p : S(0));
+  q[2] = fma(Uv[2], ud, d == 1 ? p : S(0));
+  q[3] = fma(Uv[3], ud, d == 2 ? p : S(0));
   q[4] = (K.eform ? Uv[4] : Uv[4] + p) * ud;
   q[5] = vel[0];
   q[6] = vel[1];
@@ -144,16 +144,18 @@ __device__ __forceinline__ void ghost_delta_f32(const Coef<float>& K, int d, con
 // is the local coordinate s - M (left face, face 2d), s >= M is nl + s - M
 // (right face, face 2d+1).  Ring slab index sp = 2M p + t with t < M for
 // local t and t >= M for local nl - 2M + t.
-template <typename S, int M>
-__global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __restrict__ U0,
-                                               const S* __restrict__ U1, const S* __restrict__ Ulo0,
-                                               const S* __restrict__ Ulo1, const DevState* __restrict__ ds,
-                                               const S* __restrict__ PQ, S* GH0, S* GH1, S* GH2,
-                                               double* __restrict__ ring0, double* __restrict__ ring1,
-                                               double* __restrict__ ring2, const S* __restrict__ xst,
-                                               long long xst_half, const uint8_t* __restrict__ dmap,
-                                               long long n, long long cnt0, long long cnt1, long long cnt2) {
-  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+// One ghost point j (counted over the three directions: cnt0, cnt1, cnt2
+// points) of the step at level n; delay(p, face) gives the delay of face
+// `face` of PE p at this step.
+template <typename S, int M, typename Delay>
+__device__ __forceinline__ void ghost_point(const Geom& g, const Coef<S>& K, const S* __restrict__ U0,
+                                            const S* __restrict__ U1, const S* __restrict__ Ulo0,
+                                            const S* __restrict__ Ulo1, const DevState* __restrict__ ds,
+                                            const S* __restrict__ PQ, S* GH0, S* GH1, S* GH2,
+                                            double* __restrict__ ring0, double* __restrict__ ring1,
+                                            double* __restrict__ ring2, const S* __restrict__ xst,
+                                            long long xst_half, Delay delay, long long n, long long cnt0,
+                                            long long cnt1, long long cnt2, long long j) {
   const S* __restrict__ U = (ds && ds->cur) ? U1 : U0;
   const S* __restrict__ Ulo = (ds && ds->cur) ? Ulo1 : Ulo0;   // compensated form: low words (else null)
   if (ds) n = ds->n;
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   c[d] = ped * nl;   // any coordinate inside the receiving PE
   const int p = pe_number(g, c[0], c[1], c[2]);
   const int face = 2 * d + (slot >= M ? 1 : 0);
-  const int k = dmap[p * 6 + face];
+  const int k = delay(p, face);
   const long long qstride = (long long)NS * P * plane;
   S* out = GH + (long long)gi * plane + pl;
   // the source point (in the neighbouring PE) and its slab of the ring
@@ -244,7 +246,6 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   if constexpr (sizeof(S) == 8) {
 #pragma unroll
     for (int q = 0; q < kNumGhostQ; ++q) acc[q] = S(0);
-#pragma unroll
     double lv[M + 1][5];
 #pragma unroll
     for (int l = 0; l <= M; ++l)
@@ -297,6 +298,20 @@ __global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __res
   }
 #pragma unroll
   for (int q = 0; q < kNumGhostQ; ++q) out[q * qstride] = acc[q];
+}
+
+template <typename S, int M>
+__global__ void __launch_bounds__(256) k_ghost(Geom g, Coef<S> K, const S* __restrict__ U0,
+                                               const S* __restrict__ U1, const S* __restrict__ Ulo0,
+                                               const S* __restrict__ Ulo1, const DevState* __restrict__ ds,
+                                               const S* __restrict__ PQ, S* GH0, S* GH1, S* GH2,
+                                               double* __restrict__ ring0, double* __restrict__ ring1,
+                                               double* __restrict__ ring2, const S* __restrict__ xst,
+                                               long long xst_half, const uint8_t* __restrict__ dmap,
+                                               long long n, long long cnt0, long long cnt1, long long cnt2) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  ghost_point<S, M>(g, K, U0, U1, Ulo0, Ulo1, ds, PQ, GH0, GH1, GH2, ring0, ring1, ring2, xst, xst_half,
+                    [&](int p, int face) { return (int)dmap[p * 6 + face]; }, n, cnt0, cnt1, cnt2, j);
 }
 
 // ---------------------------------------------------------------------------
@@ -577,7 +592,7 @@ template <typename S, int NT = 256>
 __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave, long long krho, long long kp,
                                              unsigned health, bool do_stats, double* partial,
                                              unsigned long long* words, double* scratch,
-                                             const S* stc = nullptr) {
+                                             const S* stc = nullptr, long long blk_index = -1) {
   constexpr int kMaxThreads = NT, kMaxWarps = kMaxThreads / 32, kParts = kMaxThreads / 16;
   double (*sh)[kMaxThreads + 1] = reinterpret_cast<double (*)[kMaxThreads + 1]>(scratch);
   float2 (*shp)[kMaxThreads + 1] = reinterpret_cast<float2 (*)[kMaxThreads + 1]>(scratch);   // FP32 pairs
@@ -587,7 +602,8 @@ __device__ __forceinline__ void block_reduce(S (&st)[kNumStat], long long kwave,
   const int nwarps = nthreads >> 5;
   const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
-  const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  const long long blk =
+      blk_index >= 0 ? blk_index : ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   const unsigned hh = __reduce_or_sync(0xffffffffu, health);
   const bool by_warp = sizeof(S) == 4;
   if (do_stats) {

@@ -44,41 +44,6 @@ __device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<con
 __device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<f2*>(p) = v; }
 __device__ __forceinline__ f2 rcp2(f2 a) { return pk(rcp_rn(a.x), rcp_rn(a.y)); }
 
-// Stencil coefficients and constants duplicated into both lanes of a pair
-// (converted on the host, read from the parameter space).
-struct CoefPair {
-  f2 c1[3], c2[3];        // D1 = c1 (f[+1] - f[-1]) + c2 (f[+2] - f[-2])
-  f2 nc1[3], nc2[3];      // -c1, -c2 (flux divergence)
-  f2 a1[3], a2[3];        // D2 = a0 f + a1 (f[+1] + f[-1]) + a2 (f[+2] + f[-2])
-  f2 a0[3], a0sum;        // a0 per direction, and their sum (Laplacian)
-  f2 hloc[3];             // scale of the PE-local stencils (1 / (12 dx))
-  f2 gamma, gm1, inv_gamma, cp_over_pr, mu0, mu0omega, dt;
-};
-
-inline CoefPair make_coef_pair(const Coef<float>& K) {
-  CoefPair P;
-  auto d2 = [](float a) { return make_float2(a, a); };
-  for (int d = 0; d < 3; ++d) {
-    P.c1[d] = d2(K.c1[d]);
-    P.c2[d] = d2(K.c2[d]);
-    P.nc1[d] = d2(-K.c1[d]);
-    P.nc2[d] = d2(-K.c2[d]);
-    P.a1[d] = d2(K.a1[d]);
-    P.a2[d] = d2(K.a2[d]);
-    P.a0[d] = d2(K.a0[d]);
-    P.hloc[d] = d2(K.hloc[d]);
-  }
-  P.a0sum = d2(K.a0[0] + K.a0[1] + K.a0[2]);
-  P.gamma = d2(K.gamma);
-  P.gm1 = d2(K.gm1);
-  P.inv_gamma = d2(K.inv_gamma);
-  P.cp_over_pr = d2(K.cp_over_pr);
-  P.mu0 = d2(K.mu0);
-  P.mu0omega = d2(K.mu0omega);
-  P.dt = d2(K.dt);
-  return P;
-}
-
 template <int TX, int TY>
 struct PairShape {
   static constexpr int TXH = TX / 2;                  // threads per tile row
@@ -246,20 +211,22 @@ __device__ __forceinline__ void pair_xwindow(int kind0, float (&c0)[6], float (&
   }
 }
 
+// One tile of the paired kernel: tile (bx, by) of TX x TY points, z chunk bz
+// of ZC planes; blk is the tile's row in the statistics partials; smem is the
+// dynamic shared memory (fused_smem_bytes<float>(TX, TY) bytes).
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
-    k_fused2(Geom g, Coef<float> K, CoefPair KP, StepArgs<float> A0, int ZC) {
-  const StepArgs<float>& A = A0;
-  const StepDyn<float> D = resolve_step(A0);
+__device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K, const CoefPair& KP,
+                                            const StepArgs<float>& A, int ZC, int bx, int by, int bz, long long blk,
+                                            unsigned char* smem) {
+  const StepDyn<float> D = resolve_step(A);
   using PS = PairShape<TX, TY>;
   using T_ = TileShape<TX, TY>;
   constexpr int CX = PS::CX, CELLS = PS::CELLS;
-  extern __shared__ __align__(16) unsigned char fused_smem[];
-  float* win = reinterpret_cast<float*>(fused_smem);
+  float* win = reinterpret_cast<float*>(smem);
   FusedGeo F;
-  F.x0 = blockIdx.x * TX;
-  F.y0 = blockIdx.y * TY;
-  const int zs = blockIdx.z * ZC;
+  F.x0 = bx * TX;
+  F.y0 = by * TY;
+  const int zs = bz * ZC;
   F.pe[0] = F.x0 / g.nl[0];
   F.pe[1] = F.y0 / g.nl[1];
   F.pe[2] = zs / g.nl[2];
@@ -709,7 +676,15 @@ __global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
     kp = okey(pmin);
   }
   block_reduce<float, (PS::NT > 256 ? 512 : (PS::NT > 128 ? 256 : 128))>(
-      st.s, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words, reinterpret_cast<double*>(fused_smem), st.c);
+      st.s, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words, reinterpret_cast<double*>(smem), st.c, blk);
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
+    k_fused2(Geom g, Coef<float> K, CoefPair KP, StepArgs<float> A0, int ZC) {
+  extern __shared__ __align__(16) unsigned char fused_smem[];
+  const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  fused2_tile<TX, TY>(g, K, KP, A0, ZC, blockIdx.x, blockIdx.y, blockIdx.z, blk, fused_smem);
 }
 
 }  // namespace atdns

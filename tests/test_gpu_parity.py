@@ -600,3 +600,156 @@ def test_device_pool_from_a_tensor(lib):
     with pytest.raises(lib.AtDnsError) as ei:
         make(lib, n, pes, pool=small, **kw)
     assert ei.value.code == lib.AT_DNS_E_OOM
+
+
+def _fp32_ensemble_specs():
+    """Uneven FP32 members whose PE extents are 16 (so each member alone takes
+    the paired 16x16 tile, the persistent step's tile): both FP32 forms,
+    different grids, PE counts, Mach numbers, viscosities and delay seeds."""
+    specs = [
+        dict(n=(32, 32, 32), pes=(2, 2, 2), precision="p32c", mu0=0.02, seed=1),
+        dict(n=(48, 48, 48), pes=(3, 3, 3), precision="p32", mu0=0.015, seed=2),
+        dict(n=(64, 32, 48), pes=(4, 2, 3), precision="p32c", mu0=0.01, seed=3),
+        dict(n=(96, 96, 96), pes=(6, 6, 6), precision="p32c", mu0=0.008, seed=4),
+        dict(n=(16, 16, 32), pes=(1, 1, 2), precision="p32", mu0=0.02, seed=5),
+    ]
+    for sp in specs:
+        sp.update(gamma=GAMMA, prandtl=PR, visc_exp=OMEGA, dt=2e-3, max_delay=2, stats_every=1)
+    states = [synth.initial_state(sp["n"], k0=3.0, mach_t=0.1 + 0.08 * i, seed=70 + i) for i, sp in enumerate(specs)]
+    return specs, states
+
+
+def _agree_below_fp32(a, b):
+    """Largest difference per variable relative to the field's scale."""
+    scale = np.max(np.abs(b.reshape(5, -1)), axis=1)
+    return np.max(np.abs((a - b).reshape(5, -1)), axis=1) / scale
+
+
+# Agreement of the persistent step with the kernels of a member stepped
+# alone (the same operations compiled into another kernel, which may round
+# single operations of the right-hand side differently): the compensated
+# form (P32C: state = high word + low word) within 1e-8 of each field's
+# scale, a sixth of one FP32 ulp (6e-8), i.e. in the low words; the plain
+# FP32 form (P32) within 8 FP32 ulps of the scale (2^-20).
+PERSISTENT_BOUND = {"p32c": 1e-8, "p32": 2.0 ** -20}
+
+
+def test_persistent_batch_matches_members_alone(lib):
+    """The batched ensemble as one persistent kernel launch per step (ghost
+    items and paired-kernel tiles of every member, each tile after its
+    member's ghost items): every member agrees with the same member stepped
+    alone on the paired 16x16 tile, through the start-up and with random
+    delays, within PERSISTENT_BOUND, and its statistics within 1e-7.  The
+    persistent step is deterministic: repeated runs, and identical members
+    within one run, give identical bits."""
+    specs, states = _fp32_ensemble_specs()
+    runs = []
+    for rep in range(2):
+        batch = lib.Batch(specs, persistent=True)
+        assert batch.persistent
+        for m, U0 in zip(batch.members, states):
+            m.set_state(U0)
+        batch.step(7, "random")
+        batch.step(5, "random")
+        runs.append([m.get_state() for m in batch.members])
+        stats = [m.stats() for m in batch.members]
+        assert all(m.info()["step"] == 12 for m in batch.members)
+        batch.close()
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+    for sp, got, st, U0 in zip(specs, runs[0], stats, states):
+        alone = lib.Solver(**sp)
+        assert alone.info()["kernel_path"] == lib.AT_DNS_PATH_PAIRED and alone.info()["tile"][:2] == [16, 16]
+        alone.set_state(U0)
+        alone.step(12, "random")
+        ref = alone.get_state()
+        err = _agree_below_fp32(got, ref)
+        assert np.all(err <= PERSISTENT_BOUND[sp["precision"]]), (sp, err)
+        b = alone.stats()
+        assert st["step"] == b["step"] == 11
+        for k in ("tke", "dissipation", "enstrophy", "mass", "energy"):
+            assert abs(st[k] - b[k]) <= 1e-7 * abs(b[k]), (k, st[k], b[k])
+        alone.close()
+    same = lib.Batch([specs[0]] * 4, persistent=True)
+    for m in same.members:
+        m.set_state(states[0])
+    same.step(6, "random")
+    outs = [m.get_state() for m in same.members]
+    same.close()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_persistent_batches_alternating_share_constant_memory(lib):
+    """Two persistent batches stepped alternately (each step re-uploads the
+    stepping batch's tile descriptions to constant memory, after the other
+    batch's last launch) end bit-identical to each batch stepped on its own;
+    a batch of 65 members (more descriptions than constant memory holds)
+    takes the graph form."""
+    specs, states = _fp32_ensemble_specs()
+    groups = [(specs[:3], states[:3]), (specs[3:], states[3:])]
+
+    def run(alternate):
+        bs = [lib.Batch(sp, persistent=True) for sp, _ in groups]
+        for b, (_, st) in zip(bs, groups):
+            assert b.persistent
+            for m, U0 in zip(b.members, st):
+                m.set_state(U0)
+        if alternate:
+            for _ in range(4):
+                for b in bs:
+                    b.step(2, "random")
+        else:
+            for b in bs:
+                b.step(8, "random")
+        out = [[m.get_state() for m in b.members] for b in bs]
+        for b in bs:
+            b.close()
+        return out
+
+    for ga, gb in zip(run(True), run(False)):
+        for a, b in zip(ga, gb):
+            assert np.array_equal(a, b)
+    many = lib.Batch([dict(specs[4], seed=100 + i) for i in range(65)])
+    assert not many.set_persistent(True)
+    many.close()
+
+
+def test_persistent_wait_gives_up_and_context_survives(lib):
+    """The bounded wait of the persistent step (a tile waiting for its
+    member's ghost items) run on a counter that nothing advances returns
+    unsatisfied after its poll limit (2^20 polls, well under a second), and
+    the context stays usable: a solver steps afterwards."""
+    import time
+    t0 = time.perf_counter()
+    assert lib.at_dns_wait_selftest(20)
+    assert time.perf_counter() - t0 < 30
+    specs, states = _fp32_ensemble_specs()
+    s = lib.Solver(**specs[0])
+    s.set_state(states[0])
+    s.step(2, "random")
+    assert np.all(np.isfinite(s.get_state()))
+    s.close()
+
+
+def test_persistent_and_graph_batch_steps_agree(lib):
+    """The same ensemble stepped with the persistent launch and with the graph
+    of per-member branches agrees within PERSISTENT_BOUND (each member takes
+    the same paired tile either way); a batch with an FP64 member cannot take
+    the persistent step."""
+    specs, states = _fp32_ensemble_specs()
+    out = []
+    for persistent in (True, False):
+        batch = lib.Batch(specs)
+        assert batch.set_persistent(persistent) == persistent
+        for m, U0 in zip(batch.members, states):
+            m.set_state(U0)
+        batch.step(10, "periodic")
+        out.append([m.get_state() for m in batch.members])
+        batch.close()
+    for sp, a, b in zip(specs, *out):
+        err = _agree_below_fp32(a, b)
+        assert np.all(err <= PERSISTENT_BOUND[sp["precision"]]), (sp, err)
+    mixed = lib.Batch(specs[:2] + [dict(specs[0], precision="p64")])
+    assert not mixed.set_persistent(True)
+    mixed.close()
