@@ -44,19 +44,15 @@ FLOP_MAIN = 390.0
 # the 6th-order scheme adds one stencil pair to every first derivative
 # (15 flux + 6 mixed: +3 flops each) and second derivative (12: +3 each)
 FLOP_MAIN6 = 489.0
-# algorithmic HBM bytes per grid point of one step (read U, R^{n-1}; write U^{n+1},
-# R^n -- and the low words of U in the compensated FP32 form; plus the FP64
-# slab ring: 1 write + T_l reads of 5 variables at the N_B fraction)
 NB_FRAC = 1.0 - (28.0 / 32.0) ** 3
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max SM clock
 # DRAM bytes (read + write) of one launch of the dominant kernel, from ncu at
-# 128^3 with 4x4x4 PEs of 32^3, scaled by the point count to the
-# 256^3 workload (same PE size; traffic grows with the points):
-# k_main<double, 2> 700.8 MB + 443.7 MB.  k_fused<float, 32, 8> measured
-# 112.5 MB + 50.0 MB before its ring-slot index moved out of the plane loop;
-# the kernel has changed since, so its traffic is reported as unmeasured.
+# 128^3 with 4x4x4 PEs of 32^3, scaled by the point count to the 256^3
+# workload (same PE size; traffic grows with the points):
+# k_main<double, 2> 700.8 MB + 443.7 MB.  k_fused2<32, 8> (P32C): None until
+# a capture of the current kernel is recorded (then read + write here).
 K_MAIN_FP64_TRAFFIC_256 = 8 * (700.768256e6 + 443.693824e6)
-K_FUSED_FP32_TRAFFIC_256 = None
+K_FUSED2_P32C_TRAFFIC_256 = None
 
 
 def set_workload(n, pes):
@@ -82,13 +78,35 @@ def nb_frac(order):
 STATE_WORDS = {"p64": (8, 4), "p32": (4, 4), "p32c": (4, 6)}   # (bytes, words moved per variable)
 
 
-def algorithmic_bytes(prec, order=4):
-    """Read U, R^{n-1}; write U^{n+1}, R^n (P32C also reads and writes the low
-    words of U); the FP64 slab ring: 1 write + T_l reads of 5 variables at the
-    N_B fraction (T_l = 3 at 4th order, 4 at 6th order)."""
+def ghost_ratio(order):
+    """AT ghost points per grid point: 2M ghost planes per PE face pair in
+    each of the three directions (M = order / 2), 2M / n_l per direction."""
+    return 0.0 if PES == 1 else 3.0 * order / (N // PES)
+
+
+def xface_ratio(order):
+    """Points of the x-face slabs (the first and last M points of a PE along
+    x) per grid point."""
+    return 0.0 if PES == 1 else order / float(N // PES)
+
+
+def algorithmic_bytes(prec, order=4, path="paired"):
+    """HBM bytes per grid point that the step's main kernel must move.
+
+    One-pass FP32 kernels (fused, paired): read U, R^{n-1} and write U^{n+1},
+    R^n (P32C also reads and writes the low words of U); read the 9 ghost
+    quantities (5 fluxes, u, v, w, T) of every AT ghost point; write the
+    x-face slabs of U^{n+1} (with their low words in P32C) that the next
+    step's ghost kernel reads.
+    The FP64 multi-pass k_main: read the 16 primitive/flux arrays PQ, the 12
+    gradients G, U and R^{n-1}, the ghost quantities; write U^{n+1} and R^n.
+    The FP64 slab ring (one write and T_l reads of 5 variables at the N_B
+    fraction) is the ghost kernel's traffic, not the main kernel's."""
     elem, words = STATE_WORDS[prec]
-    reads = 3 if order == 4 else 4
-    return words * 5 * elem + nb_frac(order) * 5 * 8 * (1 + reads)
+    ghosts = ghost_ratio(order) * 9 * elem
+    if prec == "p64" or path == "multipass":
+        return (16 + 12) * elem + words * 5 * elem + ghosts
+    return words * 5 * elem + ghosts + xface_ratio(order) * 5 * elem * (2 if prec == "p32c" else 1)
 
 
 class Clocks:
@@ -527,18 +545,21 @@ def leg_report(r, world, pts, steps, pk):
                 "traffic": traffic, "flop_per_point": flops,
                 "note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
                         "(an FMA probe measured 1.20 TFLOP/s)"}
-        # the same kernel against the HBM roof, at the step's algorithmic bytes
-        gbs = algorithmic_bytes("p64", order) * pts / t_main / 1e9
+        # the same kernel against the HBM roof, at its algorithmic bytes
+        bpp = algorithmic_bytes("p64", order, r["path"])
+        gbs = bpp * pts / t_main / 1e9
         roof["hbm"] = {"achieved": gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                       "frac": gbs / pk.get("hbm_gbs", 6800.0), "bytes_per_point": algorithmic_bytes("p64", order)}
+                       "frac": gbs / pk.get("hbm_gbs", 6800.0), "bytes_per_point": bpp}
     else:
-        achieved = algorithmic_bytes(r["prec"], order) * pts / t_main / 1e9
+        bpp = algorithmic_bytes(r["prec"], order, r["path"])
+        achieved = bpp * pts / t_main / 1e9
         kname = {"fused": "k_fused", "paired": "k_fused2"}.get(r["path"], "k_main")
-        traffic = K_FUSED_FP32_TRAFFIC_256 if (order == 4 and N == 256 and PES == 8 and r["path"] == "fused"
-                                               and list(r["tile"]) == [32, 8, 32] and K_FUSED_FP32_TRAFFIC_256) else None
+        traffic = K_FUSED2_P32C_TRAFFIC_256 if (order == 4 and N == 256 and PES == 8 and r["path"] == "paired"
+                                                and r["prec"] == "p32c" and list(r["tile"]) == [32, 8, 32]
+                                                and K_FUSED2_P32C_TRAFFIC_256) else None
         roof = {"bound": "hbm", "kernel": "%s (FP32, order %d)" % (kname, order), "achieved": achieved,
                 "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0),
-                "traffic": traffic, "bytes_per_point": algorithmic_bytes(r["prec"], order)}
+                "traffic": traffic, "bytes_per_point": bpp}
     return {"value": job_rate(world, pts, steps, r["ms"]), "unit": UNIT, "kernel_path": r["path"], "tile": r["tile"],
             "ms_per_step": r["ms"] / steps, "dtype": r["dtype"], "roofline": roof,
             "kernel_ms_per_step": {k: v[1] / v[0] for k, v in r["kt"].items()}}
