@@ -46,13 +46,13 @@ FLOP_MAIN = 390.0
 FLOP_MAIN6 = 489.0
 NB_FRAC = 1.0 - (28.0 / 32.0) ** 3
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max SM clock
-# DRAM bytes (read + write) of one launch of the dominant kernel, from ncu at
-# 128^3 with 4x4x4 PEs of 32^3, scaled by the point count to the 256^3
-# workload (same PE size; traffic grows with the points):
-# k_main<double, 2> 700.8 MB + 443.7 MB.  k_fused2<32, 8> (P32C): None until
-# a capture of the current kernel is recorded (then read + write here).
-K_MAIN_FP64_TRAFFIC_256 = 8 * (700.768256e6 + 443.693824e6)
-K_FUSED2_P32C_TRAFFIC_256 = None
+# DRAM bytes (read + write) of one launch of the dominant kernel at the
+# 256^3 workload with 8x8x8 PEs of 32^3, from a one-pass ncu capture of that
+# launch (dram__bytes_read.sum + dram__bytes_write.sum):
+# k_fused2<32, 8> (P32C): 1.25 GB + 1.04 GB; k_main<double, 2> (multi-pass
+# FP64): 7.79 GB + 3.84 GB.
+K_MAIN_FP64_TRAFFIC_256 = 7.79e9 + 3.84e9
+K_FUSED2_P32C_TRAFFIC_256 = 1.25e9 + 1.04e9
 
 
 def set_workload(n, pes):
