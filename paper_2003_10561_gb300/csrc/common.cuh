@@ -422,19 +422,23 @@ __device__ __forceinline__ S ipow(S x, int e) {
   return r;
 }
 
+// FP32 forms, power law: g = T^(omega - 1) by the hardware base-2 logarithm
+// and exponential (a few ulp for the temperatures of a flow); mu = mu0 T g,
+// dmu/dT = mu0 omega g
+__device__ __forceinline__ void viscosity_power32(const Coef<float>& K, float T, float& mu, float& dmudT) {
+  const float gg = __powf(T, K.vexpm1);
+  mu = K.mu0 * T * gg;
+  dmudT = K.mu0omega * gg;
+}
+
 template <typename S>
 __device__ __forceinline__ void viscosity(const Coef<S>& K, S T, S& mu, S& dmudT) {
   if (K.vlaw) {
     const S inv = S(1) / (T + K.suth_s);
     mu = K.suth_c * T * sqrt(T) * inv;
     dmudT = mu * (S(1.5) / T - inv);
-  } else if (sizeof(S) == 4) {
-    // FP32 forms: g = T^(omega - 1) by the hardware base-2 logarithm and
-    // exponential (a few ulp for the temperatures of a flow); mu = mu0 T g,
-    // dmu/dT = mu0 omega g
-    const S gg = (S)__powf((float)T, K.vexpm1);
-    mu = K.mu0 * T * gg;
-    dmudT = K.mu0omega * gg;
+  } else if constexpr (sizeof(S) == 4) {
+    viscosity_power32(K, T, mu, dmudT);
   } else if (K.vrat && T > S(1e-3) && T < S(1e3)) {
     // omega = p/q: g = T^(omega - 1) from an FP32 start g0, corrected as
     // g = g0 r^(-1/q) with r = g0^q T^(q - p) = 1 + d, taking two terms of the

@@ -119,9 +119,10 @@ __device__ __forceinline__ void fetch_plane2(const Geom& g, const StepArgs<float
   }
 }
 
-template <int TX, int TY>
+template <int TX, int TY, bool PLAIN>
 __device__ __forceinline__ void store_plane2(const Coef<float>& K, const CoefPair& KP, const PlaneRaw2<TX, TY>& P,
                                              float* win, int bA, int bT, int bR) {
+  const bool eform = !PLAIN && K.eform;
   using PS = PairShape<TX, TY>;
   const int tid = threadIdx.x;
 #pragma unroll
@@ -138,9 +139,9 @@ __device__ __forceinline__ void store_plane2(const Coef<float>& K, const CoefPai
       v = m1 * inv;
       w = m2 * inv;
       // (gamma-1)(E - (m.u)/2), or (gamma-1) rho e
-      const f2 p_ = K.eform ? KP.gm1 * E : KP.gm1 * fma2(bc(-0.5f), fma2(m0, u, fma2(m1, v, m2 * w)), E);
+      const f2 p_ = eform ? KP.gm1 * E : KP.gm1 * fma2(bc(-0.5f), fma2(m0, u, fma2(m1, v, m2 * w)), E);
       T = KP.gamma * p_ * inv;
-      H = K.eform ? E : E + p_;
+      H = eform ? E : E + p_;
     } else if (P.kind[it] == 2) {
       u = P.v[it][0];
       v = P.v[it][1];
@@ -213,12 +214,18 @@ __device__ __forceinline__ void pair_xwindow(int kind0, float (&c0)[6], float (&
 
 // One tile of the paired kernel: tile (bx, by) of TX x TY points, z chunk bz
 // of ZC planes; blk is the tile's row in the statistics partials; smem is the
-// dynamic shared memory (fused_smem_bytes<float>(TX, TY) bytes).
-template <int TX, int TY>
+// dynamic shared memory (fused_smem_bytes<float>(TX, TY) bytes).  PLAIN
+// compiles the step of the common configuration only -- an AB2 step that
+// updates the state (no RK3 stage, no right-hand-side output), unforced, in
+// the total-energy form with the power-law viscosity -- and leaves the code
+// of the other configurations out of the kernel; the arithmetic of that
+// configuration is the same in both instantiations.
+template <int TX, int TY, bool PLAIN = false>
 __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K, const CoefPair& KP,
                                             const StepArgs<float>& A, int ZC, int bx, int by, int bz, long long blk,
                                             unsigned char* smem) {
   const StepDyn<float> D = resolve_step(A);
+  const bool eform = !PLAIN && K.eform, update = PLAIN || A.do_update, rk = !PLAIN && A.rk;
   using PS = PairShape<TX, TY>;
   using T_ = TileShape<TX, TY>;
   constexpr int CX = PS::CX, CELLS = PS::CELLS;
@@ -284,21 +291,21 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
   for (int q = 0; q < 8; ++q) {
     PlaneRaw2<TX, TY> P;
     fetch_plane2<TX, TY>(g, A, D.U, F, zs - 4 + q, P);
-    store_plane2<TX, TY>(K, KP, P, win, slot_A<TX, TY>(q), slot_T<TX, TY>(q), slot_R<TX, TY>(q));
+    store_plane2<TX, TY, PLAIN>(K, KP, P, win, slot_A<TX, TY>(q), slot_T<TX, TY>(q), slot_R<TX, TY>(q));
   }
   PlaneRaw2<TX, TY> pf;                                       // plane z + 4, fetched one iteration ahead
   fetch_plane2<TX, TY>(g, A, D.U, F, zs + 4, pf);
 
   for (int z = zs; z < zs + ZC; ++z) {
     const int q = z - zs + 4;
-    store_plane2<TX, TY>(K, KP, pf, win, slot_A<TX, TY>(q + 4), slot_T<TX, TY>(q + 4), slot_R<TX, TY>(q + 4));
+    store_plane2<TX, TY, PLAIN>(K, KP, pf, win, slot_A<TX, TY>(q + 4), slot_T<TX, TY>(q + 4), slot_R<TX, TY>(q + 4));
     __syncthreads();
     if (z + 1 < zs + ZC) fetch_plane2<TX, TY>(g, A, D.U, F, z + 5, pf);
     const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
     const f2 m[3] = {ld2(D.U + N + idx), ld2(D.U + 2 * N + idx), ld2(D.U + 3 * N + idx)};
     const f2 Ecur = ld2(D.U + 4 * N + idx);
     f2 Rp[5], Lp[5];
-    const bool ldrp = needs_rprev(A, D), ldlo = A.do_update && D.Ulo;
+    const bool ldrp = needs_rprev(A, D), ldlo = update && D.Ulo;
 #pragma unroll
     for (int v = 0; v < 5; ++v) Rp[v] = ldrp ? ld2(A.Rprev + v * N + idx) : bc(0.f);
     // the compensated form's low words of U^n, loaded with R^{n-1}
@@ -520,14 +527,19 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
     const f2 r = ld2(win + pR);
     const f2 vel[3] = {ld2(win + pA[4]), ld2(win + pA[4] + CELLS), ld2(win + pA[4] + 2 * CELLS)};
     const f2 T = ld2(win + pT[2]);
-    const f2 p = K.eform ? KP.gm1 * Ecur
+    const f2 p = eform ? KP.gm1 * Ecur
                          : KP.gm1 * fma2(bc(-0.5f), fma2(m[0], vel[0], fma2(m[1], vel[1], m[2] * vel[2])), Ecur);
     const f2 theta = Ag[0][0] + Ag[1][1] + Ag[2][2];
     f2 mu, dmudT;
     {
       float mu0_, mu1_, d0_, d1_;
-      viscosity(K, T.x, mu0_, d0_);
-      viscosity(K, T.y, mu1_, d1_);
+      if constexpr (PLAIN) {
+        viscosity_power32(K, T.x, mu0_, d0_);
+        viscosity_power32(K, T.y, mu1_, d1_);
+      } else {
+        viscosity(K, T.x, mu0_, d0_);
+        viscosity(K, T.y, mu1_, d1_);
+      }
       mu = pk(mu0_, mu1_);
       dmudT = pk(d0_, d1_);
     }
@@ -543,7 +555,7 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
       for (int j = 0; j < 3; ++j) sm[i][j] = i == j ? fma2(bc(2.f), Ag[i][i], bc(0.f) - th23) : Ag[i][j] + Ag[j][i];
 
     f2 fo[3] = {bc(0.f), bc(0.f), bc(0.f)};
-    if (A.fB) {
+    if (!PLAIN && A.fB) {
       const long long lines = (long long)g.n[2] * g.n[1];
       const long long ln = (long long)z * g.n[1] + y;
 #pragma unroll
@@ -576,7 +588,7 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
       work = fma2(vel[i], V, work);
     }
     const f2 heat = fma2(KP.cp_over_pr, fma2(dmu[0], dT[0], fma2(dmu[1], dT[1], dmu[2] * dT[2])), kappa * lap[3]);
-    if (K.eform) R[4] = R[4] + fma2(bc(0.f) - p, theta, sigS + heat);
+    if (eform) R[4] = R[4] + fma2(bc(0.f) - p, theta, sigS + heat);
     else R[4] = R[4] + fma2(r, fma2(fo[0], vel[0], fma2(fo[1], vel[1], fo[2] * vel[2])), sigS + work + heat);
 
     if (nonpositive(r.x) || nonpositive(r.y)) health |= H_RHO;
@@ -585,14 +597,14 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
     for (int v = 0; v < 5; ++v)
       if (nonfinite(R[v].x) || nonfinite(R[v].y)) health |= H_NONFINITE;
 
-    if (A.do_update) {
+    if (update) {
       const f2 Uo[5] = {r, m[0], m[1], m[2], Ecur};
       f2 un[5], unlo[5];
-      const f2 scale = A.rk ? bc(1.f) : KP.dt;
+      const f2 scale = rk ? bc(1.f) : KP.dt;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         f2 inc, kept;
-        if (A.rk) {
+        if (rk) {
           kept = fma2(bc(A.rkA), Rp[v], KP.dt * R[v]);   // stage register dU
           inc = bc(A.rkB) * kept;
         } else {
@@ -634,7 +646,7 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
           }
         }
       }
-    } else if (A.Rout) {
+    } else if (!PLAIN && A.Rout) {
 #pragma unroll
       for (int v = 0; v < 5; ++v)
         *reinterpret_cast<double2*>(A.Rout + v * N + idx) = make_double2(f2d_bits(R[v].x), f2d_bits(R[v].y));
@@ -679,12 +691,12 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
       st.s, kwave, krho, kp, health, A.do_stats != 0, A.partial, A.words, reinterpret_cast<double*>(smem), st.c, blk);
 }
 
-template <int TX, int TY>
+template <int TX, int TY, bool PLAIN>
 __global__ void __launch_bounds__(TX * TY / 2, (TX * TY / 2 <= 128) ? 2 : 1)
     k_fused2(Geom g, Coef<float> K, CoefPair KP, StepArgs<float> A0, int ZC) {
   extern __shared__ __align__(16) unsigned char fused_smem[];
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  fused2_tile<TX, TY>(g, K, KP, A0, ZC, blockIdx.x, blockIdx.y, blockIdx.z, blk, fused_smem);
+  fused2_tile<TX, TY, PLAIN>(g, K, KP, A0, ZC, blockIdx.x, blockIdx.y, blockIdx.z, blk, fused_smem);
 }
 
 }  // namespace atdns
