@@ -49,11 +49,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max S
 # DRAM bytes (read + write) of one launch of the dominant kernel at the
 # 256^3 workload with 8x8x8 PEs of 32^3, from a one-pass ncu capture of that
 # launch (dram__bytes_read.sum + dram__bytes_write.sum):
-# k_main<double, 2> (multi-pass FP64): 7.79 GB + 3.84 GB.  k_fused2<32, 8>
-# (P32C): None until its plain-configuration instantiation is captured (the
-# general one moved 1.25 GB + 1.04 GB).
+# k_main<double, 2> (multi-pass FP64): 7.79 GB + 3.84 GB; k_fused2<32, 8, plain>
+# (P32C): 1.25 GB + 1.04 GB.
 K_MAIN_FP64_TRAFFIC_256 = 7.79e9 + 3.84e9
-K_FUSED2_P32C_TRAFFIC_256 = None
+K_FUSED2_P32C_TRAFFIC_256 = 1.25e9 + 1.04e9
 
 
 def set_workload(n, pes):

@@ -143,22 +143,49 @@ __global__ void k_join_double(const float* __restrict__ hi, const float* __restr
 // Write the PE-boundary slabs of the FP64 field U ([5][npts]) into ring slot
 // `slot` (the ring is FP64 in every precision form): the M layers next to each
 // face, slab index 2M pe + t (t < M: local t, t >= M: local nl - 2M + t).
-__global__ void k_ring_store(Geom g, const double* __restrict__ U, double* r0, double* r1, double* r2, int slot) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= g.npts) return;
-  int c[3];
-  decode(g, idx, c[0], c[1], c[2]);
-  double* rings[3] = {r0, r1, r2};
-  const int M = g.M;
-  for (int d = 0; d < 3; ++d) {
-    if (g.pes[d] == 1) continue;
-    const int pe = c[d] / g.nl[d], li = c[d] - pe * g.nl[d], nl = g.nl[d];
-    if (li >= M && li < nl - M) continue;
-    const int t = li < M ? li : li - nl + 2 * M;
-    const long long sp = 2LL * M * pe + t, PS = 2LL * M * g.pes[d];
-    const long long pl = plane_index(g, d, c[0], c[1], c[2]);
-    for (int v = 0; v < 5; ++v)
-      rings[d][(((long long)slot * 5 + v) * PS + sp) * g.plane[d] + pl] = U[v * g.npts + idx];
+// The PE-boundary slabs of an FP64 field into the ring slots first_slot,
+// first_slot + 1, ... (count slots, mod the ring length), one read of the
+// field for all of them.  One thread per slab point in the ring's own order
+// (direction d's cnt_d points: slab sp = 2M pe + t, plane point pl), so the
+// ring writes are coalesced, and so are the field reads of the y- and z-faces.
+__global__ void k_ring_store(Geom g, const double* __restrict__ U, double* r0, double* r1, double* r2, long long cnt0,
+                             long long cnt1, long long cnt2, int first_slot, int count) {
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int d = 0;
+  if (j >= cnt0) {
+    j -= cnt0;
+    d = 1;
+    if (j >= cnt1) {
+      j -= cnt1;
+      d = 2;
+      if (j >= cnt2) return;
+    }
+  }
+  const long long plane = g.plane[d];
+  const long long sp = j / plane, pl = j - sp * plane;
+  const int M = g.M, pe = (int)(sp / (2 * M)), t = (int)(sp - 2LL * M * pe);
+  const int cd = pe * g.nl[d] + (t < M ? t : g.nl[d] - 2 * M + t);
+  int x, y, z;
+  if (d == 0) {
+    x = cd;
+    z = (int)(pl / g.n[1]);
+    y = (int)(pl - (long long)z * g.n[1]);
+  } else if (d == 1) {
+    y = cd;
+    z = (int)(pl / g.n[0]);
+    x = (int)(pl - (long long)z * g.n[0]);
+  } else {
+    z = cd;
+    y = (int)(pl / g.n[0]);
+    x = (int)(pl - (long long)y * g.n[0]);
+  }
+  const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
+  double* ring = d == 0 ? r0 : (d == 1 ? r1 : r2);
+  const long long PS = 2LL * M * g.pes[d];
+  for (int v = 0; v < 5; ++v) {
+    const double val = U[v * g.npts + idx];
+    for (int s = 0, slot = first_slot; s < count; ++s, slot = slot + 1 == g.nlev ? 0 : slot + 1)
+      ring[(((long long)slot * 5 + v) * PS + sp) * plane + pl] = val;
   }
 }
 
@@ -405,11 +432,13 @@ __global__ void k_xstage_fill(Geom g, const S* __restrict__ U, const S* __restri
 }
 
 // The PE-boundary slabs of an FP64 level on the device into ring slot `slot`.
-int ring_store(at_dns* h, const double* field, int slot) {
-  const bool any = h->g.pes[0] > 1 || h->g.pes[1] > 1 || h->g.pes[2] > 1;
-  if (!any) return AT_DNS_OK;
-  k_ring_store<<<nblk(h->g.npts), kBlock, 0, h->st>>>(h->g, field, (double*)h->ring[0], (double*)h->ring[1],
-                                                      (double*)h->ring[2], slot);
+int ring_store(at_dns* h, const double* field, int first_slot, int count) {
+  long long cnt[3];
+  for (int d = 0; d < 3; ++d) cnt[d] = h->g.pes[d] > 1 ? 2LL * h->g.M * h->g.pes[d] * h->g.plane[d] : 0;
+  const long long total = cnt[0] + cnt[1] + cnt[2];
+  if (!total) return AT_DNS_OK;
+  k_ring_store<<<nblk(total), kBlock, 0, h->st>>>(h->g, field, (double*)h->ring[0], (double*)h->ring[1],
+                                                  (double*)h->ring[2], cnt[0], cnt[1], cnt[2], first_slot, count);
   CK(cudaGetLastError());
   return AT_DNS_OK;
 }
@@ -425,6 +454,12 @@ struct Ops {
   static int upload_field(at_dns* h, const double* src, int where, S* dst, const double** dev_src) {
     const long long cnt = 5 * h->g.npts;
     const double* dsrc = src;
+    if (where == AT_DNS_HOST && sizeof(S) == sizeof(double)) {
+      // FP64: straight into the state (no staging buffer, no device copy)
+      CK(cudaMemcpyAsync(dst, src, cnt * sizeof(double), cudaMemcpyHostToDevice, h->st));
+      *dev_src = (const double*)dst;
+      return AT_DNS_OK;
+    }
     if (where == AT_DNS_HOST) {
       int rc;
       if ((rc = get_stage(h))) return rc;
@@ -448,6 +483,12 @@ struct Ops {
 
   static int download(at_dns* h, double* out, int where) {
     const long long cnt = 5 * h->g.npts;
+    if (where == AT_DNS_HOST && sizeof(S) == sizeof(double)) {
+      // FP64: straight from the state (no staging buffer, no device copy)
+      CK(cudaMemcpyAsync(out, U(h, h->cur), cnt * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      return AT_DNS_OK;
+    }
     if (where == AT_DNS_HOST) {
       int rc;
       if ((rc = get_stage(h))) return rc;
@@ -990,7 +1031,9 @@ int at_dns_set_history(at_dns_t* h, const double* levels, int32_t nlevels, int64
   int rc;
   // older levels first so that U[cur] ends up holding U^step; each given level
   // is uploaded once and stored into its ring slot (the oldest one also into
-  // the slots of the older levels that were not given)
+  // the slots of the older levels that were not given: levels last .. l sit
+  // in consecutive slots from that of level `last`)
+  const double* dev_level0 = nullptr;   // U^step in FP64 on the device
   for (int l = nlevels - 1; l >= 0; --l) {
     const double* lv = levels + (size_t)l * cnt;
     const int last = l == nlevels - 1 ? h->g.nlev - 1 : l;
@@ -1000,20 +1043,17 @@ int at_dns_set_history(at_dns_t* h, const double* levels, int32_t nlevels, int64
     } else {
       if ((rc = Ops<float>::upload_field(h, lv, where, Ops<float>::U(h, h->cur), &dev_lv))) return rc;
     }
-    for (int ll = l; ll <= last; ++ll) {
-      const int slot = (int)(((step - ll) % h->g.nlev + h->g.nlev) % h->g.nlev);
-      if ((rc = ring_store(h, dev_lv, slot))) return rc;
-    }
+    const int first_slot = (int)(((step - last) % h->g.nlev + h->g.nlev) % h->g.nlev);
+    if ((rc = ring_store(h, dev_lv, first_slot, last - l + 1))) return rc;
+    if (l == 0) dev_level0 = dev_lv;
   }
   // the x-face slabs of U^step for the first ghost kernel (FP32 forms)
   rc = h->p64 ? AT_DNS_OK : Ops<float>::xstage_fill(h);
   if (rc) return rc;
-  // stage holds U^step in FP64 now (host path) -- ensure it for the dt reduction
   // U^step in FP64 on the device for the CFL reduction: the caller's level 0,
-  // or the staging buffer the host path just filled with it
-  const double* u0 = where == AT_DNS_DEVICE ? levels : h->stage;
+  // the state (FP64 form) or the staging buffer the host path filled with it
   if (!(h->has_state && h->dt > 0) || step == 0) {
-    if ((rc = set_dt(h, u0))) return rc;
+    if ((rc = set_dt(h, dev_level0))) return rc;
   }
   h->n = step;
   h->t = step * h->dt;
