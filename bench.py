@@ -7,8 +7,8 @@ points (N_B = 33 %), 4th-order AT stencils with random delays uniform on
 statistics reduced every step.  Input: the seeded solenoidal field
 E(k) ~ k^4 exp(-2 (k/4)^2), M_t = 0.3 (synthetic; the paper's forced
 stationary fields are not available).  A step is one full pass of the hot path
-(delay map, AT ghost assembly, derivative sweeps, assembly, AB2 update, ring
-write, reductions).  The working set (~8 GB) is far larger than L2, so no L2
+(delay map, AT ghost assembly with the write of the current level's ring
+slabs, derivative sweeps, assembly, AB2 update, reductions).  The working set (~8 GB) is far larger than L2, so no L2
 flush is needed between steps.
 
 Arms:
@@ -50,9 +50,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max S
 # 256^3 workload with 8x8x8 PEs of 32^3, from a one-pass ncu capture of that
 # launch (dram__bytes_read.sum + dram__bytes_write.sum):
 # k_main<double, 2> (multi-pass FP64): 7.79 GB + 3.84 GB; k_fused2<32, 8, plain>
-# (P32C): 1.25 GB + 1.04 GB.
+# (P32C): 1.25 GB + 1.04 GB; 6th order (multi-pass): k_main<double, 3>
+# 10.90 GB + 4.05 GB, k_main<float, 3> (P32C) 3.46 GB + 1.15 GB.
 K_MAIN_FP64_TRAFFIC_256 = 7.79e9 + 3.84e9
 K_FUSED2_P32C_TRAFFIC_256 = 1.25e9 + 1.04e9
+K_MAIN_FP64_O6_TRAFFIC_256 = 10.90e9 + 4.05e9
+K_MAIN_P32C_O6_TRAFFIC_256 = 3.46e9 + 1.15e9
 
 
 def set_workload(n, pes):
@@ -538,8 +541,9 @@ def leg_report(r, world, pts, steps, pk):
     if r["dtype"] == "f64":
         flops = FLOP_MAIN if order == 4 else FLOP_MAIN6
         achieved = flops * pts / t_main / 1e12
-        traffic = K_MAIN_FP64_TRAFFIC_256 if (order == 4 and N == 256 and PES == 8 and r["path"] == "multipass"
-                                              and K_MAIN_FP64_TRAFFIC_256) else None
+        traffic = None
+        if N == 256 and PES == 8 and r["path"] == "multipass":
+            traffic = K_MAIN_FP64_TRAFFIC_256 if order == 4 else K_MAIN_FP64_O6_TRAFFIC_256
         roof = {"bound": "alu", "kernel": "k_main (FP64, order %d)" % order, "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": traffic, "flop_per_point": flops,
@@ -554,9 +558,12 @@ def leg_report(r, world, pts, steps, pk):
         bpp = algorithmic_bytes(r["prec"], order, r["path"])
         achieved = bpp * pts / t_main / 1e9
         kname = {"fused": "k_fused", "paired": "k_fused2"}.get(r["path"], "k_main")
-        traffic = K_FUSED2_P32C_TRAFFIC_256 if (order == 4 and N == 256 and PES == 8 and r["path"] == "paired"
-                                                and r["prec"] == "p32c" and list(r["tile"]) == [32, 8, 32]
-                                                and K_FUSED2_P32C_TRAFFIC_256) else None
+        traffic = None
+        if N == 256 and PES == 8 and r["prec"] == "p32c":
+            if order == 4 and r["path"] == "paired" and list(r["tile"]) == [32, 8, 32]:
+                traffic = K_FUSED2_P32C_TRAFFIC_256
+            elif order == 6 and r["path"] == "multipass":
+                traffic = K_MAIN_P32C_O6_TRAFFIC_256
         roof = {"bound": "hbm", "kernel": "%s (FP32, order %d)" % (kname, order), "achieved": achieved,
                 "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0),
                 "traffic": traffic, "bytes_per_point": bpp}
