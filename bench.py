@@ -93,6 +93,16 @@ def xface_ratio(order):
     return 0.0 if PES == 1 else order / float(N // PES)
 
 
+def step_bytes(prec, order=4):
+    """Algorithmic HBM bytes per grid point of one AB2 step (the workload's
+    per-point figure): read U and R^{n-1}, write U^{n+1} and R^n (4 x 5 values;
+    6 x 5 with the low words of the compensated form), plus the FP64 slab ring
+    at the N_B fraction, one write and T_l reads of 5 values (T_l = 3 at 4th
+    order, 4 at 6th)."""
+    elem, words = STATE_WORDS[prec]
+    return words * 5 * elem + nb_frac(order) * 5 * 8 * (1 + (3 if order == 4 else 4))
+
+
 def algorithmic_bytes(prec, order=4, path="paired"):
     """HBM bytes per grid point that the step's main kernel must move.
 
@@ -534,10 +544,24 @@ def main():
 
 def leg_report(r, world, pts, steps, pk):
     """Throughput, per-kernel times and the roofline of the main kernel of one
-    measured (precision, order) leg."""
+    measured (precision, order) leg.
+
+    The HBM roofline takes the step's algorithmic bytes per point (step_bytes)
+    times the points of one launch over the main kernel's average launch time.
+    Beside it: the bytes the main kernel itself must move (algorithmic_bytes;
+    in this design the ghost kernel moves the FP64 slab ring) with that
+    kernel's own fraction, and the whole step's fraction (step bytes over the
+    step time)."""
     order = r["order"]
     main = r["kt"].get("main", (1, 1.0))
     t_main = main[1] / main[0] / 1e3
+    t_step = r["ms"] / steps / 1e3
+    hbm = pk.get("hbm_gbs", 6800.0)
+    sb = step_bytes(r["prec"], order)
+    kb = algorithmic_bytes(r["prec"], order, r["path"])
+    hbm_fields = {"peak": pk.get("hbm_gbs"), "unit": "GB/s", "bytes_per_point": sb,
+                  "kernel_bytes_per_point": kb, "kernel_frac": kb * pts / t_main / 1e9 / hbm,
+                  "step_frac": sb * pts / t_step / 1e9 / hbm}
     if r["dtype"] == "f64":
         flops = FLOP_MAIN if order == 4 else FLOP_MAIN6
         achieved = flops * pts / t_main / 1e12
@@ -549,14 +573,11 @@ def leg_report(r, world, pts, steps, pk):
                 "traffic": traffic, "flop_per_point": flops,
                 "note": "FP64 peak derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
                         "(an FMA probe measured 1.20 TFLOP/s)"}
-        # the same kernel against the HBM roof, at its algorithmic bytes
-        bpp = algorithmic_bytes("p64", order, r["path"])
-        gbs = bpp * pts / t_main / 1e9
-        roof["hbm"] = {"achieved": gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                       "frac": gbs / pk.get("hbm_gbs", 6800.0), "bytes_per_point": bpp}
+        # the same kernel against the HBM roof
+        gbs = sb * pts / t_main / 1e9
+        roof["hbm"] = dict(hbm_fields, achieved=gbs, frac=gbs / hbm)
     else:
-        bpp = algorithmic_bytes(r["prec"], order, r["path"])
-        achieved = bpp * pts / t_main / 1e9
+        achieved = sb * pts / t_main / 1e9
         kname = {"fused": "k_fused", "paired": "k_fused2"}.get(r["path"], "k_main")
         traffic = None
         if N == 256 and PES == 8 and r["prec"] == "p32c":
@@ -564,9 +585,8 @@ def leg_report(r, world, pts, steps, pk):
                 traffic = K_FUSED2_P32C_TRAFFIC_256
             elif order == 6 and r["path"] == "multipass":
                 traffic = K_MAIN_P32C_O6_TRAFFIC_256
-        roof = {"bound": "hbm", "kernel": "%s (FP32, order %d)" % (kname, order), "achieved": achieved,
-                "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0),
-                "traffic": traffic, "bytes_per_point": bpp}
+        roof = dict(hbm_fields, bound="hbm", kernel="%s (FP32, order %d)" % (kname, order), achieved=achieved,
+                    frac=achieved / hbm, traffic=traffic)
     return {"value": job_rate(world, pts, steps, r["ms"]), "unit": UNIT, "kernel_path": r["path"], "tile": r["tile"],
             "ms_per_step": r["ms"] / steps, "dtype": r["dtype"], "roofline": roof,
             "kernel_ms_per_step": {k: v[1] / v[0] for k, v in r["kt"].items()}}

@@ -48,16 +48,24 @@ def test_single_process_identity():
 
 
 def test_algorithmic_bytes_and_roofline_fields():
-    """Algorithmic bytes per point of the main kernel of one AB2 step at 8^3
-    PEs of 32^3.  One-pass FP32 kernel: 4 x 5 values of U and R (6 x 5 in the
-    compensated form, which also moves the low words of U), the 9 ghost
-    quantities of the 3 x 2M / 32 = 0.375 AT ghost points per point, and the
-    x-face slabs of U^{n+1} (2M / 32 = 0.125 points per point, with their low
-    words in P32C).  FP64 multi-pass k_main: the 16 PQ and 12 G arrays, 4 x 5
-    values of U and R, the ghost quantities.  The FP64 leg reports its
-    FP64-pipe fraction and, beside it, its HBM fraction."""
+    """Algorithmic bytes per point at 8^3 PEs of 32^3 (N_B = 1 - (28/32)^3).
+    The step's figure (the roofline's): 4 x 5 values of U and R (6 x 5 in the
+    compensated FP32 form, which also moves the low words of U) plus the FP64
+    slab ring, one write and T_l = 3 reads of 5 values at the N_B fraction.
+    The main kernel's own figure: one-pass FP32 kernel -- U, R (and low
+    words), the 9 ghost quantities of the 3 x 2M / 32 = 0.375 AT ghost points
+    per point, the x-face slabs of U^{n+1} (2M / 32 = 0.125 points per point,
+    with their low words in P32C); FP64 multi-pass k_main -- the 16 PQ and 12 G
+    arrays, 4 x 5 values of U and R, the ghost quantities.  The FP64 leg
+    reports its FP64-pipe fraction and, beside it, its HBM fraction."""
     import bench
     bench.set_workload(256, 8)
+    nb = 1.0 - (28.0 / 32.0) ** 3
+    ring = nb * 5 * 8 * 4
+    assert bench.step_bytes("p64") == pytest.approx(160.0 + ring)
+    assert bench.step_bytes("p32") == pytest.approx(80.0 + ring)
+    assert bench.step_bytes("p32c") == pytest.approx(120.0 + ring)
+    assert round(bench.step_bytes("p64"), 1) == 212.8 and round(bench.step_bytes("p32c"), 1) == 172.8
     assert bench.ghost_ratio(4) == pytest.approx(0.375) and bench.xface_ratio(4) == pytest.approx(0.125)
     assert bench.algorithmic_bytes("p32c") == pytest.approx(120.0 + 0.375 * 36 + 0.125 * 40)
     assert bench.algorithmic_bytes("p32") == pytest.approx(80.0 + 0.375 * 36 + 0.125 * 20)
@@ -71,13 +79,16 @@ def test_algorithmic_bytes_and_roofline_fields():
     assert roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
     assert roof["achieved"] == pytest.approx(bench.FLOP_MAIN * pts / 11e-3 / 1e12)
     assert roof["frac"] == pytest.approx(roof["achieved"] / bench.FP64_PEAK_TFLOPS)
-    assert roof["hbm"]["frac"] == pytest.approx(bench.algorithmic_bytes("p64", 4, "multipass") * pts / 11e-3 / 1e9
-                                                / 6801.7)
-    r32 = dict(r64, dtype="f32", prec="p32c", path="fused", tile=[32, 8, 32], kt={"main": (steps, 5 * 1.5)},
+    assert roof["hbm"]["frac"] == pytest.approx(bench.step_bytes("p64") * pts / 11e-3 / 1e9 / 6801.7)
+    assert roof["hbm"]["kernel_frac"] == pytest.approx(411.0 * pts / 11e-3 / 1e9 / 6801.7)
+    r32 = dict(r64, dtype="f32", prec="p32c", path="paired", tile=[32, 8, 32], kt={"main": (steps, 5 * 1.5)},
                ms=steps * 1.7)
     roof = bench.leg_report(r32, 1, pts, steps, {"hbm_gbs": 6801.7})["roofline"]
-    assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
-    assert roof["frac"] == pytest.approx(bench.algorithmic_bytes("p32c", 4, "fused") * pts / 1.5e-3 / 1e9 / 6801.7)
+    assert roof["bound"] == "hbm" and roof["unit"] == "GB/s" and roof["bytes_per_point"] == bench.step_bytes("p32c")
+    assert roof["frac"] == pytest.approx(bench.step_bytes("p32c") * pts / 1.5e-3 / 1e9 / 6801.7)
+    assert roof["kernel_frac"] == pytest.approx(138.5 * pts / 1.5e-3 / 1e9 / 6801.7)
+    assert roof["step_frac"] == pytest.approx(bench.step_bytes("p32c") * pts / 1.7e-3 / 1e9 / 6801.7)
+    assert roof["traffic"] == bench.K_FUSED2_P32C_TRAFFIC_256
 
 
 def test_oracle_baseline_uses_every_core():
