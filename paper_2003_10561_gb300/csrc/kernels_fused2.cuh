@@ -49,18 +49,25 @@ struct PairShape {
   static constexpr int TXH = TX / 2;                  // threads per tile row
   static constexpr int NT = TXH * TY;                 // threads of a CTA
   static constexpr int CX = TX + 4, CY = TY + 4, CELLS = CX * CY;
-  static constexpr int PAIRS = CELLS / 2;             // cell pairs of one window plane
-  static constexpr int ITER = (PAIRS + NT - 1) / NT;
+  // window fill items of one plane: the tile's own columns of every window
+  // row as aligned quads of 4 cells (x0 + 4j: one 128-bit load per variable),
+  // then the two x-halo cell pairs of every row (x0 - 2 and x0 + TX)
+  static constexpr int QROW = TX / 4, NQ = QROW * CY, NH = 2 * CY;
+  static constexpr int ITEMS = NQ + NH;
+  static constexpr int ITER = (ITEMS + NT - 1) / NT;
   static_assert(TX % 16 == 0 && TY % 8 == 0, "paired tiles are 16 or 32 wide and a multiple of 8 high");
 };
 
-// Raw values of one window plane for this thread's cell pairs (kind 1: the
-// conserved variables, 2: AT ghost u, v, w, T, 0: nothing).
+// Raw values of one window plane for this thread's fill items (a quad in
+// x, y, z, w of each variable, or a pair in x, y; kind 1: the conserved
+// variables, 2: AT ghost u, v, w, T, 0: nothing).
 template <int TX, int TY>
 struct PlaneRaw2 {
-  f2 v[PairShape<TX, TY>::ITER][5];
+  float4 v[PairShape<TX, TY>::ITER][5];
   int kind[PairShape<TX, TY>::ITER];
 };
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
 template <int TX, int TY>
 __device__ __forceinline__ void fetch_plane2(const Geom& g, const StepArgs<float>& A, const float* __restrict__ U,
@@ -71,89 +78,140 @@ __device__ __forceinline__ void fetch_plane2(const Geom& g, const StepArgs<float
   const bool bz = F.beyond(g, 2, zp);
   const int lz = zp - F.base[2];
   const bool zfar = bz && (lz < -2 || lz >= g.nl[2] + 2);
+  const int zw = wrapc(zp, g.n[2]);
 #pragma unroll
   for (int it = 0; it < PS::ITER; ++it) {
-    const int p = it * PS::NT + tid;
+    const int i = it * PS::NT + tid;
     P.kind[it] = 0;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) P.v[it][q] = bc(0.f);
-    if (p >= PS::PAIRS) continue;
-    const int c = 2 * p;
-    const int cy = c / PS::CX, cx = c - cy * PS::CX;
-    const int xg = F.x0 - 2 + cx, yg = F.y0 - 2 + cy;   // xg is even: the pair is xg, xg + 1
+    for (int q = 0; q < 5; ++q) P.v[it][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i >= PS::ITEMS) continue;
+    if (i < PS::NQ) {
+      // a quad of the tile's own columns: never beyond an x-face (tiles lie in one PE)
+      const int cy = i / PS::QROW, j = i - cy * PS::QROW;
+      const int xg = F.x0 + 4 * j, yg = F.y0 - 2 + cy;
+      const bool by = F.beyond(g, 1, yg);
+      if (bz) {
+        if (!zfar && !by) {
+          const int yw = wrapc(yg, g.n[1]);
+          const long long qs = 4LL * g.pes[2] * g.plane[2];
+          const long long gi = (long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] + (long long)yw * g.n[0] + xg;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) P.v[it][q] = ld4(A.GH[2] + (5 + q) * qs + gi);
+          P.kind[it] = 2;
+        }
+      } else if (by) {
+        const long long qs = 4LL * g.pes[1] * g.plane[1];
+        const long long gi = (long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] + (long long)zw * g.n[0] + xg;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) P.v[it][q] = ld4(A.GH[1] + (5 + q) * qs + gi);
+        P.kind[it] = 2;
+      } else {
+        const int yw = wrapc(yg, g.n[1]);
+        const long long idx = ((long long)zw * g.n[1] + yw) * g.n[0] + xg;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) P.v[it][q] = ld4(U + q * N + idx);
+        P.kind[it] = 1;
+      }
+      continue;
+    }
+    // an x-halo pair of a window row
+    const int h = i - PS::NQ, cy = h >> 1;
+    const int xg = (h & 1) ? F.x0 + TX : F.x0 - 2, yg = F.y0 - 2 + cy;   // xg is even: the pair is xg, xg + 1
     const bool bx = F.beyond(g, 0, xg), by = F.beyond(g, 1, yg);
+    auto put = [&](int q, f2 w) { P.v[it][q].x = w.x; P.v[it][q].y = w.y; };
     if (bz) {
       if (!zfar && !bx && !by) {
         const int xw = wrapc(xg, g.n[0]), yw = wrapc(yg, g.n[1]);
         const long long qs = 4LL * g.pes[2] * g.plane[2];
         const long long gi = (long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] + (long long)yw * g.n[0] + xw;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) P.v[it][q] = ld2(A.GH[2] + (5 + q) * qs + gi);
+        for (int q = 0; q < 4; ++q) put(q, ld2(A.GH[2] + (5 + q) * qs + gi));
         P.kind[it] = 2;
       }
     } else if (bx) {
       if (!by) {
         // the two cells are consecutive ghost slots of the x-face
-        const int yw = wrapc(yg, g.n[1]), zw = wrapc(zp, g.n[2]);
+        const int yw = wrapc(yg, g.n[1]);
         const long long qs = 4LL * g.pes[0] * g.plane[0];
         const long long g0 = (long long)(4 * F.pe[0] + F.ghost_slot(g, 0, xg)) * g.plane[0] + (long long)zw * g.n[1] + yw;
         const long long g1 = g0 + g.plane[0];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) P.v[it][q] = pk(A.GH[0][(5 + q) * qs + g0], A.GH[0][(5 + q) * qs + g1]);
+        for (int q = 0; q < 4; ++q) put(q, pk(A.GH[0][(5 + q) * qs + g0], A.GH[0][(5 + q) * qs + g1]));
         P.kind[it] = 2;
       }
     } else if (by) {
-      const int xw = wrapc(xg, g.n[0]), zw = wrapc(zp, g.n[2]);
+      const int xw = wrapc(xg, g.n[0]);
       const long long qs = 4LL * g.pes[1] * g.plane[1];
       const long long gi = (long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] + (long long)zw * g.n[0] + xw;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) P.v[it][q] = ld2(A.GH[1] + (5 + q) * qs + gi);
+      for (int q = 0; q < 4; ++q) put(q, ld2(A.GH[1] + (5 + q) * qs + gi));
       P.kind[it] = 2;
     } else {
-      const int xw = wrapc(xg, g.n[0]), yw = wrapc(yg, g.n[1]), zw = wrapc(zp, g.n[2]);
+      const int xw = wrapc(xg, g.n[0]), yw = wrapc(yg, g.n[1]);
       const long long idx = ((long long)zw * g.n[1] + yw) * g.n[0] + xw;
 #pragma unroll
-      for (int q = 0; q < 5; ++q) P.v[it][q] = ld2(U + q * N + idx);
+      for (int q = 0; q < 5; ++q) put(q, ld2(U + q * N + idx));
       P.kind[it] = 1;
     }
   }
 }
 
+// Window quantities of one cell pair from its raw values: u, v, w, T, rho, H
+// (zeros for kind 0; rho = H = 0 at ghost cells, whose fluxes come from the
+// ghost arrays).
+template <bool PLAIN>
+__device__ __forceinline__ void store_cells2(const Coef<float>& K, const CoefPair& KP, int kind, f2 r0, f2 m0, f2 m1,
+                                             f2 m2, f2 E, float* win, int bA, int bT, int bR, int c, int CELLS) {
+  const bool eform = !PLAIN && K.eform;
+  f2 u = bc(0.f), v = bc(0.f), w = bc(0.f), T = bc(0.f), r = bc(0.f), H = bc(0.f);
+  if (kind == 1) {
+    r = r0;
+    const f2 inv = rcp2(r);
+    u = m0 * inv;
+    v = m1 * inv;
+    w = m2 * inv;
+    // (gamma-1)(E - (m.u)/2), or (gamma-1) rho e
+    const f2 p_ = eform ? KP.gm1 * E : KP.gm1 * fma2(bc(-0.5f), fma2(m0, u, fma2(m1, v, m2 * w)), E);
+    T = KP.gamma * p_ * inv;
+    H = eform ? E : E + p_;
+  } else if (kind == 2) {
+    u = r0;
+    v = m0;
+    w = m1;
+    T = m2;
+  }
+  st2(win + bA + c, u);
+  st2(win + bA + CELLS + c, v);
+  st2(win + bA + 2 * CELLS + c, w);
+  st2(win + bT + c, T);
+  st2(win + bR + c, r);
+  st2(win + bR + CELLS + c, H);
+}
+
 template <int TX, int TY, bool PLAIN>
 __device__ __forceinline__ void store_plane2(const Coef<float>& K, const CoefPair& KP, const PlaneRaw2<TX, TY>& P,
                                              float* win, int bA, int bT, int bR) {
-  const bool eform = !PLAIN && K.eform;
   using PS = PairShape<TX, TY>;
   const int tid = threadIdx.x;
 #pragma unroll
   for (int it = 0; it < PS::ITER; ++it) {
-    const int p = it * PS::NT + tid;
-    if (p >= PS::PAIRS) break;
-    const int c = 2 * p;
-    f2 u = bc(0.f), v = bc(0.f), w = bc(0.f), T = bc(0.f), r = bc(0.f), H = bc(0.f);
-    if (P.kind[it] == 1) {
-      r = P.v[it][0];
-      const f2 m0 = P.v[it][1], m1 = P.v[it][2], m2 = P.v[it][3], E = P.v[it][4];
-      const f2 inv = rcp2(r);
-      u = m0 * inv;
-      v = m1 * inv;
-      w = m2 * inv;
-      // (gamma-1)(E - (m.u)/2), or (gamma-1) rho e
-      const f2 p_ = eform ? KP.gm1 * E : KP.gm1 * fma2(bc(-0.5f), fma2(m0, u, fma2(m1, v, m2 * w)), E);
-      T = KP.gamma * p_ * inv;
-      H = eform ? E : E + p_;
-    } else if (P.kind[it] == 2) {
-      u = P.v[it][0];
-      v = P.v[it][1];
-      w = P.v[it][2];
-      T = P.v[it][3];
+    const int i = it * PS::NT + tid;
+    if (i >= PS::ITEMS) break;
+    const float4* x = P.v[it];
+    if (i < PS::NQ) {
+      const int cy = i / PS::QROW, j = i - cy * PS::QROW;
+      const int c = cy * PS::CX + 2 + 4 * j;
+      store_cells2<PLAIN>(K, KP, P.kind[it], pk(x[0].x, x[0].y), pk(x[1].x, x[1].y), pk(x[2].x, x[2].y),
+                          pk(x[3].x, x[3].y), pk(x[4].x, x[4].y), win, bA, bT, bR, c, PS::CELLS);
+      store_cells2<PLAIN>(K, KP, P.kind[it], pk(x[0].z, x[0].w), pk(x[1].z, x[1].w), pk(x[2].z, x[2].w),
+                          pk(x[3].z, x[3].w), pk(x[4].z, x[4].w), win, bA, bT, bR, c + 2, PS::CELLS);
+    } else {
+      const int h = i - PS::NQ, cy = h >> 1;
+      const int c = cy * PS::CX + ((h & 1) ? TX + 2 : 0);
+      store_cells2<PLAIN>(K, KP, P.kind[it], pk(x[0].x, x[0].y), pk(x[1].x, x[1].y), pk(x[2].x, x[2].y),
+                          pk(x[3].x, x[3].y), pk(x[4].x, x[4].y), win, bA, bT, bR, c, PS::CELLS);
     }
-    st2(win + bA + c, u);
-    st2(win + bA + PS::CELLS + c, v);
-    st2(win + bA + 2 * PS::CELLS + c, w);
-    st2(win + bT + c, T);
-    st2(win + bR + c, r);
-    st2(win + bR + PS::CELLS + c, H);
   }
 }
 
