@@ -206,16 +206,33 @@ __device__ __forceinline__ void ghost_point(const Geom& g, const Coef<S>& K, con
   // lie in this kernel's order; the state itself would be read a grid row apart)
   const S* xs = (d == 0 && xst) ? xst + (long long)sp * plane + pl : nullptr;
   const long long xv = (long long)NS * P * plane;   // stride of a variable in xst
-  S src_hi[5];
+  // ring slot of level n - k - l (>= 1: delays start after L + T_l steps);
+  // k + l <= L + M < nlev, so one wrap of (n mod nlev) - k - l suffices
+  auto level_at = [&](int l, int v) {
+    int rs = nm - k - l;
+    if (rs < 0) rs += g.nlev;
+    return ring[(((long long)rs * 5 + v) * NS * P + sp) * plane + pl];
+  };
+  // every load of this ghost point first, all in flight together: level n of
+  // the source point (with its low words) and, under a delay, the T_l ring
+  // levels n-k .. n-k-M (slots other than that of level n, written below)
+  S src_hi[5], src_lo[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) src_hi[v] = xs ? xs[v * xv] : U[v * N + src];
+  for (int v = 0; v < 5; ++v) {
+    src_hi[v] = xs ? xs[v * xv] : U[v * N + src];
+    src_lo[v] = xs ? (xst_half ? xs[xst_half + v * xv] : S(0)) : (Ulo ? Ulo[v * N + src] : S(0));
+  }
+  double lv[M + 1][5];
+  if (k > 0) {
+#pragma unroll
+    for (int l = 0; l <= M; ++l)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) lv[l][v] = level_at(l, v);
+  }
   {
     double* rw = ring + ((long long)nm * 5 * NS * P + sp) * plane + pl;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const S lo = xs ? (xst_half ? xs[xst_half + v * xv] : S(0)) : (Ulo ? Ulo[v * N + src] : S(0));
-      rw[(long long)v * NS * P * plane] = ring_value(src_hi[v], lo);
-    }
+    for (int v = 0; v < 5; ++v) rw[(long long)v * NS * P * plane] = ring_value(src_hi[v], src_lo[v]);
   }
   if (k == 0) {
     if (PQ) {
@@ -236,21 +253,9 @@ __device__ __forceinline__ void ghost_point(const Geom& g, const Coef<S>& K, con
   int wi[M + 1];
   at_weights<M>(k, wi);
   S acc[kNumGhostQ];
-  // ring slot of level n - k - l (>= 1: delays start after L + T_l steps);
-  // k + l <= L + M < nlev, so one wrap of (n mod nlev) - k - l suffices
-  auto level_at = [&](int l, int v) {
-    int rs = nm - k - l;
-    if (rs < 0) rs += g.nlev;
-    return ring[(((long long)rs * 5 + v) * NS * P + sp) * plane + pl];
-  };
   if constexpr (sizeof(S) == 8) {
 #pragma unroll
     for (int q = 0; q < kNumGhostQ; ++q) acc[q] = S(0);
-    double lv[M + 1][5];
-#pragma unroll
-    for (int l = 0; l <= M; ++l)
-#pragma unroll
-      for (int v = 0; v < 5; ++v) lv[l][v] = level_at(l, v);
 #pragma unroll
     for (int l = 0; l <= M; ++l) {
       const S w = S(wi[l]);
@@ -262,12 +267,6 @@ __device__ __forceinline__ void ghost_point(const Geom& g, const Coef<S>& K, con
       for (int qq = 0; qq < kNumGhostQ; ++qq) acc[qq] = fma(w, q[qq], acc[qq]);
     }
   } else {
-    // every ring value of the T_l levels first (all loads in flight together)
-    double lv[M + 1][5];
-#pragma unroll
-    for (int l = 0; l <= M; ++l)
-#pragma unroll
-      for (int v = 0; v < 5; ++v) lv[l][v] = level_at(l, v);
     // base B = level n-k truncated to FP32; its own remainder is level 0's dU
     float h0, h1, h2, h3, h4, l0, l1, l2, l3, l4;
     split_double(lv[0][0], h0, l0);
