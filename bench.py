@@ -50,11 +50,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 x max S
 # 256^3 workload with 8x8x8 PEs of 32^3, from a one-pass ncu capture of that
 # launch (dram__bytes_read.sum + dram__bytes_write.sum):
 # k_main<double, 2> (multi-pass FP64): 7.79 GB + 3.84 GB; k_fused2<32, 8, plain>
-# (P32C): None until its quad-fill build is captured (the pair-fill build
-# moved 1.25 GB + 1.04 GB); 6th order (multi-pass): k_main<double, 3>
+# (P32C): 1.25 GB + 1.04 GB; 6th order (multi-pass): k_main<double, 3>
 # 10.90 GB + 4.05 GB, k_main<float, 3> (P32C) 3.46 GB + 1.15 GB.
 K_MAIN_FP64_TRAFFIC_256 = 7.79e9 + 3.84e9
-K_FUSED2_P32C_TRAFFIC_256 = None
+K_FUSED2_P32C_TRAFFIC_256 = 1.25e9 + 1.04e9
 K_MAIN_FP64_O6_TRAFFIC_256 = 10.90e9 + 4.05e9
 K_MAIN_P32C_O6_TRAFFIC_256 = 3.46e9 + 1.15e9
 
