@@ -285,6 +285,33 @@ int at_dns_tune(at_dns_t* h, int32_t delay_mode, int32_t trials, double* best_ms
  * Errors: INVALID_ARG (NULL), UNSUPPORTED (not a candidate), OOM. */
 int at_dns_set_kernel_path(at_dns_t* h, int32_t path, const int32_t tile[3]);
 
+/* ---- checkpoints ----------------------------------------------------------
+ * The run state of a handle in one self-describing buffer: U^n (and its low
+ * words in P32C), R^{n-1}, the FP64 slab ring of the last L + T_l levels, the
+ * forcing coefficients, the last statistics record, the step counter, the
+ * time step and the start-up (forward Euler) flag, after a header that
+ * records the configuration.  The delay map and the forcing noise are pure
+ * functions of (seed, step, PE, face) and (f_seed, step, mode), so a handle
+ * of the same configuration that loads the buffer continues the saved run
+ * bit for bit (the paper's checkpoints serve averaging, Sec. 4).  The layout
+ * is this library's own (not a portable file format); sections start at
+ * 256-byte offsets. */
+
+/* *bytes receives the size of a checkpoint of h.  Errors: INVALID_ARG. */
+int at_dns_checkpoint_size(const at_dns_t* h, int64_t* bytes);
+
+/* Write the run state into buf (where = AT_DNS_HOST or AT_DNS_DEVICE, at least
+ * at_dns_checkpoint_size bytes; caller-owned).  Blocks until written.
+ * Errors: INVALID_ARG, STATE (no state set), CUDA. */
+int at_dns_checkpoint_save(at_dns_t* h, void* buf, int where);
+
+/* Restore the run state from buf into h, whose configuration must equal the
+ * saved one (grid, PEs, precision, order, forms, delays, seeds, physical and
+ * forcing constants; INVALID_ARG names the first field that differs); the
+ * saved time step replaces h's.  The next step continues the saved run.
+ * Errors: INVALID_ARG, CUDA. */
+int at_dns_checkpoint_load(at_dns_t* h, const void* buf, int where);
+
 /* Block until all work queued on the handle's stream has finished. */
 int at_dns_synchronize(at_dns_t* h);
 

@@ -109,6 +109,9 @@ _SIGS = {
     "at_dns_batch_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "at_dns_batch_persistent": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "at_dns_wait_selftest": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "at_dns_checkpoint_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "at_dns_checkpoint_save": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_int]),
+    "at_dns_checkpoint_load": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_int]),
     "at_dns_batch_last_error": (ctypes.c_char_p, [_P]),
     "at_dns_batch_destroy": (None, [_P]),
     "at_dns_rhs_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_double,
@@ -308,6 +311,37 @@ def at_dns_wait_selftest(log2_polls=20):
     return out.value == 1
 
 
+def _byte_ptr(buf, size):
+    """(pointer, where) of a byte buffer of at least `size` bytes: a numpy
+    uint8 array (host) or a uint8 torch tensor (host or CUDA)."""
+    if isinstance(buf, np.ndarray):
+        if buf.dtype != np.uint8 or not buf.flags["C_CONTIGUOUS"] or buf.size < size:
+            raise TypeError("checkpoint buffers are C-contiguous uint8 arrays of at least %d bytes" % size)
+        return buf.ctypes.data, AT_DNS_HOST
+    if type(buf).__module__.startswith("torch"):
+        import torch
+        if buf.dtype != torch.uint8 or not buf.is_contiguous() or buf.numel() < size:
+            raise TypeError("checkpoint buffers are contiguous uint8 tensors of at least %d bytes" % size)
+        return buf.data_ptr(), (AT_DNS_DEVICE if buf.is_cuda else AT_DNS_HOST)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def at_dns_checkpoint_size(h):
+    n = ctypes.c_int64(0)
+    _check(load().at_dns_checkpoint_size(h, ctypes.byref(n)), h)
+    return int(n.value)
+
+
+def at_dns_checkpoint_save(h, buf):
+    p, where = _byte_ptr(buf, at_dns_checkpoint_size(h))
+    _check(load().at_dns_checkpoint_save(h, p, where), h)
+
+
+def at_dns_checkpoint_load(h, buf):
+    p, where = _byte_ptr(buf, 0)
+    _check(load().at_dns_checkpoint_load(h, p, where), h)
+
+
 def at_dns_batch_destroy(b):
     load().at_dns_batch_destroy(b)
 
@@ -459,6 +493,18 @@ class Solver:
         out = {name: getattr(i, name) for name, _ in i._fields_}
         out["tile"] = list(i.tile)
         return out
+
+    def checkpoint(self, out=None):
+        """The run state as a checkpoint buffer (a new host uint8 array, or
+        `out`: a uint8 numpy array or torch tensor, host or CUDA)."""
+        if out is None:
+            out = np.empty(at_dns_checkpoint_size(self.h), dtype=np.uint8)
+        at_dns_checkpoint_save(self.h, out)
+        return out
+
+    def restore(self, buf):
+        """Continue the run saved in `buf` (same configuration)."""
+        at_dns_checkpoint_load(self.h, buf)
 
     def synchronize(self):
         at_dns_synchronize(self.h)

@@ -821,6 +821,198 @@ int set_dt(at_dns* h, const double* U) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// checkpoints: the run state of a handle in one self-describing buffer
+namespace {
+
+struct CkptHeader {
+  char magic[8];                     // "ATDNSCK1"
+  int32_t version;
+  // the configuration the run state belongs to (compared on load)
+  int32_t n[3], pes[3];
+  int32_t precision, order, energy_form, visc_law, integrator, forcing, max_delay, comm_period;
+  uint64_t seed, f_seed;
+  double gamma, prandtl, mu0, visc_exp, sutherland_s, kf, f_amp, f_tcorr;
+  // the run state's scalars
+  int64_t step, stats_step;
+  int32_t first, stats_valid;
+  double dt, t, stats_time;
+  // byte offsets of the sections (-1: absent) and the total size
+  int64_t off_U, off_Ulo, off_R, off_ring[3], off_fhat, off_sums, off_words, total;
+};
+
+size_t ck_align(size_t x) { return (x + 255) / 256 * 256; }
+
+// Bytes of the FP64 slab ring of direction d (as allocated).
+size_t ring_bytes(const at_dns* h, int d) {
+  return (size_t)h->g.nlev * 5 * (2ull * h->g.M * h->g.pes[d] * (size_t)h->g.plane[d]) * sizeof(double);
+}
+
+// The configuration fields and the section layout of handle h.
+void ckpt_layout(const at_dns* h, CkptHeader& H) {
+  std::memset(&H, 0, sizeof(H));
+  std::memcpy(H.magic, "ATDNSCK1", 8);
+  H.version = 1;
+  const at_dns_config_t& c = h->cfg;
+  for (int d = 0; d < 3; ++d) { H.n[d] = h->g.n[d]; H.pes[d] = h->g.pes[d]; }
+  H.precision = c.precision;
+  H.order = 2 * h->g.M;
+  H.energy_form = c.energy_form;
+  H.visc_law = c.visc_law;
+  H.integrator = c.integrator;
+  H.forcing = c.forcing;
+  H.max_delay = c.max_delay;
+  H.comm_period = c.comm_period;
+  H.seed = c.seed;
+  H.f_seed = c.f_seed;
+  H.gamma = c.gamma;
+  H.prandtl = c.prandtl;
+  H.mu0 = c.mu0;
+  H.visc_exp = c.visc_exp;
+  H.sutherland_s = c.sutherland_s;
+  H.kf = c.kf;
+  H.f_amp = c.f_amp;
+  H.f_tcorr = c.f_tcorr;
+  const size_t field = 5 * (size_t)h->g.npts * h->ssize;
+  size_t off = ck_align(sizeof(CkptHeader));
+  H.off_U = (int64_t)off;
+  off = ck_align(off + field);
+  H.off_Ulo = h->comp ? (int64_t)off : -1;
+  if (h->comp) off = ck_align(off + field);
+  H.off_R = (int64_t)off;
+  off = ck_align(off + field);
+  for (int d = 0; d < 3; ++d) {
+    H.off_ring[d] = h->ring[d] ? (int64_t)off : -1;
+    if (h->ring[d]) off = ck_align(off + ring_bytes(h, d));
+  }
+  H.off_fhat = h->nmodes ? (int64_t)off : -1;
+  if (h->nmodes) off = ck_align(off + (size_t)h->nmodes * 3 * sizeof(double2));
+  H.off_sums = (int64_t)off;
+  off = ck_align(off + kNumStat * sizeof(double));
+  H.off_words = (int64_t)off;
+  off = ck_align(off + 4 * sizeof(unsigned long long));
+  H.total = (int64_t)off;
+}
+
+// The first configuration field in which a saved header differs from this
+// handle's, or null.
+const char* ckpt_mismatch(const CkptHeader& a, const CkptHeader& b) {
+  for (int d = 0; d < 3; ++d) {
+    if (a.n[d] != b.n[d]) return "grid";
+    if (a.pes[d] != b.pes[d]) return "pes";
+  }
+  if (a.precision != b.precision) return "precision";
+  if (a.order != b.order) return "order";
+  if (a.energy_form != b.energy_form) return "energy_form";
+  if (a.visc_law != b.visc_law) return "visc_law";
+  if (a.integrator != b.integrator) return "integrator";
+  if (a.forcing != b.forcing) return "forcing";
+  if (a.max_delay != b.max_delay) return "max_delay";
+  if (a.comm_period != b.comm_period) return "comm_period";
+  if (a.seed != b.seed) return "seed";
+  if (a.f_seed != b.f_seed) return "f_seed";
+  if (a.gamma != b.gamma || a.prandtl != b.prandtl || a.mu0 != b.mu0 || a.visc_exp != b.visc_exp ||
+      a.sutherland_s != b.sutherland_s)
+    return "physical constants";
+  if (a.kf != b.kf || a.f_amp != b.f_amp || a.f_tcorr != b.f_tcorr) return "forcing constants";
+  if (a.total != b.total) return "layout";
+  return nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int at_dns_checkpoint_size(const at_dns_t* h, int64_t* bytes) {
+  if (!h || !bytes) return AT_DNS_E_INVALID_ARG;
+  CkptHeader H;
+  ckpt_layout(h, H);
+  *bytes = H.total;
+  return AT_DNS_OK;
+}
+
+int at_dns_checkpoint_save(at_dns_t* h, void* buf, int where) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  if (!buf) return fail(h, AT_DNS_E_INVALID_ARG, "buf is NULL");
+  if (where != AT_DNS_HOST && where != AT_DNS_DEVICE) return fail(h, AT_DNS_E_INVALID_ARG, "bad where");
+  if (!h->has_state) return fail(h, AT_DNS_E_STATE, "no state set");
+  CkptHeader H;
+  ckpt_layout(h, H);
+  DevState dsv;   // the step counter, start-up flag and state buffer as the device has them
+  CK(cudaMemcpyAsync(&dsv, h->ds, sizeof(dsv), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  H.step = dsv.n;
+  H.first = dsv.first;
+  H.stats_step = h->stats_step;
+  H.stats_valid = h->stats_valid ? 1 : 0;
+  H.dt = h->dt;
+  H.t = h->t;
+  H.stats_time = h->stats_time;
+  const cudaMemcpyKind kind = where == AT_DNS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  char* out = (char*)buf;
+  const size_t field = 5 * (size_t)h->g.npts * h->ssize;
+  CK(cudaMemcpyAsync(out + H.off_U, h->U[dsv.cur], field, kind, h->st));
+  if (H.off_Ulo >= 0) CK(cudaMemcpyAsync(out + H.off_Ulo, h->Ulo[dsv.cur], field, kind, h->st));
+  CK(cudaMemcpyAsync(out + H.off_R, h->Rprev, field, kind, h->st));
+  for (int d = 0; d < 3; ++d)
+    if (H.off_ring[d] >= 0) CK(cudaMemcpyAsync(out + H.off_ring[d], h->ring[d], ring_bytes(h, d), kind, h->st));
+  if (H.off_fhat >= 0)
+    CK(cudaMemcpyAsync(out + H.off_fhat, h->fhat, (size_t)h->nmodes * 3 * sizeof(double2), kind, h->st));
+  CK(cudaMemcpyAsync(out + H.off_sums, h->sums, kNumStat * sizeof(double), kind, h->st));
+  CK(cudaMemcpyAsync(out + H.off_words, h->words, 4 * sizeof(unsigned long long), kind, h->st));
+  if (where == AT_DNS_HOST) std::memcpy(out, &H, sizeof(H));
+  else CK(cudaMemcpyAsync(out, &H, sizeof(H), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return AT_DNS_OK;
+}
+
+int at_dns_checkpoint_load(at_dns_t* h, const void* buf, int where) {
+  if (!h) return AT_DNS_E_INVALID_ARG;
+  h->err.clear();
+  if (!buf) return fail(h, AT_DNS_E_INVALID_ARG, "buf is NULL");
+  if (where != AT_DNS_HOST && where != AT_DNS_DEVICE) return fail(h, AT_DNS_E_INVALID_ARG, "bad where");
+  CkptHeader S, H;
+  if (where == AT_DNS_HOST) std::memcpy(&S, buf, sizeof(S));
+  else CK(cudaMemcpy(&S, buf, sizeof(S), cudaMemcpyDeviceToHost));
+  if (std::memcmp(S.magic, "ATDNSCK1", 8) != 0 || S.version != 1)
+    return fail(h, AT_DNS_E_INVALID_ARG, "not a checkpoint of this library");
+  ckpt_layout(h, H);
+  if (const char* what = ckpt_mismatch(S, H))
+    return fail(h, AT_DNS_E_INVALID_ARG, std::string("checkpoint of another configuration: ") + what + " differs");
+  if (S.step < 0 || !(S.dt > 0)) return fail(h, AT_DNS_E_INVALID_ARG, "checkpoint holds no run state");
+  const cudaMemcpyKind kind = where == AT_DNS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const char* in = (const char*)buf;
+  const size_t field = 5 * (size_t)h->g.npts * h->ssize;
+  h->cur = 0;
+  CK(cudaMemcpyAsync(h->U[0], in + H.off_U, field, kind, h->st));
+  if (H.off_Ulo >= 0) CK(cudaMemcpyAsync(h->Ulo[0], in + H.off_Ulo, field, kind, h->st));
+  CK(cudaMemcpyAsync(h->Rprev, in + H.off_R, field, kind, h->st));
+  for (int d = 0; d < 3; ++d)
+    if (H.off_ring[d] >= 0) CK(cudaMemcpyAsync(h->ring[d], in + H.off_ring[d], ring_bytes(h, d), kind, h->st));
+  if (H.off_fhat >= 0)
+    CK(cudaMemcpyAsync(h->fhat, in + H.off_fhat, (size_t)h->nmodes * 3 * sizeof(double2), kind, h->st));
+  CK(cudaMemcpyAsync(h->sums, in + H.off_sums, kNumStat * sizeof(double), kind, h->st));
+  CK(cudaMemcpyAsync(h->words, in + H.off_words, 4 * sizeof(unsigned long long), kind, h->st));
+  h->n = S.step;
+  h->first = S.first != 0;
+  h->dt = S.dt;
+  h->t = S.t;
+  h->stats_step = S.stats_step;
+  h->stats_time = S.stats_time;
+  h->stats_valid = S.stats_valid != 0;
+  h->has_state = true;
+  k_set_state<<<1, 1, 0, h->st>>>(h->ds, S.step, S.first, 0);
+  CK(cudaGetLastError());
+  // the x-face slabs of U^n that the next ghost kernel reads (FP32 forms)
+  const int rc = h->p64 ? AT_DNS_OK : Ops<float>::xstage_fill(h);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->st));
+  return AT_DNS_OK;
+}
+
+}  // extern "C"
+
 extern "C" {
 
 int at_dns_config_default(at_dns_config_t* c) {
