@@ -63,6 +63,9 @@ extern "C" {
 #define AT_DNS_E_STATE        -6   /* no state has been set yet */
 #define AT_DNS_E_TOO_LARGE    -7   /* problem above a fixed size limit (at_dns_rhs_noalloc) */
 #define AT_DNS_E_TIMEOUT      -8   /* a bounded wait inside a kernel gave up (persistent batch step) */
+#define AT_DNS_E_BOUNDS       -9   /* bounds-checked builds only (compiled with -DAT_DNS_CHECKS): an
+                                      index check in a kernel failed; the access was redirected to
+                                      index 0 of its buffer, so results of the call are not valid */
 
 /* delay modes (Sec. 3.1) */
 #define AT_DNS_SYNC      0   /* k = 0 on every face: standard scheme */

@@ -21,6 +21,7 @@ AT_DNS_E_UNSUPPORTED = -5
 AT_DNS_E_STATE = -6
 AT_DNS_E_TOO_LARGE = -7
 AT_DNS_E_TIMEOUT = -8
+AT_DNS_E_BOUNDS = -9
 AT_DNS_NOALLOC_MAX_POINTS = 262144
 
 AT_DNS_SYNC, AT_DNS_PERIODIC, AT_DNS_RANDOM, AT_DNS_FIXED = 0, 1, 2, 3
@@ -128,15 +129,18 @@ def library_path():
 
 
 def load(build_if_missing=True):
-    """Load libat_dns.so (building it in-tree first if asked and needed)."""
+    """Load libat_dns.so (building it in-tree first if asked and needed).  With
+    AT_DNS_LIBRARY=checked in the environment: the bounds-checked build
+    libat_dns_checked.so instead (index checks in the kernels)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if build_if_missing and not _build.up_to_date():
-        _build.build()
+    checked = os.environ.get("AT_DNS_LIBRARY") == "checked"
+    path = _build.LIB_CHECKED if checked else _build.LIB
+    if build_if_missing and not _build.up_to_date(checked):
+        _build.build(checked=checked)
     if not os.path.exists(path):
-        raise ImportError("libat_dns.so is not built (run paper_2003_10561_gb300.build.build())")
+        raise ImportError("%s is not built (run paper_2003_10561_gb300.build.build())" % os.path.basename(path))
     lib = ctypes.CDLL(path)
     for name, (res, args) in _SIGS.items():
         fn = getattr(lib, name)

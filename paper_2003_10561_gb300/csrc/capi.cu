@@ -164,7 +164,7 @@ __global__ void k_join_double(const float* __restrict__ hi, const float* __restr
 // (direction d's cnt_d points: slab sp = 2M pe + t, plane point pl), so the
 // ring writes are coalesced, and so are the field reads of the y- and z-faces.
 __global__ void k_ring_store(Geom g, const double* __restrict__ U, double* r0, double* r1, double* r2, long long cnt0,
-                             long long cnt1, long long cnt2, int first_slot, int count) {
+                             long long cnt1, long long cnt2, int first_slot, int count, const DevState* ds) {
   long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int d = 0;
   if (j >= cnt0) {
@@ -194,13 +194,14 @@ __global__ void k_ring_store(Geom g, const double* __restrict__ U, double* r0, d
     y = (int)(pl / g.n[0]);
     x = (int)(pl - (long long)y * g.n[0]);
   }
-  const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
+  const long long idx = checked(((long long)z * g.n[1] + y) * g.n[0] + x, g.npts, ds, CHK_STATE);
   double* ring = d == 0 ? r0 : (d == 1 ? r1 : r2);
   const long long PS = 2LL * M * g.pes[d];
+  const long long spp = checked(sp * plane + pl, PS * plane, ds, CHK_RING);
   for (int v = 0; v < 5; ++v) {
     const double val = U[v * g.npts + idx];
     for (int s = 0, slot = first_slot; s < count; ++s, slot = slot + 1 == g.nlev ? 0 : slot + 1)
-      ring[(((long long)slot * 5 + v) * PS + sp) * plane + pl] = val;
+      ring[((long long)slot * 5 + v) * PS * plane + spp] = val;
   }
 }
 
@@ -354,6 +355,27 @@ struct Timed {
   }
 };
 
+int fail(at_dns* h, int code, const std::string& msg);
+
+// Bounds-checked builds: report (and clear) the index checks that failed in
+// the handle's kernels since the last report; ordinary builds: nothing.
+int report_checks(at_dns* h) {
+#ifdef AT_DNS_CHECKS
+  unsigned long long c = 0;
+  if (cudaMemcpyAsync(&c, &h->ds->check, sizeof(c), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+      cudaStreamSynchronize(h->st) != cudaSuccess)
+    return fail(h, AT_DNS_E_CUDA, "cannot read the index checks");
+  if (c) {
+    cudaMemsetAsync(&h->ds->check, 0, sizeof(c), h->st);
+    return fail(h, AT_DNS_E_BOUNDS, "index checks failed in the kernels (bounds-checked build), classes " +
+                                        std::to_string(c));
+  }
+#else
+  (void)h;
+#endif
+  return AT_DNS_OK;
+}
+
 int fail(at_dns* h, int code, const std::string& msg) {
   h->err = msg;
   return code;
@@ -453,7 +475,8 @@ int ring_store(at_dns* h, const double* field, int first_slot, int count) {
   const long long total = cnt[0] + cnt[1] + cnt[2];
   if (!total) return AT_DNS_OK;
   k_ring_store<<<nblk(total), kBlock, 0, h->st>>>(h->g, field, (double*)h->ring[0], (double*)h->ring[1],
-                                                  (double*)h->ring[2], cnt[0], cnt[1], cnt[2], first_slot, count);
+                                                  (double*)h->ring[2], cnt[0], cnt[1], cnt[2], first_slot, count,
+                                                  h->ds);
   CK(cudaGetLastError());
   return AT_DNS_OK;
 }
@@ -1207,6 +1230,10 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
       (rc = dev_alloc(h, (void**)&h->sums, kNumStat * sizeof(double))) ||
       (rc = dev_alloc(h, (void**)&h->words, 4 * sizeof(unsigned long long))))
     return create_fail(h, rc);
+  if (cudaMemsetAsync(h->ds, 0, sizeof(DevState), h->st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return create_fail(h, AT_DNS_E_CUDA);
+  }
   // forcing tables (allocated even without forcing: the x-table is tiny)
   std::vector<Mode3> modes = forcing_modes(c.forcing ? c.kf : 1.0);
   h->nmodes = c.forcing ? (int)modes.size() : 0;
@@ -1274,7 +1301,7 @@ int at_dns_set_history(at_dns_t* h, const double* levels, int32_t nlevels, int64
   h->stats_valid = false;
   if ((rc = force_reset(h, step))) return rc;
   CK(cudaStreamSynchronize(h->st));
-  return AT_DNS_OK;
+  return report_checks(h);
 }
 
 int at_dns_set_state(at_dns_t* h, const double* u, int where) {
@@ -1320,7 +1347,7 @@ int at_dns_rhs(at_dns_t* h, int32_t delay_mode, double* rhs_out, int where) {
   if (where == AT_DNS_HOST)
     CK(cudaMemcpyAsync(rhs_out, h->stage, 5 * h->g.npts * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
-  return AT_DNS_OK;
+  return report_checks(h);
 }
 
 int at_dns_step(at_dns_t* h, int32_t nsteps, int32_t delay_mode) {
@@ -1352,6 +1379,7 @@ int at_dns_step(at_dns_t* h, int32_t nsteps, int32_t delay_mode) {
     }
   }
   if (!stats) h->stats_valid = false;
+  if ((rc = report_checks(h))) return rc;
   if (nsteps > 0) {
     unsigned long long w = 0;
     CK(cudaMemcpyAsync(&w, h->words + 3, sizeof(w), cudaMemcpyDeviceToHost, h->st));
@@ -1952,6 +1980,8 @@ int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode) {
     const cudaError_t e = cudaStreamSynchronize(b->ms[i]);
     if (e != cudaSuccess) return batch_fail(b, AT_DNS_E_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
   }
+  for (int i = 0; i < M; ++i)
+    if (report_checks(b->m[i])) return batch_fail(b, AT_DNS_E_BOUNDS, "member " + std::to_string(i) + ": " + b->m[i]->err);
   for (int i = 0; i < M; ++i)
     if (w[i]) return batch_fail(b, AT_DNS_E_UNSTABLE, "member " + std::to_string(i) + " became unstable");
   return AT_DNS_OK;

@@ -331,7 +331,24 @@ struct DevState {
   long long n;
   int first;
   int cur;
+  unsigned long long check;   // bounds-checked builds: index checks that failed (CheckBits)
 };
+
+// Bounds-checked builds (every translation unit compiled with -DAT_DNS_CHECKS):
+// an index outside [0, n) is recorded in the device step state (the class of
+// access as a CheckBits bit) and replaced by 0, so the access stays inside the
+// buffer and the host reports the failure after the call (AT_DNS_E_BOUNDS).
+// Ordinary builds return the index unchanged and compile no check.
+enum CheckBits { CHK_STATE = 1, CHK_RING = 2, CHK_GHOST = 4, CHK_STAGE = 8 };
+#ifdef AT_DNS_CHECKS
+__device__ __forceinline__ long long checked(long long i, long long n, const DevState* ds, unsigned what) {
+  if (i >= 0 && i < n) return i;
+  if (ds) atomicOr(const_cast<unsigned long long*>(&ds->check), (unsigned long long)what);
+  return 0;
+}
+#else
+__device__ __forceinline__ long long checked(long long i, long long, const DevState*, unsigned) { return i; }
+#endif
 
 template <typename S>
 struct StepArgs {

@@ -189,14 +189,15 @@ __device__ __forceinline__ void ghost_point(const Geom& g, const Coef<S>& K, con
   const int p = pe_number(g, c[0], c[1], c[2]);
   const int face = 2 * d + (slot >= M ? 1 : 0);
   const int k = delay(p, face);
-  const long long qstride = (long long)NS * P * plane;
-  S* out = GH + (long long)gi * plane + pl;
+  const long long qstride = (long long)NS * P * plane;   // points of the direction's slabs
+  S* out = GH + checked((long long)gi * plane + pl, qstride, ds, CHK_GHOST);
   // the source point (in the neighbouring PE) and its slab of the ring
   c[d] = cd;
-  const long long src = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
   const long long N = g.npts;
+  const long long src = checked(((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0], N, ds, CHK_STATE);
   const int nbr = slot < M ? (ped - 1 + P) % P : (ped + 1) % P;
   const int sp = NS * nbr + (slot < M ? slot + M : slot - M);
+  const long long spp = checked((long long)sp * plane + pl, qstride, ds, CHK_RING);   // slab point
   const int nm = ring_slot(g, n);
   // Level n of the source point into its ring slot: every slab point of the
   // ring is the source of exactly one ghost slot, and no ghost reads the slot
@@ -204,14 +205,14 @@ __device__ __forceinline__ void ghost_point(const Geom& g, const Coef<S>& K, con
   // the ring current for the later steps that read level n with a delay.
   // (x-faces of the FP32 forms: from the slabs the step kernel staged, which
   // lie in this kernel's order; the state itself would be read a grid row apart)
-  const S* xs = (d == 0 && xst) ? xst + (long long)sp * plane + pl : nullptr;
+  const S* xs = (d == 0 && xst) ? xst + spp : nullptr;
   const long long xv = (long long)NS * P * plane;   // stride of a variable in xst
   // ring slot of level n - k - l (>= 1: delays start after L + T_l steps);
   // k + l <= L + M < nlev, so one wrap of (n mod nlev) - k - l suffices
   auto level_at = [&](int l, int v) {
     int rs = nm - k - l;
     if (rs < 0) rs += g.nlev;
-    return ring[(((long long)rs * 5 + v) * NS * P + sp) * plane + pl];
+    return ring[((long long)rs * 5 + v) * qstride + spp];
   };
   // every load of this ghost point first, all in flight together: level n of
   // the source point (with its low words) and, under a delay, the T_l ring
@@ -230,7 +231,7 @@ __device__ __forceinline__ void ghost_point(const Geom& g, const Coef<S>& K, con
       for (int v = 0; v < 5; ++v) lv[l][v] = level_at(l, v);
   }
   {
-    double* rw = ring + ((long long)nm * 5 * NS * P + sp) * plane + pl;
+    double* rw = ring + (long long)nm * 5 * qstride + spp;
 #pragma unroll
     for (int v = 0; v < 5; ++v) rw[(long long)v * NS * P * plane] = ring_value(src_hi[v], src_lo[v]);
   }

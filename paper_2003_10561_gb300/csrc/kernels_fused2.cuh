@@ -95,20 +95,22 @@ __device__ __forceinline__ void fetch_plane2(const Geom& g, const StepArgs<float
         if (!zfar && !by) {
           const int yw = wrapc(yg, g.n[1]);
           const long long qs = 4LL * g.pes[2] * g.plane[2];
-          const long long gi = (long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] + (long long)yw * g.n[0] + xg;
+          const long long gi = checked((long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] +
+                                           (long long)yw * g.n[0] + xg, qs - 3, A.ds, CHK_GHOST);
 #pragma unroll
           for (int q = 0; q < 4; ++q) P.v[it][q] = ld4(A.GH[2] + (5 + q) * qs + gi);
           P.kind[it] = 2;
         }
       } else if (by) {
         const long long qs = 4LL * g.pes[1] * g.plane[1];
-        const long long gi = (long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] + (long long)zw * g.n[0] + xg;
+        const long long gi = checked((long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] +
+                                         (long long)zw * g.n[0] + xg, qs - 3, A.ds, CHK_GHOST);
 #pragma unroll
         for (int q = 0; q < 4; ++q) P.v[it][q] = ld4(A.GH[1] + (5 + q) * qs + gi);
         P.kind[it] = 2;
       } else {
         const int yw = wrapc(yg, g.n[1]);
-        const long long idx = ((long long)zw * g.n[1] + yw) * g.n[0] + xg;
+        const long long idx = checked(((long long)zw * g.n[1] + yw) * g.n[0] + xg, N - 3, A.ds, CHK_STATE);
 #pragma unroll
         for (int q = 0; q < 5; ++q) P.v[it][q] = ld4(U + q * N + idx);
         P.kind[it] = 1;
@@ -124,7 +126,8 @@ __device__ __forceinline__ void fetch_plane2(const Geom& g, const StepArgs<float
       if (!zfar && !bx && !by) {
         const int xw = wrapc(xg, g.n[0]), yw = wrapc(yg, g.n[1]);
         const long long qs = 4LL * g.pes[2] * g.plane[2];
-        const long long gi = (long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] + (long long)yw * g.n[0] + xw;
+        const long long gi = checked((long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] +
+                                         (long long)yw * g.n[0] + xw, qs - 1, A.ds, CHK_GHOST);
 #pragma unroll
         for (int q = 0; q < 4; ++q) put(q, ld2(A.GH[2] + (5 + q) * qs + gi));
         P.kind[it] = 2;
@@ -134,7 +137,8 @@ __device__ __forceinline__ void fetch_plane2(const Geom& g, const StepArgs<float
         // the two cells are consecutive ghost slots of the x-face
         const int yw = wrapc(yg, g.n[1]);
         const long long qs = 4LL * g.pes[0] * g.plane[0];
-        const long long g0 = (long long)(4 * F.pe[0] + F.ghost_slot(g, 0, xg)) * g.plane[0] + (long long)zw * g.n[1] + yw;
+        const long long g0 = checked((long long)(4 * F.pe[0] + F.ghost_slot(g, 0, xg)) * g.plane[0] +
+                                         (long long)zw * g.n[1] + yw, qs - g.plane[0], A.ds, CHK_GHOST);
         const long long g1 = g0 + g.plane[0];
 #pragma unroll
         for (int q = 0; q < 4; ++q) put(q, pk(A.GH[0][(5 + q) * qs + g0], A.GH[0][(5 + q) * qs + g1]));
@@ -143,13 +147,14 @@ __device__ __forceinline__ void fetch_plane2(const Geom& g, const StepArgs<float
     } else if (by) {
       const int xw = wrapc(xg, g.n[0]);
       const long long qs = 4LL * g.pes[1] * g.plane[1];
-      const long long gi = (long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] + (long long)zw * g.n[0] + xw;
+      const long long gi = checked((long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] +
+                                       (long long)zw * g.n[0] + xw, qs - 1, A.ds, CHK_GHOST);
 #pragma unroll
       for (int q = 0; q < 4; ++q) put(q, ld2(A.GH[1] + (5 + q) * qs + gi));
       P.kind[it] = 2;
     } else {
       const int xw = wrapc(xg, g.n[0]), yw = wrapc(yg, g.n[1]);
-      const long long idx = ((long long)zw * g.n[1] + yw) * g.n[0] + xw;
+      const long long idx = checked(((long long)zw * g.n[1] + yw) * g.n[0] + xw, N - 1, A.ds, CHK_STATE);
 #pragma unroll
       for (int q = 0; q < 5; ++q) put(q, ld2(U + q * N + idx));
       P.kind[it] = 1;
@@ -337,7 +342,8 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
   // z fluxes of this pair at window plane q = zp - zs + 4 (z ghosts beyond a PE z-face)
   auto zflux = [&](int zp, int q, f2 (&out)[5]) {
     if (F.beyond(g, 2, zp)) {
-      const long long gi = (long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] + (long long)y * g.n[0] + x;
+      const long long gi = checked((long long)(4 * F.pe[2] + F.ghost_slot(g, 2, zp)) * g.plane[2] +
+                                       (long long)y * g.n[0] + x, qsz - 1, A.ds, CHK_GHOST);
 #pragma unroll
       for (int e = 0; e < 5; ++e) out[e] = ld2(A.GH[2] + e * qsz + gi);
     } else {
@@ -359,7 +365,7 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
     store_plane2<TX, TY, PLAIN>(K, KP, pf, win, slot_A<TX, TY>(q + 4), slot_T<TX, TY>(q + 4), slot_R<TX, TY>(q + 4));
     __syncthreads();
     if (z + 1 < zs + ZC) fetch_plane2<TX, TY>(g, A, D.U, F, z + 5, pf);
-    const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
+    const long long idx = checked(((long long)z * g.n[1] + y) * g.n[0] + x, N - 1, A.ds, CHK_STATE);
     const f2 m[3] = {ld2(D.U + N + idx), ld2(D.U + 2 * N + idx), ld2(D.U + 3 * N + idx)};
     const f2 Ecur = ld2(D.U + 4 * N + idx);
     f2 Rp[5], Lp[5];
@@ -397,8 +403,8 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
         const int xg = F.x0 - 2 + cxw, yg = F.y0 + r;
         const int cw = (r + 2) * CX + cxw;
         if (F.beyond(g, 0, xg)) {
-          const long long g0 = (long long)(4 * F.pe[0] + F.ghost_slot(g, 0, xg)) * g.plane[0] +
-                               (long long)z * g.n[1] + yg;
+          const long long g0 = checked((long long)(4 * F.pe[0] + F.ghost_slot(g, 0, xg)) * g.plane[0] +
+                                           (long long)z * g.n[1] + yg, qsx - g.plane[0], A.ds, CHK_GHOST);
           const long long g1 = g0 + g.plane[0];
 #pragma unroll
           for (int e = 0; e < 5; ++e) st2(FX + e * TY * CX + c, pk(A.GH[0][e * qsx + g0], A.GH[0][e * qsx + g1]));
@@ -420,8 +426,8 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
         const int xg = F.x0 + cxl, yg = F.y0 - 2 + r;
         const int cw = r * CX + cxl + 2;
         if (F.beyond(g, 1, yg)) {
-          const long long gi = (long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] +
-                               (long long)z * g.n[0] + xg;
+          const long long gi = checked((long long)(4 * F.pe[1] + F.ghost_slot(g, 1, yg)) * g.plane[1] +
+                                           (long long)z * g.n[0] + xg, qsy - 1, A.ds, CHK_GHOST);
 #pragma unroll
           for (int e = 0; e < 5; ++e) st2(FY + e * (TY + 4) * TX + c, ld2(A.GH[1] + e * qsy + gi));
         } else {
@@ -693,7 +699,8 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
         // the pair is x-face slabs t and t + 1 of its PE
         const int t = li_x < 2 ? li_x : li_x - g.nl[0] + 4;
         const long long pv = 4LL * g.pes[0] * g.plane[0];
-        float* o = A.xst + (4LL * F.pe[0] + t) * g.plane[0] + (long long)z * g.n[1] + y;
+        float* o = A.xst + checked((4LL * F.pe[0] + t) * g.plane[0] + (long long)z * g.n[1] + y,
+                                   4LL * g.pes[0] * g.plane[0] - g.plane[0], A.ds, CHK_STAGE);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           o[v * pv] = un[v].x;
