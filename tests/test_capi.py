@@ -121,6 +121,54 @@ def test_null_arguments(lib):
     lib.at_dns_destroy(None)
 
 
+def test_null_arguments_of_checkpoint_batch_and_selftest_calls(lib):
+    """The checkpoint, batch and self-test entry points refuse null handles and
+    buffers and out-of-range arguments before any device work."""
+    import ctypes
+    n = ctypes.c_int64(0)
+    assert lib.at_dns_checkpoint_size(None, ctypes.byref(n)) == at_dns.AT_DNS_E_INVALID_ARG
+    assert lib.at_dns_checkpoint_save(None, None, 0) == at_dns.AT_DNS_E_INVALID_ARG
+    assert lib.at_dns_checkpoint_load(None, None, 0) == at_dns.AT_DNS_E_INVALID_ARG
+    assert lib.at_dns_batch_step(None, 1, 0) == at_dns.AT_DNS_E_INVALID_ARG
+    assert lib.at_dns_batch_persistent(None, 1, None) == at_dns.AT_DNS_E_INVALID_ARG
+    g = ctypes.c_int32(0)
+    assert lib.at_dns_wait_selftest(27, ctypes.byref(g)) == at_dns.AT_DNS_E_INVALID_ARG
+    assert lib.at_dns_wait_selftest(-1, ctypes.byref(g)) == at_dns.AT_DNS_E_INVALID_ARG
+    assert lib.at_dns_wait_selftest(10, None) == at_dns.AT_DNS_E_INVALID_ARG
+
+
+def test_checkpoint_buffers_are_checked_by_the_binding():
+    """Checkpoint buffers are C-contiguous uint8 arrays or tensors of at least
+    the checkpoint's size; anything else is refused before the C call."""
+    import numpy as np
+    with pytest.raises(TypeError):
+        at_dns._byte_ptr(np.zeros(16, dtype=np.float64), 8)
+    with pytest.raises(TypeError):
+        at_dns._byte_ptr(np.zeros(8, dtype=np.uint8), 16)
+    with pytest.raises(TypeError):
+        at_dns._byte_ptr(np.zeros((4, 8), dtype=np.uint8)[:, ::2], 8)
+    with pytest.raises(TypeError):
+        at_dns._byte_ptr([0] * 16, 8)
+    a = np.zeros(32, dtype=np.uint8)
+    assert at_dns._byte_ptr(a, 32) == (a.ctypes.data, at_dns.AT_DNS_HOST)
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(32, dtype=torch.uint8)
+    assert at_dns._byte_ptr(t, 32) == (t.data_ptr(), at_dns.AT_DNS_HOST)
+    with pytest.raises(TypeError):
+        at_dns._byte_ptr(torch.zeros(32, dtype=torch.float32), 8)
+
+
+def test_checked_build_variant_is_separate():
+    """The bounds-checked library is built apart (its own objects and file) with
+    -DAT_DNS_CHECKS, and at_dns.load() picks it only when asked."""
+    assert build.LIB_CHECKED != build.LIB and build.BUILD_CHECKED != build.BUILD
+    assert os.path.dirname(build.LIB_CHECKED) == os.path.dirname(build.LIB)
+    import inspect
+    src = inspect.getsource(build.build)
+    assert "-DAT_DNS_CHECKS" in src
+    assert "AT_DNS_LIBRARY" in inspect.getsource(at_dns.load)
+
+
 def test_build_is_in_tree():
     assert os.path.dirname(build.LIB) == os.path.join(ROOT, "paper_2003_10561_gb300")
     assert build.up_to_date()
