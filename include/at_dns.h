@@ -377,7 +377,17 @@ int at_dns_batch_persistent(at_dns_batch_t* b, int32_t enable, int32_t* persiste
  * the context stays usable.  Errors: INVALID_ARG, CUDA. */
 int at_dns_wait_selftest(int32_t log2_polls, int32_t* gave_up);
 
-/* at_dns_tune on every member. */
+/* Autotune the batch's graph step as a whole: each member is first tuned
+ * alone (at_dns_tune); then the batch step is timed (trials steps after one
+ * untimed step) with the members on their paths before the call, on their
+ * own picks, and on every tile shape some member supports applied to each
+ * member that has it (its largest z chunk), and the fastest of these
+ * configurations is kept: members share the GPU in the graph, so the fastest
+ * path of a member alone is not always the fastest inside the batch.  The
+ * members' run states are saved in device checkpoints before the timed steps
+ * and restored after them, so the call leaves every state as it was; without
+ * device memory for the checkpoints the members keep their own picks.
+ * Errors: INVALID_ARG, STATE, CUDA. */
 int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials);
 
 /* Text of the last batch error (NULL batch: last failed batch create). */

@@ -1988,12 +1988,126 @@ int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode) {
 }
 
 int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials) {
+  NvtxRange nvtx_range("at_dns_batch_tune");
   if (!b) return AT_DNS_E_INVALID_ARG;
   b->err.clear();
-  for (size_t i = 0; i < b->m.size(); ++i) {
-    const int rc = at_dns_tune(b->m[i], delay_mode, trials, nullptr);
-    if (rc) return batch_fail(b, rc, "member " + std::to_string(i) + ": " + b->m[i]->err);
+  if (trials < 1 || delay_mode < 0 || delay_mode > 3) return batch_fail(b, AT_DNS_E_INVALID_ARG, "bad arguments");
+  const int M = (int)b->m.size();
+  for (int i = 0; i < M; ++i)
+    if (!b->m[i]->has_state) return batch_fail(b, AT_DNS_E_STATE, "member " + std::to_string(i) + " has no state");
+  auto path_of = [](const at_dns* h) { return Candidate{h->fused, h->TX, h->TY, h->ZC, h->paired}; };
+  auto same = [](const Candidate& a, const Candidate& c) {
+    return a.fused == c.fused && a.paired == c.paired && a.TX == c.TX && a.TY == c.TY && a.ZC == c.ZC;
+  };
+  std::vector<std::vector<Candidate>> configs(1, std::vector<Candidate>(M));
+  for (int i = 0; i < M; ++i) configs[0][i] = path_of(b->m[i]);   // the members' paths now
+  // each member's own pick, timed alone (right-hand sides: no state change)
+  {
+    std::vector<Candidate> own(M);
+    for (int i = 0; i < M; ++i) {
+      const int rc = at_dns_tune(b->m[i], delay_mode, trials, nullptr);
+      if (rc) return batch_fail(b, rc, "member " + std::to_string(i) + ": " + b->m[i]->err);
+      own[i] = path_of(b->m[i]);
+    }
+    configs.push_back(own);
   }
+  // the run states, so that the timed batch steps below leave them as they are
+  std::vector<void*> saved(M, nullptr);
+  auto release = [&]() {
+    for (void*& p : saved)
+      if (p) { cudaFree(p); p = nullptr; }
+  };
+  for (int i = 0; i < M; ++i) {
+    int64_t bytes = 0;
+    at_dns_checkpoint_size(b->m[i], &bytes);
+    if (cudaMalloc(&saved[i], (size_t)bytes) != cudaSuccess) {
+      // no room for the checkpoints: keep each member's own pick
+      (void)cudaGetLastError();
+      release();
+      batch_drop(b);
+      return AT_DNS_OK;
+    }
+    if (at_dns_checkpoint_save(b->m[i], saved[i], AT_DNS_DEVICE)) {
+      release();
+      return batch_fail(b, AT_DNS_E_CUDA, "member " + std::to_string(i) + ": " + b->m[i]->err);
+    }
+  }
+  auto restore = [&]() {
+    for (int i = 0; i < M; ++i)
+      if (at_dns_checkpoint_load(b->m[i], saved[i], AT_DNS_DEVICE)) return false;
+    return true;
+  };
+  // uniform shapes: every member on the same tile shape where it has one (its
+  // largest z chunk), else on its own pick
+  {
+    std::vector<Candidate> shapes;
+    for (int i = 0; i < M; ++i)
+      for (const Candidate& c : tune_candidates(b->m[i]->g, b->m[i]->p64)) {
+        bool seen = false;
+        for (const Candidate& s : shapes)
+          seen = seen || (s.fused == c.fused && s.paired == c.paired && s.TX == c.TX && s.TY == c.TY);
+        if (!seen) shapes.push_back(c);
+      }
+    for (const Candidate& s : shapes) {
+      std::vector<Candidate> cfg = configs[1];
+      for (int i = 0; i < M; ++i)
+        for (const Candidate& c : tune_candidates(b->m[i]->g, b->m[i]->p64))
+          if (c.fused == s.fused && c.paired == s.paired && c.TX == s.TX && c.TY == s.TY) { cfg[i] = c; break; }
+      bool dup = false;
+      for (const auto& k : configs) {
+        bool eq = true;
+        for (int i = 0; i < M; ++i) eq = eq && same(k[i], cfg[i]);
+        dup = dup || eq;
+      }
+      if (!dup) configs.push_back(cfg);
+    }
+  }
+  // time one batch step of every configuration (graph form), from the saved states
+  const bool was_persistent = b->allow_persistent;
+  b->allow_persistent = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300;
+  size_t pick = 0;
+  for (size_t k = 0; k < configs.size(); ++k) {
+    bool ok = true;
+    for (int i = 0; i < M && ok; ++i) {
+      const Candidate& c = configs[k][i];
+      ok = set_path(b->m[i], c.fused, c.TX, c.TY, c.ZC, c.paired) == AT_DNS_OK;
+    }
+    ok = ok && at_dns_batch_step(b, 1, delay_mode) == AT_DNS_OK;   // captures the graph
+    if (ok) {
+      cudaEventRecord(e0, b->st);
+      ok = at_dns_batch_step(b, trials, delay_mode) == AT_DNS_OK;
+      cudaEventRecord(e1, b->st);
+      cudaEventSynchronize(e1);
+    }
+    float ms = 0.f;
+    if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / trials < best) {
+      best = ms / trials;
+      pick = k;
+    }
+    b->err.clear();
+    if (!restore()) {
+      b->allow_persistent = was_persistent;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      release();
+      return batch_fail(b, AT_DNS_E_CUDA, "cannot restore the members' states");
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->allow_persistent = was_persistent;
+  for (int i = 0; i < M; ++i) {
+    const Candidate& c = configs[pick][i];
+    if (set_path(b->m[i], c.fused, c.TX, c.TY, c.ZC, c.paired) != AT_DNS_OK) {
+      release();
+      return batch_fail(b, AT_DNS_E_CUDA, "member " + std::to_string(i) + ": " + b->m[i]->err);
+    }
+  }
+  release();
   batch_drop(b);
   return AT_DNS_OK;
 }

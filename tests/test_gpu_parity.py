@@ -731,6 +731,36 @@ def test_persistent_wait_gives_up_and_context_survives(lib):
     s.close()
 
 
+def test_batch_tune_keeps_states_and_runs_the_paths_it_picks(lib):
+    """The batch autotuner times whole batch steps but restores every member's
+    run state (bit for bit, step counter included); afterwards each member
+    runs the path it picked, and a member stepped alone on its pre-tune path
+    and then on its tuned path gives the same bits as in the batch."""
+    specs, states = _fp32_ensemble_specs()
+    batch = lib.Batch(specs)
+    for m, U0 in zip(batch.members, states):
+        m.set_state(U0)
+    batch.step(3, "random")
+    before = [m.get_state() for m in batch.members]
+    paths0 = [(m.info()["kernel_path"], m.info()["tile"]) for m in batch.members]
+    batch.tune("random", trials=1)
+    for m, u in zip(batch.members, before):
+        assert np.array_equal(m.get_state(), u)
+        assert m.info()["step"] == 3
+    paths1 = [(m.info()["kernel_path"], m.info()["tile"]) for m in batch.members]
+    batch.step(4, "random")
+    for sp, m, U0, p0, p1 in zip(specs, batch.members, states, paths0, paths1):
+        alone = lib.Solver(**sp)
+        lib.at_dns_set_kernel_path(alone.h, p0[0], p0[1])
+        alone.set_state(U0)
+        alone.step(3, "random")
+        lib.at_dns_set_kernel_path(alone.h, p1[0], p1[1])
+        alone.step(4, "random")
+        assert np.array_equal(alone.get_state(), m.get_state()), (sp, p0, p1)
+        alone.close()
+    batch.close()
+
+
 def test_persistent_and_graph_batch_steps_agree(lib):
     """The same ensemble stepped with the persistent launch and with the graph
     of per-member branches agrees within PERSISTENT_BOUND (each member takes
