@@ -5,7 +5,7 @@ Input is a state as returned by ``Solver.get_state()`` -- FP64
 [5][nz][ny][nx] with the fifth variable E (total-energy form) or rho e
 (internal-energy form) -- on the periodic (2 pi)^3 box.  Derivatives here are
 spectral (exact for the grid's band-limited interpolant), so the analysis is
-independent of the finite differences it is used to judge.
+independent of the finite differences it is used to check.
 
 Definitions (nondimensional, rho_0 = T_0 = c_0 = 1):
 

@@ -1999,8 +1999,8 @@ int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials) {
   auto same = [](const Candidate& a, const Candidate& c) {
     return a.fused == c.fused && a.paired == c.paired && a.TX == c.TX && a.TY == c.TY && a.ZC == c.ZC;
   };
-  std::vector<std::vector<Candidate>> configs(1, std::vector<Candidate>(M));
-  for (int i = 0; i < M; ++i) configs[0][i] = path_of(b->m[i]);   // the members' paths now
+  std::vector<std::vector<Candidate>> plans(1, std::vector<Candidate>(M));
+  for (int i = 0; i < M; ++i) plans[0][i] = path_of(b->m[i]);   // the members' paths now
   // each member's own pick, timed alone (right-hand sides: no state change)
   {
     std::vector<Candidate> own(M);
@@ -2009,7 +2009,7 @@ int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials) {
       if (rc) return batch_fail(b, rc, "member " + std::to_string(i) + ": " + b->m[i]->err);
       own[i] = path_of(b->m[i]);
     }
-    configs.push_back(own);
+    plans.push_back(own);
   }
   // the run states, so that the timed batch steps below leave them as they are
   std::vector<void*> saved(M, nullptr);
@@ -2049,17 +2049,17 @@ int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials) {
         if (!seen) shapes.push_back(c);
       }
     for (const Candidate& s : shapes) {
-      std::vector<Candidate> cfg = configs[1];
+      std::vector<Candidate> cfg = plans[1];
       for (int i = 0; i < M; ++i)
         for (const Candidate& c : tune_candidates(b->m[i]->g, b->m[i]->p64))
           if (c.fused == s.fused && c.paired == s.paired && c.TX == s.TX && c.TY == s.TY) { cfg[i] = c; break; }
       bool dup = false;
-      for (const auto& k : configs) {
+      for (const auto& k : plans) {
         bool eq = true;
         for (int i = 0; i < M; ++i) eq = eq && same(k[i], cfg[i]);
         dup = dup || eq;
       }
-      if (!dup) configs.push_back(cfg);
+      if (!dup) plans.push_back(cfg);
     }
   }
   // time one batch step of every configuration (graph form), from the saved states
@@ -2070,10 +2070,10 @@ int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials) {
   cudaEventCreate(&e1);
   double best = 1e300;
   size_t pick = 0;
-  for (size_t k = 0; k < configs.size(); ++k) {
+  for (size_t k = 0; k < plans.size(); ++k) {
     bool ok = true;
     for (int i = 0; i < M && ok; ++i) {
-      const Candidate& c = configs[k][i];
+      const Candidate& c = plans[k][i];
       ok = set_path(b->m[i], c.fused, c.TX, c.TY, c.ZC, c.paired) == AT_DNS_OK;
     }
     ok = ok && at_dns_batch_step(b, 1, delay_mode) == AT_DNS_OK;   // captures the graph
@@ -2101,7 +2101,7 @@ int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials) {
   cudaEventDestroy(e1);
   b->allow_persistent = was_persistent;
   for (int i = 0; i < M; ++i) {
-    const Candidate& c = configs[pick][i];
+    const Candidate& c = plans[pick][i];
     if (set_path(b->m[i], c.fused, c.TX, c.TY, c.ZC, c.paired) != AT_DNS_OK) {
       release();
       return batch_fail(b, AT_DNS_E_CUDA, "member " + std::to_string(i) + ": " + b->m[i]->err);
