@@ -58,7 +58,7 @@ import numpy as np
 from .philox import philox4x32_10, split_seed
 from .stencils import Scheme
 
-SYNC, PERIODIC, RANDOM, FIXED = 0, 1, 2, 3
+SYNC, PERIODIC, RANDOM, FIXED, ORDERED = 0, 1, 2, 3, 4
 ENERGY_TOTAL, ENERGY_INTERNAL = 0, 1
 VISC_POWER, VISC_SUTHERLAND = 0, 1
 AB2, RK3 = 0, 1
@@ -163,13 +163,27 @@ def delay_map(cfg, step, mode):
     if mode == FIXED:                       # worst case of the stability analysis (Sec. 3.2)
         k[:] = cfg.max_delay
         return k
-    if mode == RANDOM:
+    if mode in (RANDOM, ORDERED):
         p = np.arange(P, dtype=np.uint64)[:, None]
         f = np.arange(6, dtype=np.uint64)[None, :]
         k0, k1 = split_seed(cfg.seed)
-        w0, _, _, _ = philox4x32_10(np.uint64(step), p, f, np.uint64(DELAY_STREAM_TAG), k0, k1)
-        # uniform integer on {0..L}: floor(w * (L+1) / 2^32), exact in integers
-        return ((w0.astype(np.uint64) * np.uint64(cfg.max_delay + 1)) >> np.uint64(32)).astype(np.int64)
+
+        def draw(m):
+            w0, _, _, _ = philox4x32_10(np.uint64(m), p, f, np.uint64(DELAY_STREAM_TAG), k0, k1)
+            # uniform integer on {0..L}: floor(w * (L+1) / 2^32), exact in integers
+            return ((w0.astype(np.uint64) * np.uint64(cfg.max_delay + 1)) >> np.uint64(32)).astype(np.int64)
+
+        if mode == RANDOM:
+            return draw(step)
+        # ordered: the newest level a PE has received never ages by more than
+        # one step per step (its neighbour's messages arrive in order, Alg. 1):
+        # k_n = min(d_n, k_{n-1} + 1), k = 0 before n0, d the draws of RANDOM.
+        # Unrolled, k_n = min over j of (d_{n-j} + j) and (n - n0 + 1); terms
+        # with j > L exceed d_n and cannot be the minimum.
+        k = draw(step)
+        for j in range(1, min(cfg.max_delay, step - n0) + 1):
+            k = np.minimum(k, draw(step - j) + j)
+        return np.minimum(k, step - n0 + 1)
     raise ValueError("unknown delay mode")
 
 

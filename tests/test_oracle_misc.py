@@ -5,6 +5,8 @@ seeded input generator.
   synchronous start-up steps and in synchronous mode; periodic delays cycle
   0..c_r-1 with an exactly uniform histogram (Fig. del_pdf(d)); random delays
   are bounded by L and uniform (chi-square), independent per PE face;
+  ordered random delays follow k_n = min(d_n, k_{n-1} + 1) (messages arrive
+  in order, Alg. 1);
 * forcing (Sec. 4.2): coefficients orthogonal to their wavevector, the field
   real, divergence-free and supported on |kappa| <= kappa_f; the OU variance is
   stationary;
@@ -66,6 +68,33 @@ def test_random_delay_uses_philox_word0():
     k0, k1 = split_seed(cfg.seed)
     w0 = int(philox4x32_10(n, p, f, 0x4154, k0, k1)[0])
     assert ns.delay_map(cfg, n, ns.RANDOM)[p, f] == (w0 * 4) >> 32
+
+
+@pytest.mark.parametrize("L", [0, 1, 2, 4])
+def test_ordered_random_delays_follow_the_arrival_recursion(L):
+    """Ordered random delays (a PE's messages arrive in order, Alg. 1): the
+    closed form equals the recursion k_n = min(d_n, k_{n-1} + 1) iterated step
+    by step from k = 0 at the end of the start-up, with d the draws of the
+    random mode; hence k never grows by more than one per step, never exceeds
+    the step's draw or L, is zero through the start-up, and is identically
+    zero for L = 0.  It still reaches L (a message late L steps)."""
+    cfg = ns.Config(n=(24, 24, 24), pes=(3, 3, 2), max_delay=L, seed=2024)
+    n0 = cfg.n_levels
+    k = np.zeros((cfg.n_pes, 6), dtype=np.int64)       # k_{n0 - 1}
+    seen_max = 0
+    for n in range(n0 + 300):
+        got = ns.delay_map(cfg, n, ns.ORDERED)
+        if n < n0:
+            assert not got.any()
+            continue
+        d = ns.delay_map(cfg, n, ns.RANDOM)
+        k = np.minimum(d, k + 1)
+        assert np.array_equal(got, k), n
+        assert (got <= d).all() and (got >= 0).all() and (got <= L).all()
+        seen_max = max(seen_max, int(got.max()))
+    assert seen_max == L
+    # a pure function of (seed, step, PE, face): a late step without its past
+    assert np.array_equal(ns.delay_map(cfg, 2 ** 31 + 7, ns.ORDERED), ns.delay_map(cfg, 2 ** 31 + 7, ns.ORDERED))
 
 
 def test_forcing_modes_shell():
