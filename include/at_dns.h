@@ -73,6 +73,12 @@ extern "C" {
 #define AT_DNS_RANDOM    2   /* SAA: k iid uniform on {0..L} (Algorithm 1) */
 #define AT_DNS_FIXED     3   /* k = L on every face after the start-up: the worst case
                                 of the stability analysis (Sec. 3.2) */
+#define AT_DNS_ORDERED   4   /* SAA with ordered arrivals: a PE's messages arrive in order
+                                (Algorithm 1 tests its receives each step), so the newest
+                                level received ages by at most one step per step:
+                                k_n = min(d_n, k_{n-1} + 1) over the AT_DNS_RANDOM draws d,
+                                k = 0 through the start-up; a pure function of
+                                (seed, n, PE, face) via the last L + 1 draws */
 
 /* precision forms */
 #define AT_DNS_P64  0        /* FP64 storage and arithmetic */

@@ -24,7 +24,7 @@ AT_DNS_E_TIMEOUT = -8
 AT_DNS_E_BOUNDS = -9
 AT_DNS_NOALLOC_MAX_POINTS = 262144
 
-AT_DNS_SYNC, AT_DNS_PERIODIC, AT_DNS_RANDOM, AT_DNS_FIXED = 0, 1, 2, 3
+AT_DNS_SYNC, AT_DNS_PERIODIC, AT_DNS_RANDOM, AT_DNS_FIXED, AT_DNS_ORDERED = 0, 1, 2, 3, 4
 AT_DNS_P64, AT_DNS_P32, AT_DNS_P32C = 0, 1, 2
 AT_DNS_HOST, AT_DNS_DEVICE = 0, 1
 AT_DNS_PATH_AUTO, AT_DNS_PATH_MULTIPASS, AT_DNS_PATH_FUSED, AT_DNS_PATH_PAIRED = 0, 1, 2, 3
@@ -34,7 +34,8 @@ AT_DNS_AB2, AT_DNS_RK3 = 0, 1
 PATHS = {"auto": AT_DNS_PATH_AUTO, "multipass": AT_DNS_PATH_MULTIPASS, "fused": AT_DNS_PATH_FUSED,
          "paired": AT_DNS_PATH_PAIRED}
 
-MODES = {"sync": AT_DNS_SYNC, "periodic": AT_DNS_PERIODIC, "random": AT_DNS_RANDOM, "fixed": AT_DNS_FIXED}
+MODES = {"sync": AT_DNS_SYNC, "periodic": AT_DNS_PERIODIC, "random": AT_DNS_RANDOM, "fixed": AT_DNS_FIXED,
+         "ordered": AT_DNS_ORDERED}
 PRECISIONS = {"p64": AT_DNS_P64, "p32": AT_DNS_P32, "p32c": AT_DNS_P32C}
 
 

@@ -71,8 +71,8 @@ struct at_dns {
   std::string err;
   DevState* ds = nullptr;       // device copy of (n, first, cur)
   // captured one-step graphs per delay mode (replayed by at_dns_step)
-  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
-  double gdt[4] = {0, 0, 0, 0};    // dt the graphs were captured with
+  cudaGraphExec_t gexec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double gdt[5] = {0, 0, 0, 0, 0};    // dt the graphs were captured with
   bool use_graphs = true;
   // kernel path: fused single pass on TX x TY tiles marching ZC planes, or multi-pass
   bool fused = false;
@@ -736,7 +736,7 @@ bool pick_fused_shape(const Geom& g, int& TX, int& TY, int& ZC) {
 }
 
 void drop_graphs(at_dns* h) {
-  for (int m = 0; m < 4; ++m)
+  for (int m = 0; m < 5; ++m)
     if (h->gexec[m]) {
       cudaGraphExecDestroy(h->gexec[m]);
       h->gexec[m] = nullptr;
@@ -1321,7 +1321,8 @@ int at_dns_get_state(at_dns_t* h, double* u_out, int where) {
 }
 
 static int check_mode(at_dns* h, int mode) {
-  if (mode != AT_DNS_SYNC && mode != AT_DNS_PERIODIC && mode != AT_DNS_RANDOM && mode != AT_DNS_FIXED)
+  if (mode != AT_DNS_SYNC && mode != AT_DNS_PERIODIC && mode != AT_DNS_RANDOM && mode != AT_DNS_FIXED &&
+      mode != AT_DNS_ORDERED)
     return fail(h, AT_DNS_E_INVALID_ARG, "unknown delay mode");
   if (h->cfg.integrator == AT_DNS_RK3 && mode != AT_DNS_SYNC)
     return fail(h, AT_DNS_E_UNSUPPORTED, "the RK3 integrator runs synchronous steps only");
@@ -1613,8 +1614,8 @@ struct at_dns_batch {
   cudaEvent_t fork = nullptr, done = nullptr;
   cudaStream_t st = nullptr;          // batch stream
   bool own_st = false;
-  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
-  std::vector<std::string> gkey[4];   // member path + dt each graph was captured with
+  cudaGraphExec_t gexec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  std::vector<std::string> gkey[5];   // member path + dt each graph was captured with
   std::string err;
   // persistent single-launch step (eligible FP32 batches)
   bool allow_persistent = false;      // the persistent single-launch step is opt-in
@@ -1656,7 +1657,7 @@ int batch_fail(at_dns_batch* b, int code, const std::string& msg) {
 }
 
 void batch_drop(at_dns_batch* b) {
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 5; ++k)
     if (b->gexec[k]) { cudaGraphExecDestroy(b->gexec[k]); b->gexec[k] = nullptr; }
 }
 
@@ -1857,7 +1858,7 @@ int at_dns_batch_step(at_dns_batch_t* b, int32_t nsteps, int32_t delay_mode) {
   NvtxRange nvtx_range("at_dns_batch_step");
   if (!b) return AT_DNS_E_INVALID_ARG;
   b->err.clear();
-  if (nsteps < 0 || delay_mode < 0 || delay_mode > 3) return batch_fail(b, AT_DNS_E_INVALID_ARG, "bad arguments");
+  if (nsteps < 0 || delay_mode < 0 || delay_mode > 4) return batch_fail(b, AT_DNS_E_INVALID_ARG, "bad arguments");
   const int M = (int)b->m.size();
   std::vector<std::string> key(M);
   for (int i = 0; i < M; ++i) {
@@ -1991,7 +1992,7 @@ int at_dns_batch_tune(at_dns_batch_t* b, int32_t delay_mode, int32_t trials) {
   NvtxRange nvtx_range("at_dns_batch_tune");
   if (!b) return AT_DNS_E_INVALID_ARG;
   b->err.clear();
-  if (trials < 1 || delay_mode < 0 || delay_mode > 3) return batch_fail(b, AT_DNS_E_INVALID_ARG, "bad arguments");
+  if (trials < 1 || delay_mode < 0 || delay_mode > 4) return batch_fail(b, AT_DNS_E_INVALID_ARG, "bad arguments");
   const int M = (int)b->m.size();
   for (int i = 0; i < M; ++i)
     if (!b->m[i]->has_state) return batch_fail(b, AT_DNS_E_STATE, "member " + std::to_string(i) + " has no state");

@@ -244,16 +244,36 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 constexpr uint32_t kDelayTag = 0x4154u;
 constexpr uint32_t kForceTag = 0x464Fu;
 
+// The random delay draw of face f of PE p at step n: uniform on {0..L} from
+// word 0 of the counter-based generator.
+__device__ __forceinline__ int delay_draw(long long n, int p, int f, int L, uint32_t k0, uint32_t k1) {
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)n, (uint32_t)p, (uint32_t)f, kDelayTag), k0, k1);
+  return (int)(((unsigned long long)w.x * (unsigned long long)(L + 1)) >> 32);
+}
+
 // Delay of face f of PE p at step n (Sec. 3.1, Algorithms 1 and 2); the
-// first L + T_l steps are synchronous.
+// first L + T_l steps are synchronous.  Mode 4 (ordered random delays): the
+// neighbour's messages arrive in order, so the newest level received ages by
+// at most one step per step, k_n = min(d_n, k_{n-1} + 1) over the draws d of
+// mode 2 with k = 0 before the start-up ends; unrolled, the minimum over
+// j <= min(L, n - n0) of d_{n-j} + j and of n - n0 + 1 (a pure function of
+// the step, like every other mode).
 __device__ __forceinline__ int delay_of(int mode, long long n, int p, int f, int L, int tl, int cr,
                                         uint32_t k0, uint32_t k1) {
   const long long n0 = L + tl;
   if (mode == 0 || n < n0) return 0;
   if (mode == 1) return (int)((n - n0) % cr);
   if (mode == 3) return L;                  // fixed worst case (stability scans, Sec. 3.2)
-  const uint4 w = philox4x32_10(make_uint4((uint32_t)n, (uint32_t)p, (uint32_t)f, kDelayTag), k0, k1);
-  return (int)(((unsigned long long)w.x * (unsigned long long)(L + 1)) >> 32);
+  int k = delay_draw(n, p, f, L, k0, k1);
+  if (mode == 4) {
+    const long long jmax = n - n0 < L ? n - n0 : L;
+    for (long long j = 1; j <= jmax; ++j) {
+      const int c = delay_draw(n - j, p, f, L, k0, k1) + (int)j;
+      k = c < k ? c : k;
+    }
+    if (n - n0 + 1 < k) k = (int)(n - n0 + 1);
+  }
+  return k;
 }
 
 // PE-local 4th-order first-derivative stencils of the mixed-derivative rule

@@ -60,7 +60,7 @@ def ocfg(n, pes, **kw):
 
 
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("mode", ["sync", "periodic", "random", "fixed"])
+@pytest.mark.parametrize("mode", ["sync", "periodic", "random", "fixed", "ordered"])
 def test_delay_map_bit_exact(lib, mode):
     s = make(lib, (40, 30, 20), (4, 3, 2), mu0=0.01, dt=1e-3, max_delay=3, comm_period=4,
              seed=0x0123456789ABCDEF)
@@ -84,6 +84,8 @@ CASES = [
     ((48, 32, 24), (3, 2, 3), "periodic", 9, 2),      # 16 x 16 x 8 PEs
     ((32, 16, 24), (1, 2, 3), "random", 12, 3),       # x without faces, periodic wrap in a tile
     ((16, 16, 16), (2, 2, 2), "fixed", 9, 2),         # the worst case of the stability scans
+    ((16, 16, 16), (2, 2, 2), "ordered", 11, 3),      # ordered random delays (in-order arrivals)
+    ((15, 12, 20), (3, 2, 4), "ordered", 12, 2),
 ]
 
 
@@ -185,7 +187,7 @@ def test_config1_steps_parity_fp64(lib, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
-@pytest.mark.parametrize("mode", ["random", "periodic"])
+@pytest.mark.parametrize("mode", ["random", "periodic", "ordered"])
 def test_at_steps_parity_fp64(lib, mode, path):
     """16^3, 2x2x2 PEs, AT delays from the start-up on: 100 AB2 steps."""
     n, pes = (16, 16, 16), (2, 2, 2)
@@ -218,7 +220,7 @@ def test_zero_delay_equals_sync_fp64(lib):
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", ["p32", "p32c"])
 @pytest.mark.parametrize("path", PATHS32)
-@pytest.mark.parametrize("n,pes,mode,step,L", CASES[:3] + CASES[5:7])
+@pytest.mark.parametrize("n,pes,mode,step,L", CASES[:3] + CASES[5:7] + CASES[-2:-1])
 def test_rhs_parity_fp32(lib, n, pes, mode, step, L, path, prec):
     U0 = synth.initial_state(n, k0=3.0, mach_t=0.3, seed=11)
     c = ocfg(n, pes, mu0=0.02, dt=2e-3, max_delay=L, comm_period=L + 1, seed=77)
