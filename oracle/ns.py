@@ -44,6 +44,8 @@ Readings where the paper is silent:
   shared face have independent delays; a direction with one PE has no faces.
 * Quantity extrapolated by the AT weights: the differentiated quantity
   (flux, velocity component, temperature) evaluated at each delayed level.
+  Config.extrapolate_state takes the other reading: the state U is
+  extrapolated to level n first and the quantity evaluated once from it.
 * AB2 start: the first step after a state is set is a forward-Euler step.
 * Random delays: iid uniform on {0..L} from Philox4x32-10; periodic delays
   k = (n - n0) mod c_r; n0 = L + T_l synchronous start-up steps.
@@ -90,6 +92,7 @@ class Config:
     visc_law: int = VISC_POWER       # mu0 T^omega, or Sutherland with S = suth_s
     suth_s: float = 0.368
     integrator: int = AB2            # AB2, or RK3 (synchronous steps only)
+    extrapolate_state: bool = False  # AT ghosts: q of the extrapolated state, not the extrapolated q
 
     @property
     def scheme(self):
@@ -240,7 +243,7 @@ def _face_delay_field(cfg, delays, d):
     return np.broadcast_to(k, pe.shape)
 
 
-def at_derivative(cfg, qlevels, d, delays, order):
+def at_derivative(cfg, qlevels, d, delays, order, qext=None):
     """First (order=1) or second (order=2) AT derivative in direction d.
 
     qlevels[l] is the quantity at level n-l.  Literal Table B: the standard
@@ -248,6 +251,11 @@ def at_derivative(cfg, qlevels, d, delays, order):
     PE taken at level n-k-l, and the T_l results are weighted by w_l(k).
     Points inside the PE always use level n.  A direction with one PE is a
     plain periodic stencil at level n.
+
+    qext (the other reading of what Table B extrapolates): qext[k] is the
+    quantity of the state extrapolated to level n from the levels n-k-l,
+    q(sum_l w_l(k) U^{n-k-l}); the points outside the PE then take qext[k]
+    and the stencil is evaluated once.
     """
     sc = cfg.scheme
     stencil, denom = (sc.d1, sc.d1_den * cfg.dx[d]) if order == 1 else \
@@ -261,6 +269,16 @@ def at_derivative(cfg, qlevels, d, delays, order):
     nloc = cfg.nloc[d]
     li = _coord(cfg, d) % nloc
     kf = _face_delay_field(cfg, delays, d)
+    if qext is not None:
+        X = np.stack(qext)                      # [delay k, z, y, x]
+        out = np.zeros_like(qlevels[0])
+        for off, c in stencil:
+            inside = (li + off >= 0) & (li + off < nloc)
+            q0 = np.roll(qlevels[0], -off, axis=ax)
+            shifted = np.roll(X, -off, axis=ax + 1)
+            qk = np.take_along_axis(shifted, np.broadcast_to(kf, kf.shape)[None], axis=0)[0]
+            out += c * np.where(inside, q0, qk)
+        return out / denom
     Q = np.stack(qlevels)                       # [level, z, y, x]
     out = np.zeros_like(qlevels[0])
     for l in range(sc.T):
@@ -417,11 +435,26 @@ def rhs(cfg, levels, delays, fhat=None, return_aux=False):
     def q_levels(name):
         return [quantity(cfg, levels[l], name) for l in range(nlev)]
 
+    # the state extrapolated to level n for every delay k (the other reading
+    # of Table B's weights): U_k = sum_l w_l(k) U^{n-k-l}
+    if cfg.extrapolate_state:
+        sc = cfg.scheme
+        Uext = []
+        for k in range(cfg.max_delay + 1):
+            w = sc.weights(k)
+            Uk = w[0] * levels[k]
+            for l in range(1, sc.T):
+                Uk = Uk + w[l] * levels[k + l]
+            Uext.append(Uk)
+
+    def q_ext(name):
+        return [quantity(cfg, Uk, name) for Uk in Uext] if cfg.extrapolate_state else None
+
     def D1(name, d):
-        return at_derivative(cfg, q_levels(name), d, delays, 1)
+        return at_derivative(cfg, q_levels(name), d, delays, 1, q_ext(name))
 
     def D2(name, d):
-        return at_derivative(cfg, q_levels(name), d, delays, 2)
+        return at_derivative(cfg, q_levels(name), d, delays, 2, q_ext(name))
 
     rho, vel, p, T = primitives(cfg, levels[0])
     R = np.zeros_like(levels[0])

@@ -6,7 +6,10 @@ Each derivative is written out as an explicit list of (offset, time level,
 weight) terms built from Table B (Appendix B): the standard stencil of the
 configured order (4 or 6) repeated for l = 0 .. T_l-1, its points outside the
 PE taken at level n-k-l and weighted by w_l(k) -- the same rows the paper
-prints, read per point.  Mixed derivatives follow the three-step rule of
+prints, read per point.  Under the other reading of what those weights
+extrapolate (Config.extrapolate_state), a point outside the PE instead takes
+the quantity of the extrapolated state sum_l w_l(k) U^{n-k-l} at that point,
+once.  Mixed derivatives follow the three-step rule of
 Sec. 2.1.  Pure Python loops, so it is used on tiny grids (as a brute-force
 check of the vectorised oracle) and on a few hundred sampled points of
 full-size grids (parity of the CUDA path).
@@ -49,12 +52,20 @@ class PointOracle:
         return (pos[0] % n[0], pos[1] % n[1], pos[2] % n[2])
 
     def U(self, l, pos):
+        """U at one point: l is a level index n-l, or ("x", k) for the state
+        extrapolated to level n from the levels n-k-l with the weights w_l(k)."""
         pos = self._wrap(pos)
         key = (l, pos)
         if key not in self._ucache:
-            lv = self.level(l)
-            x, y, z = pos
-            self._ucache[key] = [float(lv[v, z, y, x]) for v in range(5)]
+            if isinstance(l, tuple):
+                k = l[1]
+                w = self.sc.weights(k)
+                self._ucache[key] = [sum(w[j] * self.U(k + j, pos)[v] for j in range(self.sc.T))
+                                     for v in range(5)]
+            else:
+                lv = self.level(l)
+                x, y, z = pos
+                self._ucache[key] = [float(lv[v, z, y, x]) for v in range(5)]
         return self._ucache[key]
 
     def prim(self, l, pos):
@@ -114,6 +125,9 @@ class PointOracle:
             k = int(self.delays[p][2 * d + 1])
         else:
             k = 0
+        if getattr(cfg, "extrapolate_state", False):
+            return [(off, 0 if 0 <= li + off < nloc else ("x", k), c / denom)
+                    for off, c in stencil]
         w = sc.weights(k)
         out = []
         for l in range(sc.T):

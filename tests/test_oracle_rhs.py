@@ -12,6 +12,11 @@
 * Kinetic-energy budget (Eq. (meantke)): dK/dt from the RHS matches
   <p theta> - <sigma_ij S_ij> + <rho f_i u_i> at 4th order.
 * Brute force: the vectorised RHS equals the pointwise Table B term sums.
+* The other reading of the extrapolation (the state extrapolated first, the
+  quantity evaluated once): equal to the default without delays and for the
+  linear continuity fluxes, exact on a steady history, 4th order on the
+  manufactured solution under random delays, and equal to its own pointwise
+  brute force.
 """
 import math
 
@@ -170,6 +175,83 @@ def test_brute_force_pointwise_matches_vectorised(pes):
     rng = np.random.default_rng(0)
     pts = [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(60)]
     pts += [(0, 0, 0), (N - 1, N - 1, N - 1), (1, 5, 6), (5, 6, 1), (6, 0, 11)]
+    scale = np.abs(R).max(axis=(1, 2, 3))
+    for (x, y, z) in pts:
+        r = po.rhs((x, y, z))
+        for v in range(5):
+            assert abs(r[v] - R[v, z, y, x]) <= 1e-13 * scale[v], (x, y, z, v)
+
+
+# --------------------------------------------------------------------------
+# The other reading of Table B's extrapolation: q(sum_l w_l U^{n-k-l})
+# --------------------------------------------------------------------------
+def _xcfg(cfg):
+    return ns.Config(**{**cfg.__dict__, "extrapolate_state": True})
+
+
+def test_extrapolate_state_equals_default_without_delays():
+    # k = 0 has weights (1, 0, ..): both readings take level n, bit for bit
+    N = 16
+    cfg = _cfg(N, (2, 2, 2))
+    hist = synth.history(_turb_state(N, seed=3), cfg.n_levels, eps=2e-2)
+    d = ns.delay_map(cfg, 40, ns.SYNC)
+    assert np.array_equal(ns.rhs(cfg, hist, d), ns.rhs(_xcfg(cfg), hist, d))
+
+
+def test_extrapolate_state_linear_quantities_agree():
+    # The continuity fluxes rho u_d are the state's own components, linear in
+    # U, so both readings give the same R_rho up to rounding; the nonlinear
+    # fluxes differ at the size of the extrapolation error.
+    N = 16
+    cfg = _cfg(N, (2, 2, 2))
+    hist = synth.history(_turb_state(N, seed=3), cfg.n_levels, eps=2e-2)
+    d = _random_delays(cfg)
+    a, b = ns.rhs(cfg, hist, d), ns.rhs(_xcfg(cfg), hist, d)
+    assert np.max(np.abs(a[0] - b[0])) <= 1e-12 * np.max(np.abs(a[0]))
+    assert np.max(np.abs(a[4] - b[4])) > 1e-9 * np.max(np.abs(a[4]))
+
+
+def test_extrapolate_state_steady_history_is_exact():
+    # All levels equal: the weights sum to one, so the extrapolated state is
+    # the state and both readings coincide with the synchronous RHS.
+    N = 16
+    cfg = _cfg(N, (2, 2, 2))
+    U = _turb_state(N, seed=5)
+    hist = [U.copy() for _ in range(cfg.n_levels)]
+    d = _random_delays(cfg)
+    sync = ns.rhs(cfg, hist, np.zeros_like(d))
+    scale = np.abs(sync).max(axis=(1, 2, 3))[:, None, None, None]
+    assert np.max(np.abs(ns.rhs(_xcfg(cfg), hist, d) - sync) / scale) < 1e-12
+
+
+def test_extrapolate_state_manufactured_solution_fourth_order():
+    fc, fr = mms.exact(GAMMA, PR, MU0, OMEGA)
+    errs = []
+    for N in (16, 32, 64):
+        cfg = _xcfg(_cfg(N, (2, 2, 2)))
+        dt = 0.5 * (2 * math.pi / N) ** 2
+        levels = [mms.evaluate(fc, cfg.n, 0.4 - l * dt) for l in range(cfg.n_levels)]
+        R = ns.rhs(cfg, levels, _random_delays(cfg))
+        Rex = mms.evaluate(fr, cfg.n, 0.4)
+        errs.append([float(np.max(np.abs(R[v] - Rex[v])) / np.max(np.abs(Rex[v]))) for v in range(5)])
+    for v in range(5):
+        o1 = math.log2(errs[0][v] / errs[1][v])
+        o2 = math.log2(errs[1][v] / errs[2][v])
+        assert o2 > 3.5 and o1 > 3.0, (v, errs, o1, o2)
+
+
+@pytest.mark.parametrize("pes,energy", [((2, 2, 2), ns.ENERGY_TOTAL), ((3, 1, 2), ns.ENERGY_INTERNAL)])
+def test_extrapolate_state_brute_force_pointwise(pes, energy):
+    N = 12
+    cfg = _xcfg(_cfg(N, pes, energy_form=energy))
+    U = _turb_state(N, seed=4)
+    hist = synth.history(U, cfg.n_levels, eps=2e-2)
+    delays = ns.delay_map(ns.Config(**{**cfg.__dict__, "seed": 5}), 30, ns.RANDOM)
+    R = ns.rhs(cfg, hist, delays)
+    po = PointOracle(cfg, lambda l: hist[l], delays)
+    rng = np.random.default_rng(1)
+    pts = [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(40)]
+    pts += [(0, 0, 0), (N - 1, N - 1, N - 1), (1, 5, 6), (5, 6, 1)]
     scale = np.abs(R).max(axis=(1, 2, 3))
     for (x, y, z) in pts:
         r = po.rhs((x, y, z))
