@@ -139,6 +139,13 @@ typedef struct {
                             of its buffers from -- e.g. a framework tensor; OOM if too small.
                             Each handle (and each batch member) needs its own region. */
   size_t   pool_bytes;   /* size of the pool                                            */
+  int32_t  extrapolate_state;
+                         /* what Table B's weights extrapolate at a delayed stencil point
+                            (Sec. 2.1, Eq. (at)): 0 (default) each differentiated
+                            quantity -- flux, velocity, temperature -- at the levels
+                            n-k-l; 1 the state U, the quantities then evaluated once from
+                            sum_l w_l(k) U^{n-k-l}.  The two agree without delays and for
+                            quantities linear in U                                      */
 } at_dns_config_t;
 
 /* kernel paths (same results up to rounding): the multi-pass path stores

@@ -51,6 +51,7 @@ class at_dns_config_t(ctypes.Structure):
         ("kernel_path", ctypes.c_int32), ("order", ctypes.c_int32),
         ("energy_form", ctypes.c_int32), ("visc_law", ctypes.c_int32), ("sutherland_s", ctypes.c_double),
         ("integrator", ctypes.c_int32), ("pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t),
+        ("extrapolate_state", ctypes.c_int32),
     ]
 
 

@@ -869,6 +869,7 @@ struct CkptHeader {
   // the configuration the run state belongs to (compared on load)
   int32_t n[3], pes[3];
   int32_t precision, order, energy_form, visc_law, integrator, forcing, max_delay, comm_period;
+  int32_t extrapolate_state;
   uint64_t seed, f_seed;
   double gamma, prandtl, mu0, visc_exp, sutherland_s, kf, f_amp, f_tcorr;
   // the run state's scalars
@@ -901,6 +902,7 @@ void ckpt_layout(const at_dns* h, CkptHeader& H) {
   H.forcing = c.forcing;
   H.max_delay = c.max_delay;
   H.comm_period = c.comm_period;
+  H.extrapolate_state = c.extrapolate_state;
   H.seed = c.seed;
   H.f_seed = c.f_seed;
   H.gamma = c.gamma;
@@ -947,6 +949,7 @@ const char* ckpt_mismatch(const CkptHeader& a, const CkptHeader& b) {
   if (a.forcing != b.forcing) return "forcing";
   if (a.max_delay != b.max_delay) return "max_delay";
   if (a.comm_period != b.comm_period) return "comm_period";
+  if (a.extrapolate_state != b.extrapolate_state) return "extrapolate_state";
   if (a.seed != b.seed) return "seed";
   if (a.f_seed != b.f_seed) return "f_seed";
   if (a.gamma != b.gamma || a.prandtl != b.prandtl || a.mu0 != b.mu0 || a.visc_exp != b.visc_exp ||
@@ -1081,6 +1084,7 @@ int at_dns_config_default(at_dns_config_t* c) {
   c->visc_law = AT_DNS_VISC_POWER;
   c->sutherland_s = 0.368;
   c->integrator = AT_DNS_AB2;
+  c->extrapolate_state = 0;
   return AT_DNS_OK;
 }
 
@@ -1124,6 +1128,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
     else if (c.visc_law != AT_DNS_VISC_POWER && c.visc_law != AT_DNS_VISC_SUTHERLAND) bad = "unknown visc_law";
     else if (c.visc_law == AT_DNS_VISC_SUTHERLAND && !(c.sutherland_s > 0)) bad = "sutherland_s must be > 0";
     else if (c.integrator != AT_DNS_AB2 && c.integrator != AT_DNS_RK3) bad = "unknown integrator";
+    else if (c.extrapolate_state != 0 && c.extrapolate_state != 1) bad = "extrapolate_state must be 0 or 1";
     else if (c.pool && ((uintptr_t)c.pool & 255)) bad = "pool must be 256-byte aligned";
   }
   if (bad.empty() && (long long)c.n[0] * c.n[1] * c.n[2] >= (1LL << 31)) bad = "grids must hold fewer than 2^31 points";
@@ -1141,6 +1146,7 @@ int at_dns_create(const at_dns_config_t* cfg, at_dns_t** out) {
   h->ssize = h->p64 ? 8 : 4;
   Geom& g = h->g;
   g.npts = 1;
+  g.xstate = c.extrapolate_state;
   for (int d = 0; d < 3; ++d) {
     g.n[d] = c.n[d];
     g.pes[d] = c.pes[d];

@@ -32,6 +32,8 @@ struct Geom {
   int n[3];          // points per direction
   int pes[3];        // PEs per direction
   int nl[3];         // points per PE per direction
+  int xstate;        // what Table B's weights extrapolate at a delayed stencil
+                     // point: 0 each differentiated quantity, 1 the state U
   long long npts;    // n0 n1 n2
   long long plane[3];// points of a plane normal to d: npts / n[d]
   long long stride[3];  // linear-index stride of direction d: 1, n0, n0 n1

@@ -253,6 +253,42 @@ __device__ __forceinline__ void ghost_point(const Geom& g, const Coef<S>& K, con
   }
   int wi[M + 1];
   at_weights<M>(k, wi);
+  if (g.xstate) {
+    // the other reading of Table B's extrapolation: the state U extrapolated
+    // to level n, sum_l w_l U^{n-k-l}, and the quantities evaluated once
+    S Ux[5];
+    if constexpr (sizeof(S) == 8) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        S a = S(wi[0]) * lv[0][v];
+#pragma unroll
+        for (int l = 1; l <= M; ++l) a = fma(S(wi[l]), lv[l][v], a);
+        Ux[v] = a;
+      }
+    } else {
+      // FP32: B + sum_l w_l (U_l - B) with B = level n-k truncated to FP32
+      // (the weights sum to one), each difference formed as in the
+      // quantity reading below, so that rounding stays relative to U and to
+      // the differences
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        float hb, lo, hi, lo2;
+        split_double(lv[0][v], hb, lo);
+        float e = (float)wi[0] * lo;
+#pragma unroll
+        for (int l = 1; l <= M; ++l) {
+          split_double(lv[l][v], hi, lo2);
+          e = fmaf((float)wi[l], (hi - hb) + lo2, e);
+        }
+        Ux[v] = hb + e;
+      }
+    }
+    S q[kNumGhostQ];
+    ghost_quantities(K, d, Ux, q);
+#pragma unroll
+    for (int qq = 0; qq < kNumGhostQ; ++qq) out[qq * qstride] = q[qq];
+    return;
+  }
   S acc[kNumGhostQ];
   if constexpr (sizeof(S) == 8) {
 #pragma unroll

@@ -49,6 +49,7 @@ int main(void) {
   F(at_dns_config_t, order) F(at_dns_info_t, order)
   F(at_dns_config_t, energy_form) F(at_dns_config_t, visc_law) F(at_dns_config_t, sutherland_s)
   F(at_dns_config_t, integrator) F(at_dns_config_t, pool) F(at_dns_config_t, pool_bytes)
+  F(at_dns_config_t, extrapolate_state)
   F(at_dns_stats_t, mom) F(at_dns_stats_t, min_p) F(at_dns_stats_t, unstable)
   F(at_dns_info_t, n_levels) F(at_dns_info_t, device_bytes) F(at_dns_info_t, kernels_per_step)
   F(at_dns_info_t, kernel_path) F(at_dns_info_t, tile)
@@ -88,6 +89,7 @@ def test_config_default(lib):
     ("n", (4, 32, 32)), ("pes", (3, 1, 1)), ("pes", (8, 1, 1)), ("gamma", 1.0),
     ("max_delay", -1), ("comm_period", 0), ("precision", 7), ("prandtl", 0.0), ("kernel_path", 9),
     ("order", 5), ("order", 8), ("energy_form", 2), ("visc_law", 3), ("sutherland_s", 0.0), ("integrator", 2),
+    ("extrapolate_state", 2),
 ])
 def test_create_rejects_bad_config_without_gpu(lib, field, value):
     cfg = at_dns.at_dns_config_default()
