@@ -395,10 +395,26 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
       };
       constexpr int XPR = CX / 2, XP = TY * XPR;        // x-row pairs
       constexpr int YPR = TX / 2, YP = (TY + 4) * YPR;  // y-column pairs
-      // one loop over both kinds of pair, so the passes spread evenly over the threads
-      for (int p = tid; p < XP + YP; p += PS::NT) {
-        if (p < XP) {
-        const int r = p / XPR, cxw = 2 * (p - r * XPR);
+      // one loop over both kinds of pair, so the passes spread evenly over the
+      // threads; the y-column pairs come first: their count, (TY + 4) TX / 2,
+      // is a multiple of 32 for every tile, so no warp holds pairs of both
+      // kinds.  The x-row pairs follow, the TY TX / 2 pairs of the tile's own
+      // columns (again whole warps) before the 2 TY x-halo pairs, so that the
+      // halo pairs' ghost loads do not diverge inside the warps that compute
+      // fluxes.
+      static_assert(YP % 32 == 0 && (TY * (TX / 2)) % 32 == 0, "pair groups fill whole warps");
+      constexpr int XPI = TY * (TX / 2);                // x-row pairs of the tile's own columns
+      for (int pi = tid; pi < XP + YP; pi += PS::NT) {
+        if (pi >= YP) {
+        const int p = pi - YP;
+        int r, cxw;
+        if (p < XPI) {
+          r = p / (TX / 2);
+          cxw = 2 + 2 * (p - r * (TX / 2));
+        } else {
+          r = (p - XPI) >> 1;
+          cxw = ((p - XPI) & 1) ? CX - 2 : 0;
+        }
         const int c = r * CX + cxw;
         const int xg = F.x0 - 2 + cxw, yg = F.y0 + r;
         const int cw = (r + 2) * CX + cxw;
@@ -420,7 +436,7 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
         st2(XR + XR_WZ * TY * CX + c, ddz(2, cw));
         st2(XR + XR_UZ * TY * CX + c, ddz(0, cw));
         } else {
-        const int py = p - XP;
+        const int py = pi;
         const int r = py / YPR, cxl = 2 * (py - r * YPR);
         const int c = r * TX + cxl;
         const int xg = F.x0 + cxl, yg = F.y0 - 2 + r;
@@ -648,18 +664,22 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
       f2 V = mu * fma2(gth[i], bc(1.0f / 3.0f), lap[i]);
 #pragma unroll
       for (int j = 0; j < 3; ++j) V = fma2(dmu[j], sm[i][j], V);
-      R[1 + i] = R[1 + i] + fma2(r, fo[i], V);
+      R[1 + i] = R[1 + i] + (PLAIN ? V : fma2(r, fo[i], V));   // (no forcing in PLAIN)
       work = fma2(vel[i], V, work);
     }
     const f2 heat = fma2(KP.cp_over_pr, fma2(dmu[0], dT[0], fma2(dmu[1], dT[1], dmu[2] * dT[2])), kappa * lap[3]);
     if (eform) R[4] = R[4] + fma2(bc(0.f) - p, theta, sigS + heat);
+    else if (PLAIN) R[4] = R[4] + (sigS + work + heat);
     else R[4] = R[4] + fma2(r, fma2(fo[0], vel[0], fma2(fo[1], vel[1], fo[2] * vel[2])), sigS + work + heat);
 
     if (nonpositive(r.x) || nonpositive(r.y)) health |= H_RHO;
     if (nonpositive(p.x) || nonpositive(p.y)) health |= H_P;
+    // (a step that updates checks U^{n+1}, which is not finite where R is not)
+    if (!update) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v)
-      if (nonfinite(R[v].x) || nonfinite(R[v].y)) health |= H_NONFINITE;
+      for (int v = 0; v < 5; ++v)
+        if (nonfinite(R[v].x) || nonfinite(R[v].y)) health |= H_NONFINITE;
+    }
 
     if (update) {
       const f2 Uo[5] = {r, m[0], m[1], m[2], Ecur};
@@ -736,7 +756,7 @@ __device__ __forceinline__ void fused2_tile(const Geom& g, const Coef<float>& K,
       const f2 o0 = Ag[2][1] - Ag[1][2], o1 = Ag[0][2] - Ag[2][0], o2 = Ag[1][0] - Ag[0][1];
       add(ST_ENST, fma2(o0, o0, fma2(o1, o1, o2 * o2)));
       add(ST_PTHETA, p * theta);
-      add(ST_FPOW, r * fma2(fo[0], vel[0], fma2(fo[1], vel[1], fo[2] * vel[2])));
+      if (!PLAIN) add(ST_FPOW, r * fma2(fo[0], vel[0], fma2(fo[1], vel[1], fo[2] * vel[2])));
       add(ST_U2, uu);
       add(ST_C, c);
       wmax = fmaxf(wmax, fmaxf(fmaxf(fabsf(vel[0].x), fabsf(vel[1].x)), fabsf(vel[2].x)) + c.x);
