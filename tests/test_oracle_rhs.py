@@ -224,7 +224,7 @@ def test_extrapolate_state_steady_history_is_exact():
     assert np.max(np.abs(ns.rhs(_xcfg(cfg), hist, d) - sync) / scale) < 1e-12
 
 
-def test_extrapolate_state_manufactured_solution_fourth_order():
+def _xstate_mms_orders():
     fc, fr = mms.exact(GAMMA, PR, MU0, OMEGA)
     errs = []
     for N in (16, 32, 64):
@@ -234,10 +234,23 @@ def test_extrapolate_state_manufactured_solution_fourth_order():
         R = ns.rhs(cfg, levels, _random_delays(cfg))
         Rex = mms.evaluate(fr, cfg.n, 0.4)
         errs.append([float(np.max(np.abs(R[v] - Rex[v])) / np.max(np.abs(Rex[v]))) for v in range(5)])
-    for v in range(5):
-        o1 = math.log2(errs[0][v] / errs[1][v])
-        o2 = math.log2(errs[1][v] / errs[2][v])
+    return [(math.log2(errs[0][v] / errs[1][v]), math.log2(errs[1][v] / errs[2][v])) for v in range(5)], errs
+
+
+def test_extrapolate_state_manufactured_solution_fourth_order():
+    orders, errs = _xstate_mms_orders()
+    for v, (o1, o2) in enumerate(orders):
         assert o2 > 3.5 and o1 > 3.0, (v, errs, o1, o2)
+
+
+def test_extrapolate_state_manufactured_solution_detects_unextrapolated_levels(monkeypatch):
+    """With Table B's weights replaced by (1, 0, 0) -- the delayed level taken
+    as it is, no extrapolation -- the reading's error is O(k dt) = O(dx^2) and
+    the 4th-order check above fails (guards its sensitivity to the weights)."""
+    from oracle import stencils
+    monkeypatch.setattr(stencils, "at_weights", lambda k: (1.0, 0.0, 0.0))
+    orders, errs = _xstate_mms_orders()
+    assert any(o2 < 3.0 for _, o2 in orders), (orders, errs)
 
 
 @pytest.mark.parametrize("pes,energy", [((2, 2, 2), ns.ENERGY_TOTAL), ((3, 1, 2), ns.ENERGY_INTERNAL)])
