@@ -46,6 +46,11 @@ Readings where the paper is silent:
   (flux, velocity component, temperature) evaluated at each delayed level.
   Config.extrapolate_state takes the other reading: the state U is
   extrapolated to level n first and the quantity evaluated once from it.
+* Mixed derivatives at PE faces: the three-step rule with one-sided stencils
+  (Sec. 2.1).  Config.mixed_central takes the other reading: the central
+  stencil everywhere, over the neighbour's gradient extrapolated with the
+  Table B weights beyond a face, so that zero delays give the single-PE
+  scheme.
 * AB2 start: the first step after a state is set is a forward-Euler step.
 * Random delays: iid uniform on {0..L} from Philox4x32-10; periodic delays
   k = (n - n0) mod c_r; n0 = L + T_l synchronous start-up steps.
@@ -93,6 +98,7 @@ class Config:
     suth_s: float = 0.368
     integrator: int = AB2            # AB2, or RK3 (synchronous steps only)
     extrapolate_state: bool = False  # AT ghosts: q of the extrapolated state, not the extrapolated q
+    mixed_central: bool = False      # mixed terms: central stencil over the neighbour's gradient
 
     @property
     def scheme(self):
@@ -344,6 +350,51 @@ def mixed_derivative(cfg, grad_b, grad_a, a, b):
     return np.where(interior, central, boundary)
 
 
+def mixed_central(cfg, grad_b, qb, a, b, delays):
+    """d/dx_a (d f/dx_b) by the central a-stencil at every point: the other
+    reading of the mixed terms at PE faces.
+
+    Stencil points inside the PE take the AT first derivative grad_b there.
+    A point across an a-face of delay k takes the neighbour's b-derivative
+    extrapolated to level n with the Table B weights: qb[k] is that field,
+    sum_l w_l(k) D_b f^{n-k-l} (or D_b of f of the extrapolated state), D_b
+    being the plain central stencil of the whole level.  Without delays this
+    is the central D_a D_b of the single-PE scheme.
+    """
+    sc = cfg.scheme
+    ax = _axis(a)
+    den = sc.d1_den * cfg.dx[a]
+    if cfg.pes[a] == 1:
+        return _apply(grad_b, sc.d1, ax) / den
+    nloc = cfg.nloc[a]
+    li = _coord(cfg, a) % nloc
+    kf = _face_delay_field(cfg, delays, a)
+    X = np.stack(qb)                            # [delay k, z, y, x]
+    out = np.zeros_like(grad_b)
+    for off, c in sc.d1:
+        inside = (li + off >= 0) & (li + off < nloc)
+        g_in = np.roll(grad_b, -off, axis=ax)
+        g_out = np.take_along_axis(np.roll(X, -off, axis=ax + 1), np.broadcast_to(kf, kf.shape)[None], axis=0)[0]
+        out += c * np.where(inside, g_in, g_out)
+    return out / den
+
+
+def ghost_gradients(cfg, flevels, b):
+    """Per delay k = 0 .. L: sum_l w_l(k) D_b f^{n-k-l}, D_b the plain
+    central first derivative of a whole level (flevels[l] = f at level n-l)."""
+    sc = cfg.scheme
+    den = sc.d1_den * cfg.dx[b]
+    D = [_apply(f, sc.d1, _axis(b)) / den for f in flevels]
+    out = []
+    for k in range(cfg.max_delay + 1):
+        w = sc.weights(k)
+        g = w[0] * D[k]
+        for l in range(1, sc.T):
+            g = g + w[l] * D[k + l]
+        out.append(g)
+    return out
+
+
 # --------------------------------------------------------------------------
 # forcing (Sec. 4.2): solenoidal, |kappa| <= kappa_f
 # --------------------------------------------------------------------------
@@ -480,7 +531,16 @@ def rhs(cfg, levels, delays, fhat=None, return_aux=False):
         for k in range(3):
             if k != i:
                 # mixed d/dx_i (d u_k/dx_k): grad in b=k is A[k][k], grad in a=i is A[k][i]
-                s = s + mixed_derivative(cfg, A[k][k], A[k][i], i, k)
+                if cfg.mixed_central:
+                    name = "u%d" % k
+                    if cfg.extrapolate_state:
+                        den = cfg.scheme.d1_den * cfg.dx[k]
+                        qb = [_apply(f, cfg.scheme.d1, _axis(k)) / den for f in q_ext(name)]
+                    else:
+                        qb = ghost_gradients(cfg, q_levels(name), k)
+                    s = s + mixed_central(cfg, A[k][k], qb, i, k, delays)
+                else:
+                    s = s + mixed_derivative(cfg, A[k][k], A[k][i], i, k)
         grad_theta.append(s)
 
     mu, dmu_dT = viscosity(cfg, T)

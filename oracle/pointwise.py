@@ -171,10 +171,45 @@ class PointOracle:
             s += c * gfun(tuple(p2))
         return s / (self.sc.d1_den * self.cfg.dx[d])
 
+    def _plain_d1(self, name, lev, pos, b):
+        """Central first derivative along b of quantity `name` at one level
+        (an index, or ("x", k) for the extrapolated state), no PE faces."""
+        s = 0.0
+        for off, c in self.sc.d1:
+            p2 = list(pos)
+            p2[b] += off
+            s += c * self.q(name, lev, tuple(p2))
+        return s / (self.sc.d1_den * self.cfg.dx[b])
+
+    def _ghost_grad(self, k, b, pos, kd):
+        """The neighbour's d u_k / d x_b at an outside point, extrapolated to
+        level n from the levels n-kd-l (or taken from the extrapolated state)."""
+        name = "u%d" % k
+        if getattr(self.cfg, "extrapolate_state", False):
+            return self._plain_d1(name, ("x", kd), pos, b)
+        w = self.sc.weights(kd)
+        return sum(w[l] * self._plain_d1(name, kd + l, pos, b) for l in range(self.sc.T))
+
     def mixed(self, k, a, b, pos):
         """d/dx_a (d u_k / d x_b) at pos."""
         gb = lambda p: self.grad(k, b, p)
         ga = lambda p: self.grad(k, a, p)
+        if getattr(self.cfg, "mixed_central", False):
+            # central a-stencil at every point; beyond an a-face the
+            # neighbour's extrapolated gradient
+            if self.cfg.pes[a] == 1:
+                return self._apply_d1(self.sc.d1, gb, pos, a)
+            nloc = self.cfg.nloc[a]
+            li = self.local(pos, a)
+            p = self.pe_of(pos)
+            kd = int(self.delays[p][2 * a]) if li < nloc // 2 else int(self.delays[p][2 * a + 1])
+            s = 0.0
+            for off, c in self.sc.d1:
+                p2 = list(pos)
+                p2[a] += off
+                p2 = tuple(p2)
+                s += c * (gb(p2) if 0 <= li + off < nloc else self._ghost_grad(k, b, p2, kd))
+            return s / (self.sc.d1_den * self.cfg.dx[a])
         if self._central_fits(pos, a) and self._central_fits(pos, b):
             return self._apply_d1(self.sc.d1, gb, pos, a)
         return 0.5 * (self._apply_d1(self._pe_local_stencil(pos, a), gb, pos, a)

@@ -15,27 +15,41 @@ import sympy as sp
 x, y, z, t = sp.symbols("x y z t", real=True)
 
 
-def fields():
-    """Smooth periodic rho, u, v, w, T (functions of x, y, z, t)."""
+def fields(mixed=False):
+    """Smooth periodic rho, u, v, w, T (functions of x, y, z, t).
+
+    In the default set each d u_k/d x_k depends on x_k alone and not on t, so
+    the mixed terms d/dx_i (d u_k/dx_k), i != k, of the viscous stress vanish
+    identically.  mixed=True multiplies each of those parts by a travelling
+    wave in another direction, so that every d u_k/d x_k depends on two
+    coordinates and on t, and d/dy (du/dx), d/dz (dv/dy) and d/dx (dw/dz) --
+    a mixed term with each direction outermost -- are nonzero."""
     rho = 1 + sp.Rational(1, 10) * sp.sin(x + sp.Rational(3, 10) * t) * sp.cos(y) \
         + sp.Rational(1, 20) * sp.sin(z - sp.Rational(1, 5) * t)
-    u = sp.Rational(1, 5) * sp.sin(y) * sp.cos(z + sp.Rational(1, 10) * t) + sp.Rational(1, 10) * sp.cos(x)
-    v = sp.Rational(3, 20) * sp.sin(z) * sp.cos(x - sp.Rational(1, 5) * t) + sp.Rational(1, 20) * sp.sin(y)
-    w = sp.Rational(1, 10) * sp.sin(x) * sp.sin(y + sp.Rational(3, 10) * t) + sp.Rational(2, 25) * sp.cos(z)
+    if mixed:
+        fu = sp.sin(y + sp.Rational(1, 5) * t)
+        fv = sp.cos(z - sp.Rational(3, 10) * t)
+        fw = sp.sin(x + sp.Rational(1, 4) * t)
+    else:
+        fu = fv = fw = 1
+    u = sp.Rational(1, 5) * sp.sin(y) * sp.cos(z + sp.Rational(1, 10) * t) + sp.Rational(1, 10) * sp.cos(x) * fu
+    v = sp.Rational(3, 20) * sp.sin(z) * sp.cos(x - sp.Rational(1, 5) * t) + sp.Rational(1, 20) * sp.sin(y) * fv
+    w = sp.Rational(1, 10) * sp.sin(x) * sp.sin(y + sp.Rational(3, 10) * t) + sp.Rational(2, 25) * sp.cos(z) * fw
     T = 1 + sp.Rational(1, 10) * sp.cos(x - y) * sp.sin(z + sp.Rational(1, 5) * t)
     return rho, (u, v, w), T
 
 
 @functools.lru_cache(maxsize=None)
-def exact(gamma, prandtl, mu0, omega, internal=False, sutherland=None):
+def exact(gamma, prandtl, mu0, omega, internal=False, sutherland=None, mixed=False):
     """Return (conserved(X, Y, Z, tt), rhs(X, Y, Z, tt)) numpy callables.
 
     internal: the fifth variable is rho e with the paper's Eq. (ie),
     d(rho e)/dt + d(rho e u_j)/dx_j = -p du_j/dx_j + d(k dT/dx_j)/dx_j
     + sigma_ij S_ij; else total energy.  sutherland = S: Sutherland's law
-    mu0 T^(3/2) (1 + S) / (T + S) instead of the power law."""
+    mu0 T^(3/2) (1 + S) / (T + S) instead of the power law.  mixed: the
+    field set whose mixed viscous terms are nonzero (fields(mixed=True))."""
     g = sp.nsimplify(gamma)
-    rho, vel, T = fields()
+    rho, vel, T = fields(mixed)
     X = (x, y, z)
     p = rho * T / g
     E = p / (g - 1) + rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2) / 2

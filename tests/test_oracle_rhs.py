@@ -66,6 +66,48 @@ def test_manufactured_solution_fourth_order(pes, delays_fn):
     assert max(errs[2]) < 5e-5
 
 
+def _mixed_field_orders():
+    """Orders (32 -> 64) on the field set whose mixed viscous terms are
+    nonzero, 2x2x2 PEs, random delays.  (In the default set each du_k/dx_k
+    depends on x_k alone, so the mixed terms vanish and the checks above do not
+    see the mixed rule.)"""
+    fc, fr = mms.exact(GAMMA, PR, MU0, OMEGA, mixed=True)
+    errs = []
+    for N in (16, 32, 64):
+        cfg = _cfg(N, (2, 2, 2))
+        dt = 0.5 * (2 * math.pi / N) ** 2
+        levels = [mms.evaluate(fc, cfg.n, 0.4 - l * dt) for l in range(cfg.n_levels)]
+        R = ns.rhs(cfg, levels, _random_delays(cfg))
+        Rex = mms.evaluate(fr, cfg.n, 0.4)
+        errs.append([float(np.max(np.abs(R[v] - Rex[v])) / np.max(np.abs(Rex[v]))) for v in range(5)])
+    return [math.log2(errs[1][v] / errs[2][v]) for v in range(5)], errs
+
+
+def test_manufactured_solution_with_mixed_terms_fourth_order():
+    orders, errs = _mixed_field_orders()
+    assert min(orders) > 3.5, (orders, errs)
+
+
+def test_mixed_rule_one_sided_order_is_seen(monkeypatch):
+    """The three-step rule's one-sided stencils planted as 2nd-order ones
+    ((-3, 4, -1)/2 at the first point, (-1, 0, 1)/2 at the second): the
+    momentum orders on the mixed field fall to about 3.15 (on the default field
+    they stay at 3.98)."""
+    from oracle import stencils
+
+    def second_order(self, li, nloc):
+        rows = (((0, -18.0), (1, 24.0), (2, -6.0)), ((-1, -6.0), (1, 6.0)))   # over the denominator 12
+        if li < self.M:
+            return rows[li]
+        if li >= nloc - self.M:
+            return tuple((-o, -c) for o, c in rows[nloc - 1 - li])
+        return self.d1
+
+    monkeypatch.setattr(stencils.Scheme, "one_sided", second_order)
+    orders, errs = _mixed_field_orders()
+    assert min(orders) < 3.4, (orders, errs)
+
+
 def test_manufactured_solution_detects_dropped_term(monkeypatch):
     """Removing the viscous heating sigma_ij S_ij from the oracle breaks the
     energy-equation convergence (guards the test's own sensitivity)."""
