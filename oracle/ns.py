@@ -287,8 +287,9 @@ def at_derivative(cfg, qlevels, d, delays, order, qext=None):
         return out / denom
     Q = np.stack(qlevels)                       # [level, z, y, x]
     out = np.zeros_like(qlevels[0])
+    wtab = np.array([sc.weights(k) for k in range(int(np.max(kf)) + 1)])   # Table B weights per delay
     for l in range(sc.T):
-        w = np.vectorize(lambda kk: sc.weights(kk)[l], otypes=[float])(kf)
+        w = wtab[kf, l]
         S = np.zeros_like(qlevels[0])
         for off, c in stencil:
             inside = (li + off >= 0) & (li + off < nloc)
