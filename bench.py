@@ -195,6 +195,7 @@ def job_rate(world, points, steps, ms):
 
 
 ORACLE_N, ORACLE_PES = 48, 2
+ORACLE_BASELINE_STEPS = 8      # timed steps of the cpu_baseline sample (about 10-15 s on 16 host cores)
 
 
 def _oracle_worker(steps, warmup, n, pes, seed, barrier, out):
@@ -480,11 +481,11 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, el, cores = oracle_rate(3, 1)
+        rate, el, cores = oracle_rate(ORACLE_BASELINE_STEPS, 1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "3 AB2 steps (after 1 warm-up) of the FP64 numpy oracle in each of %d processes (one per "
-                         "host core), each on its own 48^3 box with 2x2x2 PEs of 24^3 points, random delays "
-                         "L = 2; %.1f s timed (slowest process)" % (cores, el)}
+               "sample": "%d AB2 steps (after 1 warm-up) of the FP64 numpy oracle in each of %d processes (one "
+                         "per host core), each on its own 48^3 box with 2x2x2 PEs of 24^3 points, random delays "
+                         "L = 2; %.1f s timed (slowest process)" % (ORACLE_BASELINE_STEPS, cores, el)}
 
     if rank != 0:
         return 0
