@@ -195,7 +195,7 @@ def job_rate(world, points, steps, ms):
 
 
 ORACLE_N, ORACLE_PES = 48, 2
-ORACLE_BASELINE_STEPS = 8      # timed steps of the cpu_baseline sample (about 10-15 s on 16 host cores)
+ORACLE_BASELINE_STEPS = 10     # timed steps of the cpu_baseline sample (about 12 s on 16 host cores)
 
 
 def _oracle_worker(steps, warmup, n, pes, seed, barrier, out):
